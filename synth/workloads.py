@@ -1,0 +1,129 @@
+"""Seeded workload recipes (rooms, forests, training trajectories, queries).
+
+Each recipe lists every parameter a run needs, as plain values: the room,
+the resolution, the forest and relocaliser settings and the seeds.  The
+relocaliser parameter names follow the paper's parameter table; values the
+paper leaves open are this library's readings.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+from .rooms import Room, intrinsics_for, query_poses, render, training_trajectory
+
+# Default relocaliser of the paper's parameter table (Appendix B) with the
+# open values filled in.
+RANSAC_DEFAULT = dict(
+    n_hyp=1024, max_iter=6000, n_cull=64, eta=512, k_out=16, pose_update=1, use_cov=1,
+    colour_thresh=30, min_sq_dist=0.09, max_trans_err=0.05, k_top=10, n_trees_used=5,
+    lm_max_iter=10, batch_attempts=32, lm_lambda0=1e-3, lm_inlier_thresh=0.1, lm_stop=1e-6,
+    rank=1, halve_to_one=0,
+)
+FOREST_DEFAULT = dict(
+    n_trees=5, depth=15, p_depth=0.4, delta_lo=-130.0, delta_hi=130.0, tau_depth_lo=-0.2,
+    tau_depth_hi=0.2, tau_rgb_lo=-50.0, tau_rgb_hi=50.0, tau_zero=0, kappa=1024, m_max=50,
+    min_cluster_size=20, sigma=0.1, tau_c=0.05, cov_eps=1e-4, mode_precision=1, grid_step=4,
+    grid_origin=0,
+)
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    room_size: tuple
+    room_seed: int
+    width: int
+    height: int
+    forest: dict
+    forest_seed: int
+    n_train: int
+    ransac: dict
+    n_queries: int
+    query_seed: int = 1000
+    noise_sigma: float = 0.002
+
+    @property
+    def K(self):
+        return intrinsics_for(self.width, self.height)
+
+    def room(self):
+        return Room(self.room_size, self.room_seed)
+
+    def training_frames(self):
+        """Yields (depth, rgb, cam_to_world) of the training trajectory."""
+        room = self.room()
+        for i, T in enumerate(training_trajectory(room, self.n_train)):
+            d, c = render(room, self.K, T, self.noise_sigma, noise_seed=100 + i)
+            yield d, c, T
+
+    def query(self, q: int):
+        """(depth, rgb, ground-truth pose, query seed) of query q."""
+        room = self.room()
+        T = query_poses(room, q + 1, seed=self.query_seed)[q]
+        d, c = render(room, self.K, T, self.noise_sigma, noise_seed=5000 + q)
+        return d, c, T, self.query_seed + q
+
+    def queries(self, n=None):
+        room = self.room()
+        n = self.n_queries if n is None else n
+        poses = query_poses(room, n, seed=self.query_seed)
+        out = []
+        for q, T in enumerate(poses):
+            d, c = render(room, self.K, T, self.noise_sigma, noise_seed=5000 + q)
+            out.append((d, c, T, self.query_seed + q))
+        return out
+
+
+# Config 1: single query, plain method, small room render and forest.
+CONFIG1 = Workload(
+    name="room4x3x2.5_160x120_1tree_d10", room_size=(4.0, 3.0, 2.5), room_seed=5,
+    width=160, height=120,
+    forest=dict(FOREST_DEFAULT, n_trees=1, depth=10, kappa=256, m_max=10, min_cluster_size=5),
+    forest_seed=2, n_train=20,
+    ransac=dict(RANSAC_DEFAULT, n_hyp=64, n_cull=64, eta=100, k_out=1, k_top=10, n_trees_used=1),
+    n_queries=16,
+)
+
+# Config 2: paper-shaped single query at 640x480.
+CONFIG2 = Workload(
+    name="room4x3x2.5_640x480_5trees_d15", room_size=(4.0, 3.0, 2.5), room_seed=5,
+    width=640, height=480,
+    forest=dict(FOREST_DEFAULT),
+    forest_seed=2, n_train=200,
+    ransac=dict(RANSAC_DEFAULT, n_hyp=1024, n_cull=64, eta=500, k_out=16, halve_to_one=1),
+    n_queries=16,
+)
+
+# Config 3 levels (shared config-2 forest): subsample, relocaliser parameters.
+CASCADE_LEVELS = [
+    (4, dict(RANSAC_DEFAULT, n_hyp=64, n_trees_used=1, k_out=1, eta=100)),
+    (2, dict(RANSAC_DEFAULT, n_hyp=256, n_trees_used=5, k_out=1, eta=250)),
+    (1, dict(RANSAC_DEFAULT, n_hyp=1024, n_trees_used=5, k_out=16, eta=500)),
+]
+
+
+def cascade_thresholds(seed: int = 7):
+    """tau_1, tau_2 drawn uniformly from [0.04, 0.09] m (the paper tuned
+    5 cm and 7.5 cm on its datasets)."""
+    r = np.random.default_rng(seed).uniform(0.04, 0.09, size=2)
+    return [float(r[0]), float(r[1])]
+
+
+def small_case(n_trees=2, depth=8, width=96, height=72, n_train=12, **ransac):
+    """A few-second oracle case that still spans several tiles, a ragged
+    tail and multiple trees.  Its checks are loosened (colour 120, rigidity
+    0.15 m, spread 0.2 m) so that most generation slots succeed and the
+    cull, the rounds and LM all see many hypotheses."""
+    return Workload(
+        name=f"room4x3x2.5_{width}x{height}_{n_trees}trees_d{depth}", room_size=(4.0, 3.0, 2.5),
+        room_seed=5, width=width, height=height,
+        forest=dict(FOREST_DEFAULT, n_trees=n_trees, depth=depth, kappa=128, m_max=8,
+                    min_cluster_size=3, tau_c=0.2),
+        forest_seed=3, n_train=n_train,
+        ransac=dict(RANSAC_DEFAULT, n_hyp=96, n_cull=24, eta=64, k_out=4, k_top=4,
+                    n_trees_used=n_trees, max_iter=2000, colour_thresh=120, max_trans_err=0.15,
+                    min_sq_dist=0.04, halve_to_one=1, **ransac),
+        n_queries=4,
+    )

@@ -1,0 +1,100 @@
+"""Shared test helpers: run a workload through the CPU oracle and through the
+CUDA library, and compare results with the tolerances of the matching rules
+(bit-exact integer work; poses 1 mm / 0.05 deg; FP32 energies 1e-4 relative
+of FP64; cull survivors equal up to swaps of energies within 1e-5)."""
+from __future__ import annotations
+
+import functools
+import math
+
+import numpy as np
+
+import oracle
+from synth import workloads
+
+POSE_T_TOL = 1e-3                 # metres
+POSE_R_TOL = 0.05                 # degrees
+ENERGY_RTOL = 1e-4
+SWAP_RTOL = 1e-5
+
+
+def pose_err(A, B):
+    A = np.asarray(A)
+    B = np.asarray(B)
+    dt = float(np.linalg.norm(A[:3, 3] - B[:3, 3]))
+    c = (np.trace(A[:3, :3].T @ B[:3, :3]) - 1.0) / 2.0
+    return dt, math.degrees(math.acos(min(1.0, max(-1.0, c))))
+
+
+def as44(p12):
+    T = np.eye(4)
+    T[:3, :4] = np.asarray(p12).reshape(3, 4)
+    return T
+
+
+def oracle_forest_nodes(w: workloads.Workload):
+    f = w.forest
+    return oracle.forest_random(f["n_trees"], f["depth"], f["p_depth"], (f["delta_lo"], f["delta_hi"]),
+                                (f["tau_depth_lo"], f["tau_depth_hi"]),
+                                (f["tau_rgb_lo"], f["tau_rgb_hi"]), bool(f["tau_zero"]),
+                                w.forest_seed)
+
+
+@functools.lru_cache(maxsize=4)
+def oracle_model(w_name: str, n_train: int | None = None):
+    """Oracle forest, reservoirs and modes of a workload (cached)."""
+    w = WORKLOADS[w_name]
+    f = oracle_forest_nodes(w)
+    res = oracle.Reservoirs(f, w.forest["kappa"], w.forest_seed)
+    for i, (d, c, T) in enumerate(w.training_frames()):
+        if n_train is not None and i >= n_train:
+            break
+        res.add_frame(d, c, w.K, T, w.forest["grid_step"], w.forest["grid_origin"])
+    modes = oracle.Modes(res.n_leaves, w.forest["m_max"])
+    oracle.update_modes(res, modes, w.forest["sigma"], w.forest["tau_c"],
+                        w.forest["min_cluster_size"], cov_eps=w.forest["cov_eps"],
+                        fp16_offsets=bool(w.forest["mode_precision"]))
+    return f, res, modes
+
+
+def oracle_query(w_name: str, q: int, params=None, debug=True):
+    w = WORKLOADS[w_name]
+    f, res, modes = oracle_model(w_name)
+    d, c, T, seed = w.query(q)
+    p = dict(w.ransac if params is None else params)
+    lv = oracle.forest_leaves(f, d, c, w.K.fx, n_trees=p["n_trees_used"])
+    r = oracle.relocalise(p, d, c, w.K, lv, modes, w.room().lo, w.room().hi, seed,
+                          1 << w.forest["depth"], debug=debug)
+    return r, T
+
+
+WORKLOADS = {w.name: w for w in [workloads.CONFIG1, workloads.CONFIG2, workloads.small_case()]}
+SMALL = workloads.small_case().name
+
+
+def gpu_model(ctx, w: workloads.Workload, n_train=None):
+    import paper_1810_12163_gb300 as rg
+    forest = rg.Forest.random(ctx, w.forest, w.forest_seed)
+    for i, (d, c, T) in enumerate(w.training_frames()):
+        if n_train is not None and i >= n_train:
+            break
+        forest.adapt(d, c, w.K, T)
+    forest.update_modes(-1)
+    return forest
+
+
+def compare_survivors(gpu_slots, gpu_E, ora_slots, ora_E, what):
+    """Equal survivor sets, allowing swaps between energies within SWAP_RTOL
+    of the cut.  Returns True when the sets are identical."""
+    gs, os_ = list(gpu_slots), list(ora_slots)
+    assert len(gs) == len(os_), f"{what}: {len(gs)} vs {len(os_)} survivors"
+    for e_g, e_o in zip(gpu_E, ora_E):
+        assert abs(e_g - e_o) <= ENERGY_RTOL * max(abs(e_o), 1e-30) + 1e-6, \
+            f"{what}: energy {e_g} vs {e_o}"
+    if set(gs) == set(os_):
+        return True
+    cut = max(ora_E)
+    for s in set(gs) ^ set(os_):
+        e = gpu_E[gs.index(s)] if s in gs else ora_E[os_.index(s)]
+        assert abs(e - cut) <= SWAP_RTOL * abs(cut) + 1e-6, f"{what}: survivor {s} differs, E={e} cut={cut}"
+    return False
