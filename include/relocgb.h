@@ -1,0 +1,283 @@
+/*
+ * relocgb -- RGB-D camera relocalisation on GB300 (sm_103a).
+ *
+ * C ABI of the library.  It implements the per-frame relocaliser of
+ * Cavallari, Golodetz, Lord, Valentin, Prisacariu, Di Stefano and Torr,
+ * "Real-Time RGB-D Camera Pose Estimation in Novel Scenes using a
+ * Relocalisation Cascade" (TPAMI 2019):
+ *
+ *   forest factory ....... Sec. 4.5 (random complete trees)
+ *   online adaptation .... Sec. 3.2.2 (leaf reservoirs, Really Quick Shift)
+ *   pose estimation ...... Sec. 3.2.3 (Kabsch hypotheses on triples, checks,
+ *                          preemptive RANSAC with the energy of Eq. 5, LM)
+ *   hypothesis ranking ... Sec. 3.2.4 (Eq. 6-8, depth raycast of the model)
+ *   cascade .............. Sec. 3.2.5
+ *
+ * Conventions shared by every call:
+ *  - Every function returns rl_status; outputs are written only on RL_OK.
+ *    A frame for which no pose hypothesis survives is NOT an error: the
+ *    result carries status RL_NO_POSE and score +inf.
+ *  - No call traps the device, throws across the ABI, or allocates device
+ *    memory after rl_context_create: all device state lives in the
+ *    caller-owned arena handed to the context.
+ *  - Streams are passed as `void *` holding a cudaStream_t (NULL = legacy
+ *    default stream).  Calls that return results to the host synchronise
+ *    that stream before returning.
+ *  - Images: depth float32 [H][W] in metres (<= 0 or NaN = invalid), colour
+ *    uint8 [H][W][3] (RGB) registered to depth.  Poses: row-major 4x4 FP64,
+ *    camera -> world (x right, y down, z forward in the camera).
+ *  - rl_mem says where image pointers live (host memory is copied in on the
+ *    given stream; device pointers must stay valid until the stream work
+ *    completes).
+ *  - Handles are opaque and owned by the library; release them with the
+ *    matching *_destroy.  Handles are not thread-safe: one thread at a time
+ *    per handle.
+ */
+#ifndef RELOCGB_H
+#define RELOCGB_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RL_OK = 0,
+    RL_ERR_INVALID_ARG = 1, /* bad pointer, size or parameter */
+    RL_ERR_OOM = 2,         /* arena exhausted */
+    RL_ERR_ADMISSION = 3,   /* serving: request refused by the memory budget */
+    RL_ERR_CUDA = 4,        /* a CUDA runtime call failed (see rl_last_error) */
+    RL_ERR_TIMEOUT = 5,     /* a bounded wait ran out */
+    RL_ERR_BUSY = 6,        /* handle still referenced by another handle */
+    RL_ERR_IO = 7,          /* file could not be read or written */
+    RL_ERR_INTERNAL = 8     /* device-side consistency check failed */
+} rl_status;
+
+typedef enum { RL_HOST = 0, RL_DEVICE = 1 } rl_mem;
+typedef enum { RL_POSE_FOUND = 0, RL_NO_POSE = 1 } rl_pose_status;
+typedef enum { RL_MODES_FP32 = 0, RL_MODES_FP16_OFFSET = 1 } rl_mode_precision;
+
+typedef struct rl_ctx rl_ctx;
+typedef struct rl_forest rl_forest;
+typedef struct rl_scene rl_scene;
+typedef struct rl_reloc rl_reloc;
+typedef struct rl_cascade rl_cascade;
+
+typedef struct {
+    float fx, fy, cx, cy;
+    int32_t width, height;
+} rl_intrinsics;
+
+/* Forest and adaptation parameters (Sec. 3.2.2, Sec. 4.5, Table 9). */
+typedef struct {
+    int32_t n_trees;          /* trees in the forest (paper: 5) */
+    int32_t depth;            /* split levels per tree, 1..15 (paper: 15 / 14) */
+    float p_depth;            /* probability of a Depth split (paper: 0.4) */
+    float delta_lo, delta_hi; /* probe offset range, pixel*metres at f = 585 */
+    float tau_depth_lo, tau_depth_hi; /* threshold range of Depth splits (m) */
+    float tau_rgb_lo, tau_rgb_hi;     /* threshold range of DA-RGB splits */
+    int32_t tau_zero;         /* 1: every threshold is 0, as in Sec. 4.5 */
+    int32_t kappa;            /* reservoirCapacity */
+    int32_t m_max;            /* maxClusterCount (<= 64) */
+    int32_t min_cluster_size; /* minClusterSize */
+    float sigma;              /* clustererSigma, metres */
+    float tau_c;              /* clustererTau, metres */
+    float cov_eps;            /* covariance regulariser, m^2 (not in the paper) */
+    int32_t mode_precision;   /* rl_mode_precision */
+    int32_t grid_step;        /* training-pixel grid spacing (paper: 4) */
+    int32_t grid_origin;      /* first grid row/column (0) */
+} rl_forest_params;
+
+/* Relocaliser parameters (Sec. 3.2.3-3.2.4; names follow Table 9). */
+typedef struct {
+    int32_t n_hyp;            /* maxPoseCandidates, N_max (<= 4096) */
+    int32_t max_iter;         /* maxCandidateGenerationIterations */
+    int32_t n_cull;           /* maxPoseCandidatesAfterCull, N_cull (<= 64) */
+    int32_t eta;              /* ransacInliersPerIteration (<= 1024) */
+    int32_t k_out;            /* maxRelocalisationsToOutput (<= 16) */
+    int32_t pose_update;      /* poseUpdate: LM refinement on/off */
+    int32_t use_cov;          /* usePredictionCovarianceForPoseOptimization */
+    int32_t colour_thresh;    /* L-inf colour check threshold, 0..255 */
+    double min_sq_dist;       /* minSquaredDistanceBetweenSampledModes, m^2 */
+    double max_trans_err;     /* maxTranslationErrorForCorrectPose, m */
+    int32_t k_top;            /* modes per leaf used at inference */
+    int32_t n_trees_used;     /* use the first n trees of the forest */
+    int32_t lm_max_iter;      /* LM iterations per refinement */
+    int32_t batch_attempts;   /* redraws of an invalid batch pixel */
+    double lm_lambda0;        /* initial Marquardt damping */
+    double lm_inlier_thresh;  /* LM inlier radius, m */
+    double lm_stop;           /* LM stops when |step| < lm_stop */
+    int32_t rank;             /* score the chosen set by Eq. 6-8 */
+    int32_t halve_to_one;     /* keep halving after the chosen set is taken */
+} rl_ransac_params;
+
+#define RL_MAX_CHOSEN 16
+
+typedef struct {
+    double pose[16];          /* output camera->world pose (xi* if ranked) */
+    float energy;             /* Eq. 5 energy of the output pose */
+    float energy_per_pixel;   /* energy / |I| */
+    float score;              /* s(xi*) of Eq. 7 (+inf if not ranked) */
+    int32_t level;            /* cascade level that produced the pose */
+    int32_t n_hypotheses;     /* hypotheses that passed generation */
+    int32_t n_chosen;         /* |Xi| */
+    int32_t n_pixels;         /* final |I| */
+    int32_t status;           /* rl_pose_status */
+    double chosen_pose[RL_MAX_CHOSEN][16];
+    float chosen_energy[RL_MAX_CHOSEN];
+    float chosen_score[RL_MAX_CHOSEN];
+    int32_t chosen_slot[RL_MAX_CHOSEN];
+    int32_t best;             /* index of xi* in chosen_pose */
+    int32_t pad;
+} rl_result;
+
+/* ---- context --------------------------------------------------------- */
+/* Creates a context on `device` over a caller-owned device buffer of
+ * `arena_bytes` bytes (256-byte aligned) that must outlive the context.
+ * Errors: RL_ERR_INVALID_ARG (null/misaligned arena), RL_ERR_CUDA. */
+rl_status rl_context_create(int32_t device, void *arena_dev_ptr, uint64_t arena_bytes,
+                            rl_ctx **out);
+rl_status rl_context_destroy(rl_ctx *ctx);
+/* Bytes of the arena in use / high-water mark. */
+rl_status rl_context_usage(const rl_ctx *ctx, uint64_t *used, uint64_t *peak);
+/* Message of the last failed call on this thread ("" if none). */
+const char *rl_last_error(void);
+
+/* ---- forest (Sec. 4.5 factory, Sec. 3.2.2 adaptation) ---------------- */
+/* Random forest of complete trees (Sec. 4.5): per branch node a Depth split
+ * with probability p_depth, else a DA-RGB split on a uniform channel;
+ * offsets and thresholds uniform in the given ranges.  Nodes are in heap
+ * order (children 2n+1 = test false, 2n+2 = test true, Eq. 3).  Draws use
+ * Philox4x32-10 keyed by `seed`; the same seed gives the same forest.
+ * Allocates nodes, reservoirs and the mode store from the arena
+ * (RL_ERR_OOM if it does not fit).  Reservoirs start empty. */
+rl_status rl_forest_create_random(rl_ctx *ctx, const rl_forest_params *p, uint64_t seed,
+                                  rl_forest **out);
+/* RL_ERR_BUSY while a relocaliser still uses the forest. */
+rl_status rl_forest_destroy(rl_forest *f);
+/* Empties every reservoir and mode list (the leaf reset of Sec. 3.2.1). */
+rl_status rl_forest_reset_leaves(rl_forest *f, void *stream);
+/* Sec. 3.2.2 steps 1-2: the pixels of a regular grid (spacing grid_step)
+ * with valid depth are back-projected with `cam_to_world`, passed down
+ * every tree, and offered to the reached leaf's reservoir by Algorithm R
+ * (Vitter 1985) in the order (pixel row-major, tree).  Deterministic. */
+rl_status rl_forest_adapt(rl_forest *f, const float *depth, const uint8_t *rgb,
+                          const rl_intrinsics *K, const double cam_to_world[16], rl_mem mem,
+                          void *stream);
+/* Sec. 3.2.2 step 3: Really Quick Shift on the next `n_leaves` leaves in
+ * round-robin order (n_leaves < 0: every leaf); keeps the largest M_max
+ * clusters per leaf with centroid, colour, covariance. */
+rl_status rl_forest_update_modes(rl_forest *f, int32_t n_leaves, void *stream);
+/* Eq. 1-3 for every pixel: out_leaves is a DEVICE uint16 [n_trees][H][W]
+ * buffer (0xFFFF where depth is invalid).  Bit-exact FP32 arithmetic. */
+rl_status rl_forest_leaves(rl_forest *f, const float *depth, const uint8_t *rgb,
+                           const rl_intrinsics *K, int32_t n_trees, uint16_t *out_leaves,
+                           rl_mem mem, void *stream);
+/* Copies forest state to HOST buffers (any may be NULL).  Sizes: nodes
+ * T*(2^d-1); reservoirs L*kappa with L = T*2^d; modes L*m_max.
+ * node_meta = type (0 Depth, 1 DA-RGB) | channel << 8.  Mode positions are
+ * decoded to FP32; mode_U holds the upper Cholesky factor of the inverse
+ * regularised covariance (U00 U01 U02 U11 U12 U22). */
+rl_status rl_forest_export(rl_forest *f, float *node_dx, float *node_dy, float *node_tau,
+                           int32_t *node_meta, float *res_pos /* L*kappa*3 */,
+                           uint8_t *res_rgb /* L*kappa*3 */, uint32_t *res_count /* L */,
+                           uint8_t *nmodes /* L */, float *mode_pos /* L*m_max*3 */,
+                           uint8_t *mode_rgb /* L*m_max*3 */, float *mode_U /* L*m_max*6 */,
+                           int32_t *mode_size /* L*m_max */);
+/* Binary checkpoint of nodes, reservoirs, modes and the round-robin cursor. */
+rl_status rl_forest_save(rl_forest *f, const char *path);
+rl_status rl_forest_load(rl_ctx *ctx, const char *path, rl_forest **out);
+
+/* ---- scene model (stands in for the fused model of Sec. 3.2.4) -------- */
+/* Axis-aligned box room [lo, hi] (metres) rendered analytically by the
+ * ranking step's depth raycast. */
+rl_status rl_scene_box(rl_ctx *ctx, const double lo[3], const double hi[3], rl_scene **out);
+rl_status rl_scene_destroy(rl_scene *s);
+/* Eq. 6-7 for n given camera->world poses (HOST [n][16] row-major) against
+ * one live depth frame: the box is raycast at each pose (z-depth of the
+ * first face hit; exit point from inside, entry point from outside), the
+ * masked mean |D_live - D_synth| is taken over pixels valid in both, and
+ * the score is +inf when fewer than 10% of the synthetic pixels are valid.
+ * scores / valid_frac are HOST [n] (valid_frac may be NULL).  Scratch comes
+ * from the context arena (RL_ERR_OOM if it does not fit).  Synchronises
+ * `stream`. */
+rl_status rl_score_poses(rl_scene *s, const float *depth, const rl_intrinsics *K,
+                         const double *poses, int32_t n, rl_mem mem, void *stream,
+                         float *scores, float *valid_frac);
+
+/* ---- relocaliser (Sec. 3.2.3-3.2.4) ---------------------------------- */
+/* Allocates per-query state for up to `max_batch` frames of at most
+ * max_width x max_height from the arena.  `scene` may be NULL when
+ * p->rank == 0. */
+rl_status rl_reloc_create(rl_forest *f, rl_scene *scene, const rl_ransac_params *p,
+                          int32_t max_width, int32_t max_height, int32_t max_batch,
+                          rl_reloc **out);
+rl_status rl_reloc_destroy(rl_reloc *r);
+/* Relocalises one frame: Eq. 1-3 leaves for every pixel, N_max hypotheses
+ * by Kabsch on checked triples, cull to N_cull by Eq. 5 on eta pixels,
+ * preemptive rounds (grow I by eta, LM, re-score, keep the better half),
+ * then Eq. 6-8 ranking of the chosen set.  `query_seed` keys every random
+ * draw.  Synchronises `stream`; writes *out on RL_OK. */
+rl_status rl_relocalise(rl_reloc *r, const float *depth, const uint8_t *rgb,
+                        const rl_intrinsics *K, uint64_t query_seed, rl_mem mem, void *stream,
+                        rl_result *out);
+/* Batched form: n frames of the same size, contiguous ([n][H][W] depth,
+ * [n][H][W][3] colour), all work of all frames in the same launches.  Each
+ * frame's result is identical to relocalising it alone. */
+rl_status rl_relocalise_batch(rl_reloc *r, int32_t n, const float *depth, const uint8_t *rgb,
+                              const rl_intrinsics *K, const uint64_t *query_seeds, rl_mem mem,
+                              void *stream, rl_result *out);
+/* Asynchronous batched form for serving loops: inputs must be DEVICE
+ * pointers; nothing is copied back until rl_reloc_fetch. */
+rl_status rl_relocalise_batch_async(rl_reloc *r, int32_t n, const float *depth,
+                                    const uint8_t *rgb, const rl_intrinsics *K,
+                                    const uint64_t *query_seeds, void *stream);
+rl_status rl_reloc_fetch(rl_reloc *r, int32_t n, void *stream, rl_result *out);
+
+/* Intermediate results of frame `q` of the last call (HOST buffers, any may
+ * be NULL): per generation slot the 3x4 pose and the iteration that
+ * succeeded (-1 failed); the cull survivors (slot, energy) in rank order;
+ * the survivors after each preemptive round; the pixel ids of each batch. */
+rl_status rl_reloc_debug(rl_reloc *r, int32_t q, double *hyp_pose /* n_hyp*12 */,
+                         int32_t *hyp_iter /* n_hyp */, int32_t *cull_slot /* n_cull */,
+                         float *cull_energy /* n_cull */, int32_t *round_count /* 16 */,
+                         int32_t *round_slot /* 16*n_cull */, float *round_energy /* 16*n_cull */,
+                         double *round_pose /* 16*n_cull*12 */, int32_t *batch_pix /* 16*eta */,
+                         int32_t *n_rounds);
+
+/* ---- tracing ---------------------------------------------------------- */
+/* Per-kernel timing of a relocaliser: when enabled, every kernel launch of
+ * its calls is bracketed by CUDA events on the caller's stream; durations
+ * and launch counts accumulate per kernel (ids 0..8, names from
+ * rl_kernel_name), and the scoring kernels count their work units
+ * (uint64 [7]: energy (H,px) pairs, energy (H,px,mode) triples, LM pass-1
+ * (H,px) evaluations, LM (H,px,mode) triples, LM inlier accumulations,
+ * LM trial evaluations, rays cast).  Enabling resets all counters.  The
+ * paper has no counterpart; its Sec. A.1 timing breakdown is per stage. */
+rl_status rl_reloc_profile(rl_reloc *r, int32_t enable);
+rl_status rl_reloc_profile_read(rl_reloc *r, double *ms /* [9] */, int64_t *launches /* [9] */,
+                                uint64_t *work /* [7] */);
+const char *rl_kernel_name(int32_t kernel_id);
+
+/* ---- cascade (Sec. 3.2.5) -------------------------------------------- */
+/* Levels run in order on the same frame; level l works on the frame
+ * subsampled by subsample[l] (pixel (s*u, s*v), intrinsics / s) and falls
+ * back to level l+1 iff its score exceeds thresholds[l].  The levels must
+ * share one forest.  The cascade keeps pointers to the levels. */
+rl_status rl_cascade_create(rl_reloc *const *levels, const double *thresholds,
+                            const int32_t *subsample, int32_t n_levels, rl_cascade **out);
+rl_status rl_cascade_destroy(rl_cascade *c);
+rl_status rl_cascade_relocalise(rl_cascade *c, const float *depth, const uint8_t *rgb,
+                                const rl_intrinsics *K, uint64_t query_seed, rl_mem mem,
+                                void *stream, rl_result *out);
+/* Batched cascade: each frame falls back independently; all frames of a
+ * level run in the same launches. */
+rl_status rl_cascade_relocalise_batch(rl_cascade *c, int32_t n, const float *depth,
+                                      const uint8_t *rgb, const rl_intrinsics *K,
+                                      const uint64_t *query_seeds, rl_mem mem, void *stream,
+                                      rl_result *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

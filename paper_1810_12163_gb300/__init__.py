@@ -1,0 +1,293 @@
+"""relocgb: GB300-native RGB-D camera relocalisation (Cavallari et al.,
+TPAMI 2019) -- Python layer over the C ABI of librelocgb.
+
+The relocaliser runs entirely in the CUDA library; this module marshals
+arguments, owns the device arena (a PyTorch tensor) and picks streams.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import binding, presets  # noqa: F401
+from .binding import (RL_DEVICE, RL_HOST, RL_NO_POSE, RL_POSE_FOUND,  # noqa: F401
+                      ForestParams, Intrinsics, RansacParams, RelocError, Result, call, lib)
+
+__all__ = ["Context", "Forest", "Scene", "Relocaliser", "Cascade", "intrinsics", "presets",
+           "RelocError", "lib"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return ctypes.c_void_p(_torch().cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def intrinsics(K) -> Intrinsics:
+    if isinstance(K, Intrinsics):
+        return K
+    return Intrinsics(float(K.fx), float(K.fy), float(K.cx), float(K.cy), int(K.width), int(K.height))
+
+
+def _struct(cls, d: dict):
+    s = cls()
+    names = {f[0] for f in cls._fields_}
+    for k, v in d.items():
+        if k in names:
+            setattr(s, k, v)
+    return s
+
+
+class _Image:
+    """Pointer + memory kind of an image argument (numpy = host, torch = device)."""
+
+    def __init__(self, a, dtype):
+        torch = _torch()
+        if isinstance(a, torch.Tensor):
+            if not a.is_cuda:
+                a = a.numpy()
+            else:
+                if a.dtype != {np.float32: torch.float32, np.uint8: torch.uint8}[dtype]:
+                    raise TypeError(f"expected {dtype} tensor")
+                self.keep = a.contiguous()
+                self.ptr = ctypes.c_void_p(self.keep.data_ptr())
+                self.mem = RL_DEVICE
+                return
+        self.keep = np.ascontiguousarray(a, dtype=dtype)
+        self.ptr = self.keep.ctypes.data_as(ctypes.c_void_p)
+        self.mem = RL_HOST
+
+
+class Context:
+    """Device context over a caller-owned arena (a uint8 CUDA tensor)."""
+
+    def __init__(self, device: int = 0, arena_bytes: int = 4 << 30):
+        torch = _torch()
+        lib()
+        self.device = device
+        self.arena = torch.empty(arena_bytes, dtype=torch.uint8, device=f"cuda:{device}")
+        self.h = ctypes.c_void_p()
+        call("rl_context_create", device, ctypes.c_void_p(self.arena.data_ptr()), arena_bytes,
+             ctypes.byref(self.h))
+
+    def usage(self):
+        used, peak = ctypes.c_uint64(), ctypes.c_uint64()
+        call("rl_context_usage", self.h, ctypes.byref(used), ctypes.byref(peak))
+        return used.value, peak.value
+
+    def close(self):
+        if self.h:
+            call("rl_context_destroy", self.h)
+            self.h = ctypes.c_void_p()
+
+
+class Forest:
+    def __init__(self, ctx: Context, handle, params: dict):
+        self.ctx = ctx
+        self.h = handle
+        self.params = dict(params)
+        self.n_trees = params["n_trees"]
+        self.depth = params["depth"]
+        self.n_leaves = self.n_trees << self.depth
+
+    @classmethod
+    def random(cls, ctx: Context, params: dict, seed: int):
+        full = dict(presets.FOREST_DEFAULT, **params)
+        h = ctypes.c_void_p()
+        call("rl_forest_create_random", ctx.h, ctypes.byref(_struct(ForestParams, full)), seed,
+             ctypes.byref(h))
+        return cls(ctx, h, full)
+
+    @classmethod
+    def load(cls, ctx: Context, path: str, params: dict):
+        h = ctypes.c_void_p()
+        call("rl_forest_load", ctx.h, path.encode(), ctypes.byref(h))
+        return cls(ctx, h, params)
+
+    def save(self, path: str):
+        call("rl_forest_save", self.h, path.encode())
+
+    def reset_leaves(self, stream=None):
+        call("rl_forest_reset_leaves", self.h, _stream_ptr(stream))
+
+    def adapt(self, depth, rgb, K, cam_to_world, stream=None):
+        d = _Image(depth, np.float32)
+        c = _Image(rgb, np.uint8)
+        if d.mem != c.mem:
+            raise ValueError("depth and colour must live in the same memory")
+        T = np.ascontiguousarray(np.asarray(cam_to_world, np.float64).reshape(16))
+        Ki = intrinsics(K)
+        call("rl_forest_adapt", self.h, d.ptr, c.ptr, ctypes.byref(Ki),
+             T.ctypes.data_as(ctypes.c_void_p), d.mem, _stream_ptr(stream))
+
+    def update_modes(self, n_leaves: int = -1, stream=None):
+        call("rl_forest_update_modes", self.h, n_leaves, _stream_ptr(stream))
+
+    def leaves(self, depth, rgb, K, n_trees=None, stream=None):
+        torch = _torch()
+        Ki = intrinsics(K)
+        T = self.n_trees if n_trees is None else n_trees
+        out = torch.empty((T, Ki.height, Ki.width), dtype=torch.int16, device=f"cuda:{self.ctx.device}")
+        d = _Image(depth, np.float32)
+        c = _Image(rgb, np.uint8)
+        call("rl_forest_leaves", self.h, d.ptr, c.ptr, ctypes.byref(Ki), T,
+             ctypes.c_void_p(out.data_ptr()), d.mem, _stream_ptr(stream))
+        return out.cpu().numpy().view(np.uint16)
+
+    def export(self, reservoirs=False):
+        p = self.params
+        NB = self.n_trees * ((1 << self.depth) - 1)
+        L, M, K = self.n_leaves, p["m_max"], p["kappa"]
+        out = dict(dx=np.zeros(NB, np.float32), dy=np.zeros(NB, np.float32),
+                   tau=np.zeros(NB, np.float32), meta=np.zeros(NB, np.int32),
+                   res_count=np.zeros(L, np.uint32), nmodes=np.zeros(L, np.uint8),
+                   mode_pos=np.zeros((L, M, 3), np.float32), mode_rgb=np.zeros((L, M, 3), np.uint8),
+                   mode_U=np.zeros((L, M, 6), np.float32), mode_size=np.zeros((L, M), np.int32))
+        if reservoirs:
+            out["res_pos"] = np.zeros((L, K, 3), np.float32)
+            out["res_rgb"] = np.zeros((L, K, 3), np.uint8)
+        ptr = lambda k: out[k].ctypes.data_as(ctypes.c_void_p) if k in out else None
+        call("rl_forest_export", self.h, ptr("dx"), ptr("dy"), ptr("tau"), ptr("meta"),
+             ptr("res_pos"), ptr("res_rgb"), ptr("res_count"), ptr("nmodes"), ptr("mode_pos"),
+             ptr("mode_rgb"), ptr("mode_U"), ptr("mode_size"))
+        out["type"] = (out["meta"] & 255).astype(np.uint8)
+        out["channel"] = (out["meta"] >> 8).astype(np.uint8)
+        return out
+
+    def close(self):
+        if self.h:
+            call("rl_forest_destroy", self.h)
+            self.h = ctypes.c_void_p()
+
+
+class Scene:
+    def __init__(self, ctx: Context, lo, hi):
+        lo = np.ascontiguousarray(lo, np.float64)
+        hi = np.ascontiguousarray(hi, np.float64)
+        self.h = ctypes.c_void_p()
+        call("rl_scene_box", ctx.h, lo.ctypes.data_as(ctypes.c_void_p),
+             hi.ctypes.data_as(ctypes.c_void_p), ctypes.byref(self.h))
+
+    def score_poses(self, depth, K, poses, stream=None):
+        """Eq. 6-7 scores of the given camera->world poses against `depth`."""
+        d = _Image(depth, np.float32)
+        P = np.ascontiguousarray(np.asarray(poses, np.float64).reshape(-1, 16))
+        n = P.shape[0]
+        scores = np.zeros(n, np.float32)
+        frac = np.zeros(n, np.float32)
+        call("rl_score_poses", self.h, d.ptr, ctypes.byref(intrinsics(K)),
+             P.ctypes.data_as(ctypes.c_void_p), n, d.mem, _stream_ptr(stream),
+             scores.ctypes.data_as(ctypes.c_void_p), frac.ctypes.data_as(ctypes.c_void_p))
+        return scores, frac
+
+    def close(self):
+        if self.h:
+            call("rl_scene_destroy", self.h)
+            self.h = ctypes.c_void_p()
+
+
+def result_dict(r: Result) -> dict:
+    nc = max(0, r.n_chosen)
+    return dict(
+        pose=np.array(r.pose).reshape(4, 4), energy=r.energy, energy_per_pixel=r.energy_per_pixel,
+        score=r.score, level=r.level, n_hypotheses=r.n_hypotheses, n_chosen=r.n_chosen,
+        n_pixels=r.n_pixels, status=r.status, best=r.best,
+        chosen_pose=np.array([np.array(r.chosen_pose[i]).reshape(4, 4) for i in range(nc)]),
+        chosen_energy=np.array(r.chosen_energy[:nc]), chosen_score=np.array(r.chosen_score[:nc]),
+        chosen_slot=np.array(r.chosen_slot[:nc]),
+    )
+
+
+class Relocaliser:
+    def __init__(self, forest: Forest, scene: Scene | None, params: dict, max_w: int, max_h: int,
+                 max_batch: int = 1):
+        self.forest = forest
+        self.params = dict(presets.DEFAULT, **params)
+        self.max_batch = max_batch
+        self.h = ctypes.c_void_p()
+        call("rl_reloc_create", forest.h, scene.h if scene else None,
+             ctypes.byref(_struct(RansacParams, self.params)), max_w, max_h, max_batch,
+             ctypes.byref(self.h))
+
+    def relocalise_batch(self, depth, rgb, K, seeds, stream=None, raw=False):
+        d = _Image(depth, np.float32)
+        c = _Image(rgb, np.uint8)
+        seeds = np.ascontiguousarray(seeds, np.uint64)
+        n = len(seeds)
+        out = (Result * n)()
+        call("rl_relocalise_batch", self.h, n, d.ptr, c.ptr, ctypes.byref(intrinsics(K)),
+             seeds.ctypes.data_as(ctypes.c_void_p), d.mem, _stream_ptr(stream), out)
+        return out if raw else [result_dict(out[i]) for i in range(n)]
+
+    def relocalise(self, depth, rgb, K, seed, stream=None):
+        return self.relocalise_batch(depth, rgb, K, [seed], stream)[0]
+
+    def profile(self, enable: bool = True):
+        """Turn per-kernel event timing and work counters on/off (resets them)."""
+        call("rl_reloc_profile", self.h, int(enable))
+
+    def profile_read(self):
+        ms = np.zeros(9)
+        launches = np.zeros(9, np.int64)
+        work = np.zeros(7, np.uint64)
+        call("rl_reloc_profile_read", self.h, ms.ctypes.data_as(ctypes.c_void_p),
+             launches.ctypes.data_as(ctypes.c_void_p), work.ctypes.data_as(ctypes.c_void_p))
+        names = [lib().rl_kernel_name(i).decode() for i in range(9)]
+        kernels = {names[i]: dict(ms=float(ms[i]), launches=int(launches[i])) for i in range(9)}
+        keys = ["energy_pairs", "energy_modes", "lm_pairs", "lm_modes", "lm_inliers", "lm_trial", "rays"]
+        return kernels, {k: int(v) for k, v in zip(keys, work)}
+
+    def debug(self, q: int = 0):
+        p = self.params
+        N, NC, eta = p["n_hyp"], p["n_cull"], p["eta"]
+        d = dict(hyp_pose=np.zeros((N, 12)), hyp_iter=np.zeros(N, np.int32),
+                 cull_slot=np.zeros(NC, np.int32), cull_energy=np.zeros(NC, np.float32),
+                 round_count=np.zeros(16, np.int32), round_slot=np.zeros((16, NC), np.int32),
+                 round_energy=np.zeros((16, NC), np.float32), round_pose=np.zeros((16, NC, 12)),
+                 batch_pix=np.zeros((16, eta), np.int32), n_rounds=np.zeros(1, np.int32))
+        ptr = lambda k: d[k].ctypes.data_as(ctypes.c_void_p)
+        call("rl_reloc_debug", self.h, q, ptr("hyp_pose"), ptr("hyp_iter"), ptr("cull_slot"),
+             ptr("cull_energy"), ptr("round_count"), ptr("round_slot"), ptr("round_energy"),
+             ptr("round_pose"), ptr("batch_pix"), ptr("n_rounds"))
+        d["n_rounds"] = int(d["n_rounds"][0])
+        return d
+
+    def close(self):
+        if self.h:
+            call("rl_reloc_destroy", self.h)
+            self.h = ctypes.c_void_p()
+
+
+class Cascade:
+    def __init__(self, levels: list, thresholds, subsample):
+        self.levels = levels
+        n = len(levels)
+        arr = (ctypes.c_void_p * n)(*[lv.h.value for lv in levels])
+        th = np.ascontiguousarray(list(thresholds) + [0.0], np.float64)
+        ss = np.ascontiguousarray(subsample, np.int32)
+        self.h = ctypes.c_void_p()
+        call("rl_cascade_create", arr, th.ctypes.data_as(ctypes.c_void_p),
+             ss.ctypes.data_as(ctypes.c_void_p), n, ctypes.byref(self.h))
+
+    def relocalise_batch(self, depth, rgb, K, seeds, stream=None):
+        d = _Image(depth, np.float32)
+        c = _Image(rgb, np.uint8)
+        seeds = np.ascontiguousarray(seeds, np.uint64)
+        n = len(seeds)
+        out = (Result * n)()
+        call("rl_cascade_relocalise_batch", self.h, n, d.ptr, c.ptr, ctypes.byref(intrinsics(K)),
+             seeds.ctypes.data_as(ctypes.c_void_p), d.mem, _stream_ptr(stream), out)
+        return [result_dict(out[i]) for i in range(n)]
+
+    def close(self):
+        if self.h:
+            call("rl_cascade_destroy", self.h)
+            self.h = ctypes.c_void_p()

@@ -1,0 +1,137 @@
+"""ctypes binding of librelocgb (include/relocgb.h).
+
+Argument marshalling only: every step of the relocaliser runs in the CUDA
+library.  PyTorch supplies the device arena and streams.  There is no CPU
+fallback: if the library is not built, `lib()` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librelocgb.so")
+_lock = threading.Lock()
+_lib = None
+
+P = ctypes.c_void_p
+I32 = ctypes.c_int32
+U64 = ctypes.c_uint64
+
+
+class RelocError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+STATUS_NAMES = {0: "RL_OK", 1: "RL_ERR_INVALID_ARG", 2: "RL_ERR_OOM", 3: "RL_ERR_ADMISSION",
+                4: "RL_ERR_CUDA", 5: "RL_ERR_TIMEOUT", 6: "RL_ERR_BUSY", 7: "RL_ERR_IO",
+                8: "RL_ERR_INTERNAL"}
+RL_HOST, RL_DEVICE = 0, 1
+RL_POSE_FOUND, RL_NO_POSE = 0, 1
+RL_MODES_FP32, RL_MODES_FP16_OFFSET = 0, 1
+
+
+class Intrinsics(ctypes.Structure):
+    _fields_ = [("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float),
+                ("cy", ctypes.c_float), ("width", I32), ("height", I32)]
+
+
+class ForestParams(ctypes.Structure):
+    _fields_ = [("n_trees", I32), ("depth", I32), ("p_depth", ctypes.c_float),
+                ("delta_lo", ctypes.c_float), ("delta_hi", ctypes.c_float),
+                ("tau_depth_lo", ctypes.c_float), ("tau_depth_hi", ctypes.c_float),
+                ("tau_rgb_lo", ctypes.c_float), ("tau_rgb_hi", ctypes.c_float),
+                ("tau_zero", I32), ("kappa", I32), ("m_max", I32), ("min_cluster_size", I32),
+                ("sigma", ctypes.c_float), ("tau_c", ctypes.c_float), ("cov_eps", ctypes.c_float),
+                ("mode_precision", I32), ("grid_step", I32), ("grid_origin", I32)]
+
+
+class RansacParams(ctypes.Structure):
+    _fields_ = [("n_hyp", I32), ("max_iter", I32), ("n_cull", I32), ("eta", I32), ("k_out", I32),
+                ("pose_update", I32), ("use_cov", I32), ("colour_thresh", I32),
+                ("min_sq_dist", ctypes.c_double), ("max_trans_err", ctypes.c_double),
+                ("k_top", I32), ("n_trees_used", I32), ("lm_max_iter", I32),
+                ("batch_attempts", I32), ("lm_lambda0", ctypes.c_double),
+                ("lm_inlier_thresh", ctypes.c_double), ("lm_stop", ctypes.c_double),
+                ("rank", I32), ("halve_to_one", I32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("pose", ctypes.c_double * 16), ("energy", ctypes.c_float),
+                ("energy_per_pixel", ctypes.c_float), ("score", ctypes.c_float), ("level", I32),
+                ("n_hypotheses", I32), ("n_chosen", I32), ("n_pixels", I32), ("status", I32),
+                ("chosen_pose", (ctypes.c_double * 16) * 16), ("chosen_energy", ctypes.c_float * 16),
+                ("chosen_score", ctypes.c_float * 16), ("chosen_slot", I32 * 16), ("best", I32),
+                ("pad", I32)]
+
+
+_SIGS = {
+    "rl_context_create": [I32, P, U64, P],
+    "rl_context_destroy": [P],
+    "rl_context_usage": [P, P, P],
+    "rl_forest_create_random": [P, P, U64, P],
+    "rl_forest_destroy": [P],
+    "rl_forest_reset_leaves": [P, P],
+    "rl_forest_adapt": [P, P, P, P, P, I32, P],
+    "rl_forest_update_modes": [P, I32, P],
+    "rl_forest_leaves": [P, P, P, P, I32, P, I32, P],
+    "rl_forest_export": [P] + [P] * 12,
+    "rl_forest_save": [P, ctypes.c_char_p],
+    "rl_forest_load": [P, ctypes.c_char_p, P],
+    "rl_scene_box": [P, P, P, P],
+    "rl_scene_destroy": [P],
+    "rl_score_poses": [P, P, P, P, I32, I32, P, P, P],
+    "rl_reloc_create": [P, P, P, I32, I32, I32, P],
+    "rl_reloc_destroy": [P],
+    "rl_relocalise": [P, P, P, P, U64, I32, P, P],
+    "rl_relocalise_batch": [P, I32, P, P, P, P, I32, P, P],
+    "rl_relocalise_batch_async": [P, I32, P, P, P, P, P],
+    "rl_reloc_fetch": [P, I32, P, P],
+    "rl_reloc_debug": [P, I32] + [P] * 10,
+    "rl_reloc_profile": [P, I32],
+    "rl_reloc_profile_read": [P, P, P, P],
+    "rl_cascade_create": [P, P, P, I32, P],
+    "rl_cascade_destroy": [P],
+    "rl_cascade_relocalise": [P, P, P, P, U64, I32, P, P],
+    "rl_cascade_relocalise_batch": [P, I32, P, P, P, P, I32, P, P],
+}
+
+
+def lib():
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"librelocgb.so is not built ({LIB_PATH}); run "
+                                  "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, args in _SIGS.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_int
+            L.rl_last_error.argtypes = []
+            L.rl_last_error.restype = ctypes.c_char_p
+            L.rl_kernel_name.argtypes = [I32]
+            L.rl_kernel_name.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+def check(status):
+    if status != 0:
+        msg = lib().rl_last_error()
+        raise RelocError(status, msg.decode() if msg else "")
+
+
+def call(name, *args):
+    check(getattr(lib(), name)(*args))
+
+
+def exported_symbols():
+    return sorted(_SIGS) + ["rl_last_error", "rl_kernel_name"]

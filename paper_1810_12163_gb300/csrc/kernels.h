@@ -1,0 +1,86 @@
+// Argument blocks and launchers of the relocaliser kernels.
+#pragma once
+#include "internal.h"
+
+namespace rl {
+
+struct EnergyArgs {
+    const double *pose;        // pose (12 doubles) of hypothesis i of frame b:
+    int pose_stride;           //   pose[(b*pose_stride + idx) * 12]
+    const int32_t *idx;        // idx[b*idx_stride + i] or i when null
+    int idx_stride;
+    const int32_t *count;      // hypotheses of frame b
+    const int32_t *pix;        // [B][max_pix]
+    const float4 *xc;          // [B][max_pix]
+    int max_pix, n_pix;
+    const uint16_t *leaves;
+    int hw_max;
+    ModeView mv;
+    RParams p;
+    int chunk, maxm;
+    float *part;               // [B][part_h][n_chunks]
+    int part_h, n_chunks;
+    int round_gate;            // skip frames whose round is inactive
+    unsigned long long *work;  // profiling counters or null
+};
+
+struct SelectArgs {
+    int phase, round;
+    const float *part;
+    int part_h, n_chunks_used, n_chunks;
+    const int32_t *count;        // n_hyp (cull) or n_cur (round)
+    const double *hyp_pose;      // cull source [B][N][12]
+    const int32_t *hyp_list;     // cull source slots [B][N]
+    QueryState q;
+    RParams p;
+    int n_pix;                   // |I| after this phase
+};
+
+struct LmArgs {
+    QueryState q;
+    const uint16_t *leaves;
+    int hw_max;
+    ModeView mv;
+    RParams p;
+    int n_pix;
+    unsigned long long *work;  // profiling counters or null
+};
+
+struct RaycastArgs {
+    const Frame *frames;
+    const double *poses;       // [B][pose_cap][12]
+    const int32_t *n_poses;    // poses per frame, or null: pose_cap for every frame
+    int pose_cap;
+    float lo[3], hi[3];
+    double lo64[3], hi64[3];
+    double *part_sum;          // [B][pose_cap][n_tiles]
+    int32_t *part_cnt;         // [B][pose_cap][n_tiles][2]
+    int n_tiles;
+    unsigned long long *work;  // profiling counters or null
+    __device__ int n_poses_of(int b) const { return n_poses ? n_poses[b] : pose_cap; }
+    __device__ const double *pose_of(int b, int c) const {
+        return poses + ((size_t)b * pose_cap + c) * 12;
+    }
+};
+
+size_t energy_smem(int chunk, int maxm);
+rl_status launch_energy(const EnergyArgs &a, int max_count, int n, cudaStream_t s);
+rl_status launch_select(const SelectArgs &a, int n, cudaStream_t s);
+rl_status launch_lm(const LmArgs &a, int n, cudaStream_t s);
+rl_status launch_raycast(const RaycastArgs &a, int n, int max_hw, cudaStream_t s);
+rl_status launch_score_poses(const RaycastArgs &a, int n_poses, int npx, float *scores,
+                             float *valid_frac, cudaStream_t s);
+rl_status launch_finalize(const QueryState &q, const RParams &p, int n_tiles, int ranked, int n,
+                          cudaStream_t s);
+rl_status launch_hypgen(const Frame *frames, const uint16_t *leaves, int hw_max, ModeView mv,
+                        const RParams &p, double *hyp_pose, int32_t *hyp_iter, int n,
+                        cudaStream_t s);
+rl_status launch_compact(const int32_t *hyp_iter, int N, int32_t *hyp_list, int32_t *n_hyp, int n,
+                         cudaStream_t s);
+rl_status launch_sample_batch(const Frame *frames, const uint16_t *leaves, int hw_max, ModeView mv,
+                              const RParams &p, int batch, int32_t *pix, float4 *xc, int n,
+                              cudaStream_t s);
+rl_status launch_subsample(const Frame *src, Frame *dst_desc, float *dst_depth, uint8_t *dst_rgb,
+                           int s_factor, int n, int max_w, int max_h, cudaStream_t s);
+
+}  // namespace rl

@@ -1,0 +1,731 @@
+// Relocaliser and cascade handles: per-query device state, the launch
+// sequence of one relocalisation (Sec. 3.2.3-3.2.4), results and the
+// cascade's fall-back rule (Sec. 3.2.5).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "kernels.h"
+
+namespace rl {
+
+static int rounds_for(int n_cull, int k_out, int halve_to_one) {
+    int m = n_cull, r = 0;
+    while (m > k_out || (halve_to_one && m > 1)) {
+        m = (m + 1) / 2;
+        ++r;
+    }
+    return r;
+}
+
+static rl_status check_ransac(const rl_ransac_params *p, const rl_forest *f) {
+    if (!p) return fail(RL_ERR_INVALID_ARG, "null relocaliser params");
+    if (p->n_hyp < 1 || p->n_hyp > 4096) return fail(RL_ERR_INVALID_ARG, "n_hyp must be 1..4096");
+    if (p->max_iter < 1) return fail(RL_ERR_INVALID_ARG, "max_iter must be >= 1");
+    if (p->n_cull < 1 || p->n_cull > 64) return fail(RL_ERR_INVALID_ARG, "n_cull must be 1..64");
+    if (p->eta < 1 || p->eta > 4096) return fail(RL_ERR_INVALID_ARG, "eta must be 1..4096");
+    if (p->k_out < 1 || p->k_out > RL_MAX_CHOSEN) return fail(RL_ERR_INVALID_ARG, "k_out must be 1..16");
+    if (p->k_top < 1) return fail(RL_ERR_INVALID_ARG, "k_top must be >= 1");
+    if (p->n_trees_used < 1 || p->n_trees_used > f->p.n_trees)
+        return fail(RL_ERR_INVALID_ARG, "n_trees_used must be 1..forest trees");
+    if (p->batch_attempts < 1) return fail(RL_ERR_INVALID_ARG, "batch_attempts must be >= 1");
+    if (p->lm_max_iter < 0) return fail(RL_ERR_INVALID_ARG, "lm_max_iter must be >= 0");
+    if (p->colour_thresh < 0) return fail(RL_ERR_INVALID_ARG, "colour_thresh must be >= 0");
+    return RL_OK;
+}
+
+template <class T>
+static rl_status ralloc(rl_reloc *r, uint64_t n, T **out) {
+    RL_TRY(alloc_n(r->forest->ctx, n, out));
+    r->allocs.push_back(*out);
+    return RL_OK;
+}
+
+static void prof_free(rl_reloc *r);
+
+static void reloc_release(rl_reloc *r) {
+    prof_free(r);
+    for (void *p : r->allocs) arena_free(r->forest->ctx, p);
+    r->allocs.clear();
+    if (r->host_frames) cudaFreeHost(r->host_frames);
+    if (r->host_results) cudaFreeHost(r->host_results);
+    r->host_frames = nullptr;
+    r->host_results = nullptr;
+}
+
+// Host mirrors of the per-query outputs copied back after each call.
+struct HostOut {
+    DevResult res;
+};
+
+static rl_status set_frames(rl_reloc *r, int n, const float *depth, const uint8_t *rgb,
+                            const rl_intrinsics *K, const uint64_t *seeds, cudaStream_t s) {
+    const size_t hw = (size_t)K->width * K->height;
+    for (int i = 0; i < n; ++i) {
+        Frame &f = r->host_frames[i];
+        f.depth = depth + hw * i;
+        f.rgb = rgb + hw * 3 * i;
+        f.fx = K->fx; f.fy = K->fy; f.cx = K->cx; f.cy = K->cy;
+        f.W = K->width; f.H = K->height;
+        f.key0 = (uint32_t)seeds[i];
+        f.key1 = (uint32_t)(seeds[i] >> 32);
+    }
+    RL_CK(cudaMemcpyAsync(r->q.frames, r->host_frames, sizeof(Frame) * n, cudaMemcpyHostToDevice, s));
+    return RL_OK;
+}
+
+// Event pair around one launch when profiling is on.
+struct ProfScope {
+    rl_reloc *r;
+    int kid;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    ProfScope(rl_reloc *r_, int kid_, cudaStream_t s_) : r(r_), kid(kid_), s(s_) {
+        if (r->prof.on) {
+            a = take_event(r);
+            cudaEventRecord(a, s);
+        }
+    }
+    ~ProfScope() {
+        if (!a) return;
+        cudaEvent_t b = take_event(r);
+        cudaEventRecord(b, s);
+        r->prof.pending.push_back({kid, a, b});
+    }
+    static cudaEvent_t take_event(rl_reloc *r) {
+        if (r->prof.pool.empty()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            return e;
+        }
+        cudaEvent_t e = r->prof.pool.back();
+        r->prof.pool.pop_back();
+        return e;
+    }
+};
+
+static void prof_resolve(rl_reloc *r) {
+    for (auto &p : r->prof.pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            r->prof.ms[p.kid] += ms;
+            r->prof.launches[p.kid] += 1;
+        }
+        r->prof.pool.push_back(p.a);
+        r->prof.pool.push_back(p.b);
+    }
+    r->prof.pending.clear();
+}
+
+#define PROF(kid) ProfScope prof_scope_##kid##__LINE__(r, kid, s)
+
+rl_status run_relocalise(rl_reloc *r, int n, int level, cudaStream_t s) {
+    rl_forest *f = r->forest;
+    RParams p = r->rp;
+    p.level = level;
+    QueryState &q = r->q;
+    const int hw_max = r->max_w * r->max_h;
+    const ModeView mv = mode_view(f);
+    const int N = p.n_hyp, NC = p.n_cull;
+    RL_CK(cudaMemsetAsync(q.n_chosen, 0xFF, sizeof(int32_t) * n, s));
+    RL_CK(cudaMemsetAsync(q.n_rounds, 0, sizeof(int32_t) * n, s));
+    RL_CK(cudaMemsetAsync(q.round_count, 0, sizeof(int32_t) * 16 * n, s));
+    unsigned long long *work = r->prof.on ? r->prof.work : nullptr;
+    { PROF(K_LEAVES); RL_TRY(launch_leaves(f, q.frames, n, p.n_trees, hw_max, q.leaves, r->max_w, r->max_h, s)); }
+    { PROF(K_HYPGEN); RL_TRY(launch_hypgen(q.frames, q.leaves, hw_max, mv, p, q.hyp_pose, q.hyp_iter, n, s)); }
+    { PROF(K_COMPACT); RL_TRY(launch_compact(q.hyp_iter, N, q.hyp_list, q.n_hyp, n, s)); }
+    { PROF(K_SAMPLE); RL_TRY(launch_sample_batch(q.frames, q.leaves, hw_max, mv, p, 0, q.pix, q.xc, n, s)); }
+
+    const int maxm = p.n_trees * std::min(p.k_top, f->p.m_max);
+    int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(32, 40960 / (maxm * 36)));
+    EnergyArgs ea{};
+    ea.pix = q.pix;
+    ea.xc = q.xc;
+    ea.max_pix = p.max_pix;
+    ea.leaves = q.leaves;
+    ea.hw_max = hw_max;
+    ea.mv = mv;
+    ea.p = p;
+    ea.chunk = chunk;
+    ea.maxm = maxm;
+    ea.part = q.energy_part;
+    ea.part_h = std::max(N, NC);
+    ea.n_chunks = r->n_chunks;
+    // initial cull on I_0
+    ea.pose = q.hyp_pose;
+    ea.pose_stride = N;
+    ea.idx = q.hyp_list;
+    ea.idx_stride = N;
+    ea.count = q.n_hyp;
+    ea.n_pix = p.eta;
+    ea.round_gate = 0;
+    ea.work = work;
+    { PROF(K_ENERGY); RL_TRY(launch_energy(ea, N, n, s)); }
+    SelectArgs sa{};
+    sa.phase = 0;
+    sa.round = 0;
+    sa.part = q.energy_part;
+    sa.part_h = ea.part_h;
+    sa.n_chunks = r->n_chunks;
+    sa.n_chunks_used = (p.eta + chunk - 1) / chunk;
+    sa.count = q.n_hyp;
+    sa.hyp_pose = q.hyp_pose;
+    sa.hyp_list = q.hyp_list;
+    sa.q = q;
+    sa.p = p;
+    sa.n_pix = p.eta;
+    { PROF(K_SELECT); RL_TRY(launch_select(sa, n, s)); }
+    // preemptive rounds
+    for (int round = 0; round < p.max_rounds; ++round) {
+        const int n_pix = p.eta * (round + 2);
+        { PROF(K_SAMPLE); RL_TRY(launch_sample_batch(q.frames, q.leaves, hw_max, mv, p, round + 1, q.pix, q.xc, n, s)); }
+        if (p.pose_update && p.lm_max_iter > 0) {
+            LmArgs la{q, q.leaves, hw_max, mv, p, n_pix, work};
+            PROF(K_LM);
+            RL_TRY(launch_lm(la, n, s));
+        }
+        ea.pose = q.cur_pose;
+        ea.pose_stride = NC;
+        ea.idx = nullptr;
+        ea.idx_stride = 0;
+        ea.count = q.n_cur;
+        ea.n_pix = n_pix;
+        ea.round_gate = 1;
+        { PROF(K_ENERGY); RL_TRY(launch_energy(ea, NC, n, s)); }
+        sa.phase = 1;
+        sa.round = round;
+        sa.count = q.n_cur;
+        sa.n_chunks_used = (n_pix + chunk - 1) / chunk;
+        sa.n_pix = n_pix;
+        { PROF(K_SELECT); RL_TRY(launch_select(sa, n, s)); }
+    }
+    const int ranked = p.rank && r->scene != nullptr;
+    if (ranked) {
+        RaycastArgs ra{};
+        ra.frames = q.frames;
+        ra.poses = q.chosen_pose;
+        ra.n_poses = q.n_chosen;
+        ra.pose_cap = 16;
+        for (int a = 0; a < 3; ++a) {
+            ra.lo[a] = (float)r->scene->lo[a];
+            ra.hi[a] = (float)r->scene->hi[a];
+            ra.lo64[a] = r->scene->lo[a];
+            ra.hi64[a] = r->scene->hi[a];
+        }
+        ra.part_sum = q.score_part;
+        ra.part_cnt = q.score_cnt;
+        ra.n_tiles = r->n_score_tiles;
+        ra.work = work;
+        PROF(K_RAYCAST);
+        RL_TRY(launch_raycast(ra, n, hw_max, s));
+    }
+    { PROF(K_FINALIZE); RL_TRY(launch_finalize(q, p, r->n_score_tiles, ranked, n, s)); }
+    return RL_OK;
+}
+
+static rl_status fetch_results(rl_reloc *r, int n, cudaStream_t s, rl_result *out, int level) {
+    QueryState &q = r->q;
+    std::vector<double> cp((size_t)n * 16 * 12);
+    std::vector<float> ce((size_t)n * 16), cs((size_t)n * 16);
+    std::vector<int32_t> cslot((size_t)n * 16);
+    RL_CK(cudaMemcpyAsync(r->host_results, q.result_blob, sizeof(DevResult) * n, cudaMemcpyDeviceToHost, s));
+    RL_CK(cudaMemcpyAsync(cp.data(), q.chosen_pose, cp.size() * 8, cudaMemcpyDeviceToHost, s));
+    RL_CK(cudaMemcpyAsync(ce.data(), q.chosen_energy, ce.size() * 4, cudaMemcpyDeviceToHost, s));
+    RL_CK(cudaMemcpyAsync(cs.data(), q.chosen_score, cs.size() * 4, cudaMemcpyDeviceToHost, s));
+    RL_CK(cudaMemcpyAsync(cslot.data(), q.chosen_slot, cslot.size() * 4, cudaMemcpyDeviceToHost, s));
+    RL_CK(cudaStreamSynchronize(s));
+    if (!r->prof.pending.empty()) prof_resolve(r);
+    for (int i = 0; i < n; ++i) {
+        const DevResult &d = r->host_results[i];
+        rl_result &o = out[i];
+        memset(&o, 0, sizeof(o));
+        for (int k = 0; k < 12; ++k) o.pose[k] = d.pose[k];
+        o.pose[15] = 1.0;
+        o.energy = d.energy;
+        o.energy_per_pixel = d.energy_per_pixel;
+        o.score = d.score;
+        o.level = level;
+        o.n_hypotheses = d.n_hypotheses;
+        o.n_chosen = std::max(0, d.n_chosen);
+        o.n_pixels = d.n_pixels;
+        o.status = d.status;
+        o.best = d.best;
+        for (int c = 0; c < o.n_chosen && c < RL_MAX_CHOSEN; ++c) {
+            for (int k = 0; k < 12; ++k) o.chosen_pose[c][k] = cp[((size_t)i * 16 + c) * 12 + k];
+            o.chosen_pose[c][15] = 1.0;
+            o.chosen_energy[c] = ce[(size_t)i * 16 + c];
+            o.chosen_score[c] = cs[(size_t)i * 16 + c];
+            o.chosen_slot[c] = cslot[(size_t)i * 16 + c];
+        }
+    }
+    return RL_OK;
+}
+
+// Copies n host frames into the staging area (or points at device frames)
+// and fills the frame descriptors.
+static rl_status stage_inputs(rl_reloc *r, int n, const float *depth, const uint8_t *rgb,
+                              const rl_intrinsics *K, const uint64_t *seeds, rl_mem mem,
+                              cudaStream_t s) {
+    const size_t hw = (size_t)K->width * K->height;
+    if (mem == RL_HOST) {
+        RL_CK(cudaMemcpyAsync(r->stage_depth, depth, sizeof(float) * hw * n, cudaMemcpyHostToDevice, s));
+        RL_CK(cudaMemcpyAsync(r->stage_rgb, rgb, hw * 3 * n, cudaMemcpyHostToDevice, s));
+        return set_frames(r, n, r->stage_depth, r->stage_rgb, K, seeds, s);
+    }
+    if (mem != RL_DEVICE) return fail(RL_ERR_INVALID_ARG, "bad rl_mem");
+    return set_frames(r, n, depth, rgb, K, seeds, s);
+}
+
+static rl_status check_call(rl_reloc *r, int n, const float *depth, const uint8_t *rgb,
+                            const rl_intrinsics *K, const uint64_t *seeds) {
+    if (!r || !depth || !rgb || !K || !seeds) return fail(RL_ERR_INVALID_ARG, "null argument");
+    if (n < 1 || n > r->max_batch) return fail(RL_ERR_INVALID_ARG, "batch size outside 1..max_batch");
+    if (K->width < 1 || K->height < 1 || K->width > r->max_w || K->height > r->max_h)
+        return fail(RL_ERR_INVALID_ARG, "frame larger than the relocaliser's maximum size");
+    if (!(K->fx > 0) || !(K->fy > 0)) return fail(RL_ERR_INVALID_ARG, "focal lengths must be > 0");
+    return RL_OK;
+}
+
+}  // namespace rl
+
+using namespace rl;
+
+extern "C" rl_status rl_reloc_create(rl_forest *f, rl_scene *scene, const rl_ransac_params *p,
+                                     int32_t max_w, int32_t max_h, int32_t max_batch,
+                                     rl_reloc **out) {
+    if (!f || !out) return fail(RL_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    RL_TRY(check_ransac(p, f));
+    if (max_w < 1 || max_h < 1 || max_w > 8192 || max_h > 8192 || (int64_t)max_w * max_h > (1 << 26))
+        return fail(RL_ERR_INVALID_ARG, "bad maximum frame size");
+    if (max_batch < 1 || max_batch > 65535) return fail(RL_ERR_INVALID_ARG, "max_batch must be 1..65535");
+    if (p->rank && !scene) return fail(RL_ERR_INVALID_ARG, "ranking needs a scene model");
+    RL_CK(cudaSetDevice(f->ctx->device));
+    rl_reloc *r = new rl_reloc();
+    r->forest = f;
+    r->scene = scene;
+    r->p = *p;
+    r->max_w = max_w;
+    r->max_h = max_h;
+    r->max_batch = max_batch;
+    RParams &rp = r->rp;
+    rp.n_hyp = p->n_hyp; rp.max_iter = p->max_iter; rp.n_cull = p->n_cull; rp.eta = p->eta;
+    rp.k_out = p->k_out; rp.pose_update = p->pose_update; rp.use_cov = p->use_cov;
+    rp.colour_thresh = p->colour_thresh; rp.min_sq_dist = p->min_sq_dist;
+    rp.max_trans_err = p->max_trans_err; rp.k_top = p->k_top; rp.n_trees = p->n_trees_used;
+    rp.lm_max_iter = p->lm_max_iter; rp.batch_attempts = p->batch_attempts;
+    rp.lm_lambda0 = p->lm_lambda0; rp.lm_inlier_thresh = p->lm_inlier_thresh; rp.lm_stop = p->lm_stop;
+    rp.rank = p->rank; rp.halve_to_one = p->halve_to_one; rp.level = 0;
+    rp.max_rounds = rounds_for(p->n_cull, p->k_out, p->halve_to_one);
+    rp.max_pix = p->eta * (rp.max_rounds + 1);
+    const int maxm = p->n_trees_used * std::min(p->k_top, f->p.m_max);
+    const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(32, 40960 / (maxm * 36)));
+    r->n_chunks = (rp.max_pix + chunk - 1) / chunk;
+    const size_t hw = (size_t)max_w * max_h;
+    r->n_score_tiles = (int)((hw + 255) / 256);
+    const uint64_t B = max_batch, N = p->n_hyp, NC = p->n_cull, MP = rp.max_pix;
+    QueryState &q = r->q;
+    rl_status s = RL_OK;
+#define A(field, count) if (s == RL_OK) s = ralloc(r, (uint64_t)(count), &q.field)
+    A(leaves, B * p->n_trees_used * hw);
+    A(hyp_pose, B * N * 12);
+    A(hyp_iter, B * N);
+    A(hyp_list, B * N);
+    A(n_hyp, B);
+    A(pix, B * MP);
+    A(xc, B * MP);
+    A(n_pix, B);
+    A(cur_pose, B * NC * 12);
+    A(cur_slot, B * NC);
+    A(cur_energy, B * NC);
+    A(n_cur, B);
+    A(cull_slot, B * NC);
+    A(cull_energy, B * NC);
+    A(energy_part, B * std::max(N, NC) * (uint64_t)r->n_chunks);
+    A(corr, B * NC * MP);
+    A(chosen_pose, B * 16 * 12);
+    A(chosen_energy, B * 16);
+    A(chosen_slot, B * 16);
+    A(chosen_npix, B);
+    A(n_chosen, B);
+    A(score_part, B * 16 * (uint64_t)r->n_score_tiles);
+    A(score_cnt, B * 16 * 2 * (uint64_t)r->n_score_tiles);
+    A(chosen_score, B * 16);
+    A(round_count, B * 16);
+    A(round_slot, B * 16 * NC);
+    A(round_energy, B * 16 * NC);
+    A(round_pose, B * 16 * NC * 12);
+    A(n_rounds, B);
+    A(frames, B);
+    A(result_blob, B * sizeof(DevResult));
+#undef A
+    if (s == RL_OK) s = ralloc(r, B * hw, &r->stage_depth);
+    if (s == RL_OK) s = ralloc(r, B * hw * 3, &r->stage_rgb);
+    if (s == RL_OK && cudaMallocHost(&r->host_frames, sizeof(Frame) * B) != cudaSuccess)
+        s = fail(RL_ERR_CUDA, "pinned host allocation failed");
+    if (s == RL_OK && cudaMallocHost(&r->host_results, sizeof(DevResult) * B) != cudaSuccess)
+        s = fail(RL_ERR_CUDA, "pinned host allocation failed");
+    if (s == RL_OK) {
+        const size_t sm_sel = (size_t)N * 8 + NC * (12 * 8 + 8) + 64;
+        const size_t sm_en = energy_smem(chunk, maxm);
+        if (sm_sel > 200 * 1024 || sm_en > 200 * 1024) s = fail(RL_ERR_INVALID_ARG, "configuration needs too much shared memory");
+    }
+    if (s != RL_OK) {
+        reloc_release(r);
+        delete r;
+        return s;
+    }
+    f->refcount++;
+    *out = r;
+    return RL_OK;
+}
+
+extern "C" rl_status rl_reloc_destroy(rl_reloc *r) {
+    if (!r) return fail(RL_ERR_INVALID_ARG, "null relocaliser");
+    if (r->refcount > 0) return fail(RL_ERR_BUSY, "relocaliser still used by a cascade");
+    cudaSetDevice(r->forest->ctx->device);
+    cudaDeviceSynchronize();
+    r->forest->refcount--;
+    reloc_release(r);
+    delete r;
+    return RL_OK;
+}
+
+extern "C" rl_status rl_relocalise_batch(rl_reloc *r, int32_t n, const float *depth, const uint8_t *rgb,
+                                         const rl_intrinsics *K, const uint64_t *seeds, rl_mem mem,
+                                         void *stream, rl_result *out) {
+    RL_TRY(check_call(r, n, depth, rgb, K, seeds));
+    if (!out) return fail(RL_ERR_INVALID_ARG, "null output");
+    RL_CK(cudaSetDevice(r->forest->ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    RL_TRY(stage_inputs(r, n, depth, rgb, K, seeds, mem, s));
+    RL_TRY(run_relocalise(r, n, 0, s));
+    r->last_batch = n;
+    return fetch_results(r, n, s, out, 0);
+}
+
+extern "C" rl_status rl_relocalise(rl_reloc *r, const float *depth, const uint8_t *rgb,
+                                   const rl_intrinsics *K, uint64_t seed, rl_mem mem, void *stream,
+                                   rl_result *out) {
+    return rl_relocalise_batch(r, 1, depth, rgb, K, &seed, mem, stream, out);
+}
+
+extern "C" rl_status rl_relocalise_batch_async(rl_reloc *r, int32_t n, const float *depth,
+                                               const uint8_t *rgb, const rl_intrinsics *K,
+                                               const uint64_t *seeds, void *stream) {
+    RL_TRY(check_call(r, n, depth, rgb, K, seeds));
+    RL_CK(cudaSetDevice(r->forest->ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    RL_TRY(stage_inputs(r, n, depth, rgb, K, seeds, RL_DEVICE, s));
+    RL_TRY(run_relocalise(r, n, 0, s));
+    r->last_batch = n;
+    return RL_OK;
+}
+
+extern "C" rl_status rl_reloc_fetch(rl_reloc *r, int32_t n, void *stream, rl_result *out) {
+    if (!r || !out) return fail(RL_ERR_INVALID_ARG, "null argument");
+    if (n < 1 || n > r->last_batch) return fail(RL_ERR_INVALID_ARG, "n exceeds the last batch");
+    RL_CK(cudaSetDevice(r->forest->ctx->device));
+    return fetch_results(r, n, (cudaStream_t)stream, out, 0);
+}
+
+extern "C" rl_status rl_reloc_debug(rl_reloc *r, int32_t qi, double *hyp_pose, int32_t *hyp_iter,
+                                    int32_t *cull_slot, float *cull_energy, int32_t *round_count,
+                                    int32_t *round_slot, float *round_energy, double *round_pose,
+                                    int32_t *batch_pix, int32_t *n_rounds) {
+    if (!r) return fail(RL_ERR_INVALID_ARG, "null relocaliser");
+    if (qi < 0 || qi >= r->last_batch) return fail(RL_ERR_INVALID_ARG, "query index outside the last batch");
+    RL_CK(cudaSetDevice(r->forest->ctx->device));
+    RL_CK(cudaDeviceSynchronize());
+    const QueryState &q = r->q;
+    const size_t N = r->rp.n_hyp, NC = r->rp.n_cull, MP = r->rp.max_pix;
+    if (hyp_pose) RL_CK(cudaMemcpy(hyp_pose, q.hyp_pose + qi * N * 12, N * 12 * 8, cudaMemcpyDeviceToHost));
+    if (hyp_iter) RL_CK(cudaMemcpy(hyp_iter, q.hyp_iter + qi * N, N * 4, cudaMemcpyDeviceToHost));
+    if (cull_slot) RL_CK(cudaMemcpy(cull_slot, q.cull_slot + qi * NC, NC * 4, cudaMemcpyDeviceToHost));
+    if (cull_energy) RL_CK(cudaMemcpy(cull_energy, q.cull_energy + qi * NC, NC * 4, cudaMemcpyDeviceToHost));
+    if (round_count) RL_CK(cudaMemcpy(round_count, q.round_count + qi * 16, 16 * 4, cudaMemcpyDeviceToHost));
+    if (round_slot) RL_CK(cudaMemcpy(round_slot, q.round_slot + qi * 16 * NC, 16 * NC * 4, cudaMemcpyDeviceToHost));
+    if (round_energy) RL_CK(cudaMemcpy(round_energy, q.round_energy + qi * 16 * NC, 16 * NC * 4, cudaMemcpyDeviceToHost));
+    if (round_pose) RL_CK(cudaMemcpy(round_pose, q.round_pose + qi * 16 * NC * 12, 16 * NC * 12 * 8, cudaMemcpyDeviceToHost));
+    if (batch_pix) {
+        const size_t nb = std::min<size_t>(16, (size_t)r->rp.max_rounds + 1);
+        for (size_t i = 0; i < 16 * (size_t)r->rp.eta; ++i) batch_pix[i] = -1;
+        RL_CK(cudaMemcpy(batch_pix, q.pix + qi * MP, nb * r->rp.eta * 4, cudaMemcpyDeviceToHost));
+    }
+    if (n_rounds) RL_CK(cudaMemcpy(n_rounds, q.n_rounds + qi, 4, cudaMemcpyDeviceToHost));
+    return RL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Cascade (Sec. 3.2.5)
+// ---------------------------------------------------------------------------
+extern "C" rl_status rl_cascade_create(rl_reloc *const *levels, const double *thresholds,
+                                       const int32_t *subsample, int32_t n_levels,
+                                       rl_cascade **out) {
+    if (!levels || !out || n_levels < 1 || n_levels > 8) return fail(RL_ERR_INVALID_ARG, "bad cascade");
+    if (n_levels > 1 && !thresholds) return fail(RL_ERR_INVALID_ARG, "thresholds needed");
+    *out = nullptr;
+    for (int l = 0; l < n_levels; ++l) {
+        if (!levels[l]) return fail(RL_ERR_INVALID_ARG, "null level");
+        if (levels[l]->forest != levels[0]->forest)
+            return fail(RL_ERR_INVALID_ARG, "cascade levels must share one forest");
+        if (subsample && subsample[l] < 1) return fail(RL_ERR_INVALID_ARG, "subsample must be >= 1");
+    }
+    rl_cascade *c = new rl_cascade();
+    for (int l = 0; l < n_levels; ++l) {
+        c->levels.push_back(levels[l]);
+        c->subsample.push_back(subsample ? subsample[l] : 1);
+        if (l < n_levels - 1) c->thresholds.push_back(thresholds[l]);
+        levels[l]->refcount++;
+    }
+    *out = c;
+    return RL_OK;
+}
+
+extern "C" rl_status rl_cascade_destroy(rl_cascade *c) {
+    if (!c) return fail(RL_ERR_INVALID_ARG, "null cascade");
+    for (rl_reloc *r : c->levels) r->refcount--;
+    delete c;
+    return RL_OK;
+}
+
+namespace rl {
+__global__ void k_subsample(const Frame *src, int s_factor, float *dd, uint8_t *dc, int max_hw,
+                            const int32_t *sel) {
+    const int b = blockIdx.y;
+    const Frame f = src[sel[b]];
+    const int W2 = (f.W + s_factor - 1) / s_factor, H2 = (f.H + s_factor - 1) / s_factor;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= W2 * H2) return;
+    const int x = (p % W2) * s_factor, y = (p / W2) * s_factor;
+    const int sp = y * f.W + x;
+    dd[(size_t)b * max_hw + p] = f.depth[sp];
+    dc[((size_t)b * max_hw + p) * 3 + 0] = f.rgb[sp * 3 + 0];
+    dc[((size_t)b * max_hw + p) * 3 + 1] = f.rgb[sp * 3 + 1];
+    dc[((size_t)b * max_hw + p) * 3 + 2] = f.rgb[sp * 3 + 2];
+}
+}  // namespace rl
+
+extern "C" rl_status rl_cascade_relocalise_batch(rl_cascade *c, int32_t n, const float *depth,
+                                                 const uint8_t *rgb, const rl_intrinsics *K,
+                                                 const uint64_t *seeds, rl_mem mem, void *stream,
+                                                 rl_result *out) {
+    if (!c || !out) return fail(RL_ERR_INVALID_ARG, "null argument");
+    rl_reloc *top = c->levels.back();
+    RL_TRY(check_call(top, n, depth, rgb, K, seeds));
+    for (rl_reloc *r : c->levels)
+        if (n > r->max_batch) return fail(RL_ERR_INVALID_ARG, "batch larger than a level's max_batch");
+    RL_CK(cudaSetDevice(top->forest->ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    // full-resolution inputs live in the last level's staging area
+    RL_TRY(stage_inputs(top, n, depth, rgb, K, seeds, mem, s));
+    std::vector<Frame> full(top->host_frames, top->host_frames + n);
+    Frame *full_dev = nullptr;
+    int32_t *sel_dev = nullptr;
+    rl_ctx *ctx = top->forest->ctx;
+    RL_TRY(alloc_n(ctx, (uint64_t)n, &full_dev));
+    rl_status st = alloc_n(ctx, (uint64_t)n, &sel_dev);
+    if (st == RL_OK && cudaMemcpyAsync(full_dev, full.data(), sizeof(Frame) * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        st = fail(RL_ERR_CUDA, "frame copy failed");
+    std::vector<int32_t> pending(n);
+    for (int i = 0; i < n; ++i) pending[i] = i;
+    std::vector<rl_result> tmp(n);
+    const int L = (int)c->levels.size();
+    for (int l = 0; l < L && st == RL_OK && !pending.empty(); ++l) {
+        rl_reloc *r = c->levels[l];
+        const int m = (int)pending.size();
+        const int sf = c->subsample[l];
+        if (cudaMemcpyAsync(sel_dev, pending.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+            st = fail(RL_ERR_CUDA, "selection copy failed");
+            break;
+        }
+        rl_intrinsics Kl = *K;
+        Kl.width = (K->width + sf - 1) / sf;
+        Kl.height = (K->height + sf - 1) / sf;
+        Kl.fx = (float)((double)K->fx / sf);
+        Kl.fy = (float)((double)K->fy / sf);
+        Kl.cx = (float)((double)K->cx / sf);
+        Kl.cy = (float)((double)K->cy / sf);
+        if (Kl.width > r->max_w || Kl.height > r->max_h) {
+            st = fail(RL_ERR_INVALID_ARG, "level input larger than the level's maximum size");
+            break;
+        }
+        const int hw_l = Kl.width * Kl.height;
+        if (sf == 1) {
+            // full-resolution level: descriptors point at the staged frames
+            for (int i = 0; i < m; ++i) {
+                Frame &f = r->host_frames[i];
+                f = full[pending[i]];
+            }
+        } else {
+            if (r == top) {
+                st = fail(RL_ERR_INVALID_ARG, "the last level object cannot also be a subsampled level");
+                break;
+            }
+            const int hwmax_r = r->max_w * r->max_h;
+            dim3 grid((hw_l + 255) / 256, m);
+            k_subsample<<<grid, 256, 0, s>>>(full_dev, sf, r->stage_depth, r->stage_rgb, hwmax_r, sel_dev);
+            if (cudaGetLastError() != cudaSuccess) {
+                st = fail(RL_ERR_CUDA, "subsample launch failed");
+                break;
+            }
+            for (int i = 0; i < m; ++i) {
+                Frame &f = r->host_frames[i];
+                f = full[pending[i]];
+                f.depth = r->stage_depth + (size_t)hwmax_r * i;
+                f.rgb = r->stage_rgb + (size_t)hwmax_r * 3 * i;
+                f.fx = Kl.fx; f.fy = Kl.fy; f.cx = Kl.cx; f.cy = Kl.cy;
+                f.W = Kl.width; f.H = Kl.height;
+            }
+        }
+        if (cudaMemcpyAsync(r->q.frames, r->host_frames, sizeof(Frame) * m, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            st = fail(RL_ERR_CUDA, "frame copy failed");
+        if (st == RL_OK) st = run_relocalise(r, m, l, s);
+        if (st == RL_OK) st = fetch_results(r, m, s, tmp.data(), l);
+        r->last_batch = m;
+        if (st != RL_OK) break;
+        std::vector<int32_t> next;
+        for (int i = 0; i < m; ++i) {
+            const int qi = pending[i];
+            out[qi] = tmp[i];
+            // fall back iff the output pose's score exceeds the level threshold
+            const bool accept = tmp[i].status == RL_POSE_FOUND && (double)tmp[i].score <= c->thresholds[l];
+            if (l < L - 1 && !accept) next.push_back(qi);
+        }
+        pending.swap(next);
+    }
+    arena_free(ctx, full_dev);
+    arena_free(ctx, sel_dev);
+    return st;
+}
+
+extern "C" rl_status rl_cascade_relocalise(rl_cascade *c, const float *depth, const uint8_t *rgb,
+                                           const rl_intrinsics *K, uint64_t seed, rl_mem mem,
+                                           void *stream, rl_result *out) {
+    return rl_cascade_relocalise_batch(c, 1, depth, rgb, K, &seed, mem, stream, out);
+}
+
+// ---------------------------------------------------------------------------
+// Kernel profiler (tracing): CUDA events per launch on the caller's stream.
+// ---------------------------------------------------------------------------
+namespace rl {
+static void prof_free(rl_reloc *r) {
+    prof_resolve(r);
+    for (cudaEvent_t e : r->prof.pool) cudaEventDestroy(e);
+    r->prof.pool.clear();
+}
+}  // namespace rl
+
+static const char *kKernelNames[K_COUNT] = {"leaves",  "hypgen", "compact", "sample_batch", "energy",
+                                             "select", "lm",     "raycast_score", "finalize"};
+
+extern "C" const char *rl_kernel_name(int32_t kid) {
+    return (kid >= 0 && kid < K_COUNT) ? kKernelNames[kid] : "";
+}
+
+extern "C" rl_status rl_reloc_profile(rl_reloc *r, int32_t enable) {
+    if (!r) return fail(RL_ERR_INVALID_ARG, "null relocaliser");
+    RL_CK(cudaSetDevice(r->forest->ctx->device));
+    RL_CK(cudaDeviceSynchronize());
+    prof_resolve(r);
+    for (int k = 0; k < K_COUNT; ++k) {
+        r->prof.ms[k] = 0.0;
+        r->prof.launches[k] = 0;
+    }
+    if (!r->prof.work) RL_TRY(ralloc(r, W_COUNT, &r->prof.work));
+    RL_CK(cudaMemset(r->prof.work, 0, sizeof(unsigned long long) * W_COUNT));
+    r->prof.on = enable != 0;
+    return RL_OK;
+}
+
+extern "C" rl_status rl_reloc_profile_read(rl_reloc *r, double *ms, int64_t *launches, uint64_t *work) {
+    if (!r) return fail(RL_ERR_INVALID_ARG, "null relocaliser");
+    RL_CK(cudaSetDevice(r->forest->ctx->device));
+    RL_CK(cudaDeviceSynchronize());
+    prof_resolve(r);
+    for (int k = 0; k < K_COUNT; ++k) {
+        if (ms) ms[k] = r->prof.ms[k];
+        if (launches) launches[k] = r->prof.launches[k];
+    }
+    if (work) {
+        if (r->prof.work)
+            RL_CK(cudaMemcpy(work, r->prof.work, sizeof(unsigned long long) * W_COUNT, cudaMemcpyDeviceToHost));
+        else
+            for (int k = 0; k < W_COUNT; ++k) work[k] = 0;
+    }
+    return RL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Standalone ranking score (Eq. 6-7) of given poses.
+// ---------------------------------------------------------------------------
+extern "C" rl_status rl_score_poses(rl_scene *sc, const float *depth, const rl_intrinsics *K,
+                                    const double *poses, int32_t n, rl_mem mem, void *stream,
+                                    float *scores, float *valid_frac) {
+    if (!sc || !depth || !K || !poses || !scores) return fail(RL_ERR_INVALID_ARG, "null argument");
+    if (n < 1 || n > 65535) return fail(RL_ERR_INVALID_ARG, "n must be 1..65535");
+    if (K->width < 1 || K->height < 1 || K->width > 8192 || K->height > 8192 || !(K->fx > 0) || !(K->fy > 0))
+        return fail(RL_ERR_INVALID_ARG, "bad intrinsics");
+    if (mem != RL_HOST && mem != RL_DEVICE) return fail(RL_ERR_INVALID_ARG, "bad rl_mem");
+    rl_ctx *ctx = sc->ctx;
+    RL_CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int npx = K->width * K->height;
+    const int tiles = (npx + 255) / 256;
+    Frame *fr = nullptr;
+    double *pd = nullptr, *psum = nullptr;
+    int32_t *pcnt = nullptr;
+    float *sd = nullptr, *vd = nullptr, *dd = nullptr;
+    rl_status st = alloc_n(ctx, 1, &fr);
+    if (st == RL_OK) st = alloc_n(ctx, (uint64_t)n * 12, &pd);
+    if (st == RL_OK) st = alloc_n(ctx, (uint64_t)n * tiles, &psum);
+    if (st == RL_OK) st = alloc_n(ctx, (uint64_t)n * tiles * 2, &pcnt);
+    if (st == RL_OK) st = alloc_n(ctx, (uint64_t)n * 2, &sd);
+    if (st == RL_OK && mem == RL_HOST) st = alloc_n(ctx, (uint64_t)npx, &dd);
+    std::vector<double> p12((size_t)n * 12);
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < 12; ++k) p12[(size_t)i * 12 + k] = poses[(size_t)i * 16 + k];
+    Frame h{};
+    h.depth = mem == RL_HOST ? dd : depth;
+    h.rgb = nullptr;
+    h.fx = K->fx; h.fy = K->fy; h.cx = K->cx; h.cy = K->cy;
+    h.W = K->width; h.H = K->height;
+    std::vector<float> hs((size_t)n * 2);
+    if (st == RL_OK && mem == RL_HOST &&
+        cudaMemcpyAsync(dd, depth, sizeof(float) * npx, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        st = fail(RL_ERR_CUDA, "depth copy failed");
+    if (st == RL_OK && cudaMemcpyAsync(fr, &h, sizeof(Frame), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        st = fail(RL_ERR_CUDA, "frame copy failed");
+    if (st == RL_OK && cudaMemcpyAsync(pd, p12.data(), p12.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        st = fail(RL_ERR_CUDA, "pose copy failed");
+    if (st == RL_OK) {
+        vd = sd + n;
+        RaycastArgs ra{};
+        ra.frames = fr;
+        ra.poses = pd;
+        ra.n_poses = nullptr;
+        ra.pose_cap = n;
+        for (int a = 0; a < 3; ++a) {
+            ra.lo[a] = (float)sc->lo[a];
+            ra.hi[a] = (float)sc->hi[a];
+            ra.lo64[a] = sc->lo[a];
+            ra.hi64[a] = sc->hi[a];
+        }
+        ra.part_sum = psum;
+        ra.part_cnt = pcnt;
+        ra.n_tiles = tiles;
+        st = launch_score_poses(ra, n, npx, sd, vd, s);
+    }
+    if (st == RL_OK && cudaMemcpyAsync(hs.data(), sd, sizeof(float) * 2 * n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        st = fail(RL_ERR_CUDA, "score copy failed");
+    if (st == RL_OK && cudaStreamSynchronize(s) != cudaSuccess) st = fail(RL_ERR_CUDA, "scoring failed");
+    if (st == RL_OK)
+        for (int i = 0; i < n; ++i) {
+            scores[i] = hs[i];
+            if (valid_frac) valid_frac[i] = hs[n + i];
+        }
+    void *ptrs[] = {fr, pd, psum, pcnt, sd, dd};
+    for (void *p : ptrs) arena_free(ctx, p);
+    return st;
+}

@@ -1,0 +1,719 @@
+// Scoring kernels of the relocaliser: the energy of Eq. 5 on growing pixel
+// sets, cull / halving selection, Levenberg-Marquardt refinement in se(3)
+// (Sec. 3.2.3) and model-based ranking by depth raycast (Eq. 6-8).
+//
+// FP32 arithmetic with fused multiply-adds; FP64 only for poses, the 6x6
+// normal-equation solve and the SE(3) update.  Every reduction has a fixed
+// shape, so results do not depend on how many frames share a launch.
+#include <math.h>
+
+#include "internal.h"
+#include "relocgb_dev.cuh"
+#include "kernels.h"
+
+namespace rl {
+
+__device__ __forceinline__ bool round_active(int n, const RParams &p) {
+    return n > p.k_out || (p.halve_to_one && n > 1);
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 5 partial energies.  Block = HT hypotheses of one frame (one per
+// thread) x one chunk of the pixel set; the chunk's pixels and their modes
+// (decoded to FP32) are staged in shared memory and read by broadcast.
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(128) k_energy(EnergyArgs a) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    float4 *s_xc = (float4 *)smem;                         // [chunk]
+    float4 *s_m0 = s_xc + a.chunk;                         // [chunk*maxm] mu.xyz, U00
+    float4 *s_m1 = s_m0 + a.chunk * a.maxm;                // [chunk*maxm] U01 U02 U11 U12
+    float *s_m2 = (float *)(s_m1 + a.chunk * a.maxm);      // [chunk*maxm] U22
+    int *s_cnt = (int *)(s_m2 + a.chunk * a.maxm);         // [chunk]
+
+    const int b = blockIdx.z;
+    const int n = a.count[b];
+    if (a.round_gate && !round_active(n, a.p)) return;
+    const int h0 = blockIdx.x * blockDim.x;
+    if (h0 >= n) return;
+    const int p0 = blockIdx.y * a.chunk;
+    if (p0 >= a.n_pix) return;
+    const int np = min(a.chunk, a.n_pix - p0);
+    const uint16_t *lv = a.leaves + (size_t)b * a.p.n_trees * a.hw_max;
+    const int32_t *pix = a.pix + (size_t)b * a.max_pix + p0;
+    const float4 *xc = a.xc + (size_t)b * a.max_pix + p0;
+
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        const int q = pix[i];
+        s_xc[i] = xc[i];
+        s_cnt[i] = q < 0 ? 0 : mode_count(a.mv, lv, a.hw_max, q, a.p.n_trees, a.p.k_top);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < np * a.maxm; e += blockDim.x) {
+        const int i = e / a.maxm, m = e % a.maxm;
+        if (m >= s_cnt[i]) continue;
+        uint32_t L;
+        int rank;
+        mode_at(a.mv, lv, a.hw_max, pix[i], a.p.n_trees, a.p.k_top, m, &L, &rank);
+        const float3 mp = mode_pos(a.mv, L, rank);
+        const size_t me = (size_t)L * a.mv.m_max + rank;
+        if (a.p.use_cov) {
+            const float4 u0 = a.mv.mU[2 * me], u1 = a.mv.mU[2 * me + 1];
+            s_m0[e] = make_float4(mp.x, mp.y, mp.z, u0.x);
+            s_m1[e] = make_float4(u0.y, u0.z, u0.w, u1.x);
+            s_m2[e] = u1.y;
+        } else {
+            s_m0[e] = make_float4(mp.x, mp.y, mp.z, 1.f);
+        }
+    }
+    __syncthreads();
+    if (a.work && threadIdx.x == 0) {
+        unsigned long long pairs = 0, modes = 0;
+        for (int i = 0; i < np; ++i)
+            if (s_cnt[i] > 0) {
+                ++pairs;
+                modes += (unsigned long long)s_cnt[i];
+            }
+        const unsigned long long nh = (unsigned long long)min((int)blockDim.x, n - h0);
+        atomicAdd(&a.work[W_E_PAIRS], nh * pairs);
+        atomicAdd(&a.work[W_E_MODES], nh * modes);
+    }
+    const int h = h0 + threadIdx.x;
+    if (h >= n) return;
+    const int id = a.idx ? a.idx[(size_t)b * a.idx_stride + h] : h;
+    const double *P = a.pose + ((size_t)b * a.pose_stride + id) * 12;
+    const float r00 = (float)P[0], r01 = (float)P[1], r02 = (float)P[2], t0 = (float)P[3];
+    const float r10 = (float)P[4], r11 = (float)P[5], r12 = (float)P[6], t1 = (float)P[7];
+    const float r20 = (float)P[8], r21 = (float)P[9], r22 = (float)P[10], t2 = (float)P[11];
+    float acc = 0.f;
+    for (int i = 0; i < np; ++i) {
+        const int cnt = s_cnt[i];
+        if (cnt == 0) continue;
+        const float4 x = s_xc[i];
+        const float y0 = fmaf(r00, x.x, fmaf(r01, x.y, fmaf(r02, x.z, t0)));
+        const float y1 = fmaf(r10, x.x, fmaf(r11, x.y, fmaf(r12, x.z, t1)));
+        const float y2 = fmaf(r20, x.x, fmaf(r21, x.y, fmaf(r22, x.z, t2)));
+        const int base = i * a.maxm;
+        float best = INFINITY;
+        if (a.p.use_cov) {
+            for (int m = 0; m < cnt; ++m) {
+                const float4 m0 = s_m0[base + m], m1 = s_m1[base + m];
+                const float u22 = s_m2[base + m];
+                const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+                const float w0 = fmaf(m0.w, v0, fmaf(m1.x, v1, m1.y * v2));
+                const float w1 = fmaf(m1.z, v1, m1.w * v2);
+                const float w2 = u22 * v2;
+                best = fminf(best, fmaf(w0, w0, fmaf(w1, w1, w2 * w2)));
+            }
+        } else {
+            for (int m = 0; m < cnt; ++m) {
+                const float4 m0 = s_m0[base + m];
+                const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+                best = fminf(best, fmaf(v0, v0, fmaf(v1, v1, v2 * v2)));
+            }
+        }
+        acc += sqrtf(best);
+    }
+    a.part[((size_t)b * a.part_h + h) * a.n_chunks + blockIdx.y] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// Cull (phase 0) and halving rounds (phase 1): sum the partial energies in
+// chunk order, rank by (E, slot), keep the best min(n, N_cull) or ceil(n/2).
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(1024) k_select(SelectArgs a) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    float *sE = (float *)smem;                       // [n]
+    int *sS = (int *)(sE + a.p.n_hyp);               // [n]
+    double *sP = (double *)(sS + a.p.n_hyp);         // [n_cull][12]
+    float *sKE = (float *)(sP + a.p.n_cull * 12);    // [n_cull]
+    int *sKS = (int *)(sKE + a.p.n_cull);            // [n_cull]
+    const int b = blockIdx.x, tid = threadIdx.x;
+    const int n = a.count[b];
+    if (a.phase == 1 && !round_active(n, a.p)) return;
+    const int N = a.p.n_hyp, NC = a.p.n_cull;
+    for (int i = tid; i < n; i += blockDim.x) {
+        const float *pp = a.part + ((size_t)b * a.part_h + i) * a.n_chunks;
+        float e = 0.f;
+        for (int c = 0; c < a.n_chunks_used; ++c) e += pp[c];
+        if (isnan(e)) e = INFINITY;
+        sE[i] = e;
+        sS[i] = a.phase == 0 ? a.hyp_list[(size_t)b * N + i] : a.q.cur_slot[(size_t)b * NC + i];
+    }
+    __syncthreads();
+    const int keep = a.phase == 0 ? min(n, NC) : (n + 1) / 2;
+    for (int i = tid; i < n; i += blockDim.x) {
+        const float e = sE[i];
+        const int s = sS[i];
+        int rank = 0;
+        for (int j = 0; j < n; ++j) {
+            const float f = sE[j];
+            rank += (f < e) || (f == e && sS[j] < s);
+        }
+        if (rank < keep) {
+            const double *src = a.phase == 0 ? a.hyp_pose + ((size_t)b * N + s) * 12
+                                             : a.q.cur_pose + ((size_t)b * NC + i) * 12;
+            for (int k = 0; k < 12; ++k) sP[rank * 12 + k] = src[k];
+            sKE[rank] = e;
+            sKS[rank] = s;
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < keep; i += blockDim.x) {
+        for (int k = 0; k < 12; ++k) a.q.cur_pose[((size_t)b * NC + i) * 12 + k] = sP[i * 12 + k];
+        a.q.cur_energy[(size_t)b * NC + i] = sKE[i];
+        a.q.cur_slot[(size_t)b * NC + i] = sKS[i];
+    }
+    if (a.phase == 0)
+        for (int i = tid; i < keep; i += blockDim.x) {
+            a.q.cull_slot[(size_t)b * NC + i] = sKS[i];
+            a.q.cull_energy[(size_t)b * NC + i] = sKE[i];
+        }
+    const bool take = a.q.n_chosen[b] < 0 && keep <= a.p.k_out;
+    if (take)
+        for (int i = tid; i < keep; i += blockDim.x) {
+            for (int k = 0; k < 12; ++k)
+                a.q.chosen_pose[((size_t)b * 16 + i) * 12 + k] = sP[i * 12 + k];
+            a.q.chosen_energy[(size_t)b * 16 + i] = sKE[i];
+            a.q.chosen_slot[(size_t)b * 16 + i] = sKS[i];
+        }
+    if (a.phase == 1 && a.round < 16)
+        for (int i = tid; i < keep; i += blockDim.x) {
+            const size_t o = ((size_t)b * 16 + a.round) * NC + i;
+            a.q.round_slot[o] = sKS[i];
+            a.q.round_energy[o] = sKE[i];
+            for (int k = 0; k < 12; ++k) a.q.round_pose[o * 12 + k] = sP[i * 12 + k];
+        }
+    __syncthreads();
+    if (tid == 0) {
+        a.q.n_cur[b] = keep;
+        a.q.n_pix[b] = a.n_pix;
+        if (take) {
+            a.q.n_chosen[b] = keep;
+            a.q.chosen_npix[b] = a.n_pix;
+        }
+        if (a.phase == 1) {
+            if (a.round < 16) a.q.round_count[(size_t)b * 16 + a.round] = keep;
+            a.q.n_rounds[b] = a.round + 1;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Levenberg-Marquardt in se(3): one warp per hypothesis; lanes stride the
+// pixel set, accumulate J^T J (21), J^T r (6) and the cost in FP32, reduce
+// by an xor butterfly (every lane ends with the same bits); lane 0 solves
+// the damped normal equations in FP64 and applies exp(xi^) on the left.
+// ---------------------------------------------------------------------------
+__device__ bool chol_solve6(const double A[36], const double b[6], double x[6]) {
+    double L[36];
+    for (int i = 0; i < 36; ++i) L[i] = 0.0;
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = A[6 * i + j];
+            for (int k = 0; k < j; ++k) s -= L[6 * i + k] * L[6 * j + k];
+            if (i == j) {
+                if (!(s > 0.0)) return false;
+                L[6 * i + i] = sqrt(s);
+            } else {
+                L[6 * i + j] = s / L[6 * j + j];
+            }
+        }
+    double y[6];
+    for (int i = 0; i < 6; ++i) {
+        double s = b[i];
+        for (int k = 0; k < i; ++k) s -= L[6 * i + k] * y[k];
+        y[i] = s / L[6 * i + i];
+    }
+    for (int i = 5; i >= 0; --i) {
+        double s = y[i];
+        for (int k = i + 1; k < 6; ++k) s -= L[6 * k + i] * x[k];
+        x[i] = s / L[6 * i + i];
+    }
+    return true;
+}
+
+__device__ void se3_left(const double xi[6], double H[12]) {
+    const double w0 = xi[3], w1 = xi[4], w2 = xi[5];
+    const double th2 = w0 * w0 + w1 * w1 + w2 * w2, th = sqrt(th2);
+    double A, B, C;
+    if (th < 1e-8) {
+        A = 1.0 - th2 / 6.0;
+        B = 0.5 - th2 / 24.0;
+        C = 1.0 / 6.0 - th2 / 120.0;
+    } else {
+        double s, c;
+        sincos(th, &s, &c);
+        A = s / th;
+        B = (1.0 - c) / th2;
+        C = (th - s) / (th2 * th);
+    }
+    const double K[9] = {0, -w2, w1, w2, 0, -w0, -w1, w0, 0};
+    double K2[9], Rd[9], Vd[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+            K2[3 * r + c] = K[3 * r] * K[c] + K[3 * r + 1] * K[3 + c] + K[3 * r + 2] * K[6 + c];
+    for (int i = 0; i < 9; ++i) {
+        const double I = (i % 4 == 0) ? 1.0 : 0.0;
+        Rd[i] = I + A * K[i] + B * K2[i];
+        Vd[i] = I + B * K[i] + C * K2[i];
+    }
+    double N[12];
+    for (int r = 0; r < 3; ++r) {
+        const double td = Vd[3 * r] * xi[0] + Vd[3 * r + 1] * xi[1] + Vd[3 * r + 2] * xi[2];
+        for (int c = 0; c < 3; ++c)
+            N[4 * r + c] = Rd[3 * r] * H[c] + Rd[3 * r + 1] * H[4 + c] + Rd[3 * r + 2] * H[8 + c];
+        N[4 * r + 3] = Rd[3 * r] * H[3] + Rd[3 * r + 1] * H[7] + Rd[3 * r + 2] * H[11] + td;
+    }
+    for (int i = 0; i < 12; ++i) H[i] = N[i];
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+
+__global__ void __launch_bounds__(128) k_lm(LmArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int h = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int b = blockIdx.y;
+    const int n = a.q.n_cur[b];
+    if (!round_active(n, a.p) || h >= n) return;
+    const int NC = a.p.n_cull;
+    double *Pg = a.q.cur_pose + ((size_t)b * NC + h) * 12;
+    double H[12];
+    for (int k = 0; k < 12; ++k) H[k] = Pg[k];
+    const uint16_t *lv = a.leaves + (size_t)b * a.p.n_trees * a.hw_max;
+    const int32_t *pix = a.q.pix + (size_t)b * a.p.max_pix;
+    const float4 *xcs = a.q.xc + (size_t)b * a.p.max_pix;
+    int32_t *corr = a.q.corr + ((size_t)b * NC + h) * a.p.max_pix;
+    const float thr2 = (float)(a.p.lm_inlier_thresh * a.p.lm_inlier_thresh);
+    const bool cov = a.p.use_cov;
+    double lambda = a.p.lm_lambda0;
+    unsigned w_pairs = 0, w_modes = 0, w_in = 0, w_trial = 0;
+    for (int it = 0; it < a.p.lm_max_iter; ++it) {
+        const float r00 = (float)H[0], r01 = (float)H[1], r02 = (float)H[2], t0 = (float)H[3];
+        const float r10 = (float)H[4], r11 = (float)H[5], r12 = (float)H[6], t1 = (float)H[7];
+        const float r20 = (float)H[8], r21 = (float)H[9], r22 = (float)H[10], t2 = (float)H[11];
+        float acc[28];
+#pragma unroll
+        for (int k = 0; k < 28; ++k) acc[k] = 0.f;
+        int nin = 0;
+        for (int i = lane; i < a.n_pix; i += 32) {
+            const int q = pix[i];
+            int best_e = -1;
+            if (q >= 0) {
+                const float4 x = xcs[i];
+                const float y0 = fmaf(r00, x.x, fmaf(r01, x.y, fmaf(r02, x.z, t0)));
+                const float y1 = fmaf(r10, x.x, fmaf(r11, x.y, fmaf(r12, x.z, t1)));
+                const float y2 = fmaf(r20, x.x, fmaf(r21, x.y, fmaf(r22, x.z, t2)));
+                float best = INFINITY;
+                float bu[6] = {1, 0, 0, 1, 0, 1};
+                float bm0 = 0, bm1 = 0, bm2 = 0;
+                ++w_pairs;
+                for (int t = 0; t < a.p.n_trees; ++t) {
+                    const uint32_t L = (uint32_t)(t * a.mv.leaves_per_tree + lv[(size_t)t * a.hw_max + q]);
+                    int nm = a.mv.nmodes[L];
+                    nm = nm < a.p.k_top ? nm : a.p.k_top;
+                    w_modes += nm;
+                    for (int m = 0; m < nm; ++m) {
+                        const float3 mp = mode_pos(a.mv, L, m);
+                        const size_t me = (size_t)L * a.mv.m_max + m;
+                        const float v0 = y0 - mp.x, v1 = y1 - mp.y, v2 = y2 - mp.z;
+                        float d2;
+                        float4 u0 = make_float4(1, 0, 0, 1), u1 = make_float4(0, 1, 0, 0);
+                        if (cov) {
+                            u0 = a.mv.mU[2 * me];
+                            u1 = a.mv.mU[2 * me + 1];
+                            const float w0 = fmaf(u0.x, v0, fmaf(u0.y, v1, u0.z * v2));
+                            const float w1 = fmaf(u0.w, v1, u1.x * v2);
+                            const float w2 = u1.y * v2;
+                            d2 = fmaf(w0, w0, fmaf(w1, w1, w2 * w2));
+                        } else {
+                            d2 = fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
+                        }
+                        if (d2 < best) {
+                            best = d2;
+                            best_e = (int)me;
+                            bm0 = mp.x; bm1 = mp.y; bm2 = mp.z;
+                            bu[0] = u0.x; bu[1] = u0.y; bu[2] = u0.z;
+                            bu[3] = u0.w; bu[4] = u1.x; bu[5] = u1.y;
+                        }
+                    }
+                }
+                if (best_e >= 0) {
+                    const float v0 = y0 - bm0, v1 = y1 - bm1, v2 = y2 - bm2;
+                    if (fmaf(v0, v0, fmaf(v1, v1, v2 * v2)) > thr2) {
+                        best_e = -1;
+                    } else {
+                        ++nin;
+                        ++w_in;
+                        // rows of J = U [I | -[y]x] and residual r = U v
+                        const float U00 = bu[0], U01 = bu[1], U02 = bu[2];
+                        const float U11 = bu[3], U12 = bu[4], U22 = bu[5];
+                        const float j0[6] = {U00, U01, U02, U02 * y1 - U01 * y2,
+                                             U00 * y2 - U02 * y0, U01 * y0 - U00 * y1};
+                        const float j1[6] = {0.f, U11, U12, U12 * y1 - U11 * y2, -U12 * y0, U11 * y0};
+                        const float j2[6] = {0.f, 0.f, U22, U22 * y1, -U22 * y0, 0.f};
+                        const float rr0 = fmaf(U00, v0, fmaf(U01, v1, U02 * v2));
+                        const float rr1 = fmaf(U11, v1, U12 * v2);
+                        const float rr2 = U22 * v2;
+                        int k = 0;
+#pragma unroll
+                        for (int r = 0; r < 6; ++r)
+#pragma unroll
+                            for (int c = r; c < 6; ++c, ++k)
+                                acc[k] = fmaf(j0[r], j0[c], fmaf(j1[r], j1[c], fmaf(j2[r], j2[c], acc[k])));
+#pragma unroll
+                        for (int r = 0; r < 6; ++r)
+                            acc[21 + r] = fmaf(j0[r], rr0, fmaf(j1[r], rr1, fmaf(j2[r], rr2, acc[21 + r])));
+                        acc[27] = fmaf(rr0, rr0, fmaf(rr1, rr1, fmaf(rr2, rr2, acc[27])));
+                    }
+                }
+            }
+            corr[i] = best_e;
+        }
+#pragma unroll
+        for (int k = 0; k < 28; ++k) acc[k] = warp_sum(acc[k]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nin += __shfl_xor_sync(0xffffffffu, nin, o);
+        if (nin < 3) break;
+        // lane 0: damped normal equations (FP64), trial pose
+        int status = 0;  // 0 continue, 1 stop
+        double Hn[12];
+        if (lane == 0) {
+            double A[36], rhs[6], step[6];
+            int k = 0;
+            for (int r = 0; r < 6; ++r)
+                for (int c = r; c < 6; ++c, ++k) A[6 * r + c] = A[6 * c + r] = (double)acc[k];
+            for (int r = 0; r < 6; ++r) {
+                A[6 * r + r] += lambda * (double)acc[r * 6 - r * (r - 1) / 2];
+                rhs[r] = -(double)acc[21 + r];
+            }
+            if (!chol_solve6(A, rhs, step)) {
+                status = 1;
+            } else {
+                double sn = 0.0;
+                for (int r = 0; r < 6; ++r) sn += step[r] * step[r];
+                if (sqrt(sn) < a.p.lm_stop) status = 1;
+            }
+            for (int i = 0; i < 12; ++i) Hn[i] = H[i];
+            if (!status) se3_left(step, Hn);
+        }
+        status = __shfl_sync(0xffffffffu, status, 0);
+        if (status) break;
+        for (int i = 0; i < 12; ++i) Hn[i] = __shfl_sync(0xffffffffu, Hn[i], 0);
+        __syncwarp();
+        // trial cost with the same correspondences
+        const float s00 = (float)Hn[0], s01 = (float)Hn[1], s02 = (float)Hn[2], u0t = (float)Hn[3];
+        const float s10 = (float)Hn[4], s11 = (float)Hn[5], s12 = (float)Hn[6], u1t = (float)Hn[7];
+        const float s20 = (float)Hn[8], s21 = (float)Hn[9], s22 = (float)Hn[10], u2t = (float)Hn[11];
+        float trial = 0.f;
+        for (int i = lane; i < a.n_pix; i += 32) {
+            const int e = corr[i];
+            if (e < 0) continue;
+            ++w_trial;
+            const float4 x = xcs[i];
+            const float y0 = fmaf(s00, x.x, fmaf(s01, x.y, fmaf(s02, x.z, u0t)));
+            const float y1 = fmaf(s10, x.x, fmaf(s11, x.y, fmaf(s12, x.z, u1t)));
+            const float y2 = fmaf(s20, x.x, fmaf(s21, x.y, fmaf(s22, x.z, u2t)));
+            const uint32_t L = (uint32_t)e / (uint32_t)a.mv.m_max;
+            const float3 mp = mode_pos(a.mv, L, e - (int)L * a.mv.m_max);
+            const float v0 = y0 - mp.x, v1 = y1 - mp.y, v2 = y2 - mp.z;
+            if (cov) {
+                const float4 w0 = a.mv.mU[2 * (size_t)e], w1 = a.mv.mU[2 * (size_t)e + 1];
+                const float r0 = fmaf(w0.x, v0, fmaf(w0.y, v1, w0.z * v2));
+                const float r1 = fmaf(w0.w, v1, w1.x * v2);
+                const float r2 = w1.y * v2;
+                trial = fmaf(r0, r0, fmaf(r1, r1, fmaf(r2, r2, trial)));
+            } else {
+                trial = fmaf(v0, v0, fmaf(v1, v1, fmaf(v2, v2, trial)));
+            }
+        }
+        trial = warp_sum(trial);
+        if (trial < acc[27]) {
+            for (int i = 0; i < 12; ++i) H[i] = Hn[i];
+            lambda /= 10.0;
+        } else {
+            lambda *= 10.0;
+        }
+    }
+    if (lane == 0)
+        for (int k = 0; k < 12; ++k) Pg[k] = H[k];
+    if (a.work) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            w_pairs += __shfl_xor_sync(0xffffffffu, w_pairs, o);
+            w_modes += __shfl_xor_sync(0xffffffffu, w_modes, o);
+            w_in += __shfl_xor_sync(0xffffffffu, w_in, o);
+            w_trial += __shfl_xor_sync(0xffffffffu, w_trial, o);
+        }
+        if (lane == 0) {
+            atomicAdd(&a.work[W_LM_PAIRS], (unsigned long long)w_pairs);
+            atomicAdd(&a.work[W_LM_MODES], (unsigned long long)w_modes);
+            atomicAdd(&a.work[W_LM_INLIERS], (unsigned long long)w_in);
+            atomicAdd(&a.work[W_LM_TRIAL], (unsigned long long)w_trial);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 6-7: raycast of the box model at each chosen pose, masked mean
+// absolute depth difference, valid fraction.  Block = 256 pixels of one
+// (frame, chosen pose); partial sums in a fixed order.
+// ---------------------------------------------------------------------------
+
+// z-depth of the first box face hit by the ray of pixel (u, v) (exit point
+// from inside the box, entry point from outside), in FP64.
+__device__ bool ray_depth64(const double *P, int u, int v, float fx, float fy, float cx, float cy,
+                            const double lo[3], const double hi[3], double *depth) {
+    const double dc0 = ((double)u - (double)cx) / (double)fx;
+    const double dc1 = ((double)v - (double)cy) / (double)fy;
+    double tn = -INFINITY, tf = INFINITY;
+    for (int ax = 0; ax < 3; ++ax) {
+        const double d = P[4 * ax] * dc0 + P[4 * ax + 1] * dc1 + P[4 * ax + 2];
+        const double o = P[4 * ax + 3];
+        if (d == 0.0) {
+            if (o < lo[ax] || o > hi[ax]) return false;
+            continue;
+        }
+        const double t1 = (lo[ax] - o) / d, t2 = (hi[ax] - o) / d;
+        tn = fmax(tn, fmin(t1, t2));
+        tf = fmin(tf, fmax(t1, t2));
+    }
+    if (tn > tf) return false;
+    if (tn > 0.0) { *depth = tn; return true; }
+    if (tf > 0.0) { *depth = tf; return true; }
+    return false;
+}
+
+// The hit test runs in FP32; a ray whose decision lies within a relative
+// margin of 1e-4 of changing (near-parallel faces, grazing edges, a face
+// through the camera) is re-evaluated in FP64, so the valid mask of Eq. 7
+// is the FP64 one.
+__global__ void __launch_bounds__(256) k_raycast_score(RaycastArgs a) {
+    __shared__ float s_sum[8];
+    __shared__ int s_syn[8], s_both[8];
+    const int b = blockIdx.z, c = blockIdx.y;
+    if (c >= a.n_poses_of(b)) return;
+    const Frame fr = a.frames[b];
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const double *P = a.pose_of(b, c);
+    float sum = 0.f;
+    int syn = 0, both = 0;
+    if (p < fr.W * fr.H) {
+        const int u = p % fr.W, v = p / fr.W;
+        const float dc0 = ((float)u - fr.cx) / fr.fx, dc1 = ((float)v - fr.cy) / fr.fy;
+        float d[3], o[3];
+        for (int r = 0; r < 3; ++r) {
+            d[r] = fmaf((float)P[4 * r], dc0, fmaf((float)P[4 * r + 1], dc1, (float)P[4 * r + 2]));
+            o[r] = (float)P[4 * r + 3];
+        }
+        const float dn = fabsf(d[0]) + fabsf(d[1]) + fabsf(d[2]);
+        float tn = -INFINITY, tf = INFINITY;
+        bool ok = true, unsure = false;
+        for (int ax = 0; ax < 3; ++ax) {
+            if (fabsf(d[ax]) <= 1e-5f * dn) {
+                unsure = true;
+                continue;
+            }
+            const float inv = 1.0f / d[ax];
+            const float ta = (a.lo[ax] - o[ax]) * inv, tb = (a.hi[ax] - o[ax]) * inv;
+            tn = fmaxf(tn, fminf(ta, tb));
+            tf = fminf(tf, fmaxf(ta, tb));
+        }
+        float depth = 0.f;
+        if (!unsure) {
+            const float scale = fmaxf(fabsf(tn), fabsf(tf));
+            if (fabsf(tf - tn) <= 1e-4f * scale || fabsf(tn) <= 1e-4f * scale ||
+                fabsf(tf) <= 1e-4f * scale)
+                unsure = true;
+        }
+        if (unsure) {
+            double dd;
+            ok = ray_depth64(P, u, v, fr.fx, fr.fy, fr.cx, fr.cy, a.lo64, a.hi64, &dd);
+            depth = (float)dd;
+        } else if (tn <= tf && tn > 0.f) {
+            depth = tn;
+        } else if (tn <= tf && tf > 0.f) {
+            depth = tf;
+        } else {
+            ok = false;
+        }
+        if (ok) {
+            syn = 1;
+            const float dl = fr.depth[p];
+            if (dl > 0.f) {
+                both = 1;
+                sum = fabsf(dl - depth);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sum += __shfl_down_sync(0xffffffffu, sum, o);
+        syn += __shfl_down_sync(0xffffffffu, syn, o);
+        both += __shfl_down_sync(0xffffffffu, both, o);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        s_sum[w] = sum;
+        s_syn[w] = syn;
+        s_both[w] = both;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float ts = 0.f;
+        int tsyn = 0, tb = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            ts += s_sum[k];
+            tsyn += s_syn[k];
+            tb += s_both[k];
+        }
+        const size_t o = ((size_t)b * a.pose_cap + c) * a.n_tiles + blockIdx.x;
+        a.part_sum[o] = (double)ts;
+        a.part_cnt[2 * o] = tsyn;
+        a.part_cnt[2 * o + 1] = tb;
+        if (a.work)
+            atomicAdd(&a.work[W_RAYS],
+                      (unsigned long long)min((int)blockDim.x, fr.W * fr.H - (int)(blockIdx.x * blockDim.x)));
+    }
+}
+
+// Eq. 7 from the tile partials of one (frame, pose): FP64 sums in tile order.
+__device__ float score_from_tiles(const double *part_sum, const int32_t *part_cnt, size_t base,
+                                  int n_tiles, double npx, float *valid_frac) {
+    double sum = 0.0;
+    long syn = 0, both = 0;
+    for (int t = 0; t < n_tiles; ++t) {
+        sum += part_sum[base + t];
+        syn += part_cnt[2 * (base + t)];
+        both += part_cnt[2 * (base + t) + 1];
+    }
+    const double frac = (double)syn / npx;
+    if (valid_frac) *valid_frac = (float)frac;
+    return (frac >= 0.1 && both > 0) ? (float)(sum / (double)both) : INFINITY;
+}
+
+// Eq. 7-8 per frame, then the frame's result record.
+__global__ void k_finalize(QueryState q, RParams p, int n_tiles, int ranked) {
+    const int b = blockIdx.x;
+    if (threadIdx.x != 0) return;
+    DevResult *out = (DevResult *)q.result_blob + b;
+    const Frame fr = q.frames[b];
+    out->n_hypotheses = q.n_hyp[b];
+    out->n_chosen = q.n_hyp[b] > 0 ? q.n_chosen[b] : 0;
+    out->n_pixels = q.n_pix[b];
+    out->score = INFINITY;
+    out->best = -1;
+    if (q.n_hyp[b] == 0) {
+        out->status = RL_NO_POSE;
+        for (int k = 0; k < 12; ++k) out->pose[k] = (k % 5 == 0) ? 1.0 : 0.0;
+        out->energy = INFINITY;
+        out->energy_per_pixel = INFINITY;
+        return;
+    }
+    out->status = RL_POSE_FOUND;
+    const int NC = p.n_cull;
+    int best = -1;
+    float bs = INFINITY;
+    if (ranked) {
+        const double npx = (double)fr.W * (double)fr.H;
+        for (int c = 0; c < q.n_chosen[b]; ++c) {
+            const float s = score_from_tiles(q.score_part, q.score_cnt, ((size_t)b * 16 + c) * n_tiles,
+                                             n_tiles, npx, nullptr);
+            q.chosen_score[(size_t)b * 16 + c] = s;
+            if (s < bs) {
+                bs = s;
+                best = c;
+            }
+        }
+        if (best < 0) best = 0;
+        out->score = bs;
+        out->best = best;
+        for (int k = 0; k < 12; ++k) out->pose[k] = q.chosen_pose[((size_t)b * 16 + best) * 12 + k];
+        out->energy = q.chosen_energy[(size_t)b * 16 + best];
+        out->energy_per_pixel = out->energy / (float)q.chosen_npix[b];
+    } else {
+        for (int c = 0; c < q.n_chosen[b]; ++c) q.chosen_score[(size_t)b * 16 + c] = INFINITY;
+        for (int k = 0; k < 12; ++k) out->pose[k] = q.cur_pose[((size_t)b * NC) * 12 + k];
+        out->energy = q.cur_energy[(size_t)b * NC];
+        out->energy_per_pixel = out->energy / (float)q.n_pix[b];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+rl_status launch_energy(const EnergyArgs &a0, int max_count, int n, cudaStream_t s) {
+    EnergyArgs a = a0;
+    const int ht = max_count <= 32 ? 32 : (max_count <= 64 ? 64 : 128);
+    const size_t sm = (size_t)a.chunk * sizeof(float4) + (size_t)a.chunk * a.maxm * (2 * sizeof(float4) + sizeof(float)) +
+                      (size_t)a.chunk * sizeof(int);
+    dim3 grid((max_count + ht - 1) / ht, (a.n_pix + a.chunk - 1) / a.chunk, n);
+    k_energy<<<grid, ht, sm, s>>>(a);
+    RL_LAUNCH_CK();
+    return RL_OK;
+}
+
+size_t energy_smem(int chunk, int maxm) {
+    return (size_t)chunk * sizeof(float4) + (size_t)chunk * maxm * (2 * sizeof(float4) + sizeof(float)) +
+           (size_t)chunk * sizeof(int);
+}
+
+rl_status launch_select(const SelectArgs &a, int n, cudaStream_t s) {
+    const size_t sm = (size_t)a.p.n_hyp * (sizeof(float) + sizeof(int)) +
+                      (size_t)a.p.n_cull * (12 * sizeof(double) + sizeof(float) + sizeof(int)) + 64;
+    k_select<<<n, 1024, sm, s>>>(a);
+    RL_LAUNCH_CK();
+    return RL_OK;
+}
+
+rl_status launch_lm(const LmArgs &a, int n, cudaStream_t s) {
+    dim3 grid((a.p.n_cull + 3) / 4, n);
+    k_lm<<<grid, 128, 0, s>>>(a);
+    RL_LAUNCH_CK();
+    return RL_OK;
+}
+
+rl_status launch_raycast(const RaycastArgs &a, int n, int max_hw, cudaStream_t s) {
+    dim3 grid(a.n_tiles, a.pose_cap, n);
+    k_raycast_score<<<grid, 256, 0, s>>>(a);
+    RL_LAUNCH_CK();
+    return RL_OK;
+}
+
+rl_status launch_finalize(const QueryState &q, const RParams &p, int n_tiles, int ranked, int n,
+                          cudaStream_t s) {
+    k_finalize<<<n, 32, 0, s>>>(q, p, n_tiles, ranked);
+    RL_LAUNCH_CK();
+    return RL_OK;
+}
+
+}  // namespace rl
+
+namespace rl {
+// Standalone Eq. 6-7 scorer: poses [n][12] against one live depth frame.
+__global__ void k_scores_final(const double *part_sum, const int32_t *part_cnt, int n_tiles,
+                               int n, double npx, float *scores, float *valid_frac) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    float vf;
+    scores[c] = score_from_tiles(part_sum, part_cnt, (size_t)c * n_tiles, n_tiles, npx, &vf);
+    valid_frac[c] = vf;
+}
+
+rl_status launch_score_poses(const RaycastArgs &a, int n_poses, int npx, float *scores,
+                             float *valid_frac, cudaStream_t s) {
+    dim3 grid(a.n_tiles, n_poses, 1);
+    k_raycast_score<<<grid, 256, 0, s>>>(a);
+    RL_LAUNCH_CK();
+    k_scores_final<<<(n_poses + 63) / 64, 64, 0, s>>>(a.part_sum, a.part_cnt, a.n_tiles, n_poses,
+                                                      (double)npx, scores, valid_frac);
+    RL_LAUNCH_CK();
+    return RL_OK;
+}
+}  // namespace rl
