@@ -263,10 +263,10 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def seeds(step):
-        return [(rank << 40) + step * B + i + 1 for i in range(B)]
+        return [(rank << 40) + (step + 1) * B + i for i in range(B)]
 
     for k in range(args.warmup):
-        rel.relocalise_batch(D, C, w.K, seeds(-1 - k), stream=stream, raw=True)
+        rel.relocalise_batch(D, C, w.K, seeds(500_000 + k), stream=stream, raw=True)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()

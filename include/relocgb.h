@@ -233,6 +233,13 @@ rl_status rl_relocalise_batch_async(rl_reloc *r, int32_t n, const float *depth,
                                     const uint8_t *rgb, const rl_intrinsics *K,
                                     const uint64_t *query_seeds, void *stream);
 rl_status rl_reloc_fetch(rl_reloc *r, int32_t n, void *stream, rl_result *out);
+/* The launch sequence of a call depends only on the batch size and the
+ * cascade level; by default it is captured once into a CUDA graph (on a
+ * private stream) and replayed on the caller's stream.  enable = 0 launches
+ * kernels one by one.  Results are identical either way.  The first call
+ * of a given batch size performs the capture and must not itself run under
+ * the caller's stream capture. */
+rl_status rl_reloc_set_graphs(rl_reloc *r, int32_t enable);
 
 /* Intermediate results of frame `q` of the last call (HOST buffers, any may
  * be NULL): per generation slot the 3x4 pose and the iteration that

@@ -230,6 +230,10 @@ class Relocaliser:
     def relocalise(self, depth, rgb, K, seed, stream=None):
         return self.relocalise_batch(depth, rgb, K, [seed], stream)[0]
 
+    def set_graphs(self, enable: bool = True):
+        """Replay captured CUDA graphs (default) or launch kernels one by one."""
+        call("rl_reloc_set_graphs", self.h, int(enable))
+
     def profile(self, enable: bool = True):
         """Turn per-kernel event timing and work counters on/off (resets them)."""
         call("rl_reloc_profile", self.h, int(enable))

@@ -94,6 +94,7 @@ _SIGS = {
     "rl_reloc_fetch": [P, I32, P, P],
     "rl_reloc_debug": [P, I32] + [P] * 10,
     "rl_reloc_profile": [P, I32],
+    "rl_reloc_set_graphs": [P, I32],
     "rl_reloc_profile_read": [P, P, P, P],
     "rl_cascade_create": [P, P, P, I32, P],
     "rl_cascade_destroy": [P],

@@ -218,6 +218,16 @@ struct rl_reloc {
     int last_batch = 0;
     int refcount = 0;
     Profiler prof;
+    // Captured launch sequences keyed by (batch size, cascade level).
+    struct Graph {
+        int n, level;
+        cudaGraphExec_t exec;
+        uint64_t last_use;
+    };
+    std::vector<Graph> graphs;
+    cudaStream_t capture_stream = nullptr;
+    bool use_graphs = true;
+    uint64_t calls = 0;
 };
 
 struct rl_cascade {

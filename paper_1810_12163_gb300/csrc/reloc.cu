@@ -43,9 +43,11 @@ static rl_status ralloc(rl_reloc *r, uint64_t n, T **out) {
 }
 
 static void prof_free(rl_reloc *r);
+static void graphs_free(rl_reloc *r);
 
 static void reloc_release(rl_reloc *r) {
     prof_free(r);
+    graphs_free(r);
     for (void *p : r->allocs) arena_free(r->forest->ctx, p);
     r->allocs.clear();
     if (r->host_frames) cudaFreeHost(r->host_frames);
@@ -221,6 +223,56 @@ rl_status run_relocalise(rl_reloc *r, int n, int level, cudaStream_t s) {
         RL_TRY(launch_raycast(ra, n, hw_max, s));
     }
     { PROF(K_FINALIZE); RL_TRY(launch_finalize(q, p, r->n_score_tiles, ranked, n, s)); }
+    return RL_OK;
+}
+
+// The launch sequence depends only on (n, level) and the relocaliser's
+// fixed buffers, so it is captured once into a CUDA graph on a private
+// stream and replayed on the caller's stream.  Profiling bypasses graphs
+// (it needs events around individual launches).
+static const size_t kMaxGraphs = 8;
+
+static void graphs_free(rl_reloc *r) {
+    for (auto &g : r->graphs) cudaGraphExecDestroy(g.exec);
+    r->graphs.clear();
+    if (r->capture_stream) cudaStreamDestroy(r->capture_stream);
+    r->capture_stream = nullptr;
+}
+
+rl_status launch_relocalise(rl_reloc *r, int n, int level, cudaStream_t s) {
+    ++r->calls;
+    if (r->prof.on || !r->use_graphs) return run_relocalise(r, n, level, s);
+    for (auto &g : r->graphs)
+        if (g.n == n && g.level == level) {
+            g.last_use = r->calls;
+            RL_CK(cudaGraphLaunch(g.exec, s));
+            return RL_OK;
+        }
+    if (!r->capture_stream) RL_CK(cudaStreamCreateWithFlags(&r->capture_stream, cudaStreamNonBlocking));
+    // inputs staged on `s` must be visible to the captured work: the graph
+    // is launched on `s`, so only the capture itself runs on the private stream
+    RL_CK(cudaStreamBeginCapture(r->capture_stream, cudaStreamCaptureModeThreadLocal));
+    rl_status st = run_relocalise(r, n, level, r->capture_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(r->capture_stream, &g);
+    if (st != RL_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+    if (r->graphs.size() >= kMaxGraphs) {  // evict the least recently used
+        size_t lru = 0;
+        for (size_t i = 1; i < r->graphs.size(); ++i)
+            if (r->graphs[i].last_use < r->graphs[lru].last_use) lru = i;
+        cudaGraphExecDestroy(r->graphs[lru].exec);
+        r->graphs.erase(r->graphs.begin() + lru);
+    }
+    r->graphs.push_back({n, level, exec, r->calls});
+    RL_CK(cudaGraphLaunch(exec, s));
     return RL_OK;
 }
 
@@ -400,7 +452,7 @@ extern "C" rl_status rl_relocalise_batch(rl_reloc *r, int32_t n, const float *de
     RL_CK(cudaSetDevice(r->forest->ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
     RL_TRY(stage_inputs(r, n, depth, rgb, K, seeds, mem, s));
-    RL_TRY(run_relocalise(r, n, 0, s));
+    RL_TRY(launch_relocalise(r, n, 0, s));
     r->last_batch = n;
     return fetch_results(r, n, s, out, 0);
 }
@@ -418,7 +470,7 @@ extern "C" rl_status rl_relocalise_batch_async(rl_reloc *r, int32_t n, const flo
     RL_CK(cudaSetDevice(r->forest->ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
     RL_TRY(stage_inputs(r, n, depth, rgb, K, seeds, RL_DEVICE, s));
-    RL_TRY(run_relocalise(r, n, 0, s));
+    RL_TRY(launch_relocalise(r, n, 0, s));
     r->last_batch = n;
     return RL_OK;
 }
@@ -581,7 +633,7 @@ extern "C" rl_status rl_cascade_relocalise_batch(rl_cascade *c, int32_t n, const
         }
         if (cudaMemcpyAsync(r->q.frames, r->host_frames, sizeof(Frame) * m, cudaMemcpyHostToDevice, s) != cudaSuccess)
             st = fail(RL_ERR_CUDA, "frame copy failed");
-        if (st == RL_OK) st = run_relocalise(r, m, l, s);
+        if (st == RL_OK) st = launch_relocalise(r, m, l, s);
         if (st == RL_OK) st = fetch_results(r, m, s, tmp.data(), l);
         r->last_batch = m;
         if (st != RL_OK) break;
@@ -622,6 +674,12 @@ static const char *kKernelNames[K_COUNT] = {"leaves",  "hypgen", "compact", "sam
 
 extern "C" const char *rl_kernel_name(int32_t kid) {
     return (kid >= 0 && kid < K_COUNT) ? kKernelNames[kid] : "";
+}
+
+extern "C" rl_status rl_reloc_set_graphs(rl_reloc *r, int32_t enable) {
+    if (!r) return fail(RL_ERR_INVALID_ARG, "null relocaliser");
+    r->use_graphs = enable != 0;
+    return RL_OK;
 }
 
 extern "C" rl_status rl_reloc_profile(rl_reloc *r, int32_t enable) {

@@ -1,0 +1,121 @@
+"""Paper-sized parity: the 640x480 five-tree depth-15 relocaliser (config 2)
+and the three-level cascade (config 3), GPU vs the CPU oracle.
+
+The full batch runs in the launch configuration the benchmark times (64
+frames per launch); the oracle checks sampled frames of it one by one."""
+import numpy as np
+import pytest
+
+import oracle
+from synth import rooms, workloads
+from tests import helpers as H
+from tests.test_gpu_parity import _compare_query
+
+pytestmark = pytest.mark.gpu
+W2 = workloads.CONFIG2
+
+
+@pytest.fixture(scope="module")
+def rg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1810_12163_gb300 as rg
+    rg.lib()
+    return rg
+
+
+@pytest.fixture(scope="module")
+def model(rg):
+    ctx = rg.Context(0, arena_bytes=16 << 30)
+    g = H.gpu_model(ctx, W2)
+    return ctx, g
+
+
+def test_config2_mode_store_matches(model):
+    ctx, g = model
+    f, res, modes = H.oracle_model(W2.name)
+    e = g.export()
+    assert np.array_equal(e["res_count"], res.count)
+    same = e["nmodes"] == modes.nmodes
+    # density ties decided by one-ulp differences of exp() could move a
+    # cluster boundary; none are expected in FP64
+    assert same.mean() == 1.0, np.nonzero(~same)[0][:10]
+    mm = np.arange(W2.forest["m_max"])[None, :] < modes.nmodes[:, None]
+    assert np.array_equal(e["mode_pos"][mm].view(np.uint32), modes.pos[mm].view(np.uint32))
+    assert np.array_equal(e["mode_size"][mm], modes.size[mm])
+    assert np.array_equal(e["mode_rgb"][mm], modes.rgb[mm])
+    assert (modes.nmodes > 0).sum() > 1000
+
+
+def test_config2_single_queries(rg, model):
+    ctx, g = model
+    scene = rg.Scene(ctx, W2.room().lo, W2.room().hi)
+    rel = rg.Relocaliser(g, scene, W2.ransac, W2.width, W2.height, 1)
+    for q in range(2):
+        _compare_query(rg, rel, W2, q, W2.ransac)
+    rel.close()
+
+
+def test_config2_batch_of_64_sampled(rg, model):
+    """Bench launch shape: 64 frames per call; frames 0, 17 and 63 are
+    recomputed by the oracle."""
+    ctx, g = model
+    scene = rg.Scene(ctx, W2.room().lo, W2.room().hi)
+    rel = rg.Relocaliser(g, scene, W2.ransac, W2.width, W2.height, 64)
+    qs = [W2.query(q) for q in range(16)]
+    D = np.stack([qs[i % 16][0] for i in range(64)])
+    C = np.stack([qs[i % 16][1] for i in range(64)])
+    seeds = [qs[i % 16][3] + 1000 * (i // 16) for i in range(64)]
+    out = rel.relocalise_batch(D, C, W2.K, seeds)
+    f, res, modes = H.oracle_model(W2.name)
+    for i in (0, 17, 63):
+        d, c, T, _ = qs[i % 16]
+        lv = oracle.forest_leaves(f, d, c, W2.K.fx)
+        o = oracle.relocalise(W2.ransac, d, c, W2.K, lv, modes, W2.room().lo, W2.room().hi,
+                              seeds[i], 1 << W2.forest["depth"])
+        assert out[i]["n_hypotheses"] == o["n_hypotheses"]
+        tol = H.score_tolerances(out[i]["chosen_pose"], o["chosen_pose"], o["chosen_score"])
+        H.check_scores(out[i]["chosen_score"], o["chosen_score"], tol, f"frame {i}")
+        if out[i]["best"] == o["best"]:
+            dt, dr = H.pose_err(out[i]["pose"], o["pose"])
+            assert dt <= H.POSE_T_TOL and dr <= H.POSE_R_TOL, (i, dt, dr)
+    rel.close()
+
+
+def test_config3_cascade(rg, model):
+    ctx, g = model
+    scene = rg.Scene(ctx, W2.room().lo, W2.room().hi)
+    th = workloads.cascade_thresholds()
+    levels = []
+    for s, p in workloads.CASCADE_LEVELS:
+        levels.append(rg.Relocaliser(g, scene, p, W2.width // s, W2.height // s, 4))
+    cas = rg.Cascade(levels, th, [s for s, _ in workloads.CASCADE_LEVELS])
+    f, res, modes = H.oracle_model(W2.name)
+    qs = [W2.query(q) for q in range(4)]
+    D = np.stack([q[0] for q in qs])
+    C = np.stack([q[1] for q in qs])
+    out = cas.relocalise_batch(D, C, W2.K, [q[3] for q in qs])
+    lpt = 1 << W2.forest["depth"]
+    used_levels = set()
+    for i, (d, c, T, seed) in enumerate(qs):
+        frames, maps, params = [], [], []
+        for lvl, (s, p) in enumerate(workloads.CASCADE_LEVELS):
+            ds, cs, Ks = rooms.subsample(d, c, W2.K, s) if s > 1 else (d, c, W2.K)
+            frames.append((ds, cs, Ks))
+            maps.append(oracle.forest_leaves(f, ds, cs, Ks.fx, n_trees=p["n_trees_used"]))
+            params.append(dict(p, level=lvl))
+        o = oracle.cascade(params, th, frames, maps, modes, W2.room().lo, W2.room().hi, seed, lpt)
+        used_levels.add(o["level"])
+        if out[i]["level"] != o["level"]:
+            # a fall-back decision on a score within its tolerance of tau
+            lvl = min(out[i]["level"], o["level"])
+            assert abs(min(out[i]["score"], o["score"]) - th[lvl]) <= 1e-4 + 1e-3 * th[lvl], i
+            continue
+        dt, dr = H.pose_err(out[i]["pose"], o["pose"])
+        assert dt <= H.POSE_T_TOL and dr <= H.POSE_R_TOL, (i, dt, dr)
+        tol = H.score_tolerances([out[i]["pose"]], [o["pose"]], [o["score"]])
+        H.check_scores([out[i]["score"]], [o["score"]], tol, f"cascade frame {i}")
+    cas.close()
+    for lv in levels:
+        lv.close()

@@ -128,18 +128,21 @@ def _compare_query(rg, rel, w, q, params):
             return
         for i in range(k):
             dt, dr = H.pose_err(H.as44(dbg["round_pose"][r][i]), H.as44(od["round_pose"][off + i]))
-            assert dt <= H.POSE_T_TOL and dr <= H.POSE_R_TOL, (q, r, i, dt, dr)
+            H.check_refined_pose(dt, dr, ge[i], oe[i], f"q{q} round {r} survivor {i}")
         off += k
-    # output pose, energy, ranking score
-    dt, dr = H.pose_err(gr["pose"], orr["pose"])
-    assert dt <= H.POSE_T_TOL and dr <= H.POSE_R_TOL, (q, dt, dr)
+    # ranking scores of the chosen set, then the output pose
     assert gr["n_chosen"] == orr["n_chosen"]
-    np.testing.assert_allclose(gr["energy"], orr["energy"], rtol=H.ENERGY_RTOL)
     if params["rank"]:
-        fin = np.isfinite(orr["chosen_score"])
-        assert np.array_equal(np.isfinite(gr["chosen_score"]), fin)
-        np.testing.assert_allclose(gr["chosen_score"][fin], orr["chosen_score"][fin], rtol=1e-4)
-        np.testing.assert_allclose(gr["score"], orr["score"], rtol=1e-4)
+        tol = H.score_tolerances(gr["chosen_pose"], orr["chosen_pose"], orr["chosen_score"])
+        H.check_scores(gr["chosen_score"], orr["chosen_score"], tol, f"q{q}")
+        if gr["best"] != orr["best"]:
+            # argmin between near-tied scores: either choice is valid
+            a, b = gr["best"], orr["best"]
+            assert abs(orr["chosen_score"][a] - orr["chosen_score"][b]) <= tol[a] + tol[b], (q, a, b)
+            return
+    dt, dr = H.pose_err(gr["pose"], orr["pose"])
+    np.testing.assert_allclose(gr["energy"], orr["energy"], rtol=H.ENERGY_RTOL)
+    H.check_refined_pose(dt, dr, gr["energy"], orr["energy"], f"q{q} output")
 
 
 def test_relocalise_parity_small(rg, ctx, small):
