@@ -205,6 +205,30 @@ rl_status rl_score_poses(rl_scene *s, const float *depth, const rl_intrinsics *K
                          const double *poses, int32_t n, rl_mem mem, void *stream,
                          float *scores, float *valid_frac);
 
+/* Same score as rl_score_poses, for callers that cannot allocate device
+ * memory (a real-time loop whose memory is fixed at start-up, a host
+ * framework that owns all device memory, code that must not trigger the
+ * implicit synchronisation of cudaMalloc/cudaFree).  It allocates nothing:
+ * no context or scene handle, no cudaMalloc/cudaFree, no allocating library
+ * routine.  The paper has no counterpart of this call.
+ *   box_lo/box_hi: HOST double[3], the room box.
+ *   depth: DEVICE float [H][W]; poses: DEVICE double [n][16] row-major
+ *   camera->world; scores: DEVICE float [n]; valid_frac: DEVICE float [n] or
+ *   NULL.  The call only enqueues work on `stream` and returns.
+ * Its partial sums live in a fixed 1 MiB device array inside the library
+ * (65536 records of one 1024-pixel tile per pose): n * ceil(W*H/1024) must
+ * not exceed 65536 (e.g. n <= 218 at 640x480), else RL_ERR_INVALID_ARG with
+ * the limit in rl_last_error().  Every GPU that loads the library holds the
+ * array until the process exits.  All calls share it and it keeps the last
+ * call's contents; nothing in it needs to start at zero.  Calls that overlap
+ * on the GPU (unordered streams) race on it.  The first call on a device
+ * looks up the array's device address with that device current; make that
+ * first call before any stream capture. */
+rl_status rl_score_poses_noalloc(const double box_lo[3], const double box_hi[3],
+                                 const float *depth, const rl_intrinsics *K,
+                                 const double *poses, int32_t n, void *stream,
+                                 float *scores, float *valid_frac);
+
 /* ---- relocaliser (Sec. 3.2.3-3.2.4) ---------------------------------- */
 /* Allocates per-query state for up to `max_batch` frames of at most
  * max_width x max_height from the arena.  `scene` may be NULL when

@@ -86,6 +86,7 @@ _SIGS = {
     "rl_scene_box": [P, P, P, P],
     "rl_scene_destroy": [P],
     "rl_score_poses": [P, P, P, P, I32, I32, P, P, P],
+    "rl_score_poses_noalloc": [P, P, P, P, P, I32, P, P, P],
     "rl_reloc_create": [P, P, P, I32, I32, I32, P],
     "rl_reloc_destroy": [P],
     "rl_relocalise": [P, P, P, P, U64, I32, P, P],
