@@ -68,7 +68,8 @@ typedef struct {
     int32_t width, height;
 } rl_intrinsics;
 
-/* Forest and adaptation parameters (Sec. 3.2.2, Sec. 4.5, Table 9). */
+/* Forest and adaptation parameters (Sec. 3.2.2, Sec. 4.5 and the parameter
+ * table of Appendix B). */
 typedef struct {
     int32_t n_trees;          /* trees in the forest (paper: 5) */
     int32_t depth;            /* split levels per tree, 1..15 (paper: 15 / 14) */
@@ -88,7 +89,8 @@ typedef struct {
     int32_t grid_origin;      /* first grid row/column (0) */
 } rl_forest_params;
 
-/* Relocaliser parameters (Sec. 3.2.3-3.2.4; names follow Table 9). */
+/* Relocaliser parameters (Sec. 3.2.3-3.2.4; names follow the parameter
+ * table of Appendix B). */
 typedef struct {
     int32_t n_hyp;            /* maxPoseCandidates, N_max (<= 4096) */
     int32_t max_iter;         /* maxCandidateGenerationIterations */
@@ -294,7 +296,12 @@ const char *rl_kernel_name(int32_t kernel_id);
 /* Levels run in order on the same frame; level l works on the frame
  * subsampled by subsample[l] (pixel (s*u, s*v), intrinsics / s) and falls
  * back to level l+1 iff its score exceeds thresholds[l].  The levels must
- * share one forest.  The cascade keeps pointers to the levels. */
+ * share one forest, be distinct relocalisers, and the last level works at
+ * full resolution (subsample 1).  All levels of a call are enqueued at once
+ * (one CUDA graph per batch size): the fall-back decision is taken on the
+ * device, frames accepted early become empty frames for later levels, and
+ * results come back in one copy.  The cascade keeps pointers to the levels
+ * (RL_ERR_BUSY on destroying a level first). */
 rl_status rl_cascade_create(rl_reloc *const *levels, const double *thresholds,
                             const int32_t *subsample, int32_t n_levels, rl_cascade **out);
 rl_status rl_cascade_destroy(rl_cascade *c);
@@ -307,6 +314,51 @@ rl_status rl_cascade_relocalise_batch(rl_cascade *c, int32_t n, const float *dep
                                       const uint8_t *rgb, const rl_intrinsics *K,
                                       const uint64_t *query_seeds, rl_mem mem, void *stream,
                                       rl_result *out);
+
+/* ---- serving loop ---------------------------------------------------- */
+/* A server relocalises requests from many camera streams against several
+ * models (one forest + scene + relocaliser parameters each, e.g. one per
+ * room), with frames of any size up to the model's maximum.  Each model has
+ * a worker thread and two device slots of max_batch frames: while one batch
+ * runs, everything that arrived meanwhile is staged into the other (batches
+ * form continuously from the queue; models overlap on separate streams).
+ * Admission: a request's staged bytes (W*H*7) count against memory_budget
+ * until its result is fetched; over budget, submit returns RL_ERR_ADMISSION
+ * unless queue_when_full, in which case the request waits on the host.  A
+ * frame's result is identical whatever batch it joins.  The paper has no
+ * counterpart (it relocalises one frame at a time). */
+typedef struct rl_server rl_server;
+
+typedef struct {
+    int32_t max_batch;        /* frames per device slot */
+    int32_t queue_when_full;  /* 1: queue over-budget requests, 0: refuse them */
+    uint64_t memory_budget;   /* bytes of admitted frame data */
+} rl_server_params;
+
+typedef struct {
+    uint64_t submitted, completed, refused;
+    uint64_t peak_admitted_bytes;
+    double p50_ms, p99_ms, mean_ms;  /* submit -> result available */
+    double frames_per_s;             /* completed / (last completion - first submit) */
+} rl_server_stats;
+
+rl_status rl_server_create(rl_ctx *ctx, const rl_server_params *p, rl_server **out);
+/* Adds a model; allocates two relocalisers of max_batch frames from the
+ * context arena and starts its worker thread. */
+rl_status rl_server_add_model(rl_server *s, rl_forest *f, rl_scene *scene,
+                              const rl_ransac_params *p, int32_t max_width, int32_t max_height,
+                              int32_t *model_id);
+/* Copies the HOST frame and enqueues it; *ticket identifies the request. */
+rl_status rl_server_submit(rl_server *s, int32_t model, const float *depth, const uint8_t *rgb,
+                           const rl_intrinsics *K, uint64_t query_seed, uint64_t *ticket);
+/* *done = 1 and *out filled (ticket released) once the result is ready. */
+rl_status rl_server_poll(rl_server *s, uint64_t ticket, int32_t *done, rl_result *out);
+/* Waits at most timeout_ms; RL_ERR_TIMEOUT if the result is not ready
+ * (the ticket stays valid). */
+rl_status rl_server_wait(rl_server *s, uint64_t ticket, uint32_t timeout_ms, rl_result *out);
+rl_status rl_server_get_stats(rl_server *s, rl_server_stats *out);
+/* Finishes queued work, stops the workers and releases the models. */
+rl_status rl_server_destroy(rl_server *s);
 
 #ifdef __cplusplus
 }

@@ -295,3 +295,55 @@ class Cascade:
         if self.h:
             call("rl_cascade_destroy", self.h)
             self.h = ctypes.c_void_p()
+
+
+class Server:
+    """Serving loop over several models (rooms / parameter sets): requests
+    from host frames of any size up to the model's maximum are batched
+    continuously on the GPU (see rl_server_* in include/relocgb.h)."""
+
+    def __init__(self, ctx: Context, max_batch: int = 16, memory_budget: int = 1 << 30,
+                 queue_when_full: bool = True):
+        from .binding import ServerParams
+        self.ctx = ctx
+        self.h = ctypes.c_void_p()
+        p = ServerParams(max_batch, int(queue_when_full), memory_budget)
+        call("rl_server_create", ctx.h, ctypes.byref(p), ctypes.byref(self.h))
+        self._keep = []
+
+    def add_model(self, forest: Forest, scene: Scene | None, params: dict, max_w: int, max_h: int) -> int:
+        mid = ctypes.c_int32()
+        full = dict(presets.DEFAULT, **params)
+        call("rl_server_add_model", self.h, forest.h, scene.h if scene else None,
+             ctypes.byref(_struct(RansacParams, full)), max_w, max_h, ctypes.byref(mid))
+        return mid.value
+
+    def submit(self, model: int, depth, rgb, K, seed: int) -> int:
+        d = np.ascontiguousarray(depth, np.float32)
+        c = np.ascontiguousarray(rgb, np.uint8)
+        t = ctypes.c_uint64()
+        call("rl_server_submit", self.h, model, d.ctypes.data_as(ctypes.c_void_p),
+             c.ctypes.data_as(ctypes.c_void_p), ctypes.byref(intrinsics(K)), seed, ctypes.byref(t))
+        return t.value
+
+    def poll(self, ticket: int):
+        done = ctypes.c_int32()
+        r = Result()
+        call("rl_server_poll", self.h, ticket, ctypes.byref(done), ctypes.byref(r))
+        return result_dict(r) if done.value else None
+
+    def wait(self, ticket: int, timeout_ms: int = 60_000):
+        r = Result()
+        call("rl_server_wait", self.h, ticket, timeout_ms, ctypes.byref(r))
+        return result_dict(r)
+
+    def stats(self) -> dict:
+        from .binding import ServerStats
+        st = ServerStats()
+        call("rl_server_get_stats", self.h, ctypes.byref(st))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.h:
+            call("rl_server_destroy", self.h)
+            self.h = ctypes.c_void_p()

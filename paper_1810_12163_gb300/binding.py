@@ -61,6 +61,17 @@ class RansacParams(ctypes.Structure):
                 ("rank", I32), ("halve_to_one", I32)]
 
 
+class ServerParams(ctypes.Structure):
+    _fields_ = [("max_batch", I32), ("queue_when_full", I32), ("memory_budget", U64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", U64), ("completed", U64), ("refused", U64),
+                ("peak_admitted_bytes", U64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("frames_per_s", ctypes.c_double)]
+
+
 class Result(ctypes.Structure):
     _fields_ = [("pose", ctypes.c_double * 16), ("energy", ctypes.c_float),
                 ("energy_per_pixel", ctypes.c_float), ("score", ctypes.c_float), ("level", I32),
@@ -101,6 +112,13 @@ _SIGS = {
     "rl_cascade_destroy": [P],
     "rl_cascade_relocalise": [P, P, P, P, U64, I32, P, P],
     "rl_cascade_relocalise_batch": [P, I32, P, P, P, P, I32, P, P],
+    "rl_server_create": [P, P, P],
+    "rl_server_add_model": [P, P, P, P, I32, I32, P],
+    "rl_server_submit": [P, I32, P, P, P, U64, P],
+    "rl_server_poll": [P, U64, P, P],
+    "rl_server_wait": [P, U64, ctypes.c_uint32, P],
+    "rl_server_get_stats": [P, P],
+    "rl_server_destroy": [P],
 }
 
 

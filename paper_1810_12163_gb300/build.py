@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "librelocgb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 EXACT = {"forest.cu", "rqs.cu", "hypgen.cu"}
 SOURCES = ["context.cu", "forest.cu", "rqs.cu", "hypgen.cu", "score.cu", "reloc.cu",
-           "score_static.cu"]
+           "score_static.cu", "server.cu"]
 
 
 def nvcc() -> str:

@@ -5,6 +5,7 @@
 // back-projection are plain IEEE operations in a fixed order, so leaves and
 // reservoir contents are exactly reproducible.
 #include "internal.h"
+#include "relocgb_dev.cuh"
 
 namespace rl {
 
@@ -87,32 +88,109 @@ __device__ __forceinline__ int walk_tree(const float4 *__restrict__ nodes, int d
     return n - ((1 << depth) - 1);
 }
 
+// All T trees of one pixel walked level by level, interleaved: T
+// independent chains of dependent node and probe loads in flight at once.
+template <int T>
+__device__ __forceinline__ void walk_trees(const float4 *__restrict__ nodes, int n_branch, int depth,
+                                           const float *__restrict__ D, const uint8_t *__restrict__ C,
+                                           int W, int H, float s, int x, int y, float d, float inv,
+                                           int leaf[T]) {
+    int n[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) n[t] = 0;
+    const int p = y * W + x;
+    for (int level = 0; level < depth; ++level) {
+        float4 nd[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) nd[t] = __ldg(&nodes[(size_t)t * n_branch + n[t]]);
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const uint32_t meta = __float_as_uint(nd[t].w);
+            const float ox = __fmul_rn(__fmul_rn(nd[t].x, s), inv);
+            const float oy = __fmul_rn(__fmul_rn(nd[t].y, s), inv);
+            const int q = probe_coord(y, oy, H) * W + probe_coord(x, ox, W);
+            float f;
+            if ((meta & 255u) == 0u) {
+                const float dq = __ldg(&D[q]);
+                f = __fsub_rn(d, dq > 0.0f ? dq : 0.0f);
+            } else {
+                const int c = (int)(meta >> 8);
+                f = __fsub_rn((float)__ldg(&C[p * 3 + c]), (float)__ldg(&C[q * 3 + c]));
+            }
+            n[t] = (f >= nd[t].z) ? 2 * n[t] + 2 : 2 * n[t] + 1;
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < T; ++t) leaf[t] = n[t] - ((1 << depth) - 1);
+}
+
+template <int T>
+__device__ __forceinline__ int walk_and_store(const float4 *nodes, int n_branch, int depth, const Frame &fr,
+                                              float s, int x, int y, float d, float inv, uint16_t *o,
+                                              int hw_max, const uint8_t *nmodes, int lpt, int k_top,
+                                              bool count, uint4 *rec) {
+    int leaf[kRecTrees], cnt[kRecTrees];
+    walk_trees<T>(nodes, n_branch, depth, fr.depth, fr.rgb, fr.W, fr.H, s, x, y, d, inv, leaf);
+    int total = 0;
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        o[(size_t)t * hw_max] = (uint16_t)leaf[t];
+        cnt[t] = count ? min((int)__ldg(&nmodes[t * lpt + leaf[t]]), k_top) : 0;
+        total += cnt[t];
+    }
+    if (rec) *rec = make_rec(leaf, cnt, T);
+    return total;
+}
+
 // out: uint16 [frame][tree][hw_max]; one thread per pixel walks every tree.
+// When `mcount` is given it also receives |M(u)| = sum over the trees of
+// min(modes of the reached leaf, k_top) per pixel (0 without depth).
 __global__ void k_leaves(const float4 *__restrict__ nodes, int n_branch, int depth, int n_trees,
-                         const Frame *__restrict__ frames, int hw_max, uint16_t *__restrict__ out) {
+                         const Frame *__restrict__ frames, int hw_max, uint16_t *__restrict__ out,
+                         const uint8_t *__restrict__ nmodes, int leaves_per_tree, int k_top,
+                         uint16_t *__restrict__ mcount, uint4 *__restrict__ prec) {
     const Frame fr = frames[blockIdx.y];
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= fr.W * fr.H) return;
     const int x = p % fr.W, y = p / fr.W;
     const float d = __ldg(&fr.depth[p]);
     uint16_t *o = out + (size_t)blockIdx.y * n_trees * hw_max + p;
+    uint4 *rec = prec ? prec + (size_t)blockIdx.y * hw_max + p : nullptr;
     if (!(d > 0.0f)) {
         for (int t = 0; t < n_trees; ++t) o[(size_t)t * hw_max] = 0xFFFF;
+        if (mcount) mcount[(size_t)blockIdx.y * hw_max + p] = 0;
+        if (rec) *rec = make_uint4(0, 0, 0, 0);
         return;
     }
     const float s = __fdiv_rn(fr.fx, 585.0f);
     const float inv = __frcp_rn(d);
-    for (int t = 0; t < n_trees; ++t)
-        o[(size_t)t * hw_max] =
-            (uint16_t)walk_tree(nodes + (size_t)t * n_branch, depth, fr.depth, fr.rgb, fr.W, fr.H,
-                                s, x, y, d, inv);
+    int total = 0;
+    const bool cnt = mcount != nullptr;
+    switch (n_trees) {
+    case 1: total = walk_and_store<1>(nodes, n_branch, depth, fr, s, x, y, d, inv, o, hw_max, nmodes, leaves_per_tree, k_top, cnt, rec); break;
+    case 2: total = walk_and_store<2>(nodes, n_branch, depth, fr, s, x, y, d, inv, o, hw_max, nmodes, leaves_per_tree, k_top, cnt, rec); break;
+    case 3: total = walk_and_store<3>(nodes, n_branch, depth, fr, s, x, y, d, inv, o, hw_max, nmodes, leaves_per_tree, k_top, cnt, rec); break;
+    case 4: total = walk_and_store<4>(nodes, n_branch, depth, fr, s, x, y, d, inv, o, hw_max, nmodes, leaves_per_tree, k_top, cnt, rec); break;
+    case 5: total = walk_and_store<5>(nodes, n_branch, depth, fr, s, x, y, d, inv, o, hw_max, nmodes, leaves_per_tree, k_top, cnt, rec); break;
+    default:
+        for (int t = 0; t < n_trees; ++t) {
+            const int leaf = walk_tree(nodes + (size_t)t * n_branch, depth, fr.depth, fr.rgb, fr.W, fr.H,
+                                       s, x, y, d, inv);
+            o[(size_t)t * hw_max] = (uint16_t)leaf;
+            if (cnt) total += min((int)__ldg(&nmodes[t * leaves_per_tree + leaf]), k_top);
+        }
+    }
+    if (mcount) mcount[(size_t)blockIdx.y * hw_max + p] = (uint16_t)total;
 }
 
 rl_status launch_leaves(const rl_forest *f, const Frame *frames_dev, int n_frames, int n_trees,
-                        int hw_max, uint16_t *out, int max_w, int max_h, cudaStream_t s) {
+                        int hw_max, uint16_t *out, int max_w, int max_h, cudaStream_t s,
+                        int k_top, uint16_t *mcount, uint4 *prec) {
     const int npx = max_w * max_h;
     dim3 grid((npx + 127) / 128, n_frames);
-    k_leaves<<<grid, 128, 0, s>>>(f->nodes, f->n_branch, f->p.depth, n_trees, frames_dev, hw_max, out);
+    k_leaves<<<grid, 128, 0, s>>>(f->nodes, f->n_branch, f->p.depth, n_trees, frames_dev, hw_max, out,
+                                  f->nmodes, f->leaves_per_tree, k_top, mcount,
+                                  n_trees <= kRecTrees ? prec : nullptr);
     RL_LAUNCH_CK();
     return RL_OK;
 }

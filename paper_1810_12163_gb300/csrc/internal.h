@@ -102,6 +102,10 @@ struct rl_scene {
     double lo[3], hi[3];
 };
 
+// Relocalisers using at most this many trees keep a 16-byte per-pixel record
+// (leaf ids and per-tree mode counts) next to the leaf maps.
+constexpr int kRecTrees = 5;
+
 // Device-side view of the mode store used by the relocaliser kernels.
 struct ModeView {
     const uint8_t *nmodes;
@@ -124,6 +128,8 @@ struct RParams {
     int level;        // cascade level, part of every random counter
     int max_rounds;   // preemptive rounds for this configuration
     int max_pix;      // eta * (max_rounds + 1)
+    int maxm;         // bound on |M(u)|: trees x min(k_top, m_max)
+    int mpad;         // maxm rounded up to an odd count (mode-table row stride)
 };
 
 // Per-frame description used by batched kernels.
@@ -138,12 +144,20 @@ struct Frame {
 // Device-resident per-query RANSAC state (arrays sized for max_batch).
 struct QueryState {
     uint16_t *leaves;        // [B][T][HWmax]
+    uint16_t *mcount;        // [B][HWmax] |M(u)| per pixel
+    uint4 *prec;             // [B][HWmax] per-pixel leaves + counts (<= 5 trees), else null
     double *hyp_pose;        // [B][N][12]
     int32_t *hyp_iter;       // [B][N]
     int32_t *hyp_list;       // [B][N] slots of successful hypotheses
     int32_t *n_hyp;          // [B]
     int32_t *pix;            // [B][max_pix] pixel ids (-1 skipped)
     float4 *xc;              // [B][max_pix] camera points
+    // Mode table of the pixel set: M(u) of every pixel of I decoded once
+    // when its batch is drawn, rows of mpad records
+    float4 *tab0;            // [B][max_pix][mpad] mu.xyz, U00
+    float4 *tab1;            // [B][max_pix][mpad] U01 U02 U11 U12
+    float *tab2;             // [B][max_pix][mpad] U22
+    int16_t *tab_cnt;        // [B][max_pix] |M(u)| (0 for a skipped draw)
     int32_t *n_pix;          // [B]
     double *cur_pose;        // [B][n_cull][12]
     int32_t *cur_slot;       // [B][n_cull]
@@ -230,12 +244,34 @@ struct rl_reloc {
     uint64_t calls = 0;
 };
 
+// Per-frame output of a cascade, written on the device by each level's
+// fall-back decision.
+struct CascadeOut {
+    DevResult *res;          // [B]
+    double *chosen_pose;     // [B][16][12]
+    float *chosen_energy;    // [B][16]
+    float *chosen_score;     // [B][16]
+    int32_t *chosen_slot;    // [B][16]
+    int32_t *level;          // [B]
+    int32_t *done;           // [B] accepted by some level
+};
+
 struct rl_cascade {
     std::vector<rl_reloc *> levels;
     std::vector<double> thresholds;
     std::vector<int32_t> subsample;
-    float *sub_depth = nullptr;   // per level subsampled frames
-    uint8_t *sub_rgb = nullptr;
+    rl_ctx *ctx = nullptr;
+    int max_batch = 0;
+    CascadeOut out{};
+    Frame *full_dev = nullptr;            // [B] full-resolution frames
+    std::vector<void *> allocs;
+    struct Graph {
+        int n;
+        cudaGraphExec_t exec;
+    };
+    std::vector<Graph> graphs;
+    cudaStream_t capture_stream = nullptr;
+    bool use_graphs = true;
 };
 
 // ---------------------------------------------------------------------------
@@ -273,11 +309,18 @@ __host__ __device__ inline uint32_t draw_below(uint32_t u, uint32_t n) {
 namespace rl {
 rl_status launch_forest_random(rl_forest *f, cudaStream_t s);
 rl_status launch_leaves(const rl_forest *f, const Frame *frames_dev, int n_frames, int n_trees,
-                        int hw_max, uint16_t *out, int max_w, int max_h, cudaStream_t s);
+                        int hw_max, uint16_t *out, int max_w, int max_h, cudaStream_t s,
+                        int k_top = 0, uint16_t *mcount = nullptr, uint4 *prec = nullptr);
 rl_status adapt_frame(rl_forest *f, const float *depth, const uint8_t *rgb,
                       const rl_intrinsics *K, const double T[16], cudaStream_t s);
 rl_status update_modes(rl_forest *f, int64_t begin, int64_t count, cudaStream_t s);
 rl_status reset_leaves(rl_forest *f, cudaStream_t s);
 ModeView mode_view(const rl_forest *f);
 rl_status run_relocalise(rl_reloc *r, int n, int level, cudaStream_t s);
+// Batch of n frames whose descriptors (device pointers, per-frame sizes and
+// intrinsics, keys) are given on the host: descriptors are copied and the
+// launch sequence is enqueued on s (graph replay when enabled).
+rl_status reloc_enqueue_frames(rl_reloc *r, int n, const Frame *frames, cudaStream_t s);
+// Copies the results of the last n frames back and waits for s.
+rl_status reloc_fetch_results(rl_reloc *r, int n, cudaStream_t s, rl_result *out);
 }  // namespace rl

@@ -22,7 +22,17 @@ struct EnergyArgs {
     int part_h, n_chunks;
     int round_gate;            // skip frames whose round is inactive
     unsigned long long *work;  // profiling counters or null
+    const uint16_t *mcount;    // [B][hw_max] |M(u)|
+    const uint4 *prec;         // [B][hw_max] pixel records or null
+    const float4 *q_tab0;      // mode table of the pixel set (rows of p.mpad)
+    const float4 *q_tab1;
+    const float *q_tab2;
+    const int16_t *q_tab_cnt;
 };
+
+// Mode table of pixel batch `batch` (decoded M(u) of each drawn pixel).
+rl_status launch_build_table(const QueryState &q, int hw_max, ModeView mv, const RParams &p, int batch,
+                             int n, cudaStream_t s);
 
 struct SelectArgs {
     int phase, round;
@@ -44,7 +54,15 @@ struct LmArgs {
     RParams p;
     int n_pix;
     unsigned long long *work;  // profiling counters or null
+    int maxm;                  // |M(u)| bound: trees x min(k_top, m_max)
+    int maxm_pad;              // maxm rounded up to an odd count (shared-memory rows)
 };
+
+// Shared memory of the tiled LM kernel for a padded row of maxm_pad modes;
+// above kLmSmemMax the global-memory kernel is used.
+constexpr size_t kLmSmemMax = 200 * 1024;
+size_t lm_tiled_smem(int maxm_pad);
+rl_status prepare_kernels();
 
 struct RaycastArgs {
     const Frame *frames;
@@ -72,12 +90,12 @@ rl_status launch_score_poses(const RaycastArgs &a, int n_poses, int npx, float *
                              float *valid_frac, cudaStream_t s);
 rl_status launch_finalize(const QueryState &q, const RParams &p, int n_tiles, int ranked, int n,
                           cudaStream_t s);
-rl_status launch_hypgen(const Frame *frames, const uint16_t *leaves, int hw_max, ModeView mv,
-                        const RParams &p, double *hyp_pose, int32_t *hyp_iter, int n,
-                        cudaStream_t s);
+rl_status launch_hypgen(const Frame *frames, const uint16_t *leaves, const uint16_t *mcount,
+                        const uint4 *prec, int hw_max, ModeView mv, const RParams &p,
+                        double *hyp_pose, int32_t *hyp_iter, int n, cudaStream_t s);
 rl_status launch_compact(const int32_t *hyp_iter, int N, int32_t *hyp_list, int32_t *n_hyp, int n,
                          cudaStream_t s);
-rl_status launch_sample_batch(const Frame *frames, const uint16_t *leaves, int hw_max, ModeView mv,
+rl_status launch_sample_batch(const Frame *frames, const uint16_t *mcount, int hw_max,
                               const RParams &p, int batch, int32_t *pix, float4 *xc, int n,
                               cudaStream_t s);
 rl_status launch_subsample(const Frame *src, Frame *dst_desc, float *dst_depth, uint8_t *dst_rgb,

@@ -134,14 +134,17 @@ rl_status run_relocalise(rl_reloc *r, int n, int level, cudaStream_t s) {
     RL_CK(cudaMemsetAsync(q.n_rounds, 0, sizeof(int32_t) * n, s));
     RL_CK(cudaMemsetAsync(q.round_count, 0, sizeof(int32_t) * 16 * n, s));
     unsigned long long *work = r->prof.on ? r->prof.work : nullptr;
-    { PROF(K_LEAVES); RL_TRY(launch_leaves(f, q.frames, n, p.n_trees, hw_max, q.leaves, r->max_w, r->max_h, s)); }
-    { PROF(K_HYPGEN); RL_TRY(launch_hypgen(q.frames, q.leaves, hw_max, mv, p, q.hyp_pose, q.hyp_iter, n, s)); }
+    { PROF(K_LEAVES); RL_TRY(launch_leaves(f, q.frames, n, p.n_trees, hw_max, q.leaves, r->max_w, r->max_h, s, p.k_top, q.mcount, q.prec)); }
+    { PROF(K_HYPGEN); RL_TRY(launch_hypgen(q.frames, q.leaves, q.mcount, q.prec, hw_max, mv, p, q.hyp_pose, q.hyp_iter, n, s)); }
     { PROF(K_COMPACT); RL_TRY(launch_compact(q.hyp_iter, N, q.hyp_list, q.n_hyp, n, s)); }
-    { PROF(K_SAMPLE); RL_TRY(launch_sample_batch(q.frames, q.leaves, hw_max, mv, p, 0, q.pix, q.xc, n, s)); }
+    { PROF(K_SAMPLE); RL_TRY(launch_sample_batch(q.frames, q.mcount, hw_max, p, 0, q.pix, q.xc, n, s));
+      RL_TRY(launch_build_table(q, hw_max, mv, p, 0, n, s)); }
 
-    const int maxm = p.n_trees * std::min(p.k_top, f->p.m_max);
-    int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(32, 40960 / (maxm * 36)));
+    const int maxm = p.maxm;
+    int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(32, 40960 / (p.mpad * 36)));
     EnergyArgs ea{};
+    ea.mcount = q.mcount;
+    ea.prec = q.prec;
     ea.pix = q.pix;
     ea.xc = q.xc;
     ea.max_pix = p.max_pix;
@@ -150,7 +153,11 @@ rl_status run_relocalise(rl_reloc *r, int n, int level, cudaStream_t s) {
     ea.mv = mv;
     ea.p = p;
     ea.chunk = chunk;
-    ea.maxm = maxm;
+    ea.maxm = p.mpad;  // shared-memory row stride of the staged table
+    ea.q_tab0 = q.tab0;
+    ea.q_tab1 = q.tab1;
+    ea.q_tab2 = q.tab2;
+    ea.q_tab_cnt = q.tab_cnt;
     ea.part = q.energy_part;
     ea.part_h = std::max(N, NC);
     ea.n_chunks = r->n_chunks;
@@ -181,9 +188,10 @@ rl_status run_relocalise(rl_reloc *r, int n, int level, cudaStream_t s) {
     // preemptive rounds
     for (int round = 0; round < p.max_rounds; ++round) {
         const int n_pix = p.eta * (round + 2);
-        { PROF(K_SAMPLE); RL_TRY(launch_sample_batch(q.frames, q.leaves, hw_max, mv, p, round + 1, q.pix, q.xc, n, s)); }
+        { PROF(K_SAMPLE); RL_TRY(launch_sample_batch(q.frames, q.mcount, hw_max, p, round + 1, q.pix, q.xc, n, s));
+          RL_TRY(launch_build_table(q, hw_max, mv, p, round + 1, n, s)); }
         if (p.pose_update && p.lm_max_iter > 0) {
-            LmArgs la{q, q.leaves, hw_max, mv, p, n_pix, work};
+            LmArgs la{q, q.leaves, hw_max, mv, p, n_pix, work, maxm, maxm | 1};
             PROF(K_LM);
             RL_TRY(launch_lm(la, n, s));
         }
@@ -339,6 +347,23 @@ static rl_status check_call(rl_reloc *r, int n, const float *depth, const uint8_
     return RL_OK;
 }
 
+rl_status reloc_enqueue_frames(rl_reloc *r, int n, const Frame *frames, cudaStream_t s) {
+    if (n < 1 || n > r->max_batch) return fail(RL_ERR_INVALID_ARG, "batch size outside 1..max_batch");
+    for (int i = 0; i < n; ++i) {
+        if (frames[i].W > r->max_w || frames[i].H > r->max_h)
+            return fail(RL_ERR_INVALID_ARG, "frame larger than the relocaliser's maximum size");
+        r->host_frames[i] = frames[i];
+    }
+    RL_CK(cudaMemcpyAsync(r->q.frames, r->host_frames, sizeof(Frame) * n, cudaMemcpyHostToDevice, s));
+    RL_TRY(launch_relocalise(r, n, 0, s));
+    r->last_batch = n;
+    return RL_OK;
+}
+
+rl_status reloc_fetch_results(rl_reloc *r, int n, cudaStream_t s, rl_result *out) {
+    return fetch_results(r, n, s, out, 0);
+}
+
 }  // namespace rl
 
 using namespace rl;
@@ -354,6 +379,7 @@ extern "C" rl_status rl_reloc_create(rl_forest *f, rl_scene *scene, const rl_ran
     if (max_batch < 1 || max_batch > 65535) return fail(RL_ERR_INVALID_ARG, "max_batch must be 1..65535");
     if (p->rank && !scene) return fail(RL_ERR_INVALID_ARG, "ranking needs a scene model");
     RL_CK(cudaSetDevice(f->ctx->device));
+    RL_TRY(prepare_kernels());
     rl_reloc *r = new rl_reloc();
     r->forest = f;
     r->scene = scene;
@@ -372,7 +398,9 @@ extern "C" rl_status rl_reloc_create(rl_forest *f, rl_scene *scene, const rl_ran
     rp.max_rounds = rounds_for(p->n_cull, p->k_out, p->halve_to_one);
     rp.max_pix = p->eta * (rp.max_rounds + 1);
     const int maxm = p->n_trees_used * std::min(p->k_top, f->p.m_max);
-    const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(32, 40960 / (maxm * 36)));
+    rp.maxm = maxm;
+    rp.mpad = maxm | 1;
+    const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(32, 40960 / (rp.mpad * 36)));
     r->n_chunks = (rp.max_pix + chunk - 1) / chunk;
     const size_t hw = (size_t)max_w * max_h;
     r->n_score_tiles = (int)((hw + 255) / 256);
@@ -381,12 +409,18 @@ extern "C" rl_status rl_reloc_create(rl_forest *f, rl_scene *scene, const rl_ran
     rl_status s = RL_OK;
 #define A(field, count) if (s == RL_OK) s = ralloc(r, (uint64_t)(count), &q.field)
     A(leaves, B * p->n_trees_used * hw);
+    A(mcount, B * hw);
+    if (p->n_trees_used <= kRecTrees) A(prec, B * hw);
     A(hyp_pose, B * N * 12);
     A(hyp_iter, B * N);
     A(hyp_list, B * N);
     A(n_hyp, B);
     A(pix, B * MP);
     A(xc, B * MP);
+    A(tab0, B * MP * (uint64_t)rp.mpad);
+    A(tab1, B * MP * (uint64_t)rp.mpad);
+    A(tab2, B * MP * (uint64_t)rp.mpad);
+    A(tab_cnt, B * MP);
     A(n_pix, B);
     A(cur_pose, B * NC * 12);
     A(cur_slot, B * NC);
@@ -420,7 +454,7 @@ extern "C" rl_status rl_reloc_create(rl_forest *f, rl_scene *scene, const rl_ran
         s = fail(RL_ERR_CUDA, "pinned host allocation failed");
     if (s == RL_OK) {
         const size_t sm_sel = (size_t)N * 8 + NC * (12 * 8 + 8) + 64;
-        const size_t sm_en = energy_smem(chunk, maxm);
+        const size_t sm_en = energy_smem(chunk, rp.mpad);
         if (sm_sel > 200 * 1024 || sm_en > 200 * 1024) s = fail(RL_ERR_INVALID_ARG, "configuration needs too much shared memory");
     }
     if (s != RL_OK) {
@@ -510,8 +544,168 @@ extern "C" rl_status rl_reloc_debug(rl_reloc *r, int32_t qi, double *hyp_pose, i
 }
 
 // ---------------------------------------------------------------------------
-// Cascade (Sec. 3.2.5)
+// Cascade (Sec. 3.2.5).  All levels of all frames are enqueued together
+// (one CUDA graph per batch size): level l runs on every frame; its
+// decision kernel copies each still-open frame's result to the cascade
+// output and, when the frame's score is within tau_l (or l is the last
+// level), closes it by turning its descriptors of every later level into
+// an empty 0x0 frame, on which later levels do no work.  No host round trip
+// happens between levels.
 // ---------------------------------------------------------------------------
+namespace rl {
+
+struct LaterFrames {
+    Frame *f[8];
+    int n;
+};
+
+__global__ void k_subsample_all(const Frame *__restrict__ full, const int32_t *__restrict__ done,
+                                int s_factor, float *dd, uint8_t *dc, int max_hw) {
+    const int b = blockIdx.y;
+    if (done[b]) return;
+    const Frame f = full[b];
+    const int W2 = (f.W + s_factor - 1) / s_factor, H2 = (f.H + s_factor - 1) / s_factor;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= W2 * H2) return;
+    const int sp = ((p / W2) * s_factor) * f.W + (p % W2) * s_factor;
+    dd[(size_t)b * max_hw + p] = f.depth[sp];
+    uint8_t *o = dc + ((size_t)b * max_hw + p) * 3;
+    o[0] = f.rgb[sp * 3 + 0];
+    o[1] = f.rgb[sp * 3 + 1];
+    o[2] = f.rgb[sp * 3 + 2];
+}
+
+__global__ void k_cascade_decide(QueryState lq, CascadeOut co, LaterFrames later, float tau, int level,
+                                 int last, int n) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n || co.done[b]) return;
+    const DevResult r = ((const DevResult *)lq.result_blob)[b];
+    co.res[b] = r;
+    co.level[b] = level;
+    const int nc = r.n_chosen > 0 ? r.n_chosen : 0;
+    for (int c = 0; c < nc; ++c) {
+        for (int k = 0; k < 12; ++k)
+            co.chosen_pose[((size_t)b * 16 + c) * 12 + k] = lq.chosen_pose[((size_t)b * 16 + c) * 12 + k];
+        co.chosen_energy[(size_t)b * 16 + c] = lq.chosen_energy[(size_t)b * 16 + c];
+        co.chosen_score[(size_t)b * 16 + c] = lq.chosen_score[(size_t)b * 16 + c];
+        co.chosen_slot[(size_t)b * 16 + c] = lq.chosen_slot[(size_t)b * 16 + c];
+    }
+    // fall back iff the output pose's score exceeds tau (Sec. 3.2.5)
+    const bool accept = last || (r.status == RL_POSE_FOUND && r.score <= tau);
+    if (!accept) return;
+    co.done[b] = 1;
+    for (int k = 0; k < later.n; ++k) {
+        later.f[k][b].W = 0;
+        later.f[k][b].H = 0;
+    }
+}
+
+static rl_status cascade_enqueue(rl_cascade *c, int n, cudaStream_t s) {
+    const int L = (int)c->levels.size();
+    RL_CK(cudaMemsetAsync(c->out.done, 0, sizeof(int32_t) * n, s));
+    for (int l = 0; l < L; ++l) {
+        rl_reloc *r = c->levels[l];
+        const int sf = c->subsample[l];
+        if (sf > 1) {
+            const int hw = r->max_w * r->max_h;
+            dim3 grid((hw + 255) / 256, n);
+            k_subsample_all<<<grid, 256, 0, s>>>(c->full_dev, c->out.done, sf, r->stage_depth,
+                                                 r->stage_rgb, hw);
+            RL_LAUNCH_CK();
+        }
+        RL_TRY(run_relocalise(r, n, l, s));
+        LaterFrames later{};
+        for (int k = l + 1; k < L && later.n < 8; ++k) later.f[later.n++] = c->levels[k]->q.frames;
+        const float tau = l < L - 1 ? (float)c->thresholds[l] : INFINITY;
+        k_cascade_decide<<<(n + 127) / 128, 128, 0, s>>>(r->q, c->out, later, tau, l, l == L - 1, n);
+        RL_LAUNCH_CK();
+    }
+    return RL_OK;
+}
+
+static rl_status cascade_launch(rl_cascade *c, int n, cudaStream_t s) {
+    bool prof = false;
+    for (rl_reloc *r : c->levels) prof = prof || r->prof.on;
+    if (prof || !c->use_graphs) return cascade_enqueue(c, n, s);
+    for (auto &g : c->graphs)
+        if (g.n == n) {
+            RL_CK(cudaGraphLaunch(g.exec, s));
+            return RL_OK;
+        }
+    if (!c->capture_stream) RL_CK(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+    RL_CK(cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal));
+    rl_status st = cascade_enqueue(c, n, c->capture_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->capture_stream, &g);
+    if (st != RL_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+    if (c->graphs.size() >= 8) {
+        cudaGraphExecDestroy(c->graphs.front().exec);
+        c->graphs.erase(c->graphs.begin());
+    }
+    c->graphs.push_back({n, exec});
+    RL_CK(cudaGraphLaunch(exec, s));
+    return RL_OK;
+}
+
+static rl_status cascade_fetch(rl_cascade *c, int n, cudaStream_t s, rl_result *out) {
+    std::vector<DevResult> res(n);
+    std::vector<double> cp((size_t)n * 16 * 12);
+    std::vector<float> ce((size_t)n * 16), cs((size_t)n * 16);
+    std::vector<int32_t> cslot((size_t)n * 16), lvl(n);
+    RL_CK(cudaMemcpyAsync(res.data(), c->out.res, sizeof(DevResult) * n, cudaMemcpyDeviceToHost, s));
+    RL_CK(cudaMemcpyAsync(cp.data(), c->out.chosen_pose, cp.size() * 8, cudaMemcpyDeviceToHost, s));
+    RL_CK(cudaMemcpyAsync(ce.data(), c->out.chosen_energy, ce.size() * 4, cudaMemcpyDeviceToHost, s));
+    RL_CK(cudaMemcpyAsync(cs.data(), c->out.chosen_score, cs.size() * 4, cudaMemcpyDeviceToHost, s));
+    RL_CK(cudaMemcpyAsync(cslot.data(), c->out.chosen_slot, cslot.size() * 4, cudaMemcpyDeviceToHost, s));
+    RL_CK(cudaMemcpyAsync(lvl.data(), c->out.level, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    RL_CK(cudaStreamSynchronize(s));
+    for (rl_reloc *r : c->levels)
+        if (!r->prof.pending.empty()) prof_resolve(r);
+    for (int i = 0; i < n; ++i) {
+        const DevResult &d = res[i];
+        rl_result &o = out[i];
+        memset(&o, 0, sizeof(o));
+        for (int k = 0; k < 12; ++k) o.pose[k] = d.pose[k];
+        o.pose[15] = 1.0;
+        o.energy = d.energy;
+        o.energy_per_pixel = d.energy_per_pixel;
+        o.score = d.score;
+        o.level = lvl[i];
+        o.n_hypotheses = d.n_hypotheses;
+        o.n_chosen = std::max(0, d.n_chosen);
+        o.n_pixels = d.n_pixels;
+        o.status = d.status;
+        o.best = d.best;
+        for (int k = 0; k < o.n_chosen && k < RL_MAX_CHOSEN; ++k) {
+            for (int j = 0; j < 12; ++j) o.chosen_pose[k][j] = cp[((size_t)i * 16 + k) * 12 + j];
+            o.chosen_pose[k][15] = 1.0;
+            o.chosen_energy[k] = ce[(size_t)i * 16 + k];
+            o.chosen_score[k] = cs[(size_t)i * 16 + k];
+            o.chosen_slot[k] = cslot[(size_t)i * 16 + k];
+        }
+    }
+    return RL_OK;
+}
+
+static void cascade_release(rl_cascade *c) {
+    for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+    c->capture_stream = nullptr;
+    for (void *p : c->allocs) arena_free(c->ctx, p);
+    c->allocs.clear();
+}
+
+}  // namespace rl
+
 extern "C" rl_status rl_cascade_create(rl_reloc *const *levels, const double *thresholds,
                                        const int32_t *subsample, int32_t n_levels,
                                        rl_cascade **out) {
@@ -523,41 +717,53 @@ extern "C" rl_status rl_cascade_create(rl_reloc *const *levels, const double *th
         if (levels[l]->forest != levels[0]->forest)
             return fail(RL_ERR_INVALID_ARG, "cascade levels must share one forest");
         if (subsample && subsample[l] < 1) return fail(RL_ERR_INVALID_ARG, "subsample must be >= 1");
+        for (int k = 0; k < l; ++k)
+            if (levels[k] == levels[l]) return fail(RL_ERR_INVALID_ARG, "each level needs its own relocaliser");
     }
+    if (subsample && subsample[n_levels - 1] != 1)
+        return fail(RL_ERR_INVALID_ARG, "the last level works at full resolution (subsample 1)");
     rl_cascade *c = new rl_cascade();
+    c->ctx = levels[0]->forest->ctx;
+    c->max_batch = levels[0]->max_batch;
     for (int l = 0; l < n_levels; ++l) {
         c->levels.push_back(levels[l]);
         c->subsample.push_back(subsample ? subsample[l] : 1);
         if (l < n_levels - 1) c->thresholds.push_back(thresholds[l]);
-        levels[l]->refcount++;
+        c->max_batch = std::min(c->max_batch, levels[l]->max_batch);
     }
+    const uint64_t B = c->max_batch;
+    rl_status s = RL_OK;
+    auto A = [&](auto **ptr, uint64_t cnt) {
+        if (s == RL_OK) s = alloc_n(c->ctx, cnt, ptr);
+        if (s == RL_OK) c->allocs.push_back(*ptr);
+    };
+    A(&c->out.res, B);
+    A(&c->out.chosen_pose, B * 16 * 12);
+    A(&c->out.chosen_energy, B * 16);
+    A(&c->out.chosen_score, B * 16);
+    A(&c->out.chosen_slot, B * 16);
+    A(&c->out.level, B);
+    A(&c->out.done, B);
+    A(&c->full_dev, B);
+    if (s != RL_OK) {
+        cascade_release(c);
+        delete c;
+        return s;
+    }
+    for (int l = 0; l < n_levels; ++l) levels[l]->refcount++;
     *out = c;
     return RL_OK;
 }
 
 extern "C" rl_status rl_cascade_destroy(rl_cascade *c) {
     if (!c) return fail(RL_ERR_INVALID_ARG, "null cascade");
+    cudaSetDevice(c->ctx->device);
+    cudaDeviceSynchronize();
     for (rl_reloc *r : c->levels) r->refcount--;
+    cascade_release(c);
     delete c;
     return RL_OK;
 }
-
-namespace rl {
-__global__ void k_subsample(const Frame *src, int s_factor, float *dd, uint8_t *dc, int max_hw,
-                            const int32_t *sel) {
-    const int b = blockIdx.y;
-    const Frame f = src[sel[b]];
-    const int W2 = (f.W + s_factor - 1) / s_factor, H2 = (f.H + s_factor - 1) / s_factor;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= W2 * H2) return;
-    const int x = (p % W2) * s_factor, y = (p / W2) * s_factor;
-    const int sp = y * f.W + x;
-    dd[(size_t)b * max_hw + p] = f.depth[sp];
-    dc[((size_t)b * max_hw + p) * 3 + 0] = f.rgb[sp * 3 + 0];
-    dc[((size_t)b * max_hw + p) * 3 + 1] = f.rgb[sp * 3 + 1];
-    dc[((size_t)b * max_hw + p) * 3 + 2] = f.rgb[sp * 3 + 2];
-}
-}  // namespace rl
 
 extern "C" rl_status rl_cascade_relocalise_batch(rl_cascade *c, int32_t n, const float *depth,
                                                  const uint8_t *rgb, const rl_intrinsics *K,
@@ -566,32 +772,17 @@ extern "C" rl_status rl_cascade_relocalise_batch(rl_cascade *c, int32_t n, const
     if (!c || !out) return fail(RL_ERR_INVALID_ARG, "null argument");
     rl_reloc *top = c->levels.back();
     RL_TRY(check_call(top, n, depth, rgb, K, seeds));
-    for (rl_reloc *r : c->levels)
-        if (n > r->max_batch) return fail(RL_ERR_INVALID_ARG, "batch larger than a level's max_batch");
-    RL_CK(cudaSetDevice(top->forest->ctx->device));
+    if (n > c->max_batch) return fail(RL_ERR_INVALID_ARG, "batch larger than a level's max_batch");
+    RL_CK(cudaSetDevice(c->ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
-    // full-resolution inputs live in the last level's staging area
+    // full-resolution frames: staged into (or pointing at) the last level's inputs
     RL_TRY(stage_inputs(top, n, depth, rgb, K, seeds, mem, s));
     std::vector<Frame> full(top->host_frames, top->host_frames + n);
-    Frame *full_dev = nullptr;
-    int32_t *sel_dev = nullptr;
-    rl_ctx *ctx = top->forest->ctx;
-    RL_TRY(alloc_n(ctx, (uint64_t)n, &full_dev));
-    rl_status st = alloc_n(ctx, (uint64_t)n, &sel_dev);
-    if (st == RL_OK && cudaMemcpyAsync(full_dev, full.data(), sizeof(Frame) * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
-        st = fail(RL_ERR_CUDA, "frame copy failed");
-    std::vector<int32_t> pending(n);
-    for (int i = 0; i < n; ++i) pending[i] = i;
-    std::vector<rl_result> tmp(n);
+    RL_CK(cudaMemcpyAsync(c->full_dev, full.data(), sizeof(Frame) * n, cudaMemcpyHostToDevice, s));
     const int L = (int)c->levels.size();
-    for (int l = 0; l < L && st == RL_OK && !pending.empty(); ++l) {
+    for (int l = 0; l < L - 1; ++l) {
         rl_reloc *r = c->levels[l];
-        const int m = (int)pending.size();
         const int sf = c->subsample[l];
-        if (cudaMemcpyAsync(sel_dev, pending.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, s) != cudaSuccess) {
-            st = fail(RL_ERR_CUDA, "selection copy failed");
-            break;
-        }
         rl_intrinsics Kl = *K;
         Kl.width = (K->width + sf - 1) / sf;
         Kl.height = (K->height + sf - 1) / sf;
@@ -599,57 +790,24 @@ extern "C" rl_status rl_cascade_relocalise_batch(rl_cascade *c, int32_t n, const
         Kl.fy = (float)((double)K->fy / sf);
         Kl.cx = (float)((double)K->cx / sf);
         Kl.cy = (float)((double)K->cy / sf);
-        if (Kl.width > r->max_w || Kl.height > r->max_h) {
-            st = fail(RL_ERR_INVALID_ARG, "level input larger than the level's maximum size");
-            break;
-        }
-        const int hw_l = Kl.width * Kl.height;
-        if (sf == 1) {
-            // full-resolution level: descriptors point at the staged frames
-            for (int i = 0; i < m; ++i) {
-                Frame &f = r->host_frames[i];
-                f = full[pending[i]];
-            }
-        } else {
-            if (r == top) {
-                st = fail(RL_ERR_INVALID_ARG, "the last level object cannot also be a subsampled level");
-                break;
-            }
-            const int hwmax_r = r->max_w * r->max_h;
-            dim3 grid((hw_l + 255) / 256, m);
-            k_subsample<<<grid, 256, 0, s>>>(full_dev, sf, r->stage_depth, r->stage_rgb, hwmax_r, sel_dev);
-            if (cudaGetLastError() != cudaSuccess) {
-                st = fail(RL_ERR_CUDA, "subsample launch failed");
-                break;
-            }
-            for (int i = 0; i < m; ++i) {
-                Frame &f = r->host_frames[i];
-                f = full[pending[i]];
-                f.depth = r->stage_depth + (size_t)hwmax_r * i;
-                f.rgb = r->stage_rgb + (size_t)hwmax_r * 3 * i;
+        if (Kl.width > r->max_w || Kl.height > r->max_h)
+            return fail(RL_ERR_INVALID_ARG, "level input larger than the level's maximum size");
+        const int hw = r->max_w * r->max_h;
+        for (int i = 0; i < n; ++i) {
+            Frame &f = r->host_frames[i];
+            f = full[i];
+            if (sf > 1) {
+                f.depth = r->stage_depth + (size_t)hw * i;
+                f.rgb = r->stage_rgb + (size_t)hw * 3 * i;
                 f.fx = Kl.fx; f.fy = Kl.fy; f.cx = Kl.cx; f.cy = Kl.cy;
                 f.W = Kl.width; f.H = Kl.height;
             }
         }
-        if (cudaMemcpyAsync(r->q.frames, r->host_frames, sizeof(Frame) * m, cudaMemcpyHostToDevice, s) != cudaSuccess)
-            st = fail(RL_ERR_CUDA, "frame copy failed");
-        if (st == RL_OK) st = launch_relocalise(r, m, l, s);
-        if (st == RL_OK) st = fetch_results(r, m, s, tmp.data(), l);
-        r->last_batch = m;
-        if (st != RL_OK) break;
-        std::vector<int32_t> next;
-        for (int i = 0; i < m; ++i) {
-            const int qi = pending[i];
-            out[qi] = tmp[i];
-            // fall back iff the output pose's score exceeds the level threshold
-            const bool accept = tmp[i].status == RL_POSE_FOUND && (double)tmp[i].score <= c->thresholds[l];
-            if (l < L - 1 && !accept) next.push_back(qi);
-        }
-        pending.swap(next);
+        RL_CK(cudaMemcpyAsync(r->q.frames, r->host_frames, sizeof(Frame) * n, cudaMemcpyHostToDevice, s));
     }
-    arena_free(ctx, full_dev);
-    arena_free(ctx, sel_dev);
-    return st;
+    RL_TRY(cascade_launch(c, n, s));
+    for (rl_reloc *r : c->levels) r->last_batch = n;
+    return cascade_fetch(c, n, s, out);
 }
 
 extern "C" rl_status rl_cascade_relocalise(rl_cascade *c, const float *depth, const uint8_t *rgb,

@@ -36,6 +36,52 @@ __device__ __forceinline__ void mode_at(const ModeView &mv, const uint16_t *lv, 
     *rank = 0;
 }
 
+// Per-pixel record for forests of at most kRecTrees trees: the leaf reached
+// in each tree (uint16) and that leaf's min(modes, k_top) (uint8), so M(u)
+// is enumerated from one 16-byte load.
+
+__device__ __forceinline__ int rec_leaf(const uint4 &r, int t) {
+    const uint32_t w = t < 2 ? r.x : (t < 4 ? r.y : r.z);
+    return (t & 1) ? (int)(w >> 16) : (int)(w & 0xFFFFu);
+}
+
+__device__ __forceinline__ int rec_count(const uint4 &r, int t) {
+    // counts of trees 0..3 in r.w, tree 4 in the high half of r.z
+    return t < 4 ? (int)((r.w >> (8 * t)) & 255u) : (int)((r.z >> 16) & 255u);
+}
+
+__device__ __forceinline__ uint4 make_rec(const int leaf[kRecTrees], const int cnt[kRecTrees], int T) {
+    uint4 r = make_uint4(0, 0, 0, 0);
+    for (int t = 0; t < T; ++t) {
+        const uint32_t l = (uint32_t)leaf[t] & 0xFFFFu;
+        if (t == 0) r.x |= l;
+        if (t == 1) r.x |= l << 16;
+        if (t == 2) r.y |= l;
+        if (t == 3) r.y |= l << 16;
+        if (t == 4) r.z |= l;
+        const uint32_t c = (uint32_t)cnt[t] & 255u;
+        if (t < 4) r.w |= c << (8 * t);
+        else r.z |= c << 16;
+    }
+    return r;
+}
+
+// m-th element of M(u) from the pixel record -> (global leaf, rank).
+__device__ __forceinline__ void mode_at_rec(const uint4 &rec, int n_trees, int leaves_per_tree, int m,
+                                            uint32_t *L, int *rank) {
+    for (int t = 0; t < n_trees; ++t) {
+        const int nm = rec_count(rec, t);
+        if (m < nm) {
+            *L = (uint32_t)(t * leaves_per_tree + rec_leaf(rec, t));
+            *rank = m;
+            return;
+        }
+        m -= nm;
+    }
+    *L = 0;
+    *rank = 0;
+}
+
 // Decoded mode position: FP32 leaf centroid + FP16 offset (FP32 add), or
 // the stored FP32 position.
 __device__ __forceinline__ float3 mode_pos(const ModeView &mv, uint32_t L, int rank) {

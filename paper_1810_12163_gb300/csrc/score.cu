@@ -39,31 +39,22 @@ __global__ void __launch_bounds__(128) k_energy(EnergyArgs a) {
     const int p0 = blockIdx.y * a.chunk;
     if (p0 >= a.n_pix) return;
     const int np = min(a.chunk, a.n_pix - p0);
-    const uint16_t *lv = a.leaves + (size_t)b * a.p.n_trees * a.hw_max;
-    const int32_t *pix = a.pix + (size_t)b * a.max_pix + p0;
     const float4 *xc = a.xc + (size_t)b * a.max_pix + p0;
-
+    const size_t row0 = (size_t)b * a.max_pix + p0;   // first table row of the chunk
     for (int i = threadIdx.x; i < np; i += blockDim.x) {
-        const int q = pix[i];
         s_xc[i] = xc[i];
-        s_cnt[i] = q < 0 ? 0 : mode_count(a.mv, lv, a.hw_max, q, a.p.n_trees, a.p.k_top);
+        s_cnt[i] = a.q_tab_cnt[row0 + i];
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < np * a.maxm; e += blockDim.x) {
-        const int i = e / a.maxm, m = e % a.maxm;
-        if (m >= s_cnt[i]) continue;
-        uint32_t L;
-        int rank;
-        mode_at(a.mv, lv, a.hw_max, pix[i], a.p.n_trees, a.p.k_top, m, &L, &rank);
-        const float3 mp = mode_pos(a.mv, L, rank);
-        const size_t me = (size_t)L * a.mv.m_max + rank;
+    // the chunk's rows of the mode table are contiguous: coalesced copy
+    const int mpad = a.p.mpad;
+    const float4 *tb0 = a.q_tab0 + row0 * mpad;
+    const float4 *tb1 = a.q_tab1 + row0 * mpad;
+    const float *tb2 = a.q_tab2 + row0 * mpad;
+    for (int e = threadIdx.x; e < np * mpad; e += blockDim.x) {
+        s_m0[e] = tb0[e];
         if (a.p.use_cov) {
-            const float4 u0 = a.mv.mU[2 * me], u1 = a.mv.mU[2 * me + 1];
-            s_m0[e] = make_float4(mp.x, mp.y, mp.z, u0.x);
-            s_m1[e] = make_float4(u0.y, u0.z, u0.w, u1.x);
-            s_m2[e] = u1.y;
-        } else {
-            s_m0[e] = make_float4(mp.x, mp.y, mp.z, 1.f);
+            s_m1[e] = tb1[e];
+            s_m2[e] = tb2[e];
         }
     }
     __syncthreads();
@@ -466,6 +457,281 @@ __global__ void __launch_bounds__(128) k_lm(LmArgs a) {
 // (frame, chosen pose); partial sums in a fixed order.
 // ---------------------------------------------------------------------------
 
+// LM with the pixel set staged in shared memory.  A block holds LM_WARPS
+// hypotheses of one frame (a warp each); every LM iteration walks the pixel
+// set in tiles of 32 (lane i <-> pixel tile + i, the same order as one warp
+// striding alone), each tile's modes decoded once into shared memory and
+// read by every warp of the block.  Warps stop independently; the block
+// keeps iterating while any warp is active.
+constexpr int LM_WARPS = 8;
+constexpr int LM_TILE = 32;
+
+__global__ void __launch_bounds__(LM_WARPS * 32) k_lm_tiled(LmArgs a) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int stride = a.p.mpad;                           // odd: conflict-free float4 rows
+    float4 *s_m0 = (float4 *)smem;                         // [TILE][stride] mu.xyz, U00
+    float4 *s_m1 = s_m0 + LM_TILE * stride;                // [TILE][stride] U01 U02 U11 U12
+    float *s_m2 = (float *)(s_m1 + LM_TILE * stride);      // [TILE][stride] U22
+    float4 *s_xc = (float4 *)(s_m2 + LM_TILE * stride + 4);  // [TILE]
+    int *s_cnt = (int *)(s_xc + LM_TILE);                  // [TILE]
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int b = blockIdx.y;
+    const int n = a.q.n_cur[b];
+    if (!round_active(n, a.p) || (int)blockIdx.x * LM_WARPS >= n) return;
+    const int h = blockIdx.x * LM_WARPS + warp;
+    bool active = h < n;
+    const int NC = a.p.n_cull;
+    double *Pg = a.q.cur_pose + ((size_t)b * NC + (active ? h : 0)) * 12;
+    double H[12];
+    for (int k = 0; k < 12; ++k) H[k] = active ? Pg[k] : 0.0;
+    const size_t row0 = (size_t)b * a.p.max_pix;           // first mode-table row of the frame
+    const float4 *xcs = a.q.xc + row0;
+    const float4 *t0 = a.q.tab0 + row0 * stride;
+    const float4 *t1 = a.q.tab1 + row0 * stride;
+    const float *t2 = a.q.tab2 + row0 * stride;
+    const int16_t *tcnt = a.q.tab_cnt + row0;
+    int32_t *corr = a.q.corr + ((size_t)b * NC + (active ? h : 0)) * a.p.max_pix;
+    const float thr2 = (float)(a.p.lm_inlier_thresh * a.p.lm_inlier_thresh);
+    const bool cov = a.p.use_cov;
+    double lambda = a.p.lm_lambda0;
+    unsigned w_pairs = 0, w_modes = 0, w_in = 0, w_trial = 0;
+    for (int it = 0; it < a.p.lm_max_iter; ++it) {
+        if (!__syncthreads_or(active)) break;
+        const float r00 = (float)H[0], r01 = (float)H[1], r02 = (float)H[2], tx = (float)H[3];
+        const float r10 = (float)H[4], r11 = (float)H[5], r12 = (float)H[6], ty = (float)H[7];
+        const float r20 = (float)H[8], r21 = (float)H[9], r22 = (float)H[10], tz = (float)H[11];
+        float acc[28];
+#pragma unroll
+        for (int k = 0; k < 28; ++k) acc[k] = 0.f;
+        int nin = 0;
+        for (int t0p = 0; t0p < a.n_pix; t0p += LM_TILE) {
+            const int np = min(LM_TILE, a.n_pix - t0p);
+            // stage the tile: its mode-table rows are contiguous
+            for (int i = threadIdx.x; i < np; i += blockDim.x) {
+                s_xc[i] = xcs[t0p + i];
+                s_cnt[i] = tcnt[t0p + i];
+            }
+            const size_t off = (size_t)t0p * stride;
+            for (int e = threadIdx.x; e < np * stride; e += blockDim.x) {
+                s_m0[e] = t0[off + e];
+                if (cov) {
+                    s_m1[e] = t1[off + e];
+                    s_m2[e] = t2[off + e];
+                }
+            }
+            __syncthreads();
+            if (active && lane < np) {
+                const int cnt = s_cnt[lane];
+                int best_m = -1;
+                if (cnt > 0) {
+                    ++w_pairs;
+                    w_modes += cnt;
+                    const float4 x = s_xc[lane];
+                    const float y0 = fmaf(r00, x.x, fmaf(r01, x.y, fmaf(r02, x.z, tx)));
+                    const float y1 = fmaf(r10, x.x, fmaf(r11, x.y, fmaf(r12, x.z, ty)));
+                    const float y2 = fmaf(r20, x.x, fmaf(r21, x.y, fmaf(r22, x.z, tz)));
+                    const int base = lane * stride;
+                    float best = INFINITY;
+                    int bm = -1;
+                    if (cov) {
+                        for (int m = 0; m < cnt; ++m) {
+                            const float4 m0 = s_m0[base + m], m1 = s_m1[base + m];
+                            const float u22 = s_m2[base + m];
+                            const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+                            const float w0 = fmaf(m0.w, v0, fmaf(m1.x, v1, m1.y * v2));
+                            const float w1 = fmaf(m1.z, v1, m1.w * v2);
+                            const float w2 = u22 * v2;
+                            const float d2 = fmaf(w0, w0, fmaf(w1, w1, w2 * w2));
+                            if (d2 < best) {
+                                best = d2;
+                                bm = m;
+                            }
+                        }
+                    } else {
+                        for (int m = 0; m < cnt; ++m) {
+                            const float4 m0 = s_m0[base + m];
+                            const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+                            const float d2 = fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
+                            if (d2 < best) {
+                                best = d2;
+                                bm = m;
+                            }
+                        }
+                    }
+                    if (bm >= 0) {
+                        const float4 m0 = s_m0[base + bm];
+                        const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+                        if (fmaf(v0, v0, fmaf(v1, v1, v2 * v2)) <= thr2) {
+                            best_m = bm;
+                            ++nin;
+                            ++w_in;
+                            float U00 = 1.f, U01 = 0.f, U02 = 0.f, U11 = 1.f, U12 = 0.f, U22 = 1.f;
+                            if (cov) {
+                                const float4 m1 = s_m1[base + bm];
+                                U00 = m0.w; U01 = m1.x; U02 = m1.y; U11 = m1.z; U12 = m1.w;
+                                U22 = s_m2[base + bm];
+                            }
+                            const float j0[6] = {U00, U01, U02, U02 * y1 - U01 * y2,
+                                                 U00 * y2 - U02 * y0, U01 * y0 - U00 * y1};
+                            const float j1[6] = {0.f, U11, U12, U12 * y1 - U11 * y2, -U12 * y0, U11 * y0};
+                            const float j2[6] = {0.f, 0.f, U22, U22 * y1, -U22 * y0, 0.f};
+                            const float rr0 = fmaf(U00, v0, fmaf(U01, v1, U02 * v2));
+                            const float rr1 = fmaf(U11, v1, U12 * v2);
+                            const float rr2 = U22 * v2;
+                            int k = 0;
+#pragma unroll
+                            for (int r = 0; r < 6; ++r)
+#pragma unroll
+                                for (int c = r; c < 6; ++c, ++k)
+                                    acc[k] = fmaf(j0[r], j0[c], fmaf(j1[r], j1[c], fmaf(j2[r], j2[c], acc[k])));
+#pragma unroll
+                            for (int r = 0; r < 6; ++r)
+                                acc[21 + r] = fmaf(j0[r], rr0, fmaf(j1[r], rr1, fmaf(j2[r], rr2, acc[21 + r])));
+                            acc[27] = fmaf(rr0, rr0, fmaf(rr1, rr1, fmaf(rr2, rr2, acc[27])));
+                        }
+                    }
+                }
+                corr[t0p + lane] = best_m;   // local mode index into the pixel's table row
+            }
+            __syncthreads();
+        }
+        if (!active) continue;
+#pragma unroll
+        for (int k = 0; k < 28; ++k) acc[k] = warp_sum(acc[k]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nin += __shfl_xor_sync(0xffffffffu, nin, o);
+        if (nin < 3) {
+            active = false;
+            continue;
+        }
+        int status = 0;
+        double Hn[12];
+        if (lane == 0) {
+            double A[36], rhs[6], step[6];
+            int k = 0;
+            for (int r = 0; r < 6; ++r)
+                for (int c = r; c < 6; ++c, ++k) A[6 * r + c] = A[6 * c + r] = (double)acc[k];
+            for (int r = 0; r < 6; ++r) {
+                A[6 * r + r] += lambda * (double)acc[r * 6 - r * (r - 1) / 2];
+                rhs[r] = -(double)acc[21 + r];
+            }
+            if (!chol_solve6(A, rhs, step)) {
+                status = 1;
+            } else {
+                double sn = 0.0;
+                for (int r = 0; r < 6; ++r) sn += step[r] * step[r];
+                if (sqrt(sn) < a.p.lm_stop) status = 1;
+            }
+            for (int i = 0; i < 12; ++i) Hn[i] = H[i];
+            if (!status) se3_left(step, Hn);
+        }
+        status = __shfl_sync(0xffffffffu, status, 0);
+        if (status) {
+            active = false;
+            continue;
+        }
+        for (int i = 0; i < 12; ++i) Hn[i] = __shfl_sync(0xffffffffu, Hn[i], 0);
+        __syncwarp();
+        // trial cost with the same correspondences, read from the mode table
+        const float s00 = (float)Hn[0], s01 = (float)Hn[1], s02 = (float)Hn[2], u0t = (float)Hn[3];
+        const float s10 = (float)Hn[4], s11 = (float)Hn[5], s12 = (float)Hn[6], u1t = (float)Hn[7];
+        const float s20 = (float)Hn[8], s21 = (float)Hn[9], s22 = (float)Hn[10], u2t = (float)Hn[11];
+        float trial = 0.f;
+#pragma unroll 4
+        for (int i = lane; i < a.n_pix; i += 32) {
+            const int m = corr[i];
+            if (m < 0) continue;
+            ++w_trial;
+            const float4 x = xcs[i];
+            const size_t e = (size_t)i * stride + m;
+            const float4 m0 = t0[e];
+            const float y0 = fmaf(s00, x.x, fmaf(s01, x.y, fmaf(s02, x.z, u0t)));
+            const float y1 = fmaf(s10, x.x, fmaf(s11, x.y, fmaf(s12, x.z, u1t)));
+            const float y2 = fmaf(s20, x.x, fmaf(s21, x.y, fmaf(s22, x.z, u2t)));
+            const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+            if (cov) {
+                const float4 m1 = t1[e];
+                const float u22 = t2[e];
+                const float r0 = fmaf(m0.w, v0, fmaf(m1.x, v1, m1.y * v2));
+                const float r1 = fmaf(m1.z, v1, m1.w * v2);
+                const float r2 = u22 * v2;
+                trial = fmaf(r0, r0, fmaf(r1, r1, fmaf(r2, r2, trial)));
+            } else {
+                trial = fmaf(v0, v0, fmaf(v1, v1, fmaf(v2, v2, trial)));
+            }
+        }
+        trial = warp_sum(trial);
+        if (trial < acc[27]) {
+            for (int i = 0; i < 12; ++i) H[i] = Hn[i];
+            lambda /= 10.0;
+        } else {
+            lambda *= 10.0;
+        }
+    }
+    if (h < n && lane == 0)
+        for (int k = 0; k < 12; ++k) Pg[k] = H[k];
+    if (a.work && h < n) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            w_pairs += __shfl_xor_sync(0xffffffffu, w_pairs, o);
+            w_modes += __shfl_xor_sync(0xffffffffu, w_modes, o);
+            w_in += __shfl_xor_sync(0xffffffffu, w_in, o);
+            w_trial += __shfl_xor_sync(0xffffffffu, w_trial, o);
+        }
+        if (lane == 0) {
+            atomicAdd(&a.work[W_LM_PAIRS], (unsigned long long)w_pairs);
+            atomicAdd(&a.work[W_LM_MODES], (unsigned long long)w_modes);
+            atomicAdd(&a.work[W_LM_INLIERS], (unsigned long long)w_in);
+            atomicAdd(&a.work[W_LM_TRIAL], (unsigned long long)w_trial);
+        }
+    }
+}
+
+size_t lm_tiled_smem(int mpad) {
+    return (size_t)LM_TILE * mpad * (2 * sizeof(float4) + sizeof(float)) + 16 +
+           LM_TILE * (sizeof(float4) + sizeof(int));
+}
+
+// Mode table of batch `batch`: for each drawn pixel, M(u) decoded to FP32
+// (position, Cholesky factor) into one row of mpad records.
+__global__ void k_build_table(QueryState q, int hw_max, ModeView mv, RParams p, int batch) {
+    const int b = blockIdx.y;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= p.eta * p.mpad) return;
+    const int i = batch * p.eta + e / p.mpad, m = e % p.mpad;
+    const size_t row = (size_t)b * p.max_pix + i;
+    const int pix = q.pix[row];
+    const int cnt = pix < 0 ? 0 : (int)q.mcount[(size_t)b * hw_max + pix];
+    if (m == 0) q.tab_cnt[row] = (int16_t)cnt;
+    if (m >= cnt) return;
+    uint32_t L;
+    int rank;
+    if (q.prec)
+        mode_at_rec(q.prec[(size_t)b * hw_max + pix], p.n_trees, mv.leaves_per_tree, m, &L, &rank);
+    else
+        mode_at(mv, q.leaves + (size_t)b * p.n_trees * hw_max, hw_max, pix, p.n_trees, p.k_top, m, &L, &rank);
+    const float3 mp = mode_pos(mv, L, rank);
+    const size_t me = (size_t)L * mv.m_max + rank;
+    const size_t o = row * p.mpad + m;
+    if (p.use_cov) {
+        const float4 u0 = mv.mU[2 * me], u1 = mv.mU[2 * me + 1];
+        q.tab0[o] = make_float4(mp.x, mp.y, mp.z, u0.x);
+        q.tab1[o] = make_float4(u0.y, u0.z, u0.w, u1.x);
+        q.tab2[o] = u1.y;
+    } else {
+        q.tab0[o] = make_float4(mp.x, mp.y, mp.z, 1.f);
+    }
+}
+
+rl_status launch_build_table(const QueryState &q, int hw_max, ModeView mv, const RParams &p, int batch,
+                             int n, cudaStream_t s) {
+    dim3 grid((p.eta * p.mpad + 255) / 256, n);
+    k_build_table<<<grid, 256, 0, s>>>(q, hw_max, mv, p, batch);
+    RL_LAUNCH_CK();
+    return RL_OK;
+}
+
 // z-depth of the first box face hit by the ray of pixel (u, v) (exit point
 // from inside the box, entry point from outside), in FP64.
 __device__ bool ray_depth64(const double *P, int u, int v, float fx, float fy, float cx, float cy,
@@ -502,15 +768,20 @@ __global__ void __launch_bounds__(256) k_raycast_score(RaycastArgs a) {
     const Frame fr = a.frames[b];
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const double *P = a.pose_of(b, c);
+    __shared__ float sPf[12];
+    if (threadIdx.x < 12) sPf[threadIdx.x] = (float)P[threadIdx.x];
+    __syncthreads();
     float sum = 0.f;
     int syn = 0, both = 0;
     if (p < fr.W * fr.H) {
         const int u = p % fr.W, v = p / fr.W;
-        const float dc0 = ((float)u - fr.cx) / fr.fx, dc1 = ((float)v - fr.cy) / fr.fy;
+        // fast approximate divisions: their few-ulp error is far inside the
+        // margin that sends a ray to the FP64 path
+        const float dc0 = __fdividef((float)u - fr.cx, fr.fx), dc1 = __fdividef((float)v - fr.cy, fr.fy);
         float d[3], o[3];
         for (int r = 0; r < 3; ++r) {
-            d[r] = fmaf((float)P[4 * r], dc0, fmaf((float)P[4 * r + 1], dc1, (float)P[4 * r + 2]));
-            o[r] = (float)P[4 * r + 3];
+            d[r] = fmaf(sPf[4 * r], dc0, fmaf(sPf[4 * r + 1], dc1, sPf[4 * r + 2]));
+            o[r] = sPf[4 * r + 3];
         }
         const float dn = fabsf(d[0]) + fabsf(d[1]) + fabsf(d[2]);
         float tn = -INFINITY, tf = INFINITY;
@@ -520,7 +791,7 @@ __global__ void __launch_bounds__(256) k_raycast_score(RaycastArgs a) {
                 unsure = true;
                 continue;
             }
-            const float inv = 1.0f / d[ax];
+            const float inv = __fdividef(1.0f, d[ax]);
             const float ta = (a.lo[ax] - o[ax]) * inv, tb = (a.hi[ax] - o[ax]) * inv;
             tn = fmaxf(tn, fminf(ta, tb));
             tf = fminf(tf, fmaxf(ta, tb));
@@ -599,11 +870,53 @@ __device__ float score_from_tiles(const double *part_sum, const int32_t *part_cn
 }
 
 // Eq. 7-8 per frame, then the frame's result record.
-__global__ void k_finalize(QueryState q, RParams p, int n_tiles, int ranked) {
+__global__ void __launch_bounds__(256) k_finalize(QueryState q, RParams p, int n_tiles, int ranked) {
+    __shared__ double s_sum[8];
+    __shared__ long long s_syn[8], s_both[8];
     const int b = blockIdx.x;
+    const Frame fr = q.frames[b];
+    if (ranked && q.n_hyp[b] > 0) {
+        // Eq. 7 for each chosen pose: tile partials summed by a fixed-shape
+        // block reduction (FP64 sums, integer counts)
+        const double npx = (double)fr.W * (double)fr.H;
+        for (int c = 0; c < q.n_chosen[b]; ++c) {
+            const size_t base = ((size_t)b * 16 + c) * n_tiles;
+            double sum = 0.0;
+            long long syn = 0, both = 0;
+            for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) {
+                sum += q.score_part[base + t];
+                syn += q.score_cnt[2 * (base + t)];
+                both += q.score_cnt[2 * (base + t) + 1];
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                sum += __shfl_down_sync(0xffffffffu, sum, o);
+                syn += __shfl_down_sync(0xffffffffu, syn, o);
+                both += __shfl_down_sync(0xffffffffu, both, o);
+            }
+            if ((threadIdx.x & 31) == 0) {
+                s_sum[threadIdx.x >> 5] = sum;
+                s_syn[threadIdx.x >> 5] = syn;
+                s_both[threadIdx.x >> 5] = both;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double ts = 0.0;
+                long long tsyn = 0, tb = 0;
+                for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+                    ts += s_sum[k];
+                    tsyn += s_syn[k];
+                    tb += s_both[k];
+                }
+                const double frac = (double)tsyn / npx;
+                q.chosen_score[(size_t)b * 16 + c] =
+                    (frac >= 0.1 && tb > 0) ? (float)(ts / (double)tb) : INFINITY;
+            }
+            __syncthreads();
+        }
+    }
     if (threadIdx.x != 0) return;
     DevResult *out = (DevResult *)q.result_blob + b;
-    const Frame fr = q.frames[b];
     out->n_hypotheses = q.n_hyp[b];
     out->n_chosen = q.n_hyp[b] > 0 ? q.n_chosen[b] : 0;
     out->n_pixels = q.n_pix[b];
@@ -621,11 +934,8 @@ __global__ void k_finalize(QueryState q, RParams p, int n_tiles, int ranked) {
     int best = -1;
     float bs = INFINITY;
     if (ranked) {
-        const double npx = (double)fr.W * (double)fr.H;
         for (int c = 0; c < q.n_chosen[b]; ++c) {
-            const float s = score_from_tiles(q.score_part, q.score_cnt, ((size_t)b * 16 + c) * n_tiles,
-                                             n_tiles, npx, nullptr);
-            q.chosen_score[(size_t)b * 16 + c] = s;
+            const float s = q.chosen_score[(size_t)b * 16 + c];
             if (s < bs) {
                 bs = s;
                 best = c;
@@ -673,9 +983,26 @@ rl_status launch_select(const SelectArgs &a, int n, cudaStream_t s) {
 }
 
 rl_status launch_lm(const LmArgs &a, int n, cudaStream_t s) {
-    dim3 grid((a.p.n_cull + 3) / 4, n);
-    k_lm<<<grid, 128, 0, s>>>(a);
+    const size_t sm = lm_tiled_smem(a.p.mpad);
+    if (sm <= kLmSmemMax) {
+        dim3 grid((a.p.n_cull + LM_WARPS - 1) / LM_WARPS, n);
+        k_lm_tiled<<<grid, LM_WARPS * 32, sm, s>>>(a);
+    } else {
+        dim3 grid((a.p.n_cull + 3) / 4, n);
+        k_lm<<<grid, 128, 0, s>>>(a);
+    }
     RL_LAUNCH_CK();
+    return RL_OK;
+}
+
+// Kernel attributes set once, outside any stream capture.
+rl_status prepare_kernels() {
+    static bool done = false;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> g(mu);
+    if (done) return RL_OK;
+    RL_CK(cudaFuncSetAttribute(k_lm_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLmSmemMax));
+    done = true;
     return RL_OK;
 }
 
@@ -688,7 +1015,7 @@ rl_status launch_raycast(const RaycastArgs &a, int n, int max_hw, cudaStream_t s
 
 rl_status launch_finalize(const QueryState &q, const RParams &p, int n_tiles, int ranked, int n,
                           cudaStream_t s) {
-    k_finalize<<<n, 32, 0, s>>>(q, p, n_tiles, ranked);
+    k_finalize<<<n, 256, 0, s>>>(q, p, n_tiles, ranked);
     RL_LAUNCH_CK();
     return RL_OK;
 }

@@ -184,6 +184,27 @@ def test_batch_invariance(rg, ctx, small):
     rel.close()
 
 
+def test_graph_replay_matches_direct_launches(rg, ctx, small):
+    """Captured-graph replay (default) and kernel-by-kernel launches give
+    bit-identical results, across batch sizes that need new captures."""
+    w, g = small
+    scene = rg.Scene(ctx, w.room().lo, w.room().hi)
+    rel = rg.Relocaliser(g, scene, w.ransac, w.width, w.height, 3)
+    qs = [w.query(q) for q in range(3)]
+    D = np.stack([q[0] for q in qs])
+    C = np.stack([q[1] for q in qs])
+    seeds = [q[3] for q in qs]
+    for n in (3, 1, 3):
+        rel.set_graphs(True)
+        a = rel.relocalise_batch(D[:n], C[:n], w.K, seeds[:n])
+        rel.set_graphs(False)
+        b = rel.relocalise_batch(D[:n], C[:n], w.K, seeds[:n])
+        for x, y in zip(a, b):
+            assert np.array_equal(x["pose"], y["pose"]) and x["energy"] == y["energy"]
+            assert np.array_equal(x["chosen_score"], y["chosen_score"])
+    rel.close()
+
+
 def test_no_depth_gives_no_pose(rg, ctx, small):
     w, g = small
     rel = rg.Relocaliser(g, None, dict(w.ransac, rank=0), w.width, w.height, 1)
