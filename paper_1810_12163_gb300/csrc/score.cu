@@ -688,6 +688,256 @@ __global__ void __launch_bounds__(LM_WARPS * 32) k_lm_tiled(LmArgs a) {
     }
 }
 
+// LM, hypotheses spread over threads.  A round's n hypotheses of a frame are
+// split over up to LM3_BPQ blocks; inside a block, thread t works for
+// hypothesis h = t % HB on the pixels g, g + G, ... (g = t / HB, G = 256/HB,
+// HB = the next power of two >= the block's hypothesis count).  As rounds
+// halve n, each hypothesis gets more threads.  Partial normal equations are
+// tree-reduced over the G groups in shared memory (fixed shape), the 6x6
+// system of each hypothesis is solved in FP64 by one thread, and the trial
+// cost with the same correspondences is reduced the same way.
+constexpr int LM3_THREADS = 256;
+constexpr int LM3_BPQ = 4;
+
+__device__ __forceinline__ void lm3_accumulate(float y0, float y1, float y2, float v0, float v1, float v2,
+                                               float U00, float U01, float U02, float U11, float U12,
+                                               float U22, float acc[28]) {
+    const float j0[6] = {U00, U01, U02, U02 * y1 - U01 * y2, U00 * y2 - U02 * y0, U01 * y0 - U00 * y1};
+    const float j1[6] = {0.f, U11, U12, U12 * y1 - U11 * y2, -U12 * y0, U11 * y0};
+    const float j2[6] = {0.f, 0.f, U22, U22 * y1, -U22 * y0, 0.f};
+    const float rr0 = fmaf(U00, v0, fmaf(U01, v1, U02 * v2));
+    const float rr1 = fmaf(U11, v1, U12 * v2);
+    const float rr2 = U22 * v2;
+    int k = 0;
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c = r; c < 6; ++c, ++k)
+            acc[k] = fmaf(j0[r], j0[c], fmaf(j1[r], j1[c], fmaf(j2[r], j2[c], acc[k])));
+#pragma unroll
+    for (int r = 0; r < 6; ++r) acc[21 + r] = fmaf(j0[r], rr0, fmaf(j1[r], rr1, fmaf(j2[r], rr2, acc[21 + r])));
+    acc[27] = fmaf(rr0, rr0, fmaf(rr1, rr1, fmaf(rr2, rr2, acc[27])));
+}
+
+__global__ void __launch_bounds__(LM3_THREADS, 2) k_lm_spread(LmArgs a) {
+    __shared__ float s_red[LM3_THREADS * 8];         // 8 partial values per thread per pass
+    __shared__ double s_H[64][12];                    // current pose per local hypothesis
+    __shared__ double s_Hn[64][12];                   // trial pose
+    __shared__ double s_lambda[64];
+    __shared__ float s_tot[64][28];
+    __shared__ int s_state[64];                       // 1 active, 0 stopped
+    __shared__ int s_nin[64];
+    const int b = blockIdx.y;
+    const int n = a.q.n_cur[b];
+    if (!round_active(n, a.p)) return;
+    // hypotheses of this block: [h0, h0 + nb)
+    const int per = (n + LM3_BPQ - 1) / LM3_BPQ;
+    const int h0 = blockIdx.x * per;
+    const int nb = min(per, n - h0);
+    if (nb <= 0) return;
+    int HB = 1;
+    while (HB < nb) HB <<= 1;
+    const int G = LM3_THREADS / HB;
+    const int t = threadIdx.x;
+    const int hl = t % HB, g = t / HB;
+    const bool mine = hl < nb;
+    const int NC = a.p.n_cull;
+    const size_t row0 = (size_t)b * a.p.max_pix;
+    const int stride = a.p.mpad;
+    const float4 *xcs = a.q.xc + row0;
+    const float4 *t0 = a.q.tab0 + row0 * stride;
+    const float4 *t1 = a.q.tab1 + row0 * stride;
+    const float *t2 = a.q.tab2 + row0 * stride;
+    const int16_t *tcnt = a.q.tab_cnt + row0;
+    // correspondences [pixel][nb] of this block's hypotheses (local mode index, -1 none)
+    int32_t *corr = a.q.corr + ((size_t)b * NC + h0) * a.p.max_pix;
+    const float thr2 = (float)(a.p.lm_inlier_thresh * a.p.lm_inlier_thresh);
+    const bool cov = a.p.use_cov;
+    for (int i = t; i < nb * 12; i += LM3_THREADS) s_H[i / 12][i % 12] = a.q.cur_pose[((size_t)b * NC + h0 + i / 12) * 12 + i % 12];
+    for (int i = t; i < nb; i += LM3_THREADS) {
+        s_lambda[i] = a.p.lm_lambda0;
+        s_state[i] = 1;
+    }
+    __syncthreads();
+    unsigned w_pairs = 0, w_modes = 0, w_in = 0, w_trial = 0;
+    for (int it = 0; it < a.p.lm_max_iter; ++it) {
+        const bool act = mine && s_state[hl];
+        if (!__syncthreads_or(act)) break;
+        float acc[28];
+#pragma unroll
+        for (int k = 0; k < 28; ++k) acc[k] = 0.f;
+        int nin = 0;
+        if (act) {
+            const float r00 = (float)s_H[hl][0], r01 = (float)s_H[hl][1], r02 = (float)s_H[hl][2], tx = (float)s_H[hl][3];
+            const float r10 = (float)s_H[hl][4], r11 = (float)s_H[hl][5], r12 = (float)s_H[hl][6], ty = (float)s_H[hl][7];
+            const float r20 = (float)s_H[hl][8], r21 = (float)s_H[hl][9], r22 = (float)s_H[hl][10], tz = (float)s_H[hl][11];
+            for (int i = g; i < a.n_pix; i += G) {
+                const int cnt = tcnt[i];
+                int best_m = -1;
+                if (cnt > 0) {
+                    ++w_pairs;
+                    w_modes += cnt;
+                    const float4 x = xcs[i];
+                    const float y0 = fmaf(r00, x.x, fmaf(r01, x.y, fmaf(r02, x.z, tx)));
+                    const float y1 = fmaf(r10, x.x, fmaf(r11, x.y, fmaf(r12, x.z, ty)));
+                    const float y2 = fmaf(r20, x.x, fmaf(r21, x.y, fmaf(r22, x.z, tz)));
+                    const size_t base = (size_t)i * stride;
+                    float best = INFINITY;
+                    if (cov) {
+                        for (int m = 0; m < cnt; ++m) {
+                            const float4 m0 = __ldg(&t0[base + m]), m1 = __ldg(&t1[base + m]);
+                            const float u22 = __ldg(&t2[base + m]);
+                            const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+                            const float w0 = fmaf(m0.w, v0, fmaf(m1.x, v1, m1.y * v2));
+                            const float w1 = fmaf(m1.z, v1, m1.w * v2);
+                            const float w2 = u22 * v2;
+                            const float d2 = fmaf(w0, w0, fmaf(w1, w1, w2 * w2));
+                            if (d2 < best) {
+                                best = d2;
+                                best_m = m;
+                            }
+                        }
+                    } else {
+                        for (int m = 0; m < cnt; ++m) {
+                            const float4 m0 = __ldg(&t0[base + m]);
+                            const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+                            const float d2 = fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
+                            if (d2 < best) {
+                                best = d2;
+                                best_m = m;
+                            }
+                        }
+                    }
+                    if (best_m >= 0) {
+                        const float4 m0 = __ldg(&t0[base + best_m]);
+                        const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+                        if (fmaf(v0, v0, fmaf(v1, v1, v2 * v2)) <= thr2) {
+                            ++nin;
+                            ++w_in;
+                            if (cov) {
+                                const float4 m1 = __ldg(&t1[base + best_m]);
+                                lm3_accumulate(y0, y1, y2, v0, v1, v2, m0.w, m1.x, m1.y, m1.z, m1.w,
+                                               __ldg(&t2[base + best_m]), acc);
+                            } else {
+                                lm3_accumulate(y0, y1, y2, v0, v1, v2, 1.f, 0.f, 0.f, 1.f, 0.f, 1.f, acc);
+                            }
+                        } else {
+                            best_m = -1;
+                        }
+                    }
+                }
+                corr[(size_t)i * nb + hl] = best_m;
+            }
+        }
+        // tree reduction of the 28 sums and the inlier count over the groups
+        for (int part = 0; part < 4; ++part) {
+            for (int k = 0; k < 7; ++k) s_red[t * 8 + k] = acc[part * 7 + k];
+            if (part == 0) s_red[t * 8 + 7] = __int_as_float(nin);
+            __syncthreads();
+            for (int s = G >> 1; s > 0; s >>= 1) {
+                if (g < s)
+                    for (int k = 0; k < 8; ++k) {
+                        if (k == 7 && part != 0) continue;
+                        const int o1 = t * 8 + k, o2 = (t + s * HB) * 8 + k;
+                        if (k == 7)
+                            s_red[o1] = __int_as_float(__float_as_int(s_red[o1]) + __float_as_int(s_red[o2]));
+                        else
+                            s_red[o1] += s_red[o2];
+                    }
+                __syncthreads();
+            }
+            if (g == 0 && mine) {
+                for (int k = 0; k < 7; ++k) s_tot[hl][part * 7 + k] = s_red[t * 8 + k];
+                if (part == 0) s_nin[hl] = __float_as_int(s_red[t * 8 + 7]);
+            }
+            __syncthreads();
+        }
+        // FP64 solve per active hypothesis
+        if (g == 0 && act) {
+            int status = s_nin[hl] < 3 ? 1 : 0;
+            double step[6];
+            if (!status) {
+                double A[36], rhs[6];
+                int k = 0;
+                for (int r = 0; r < 6; ++r)
+                    for (int c = r; c < 6; ++c, ++k) A[6 * r + c] = A[6 * c + r] = (double)s_tot[hl][k];
+                for (int r = 0; r < 6; ++r) {
+                    A[6 * r + r] += s_lambda[hl] * (double)s_tot[hl][r * 6 - r * (r - 1) / 2];
+                    rhs[r] = -(double)s_tot[hl][21 + r];
+                }
+                if (!chol_solve6(A, rhs, step)) {
+                    status = 1;
+                } else {
+                    double sn = 0.0;
+                    for (int r = 0; r < 6; ++r) sn += step[r] * step[r];
+                    if (sqrt(sn) < a.p.lm_stop) status = 1;
+                }
+            }
+            if (status) {
+                s_state[hl] = 0;
+            } else {
+                double Hn[12];
+                for (int i = 0; i < 12; ++i) Hn[i] = s_H[hl][i];
+                se3_left(step, Hn);
+                for (int i = 0; i < 12; ++i) s_Hn[hl][i] = Hn[i];
+            }
+        }
+        __syncthreads();
+        // trial cost with the same correspondences
+        const bool act2 = mine && s_state[hl];
+        float trial = 0.f;
+        if (act2) {
+            const float s00 = (float)s_Hn[hl][0], s01 = (float)s_Hn[hl][1], s02 = (float)s_Hn[hl][2], u0t = (float)s_Hn[hl][3];
+            const float s10 = (float)s_Hn[hl][4], s11 = (float)s_Hn[hl][5], s12 = (float)s_Hn[hl][6], u1t = (float)s_Hn[hl][7];
+            const float s20 = (float)s_Hn[hl][8], s21 = (float)s_Hn[hl][9], s22 = (float)s_Hn[hl][10], u2t = (float)s_Hn[hl][11];
+            for (int i = g; i < a.n_pix; i += G) {
+                const int m = corr[(size_t)i * nb + hl];
+                if (m < 0) continue;
+                ++w_trial;
+                const float4 x = xcs[i];
+                const size_t e = (size_t)i * stride + m;
+                const float4 m0 = __ldg(&t0[e]);
+                const float y0 = fmaf(s00, x.x, fmaf(s01, x.y, fmaf(s02, x.z, u0t)));
+                const float y1 = fmaf(s10, x.x, fmaf(s11, x.y, fmaf(s12, x.z, u1t)));
+                const float y2 = fmaf(s20, x.x, fmaf(s21, x.y, fmaf(s22, x.z, u2t)));
+                const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+                if (cov) {
+                    const float4 m1 = __ldg(&t1[e]);
+                    const float r0 = fmaf(m0.w, v0, fmaf(m1.x, v1, m1.y * v2));
+                    const float r1 = fmaf(m1.z, v1, m1.w * v2);
+                    const float r2 = __ldg(&t2[e]) * v2;
+                    trial = fmaf(r0, r0, fmaf(r1, r1, fmaf(r2, r2, trial)));
+                } else {
+                    trial = fmaf(v0, v0, fmaf(v1, v1, fmaf(v2, v2, trial)));
+                }
+            }
+        }
+        s_red[t * 8] = trial;
+        __syncthreads();
+        for (int s = G >> 1; s > 0; s >>= 1) {
+            if (g < s) s_red[t * 8] += s_red[(t + s * HB) * 8];
+            __syncthreads();
+        }
+        if (g == 0 && act2) {
+            if (s_red[t * 8] < s_tot[hl][27]) {
+                for (int i = 0; i < 12; ++i) s_H[hl][i] = s_Hn[hl][i];
+                s_lambda[hl] /= 10.0;
+            } else {
+                s_lambda[hl] *= 10.0;
+            }
+        }
+        __syncthreads();
+    }
+    for (int i = t; i < nb * 12; i += LM3_THREADS)
+        a.q.cur_pose[((size_t)b * NC + h0 + i / 12) * 12 + i % 12] = s_H[i / 12][i % 12];
+    if (a.work && mine) {
+        atomicAdd(&a.work[W_LM_PAIRS], (unsigned long long)w_pairs);
+        atomicAdd(&a.work[W_LM_MODES], (unsigned long long)w_modes);
+        atomicAdd(&a.work[W_LM_INLIERS], (unsigned long long)w_in);
+        atomicAdd(&a.work[W_LM_TRIAL], (unsigned long long)w_trial);
+    }
+}
+
 size_t lm_tiled_smem(int mpad) {
     return (size_t)LM_TILE * mpad * (2 * sizeof(float4) + sizeof(float)) + 16 +
            LM_TILE * (sizeof(float4) + sizeof(int));
@@ -984,7 +1234,10 @@ rl_status launch_select(const SelectArgs &a, int n, cudaStream_t s) {
 
 rl_status launch_lm(const LmArgs &a, int n, cudaStream_t s) {
     const size_t sm = lm_tiled_smem(a.p.mpad);
-    if (sm <= kLmSmemMax) {
+    if (a.p.n_cull <= 64) {
+        dim3 grid(LM3_BPQ, n);
+        k_lm_spread<<<grid, LM3_THREADS, 0, s>>>(a);
+    } else if (sm <= kLmSmemMax) {
         dim3 grid((a.p.n_cull + LM_WARPS - 1) / LM_WARPS, n);
         k_lm_tiled<<<grid, LM_WARPS * 32, sm, s>>>(a);
     } else {
