@@ -93,7 +93,7 @@ typedef struct {
  * table of Appendix B). */
 typedef struct {
     int32_t n_hyp;            /* maxPoseCandidates, N_max (<= 4096) */
-    int32_t max_iter;         /* maxCandidateGenerationIterations */
+    int32_t max_iter;         /* maxCandidateGenerationIterations, 1 .. 2^30 - 64 */
     int32_t n_cull;           /* maxPoseCandidatesAfterCull, N_cull (<= 64) */
     int32_t eta;              /* ransacInliersPerIteration (<= 1024) */
     int32_t k_out;            /* maxRelocalisationsToOutput (<= 16) */
@@ -281,14 +281,16 @@ rl_status rl_reloc_debug(rl_reloc *r, int32_t q, double *hyp_pose /* n_hyp*12 */
 /* ---- tracing ---------------------------------------------------------- */
 /* Per-kernel timing of a relocaliser: when enabled, every kernel launch of
  * its calls is bracketed by CUDA events on the caller's stream; durations
- * and launch counts accumulate per kernel (ids 0..8, names from
- * rl_kernel_name), and the scoring kernels count their work units
+ * and launch counts accumulate per kernel (ids 0..RL_N_KERNELS-1, names
+ * from rl_kernel_name), and the scoring kernels count their work units
  * (uint64 [7]: energy (H,px) pairs, energy (H,px,mode) triples, LM pass-1
  * (H,px) evaluations, LM (H,px,mode) triples, LM inlier accumulations,
  * LM trial evaluations, rays cast).  Enabling resets all counters.  The
  * paper has no counterpart; its Sec. A.1 timing breakdown is per stage. */
+#define RL_N_KERNELS 10
 rl_status rl_reloc_profile(rl_reloc *r, int32_t enable);
-rl_status rl_reloc_profile_read(rl_reloc *r, double *ms /* [9] */, int64_t *launches /* [9] */,
+rl_status rl_reloc_profile_read(rl_reloc *r, double *ms /* [RL_N_KERNELS] */,
+                                int64_t *launches /* [RL_N_KERNELS] */,
                                 uint64_t *work /* [7] */);
 const char *rl_kernel_name(int32_t kernel_id);
 

@@ -11,6 +11,7 @@ import ctypes
 import numpy as np
 
 from . import binding, presets  # noqa: F401
+from .binding import RL_N_KERNELS as N_KERNELS
 from .binding import (RL_DEVICE, RL_HOST, RL_NO_POSE, RL_POSE_FOUND,  # noqa: F401
                       ForestParams, Intrinsics, RansacParams, RelocError, Result, call, lib)
 
@@ -239,13 +240,13 @@ class Relocaliser:
         call("rl_reloc_profile", self.h, int(enable))
 
     def profile_read(self):
-        ms = np.zeros(9)
-        launches = np.zeros(9, np.int64)
+        ms = np.zeros(N_KERNELS)
+        launches = np.zeros(N_KERNELS, np.int64)
         work = np.zeros(7, np.uint64)
         call("rl_reloc_profile_read", self.h, ms.ctypes.data_as(ctypes.c_void_p),
              launches.ctypes.data_as(ctypes.c_void_p), work.ctypes.data_as(ctypes.c_void_p))
-        names = [lib().rl_kernel_name(i).decode() for i in range(9)]
-        kernels = {names[i]: dict(ms=float(ms[i]), launches=int(launches[i])) for i in range(9)}
+        names = [lib().rl_kernel_name(i).decode() for i in range(N_KERNELS)]
+        kernels = {names[i]: dict(ms=float(ms[i]), launches=int(launches[i])) for i in range(N_KERNELS)}
         keys = ["energy_pairs", "energy_modes", "lm_pairs", "lm_modes", "lm_inliers", "lm_trial", "rays"]
         return kernels, {k: int(v) for k, v in zip(keys, work)}
 

@@ -1,112 +1,17 @@
-// Hypothesis generation (Sec. 3.2.3): Kabsch on checked triples of
-// pixel-to-mode correspondences, one warp per hypothesis slot; compaction of
-// the successful slots; pixel batches of the preemptive RANSAC.
+// Hypothesis generation (Sec. 3.2.3): the first iteration of each slot whose
+// triple of pixel-to-mode correspondences passes the three checks, one warp
+// per hypothesis slot (the pose of that triple is fitted by a separate
+// kernel); compaction of the successful slots; pixel batches of the
+// preemptive RANSAC.
 //
 // Compiled with --fmad=false: back-projection (FP32) and the three checks
 // (FP64 from FP32 inputs) are plain IEEE operations in a fixed order, so
 // every accept/reject decision, and therefore the winning iteration of each
 // slot, is exactly reproducible.
-#include "internal.h"
+#include "hypgen_dev.cuh"
 #include "kernels.h"
-#include "relocgb_dev.cuh"
 
 namespace rl {
-
-// Largest-eigenvalue eigenvector of a symmetric 4x4 matrix by cyclic Jacobi.
-__device__ void jacobi4_max_eigvec(double A[4][4], double q[4]) {
-    double V[4][4];
-    for (int i = 0; i < 4; ++i)
-        for (int j = 0; j < 4; ++j) V[i][j] = (i == j) ? 1.0 : 0.0;
-    for (int sweep = 0; sweep < 30; ++sweep) {
-        double off = 0.0, dg = 0.0;
-        for (int i = 0; i < 4; ++i) {
-            dg += A[i][i] * A[i][i];
-            for (int j = i + 1; j < 4; ++j) off += A[i][j] * A[i][j];
-        }
-        if (off <= 1e-32 * dg || off == 0.0) break;
-        for (int p = 0; p < 3; ++p)
-            for (int r = p + 1; r < 4; ++r) {
-                const double apr = A[p][r];
-                if (apr == 0.0) continue;
-                const double theta = (A[r][r] - A[p][p]) / (2.0 * apr);
-                const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-                for (int k = 0; k < 4; ++k) {
-                    if (k == p || k == r) continue;
-                    const double akp = A[k][p], akr = A[k][r];
-                    A[k][p] = A[p][k] = c * akp - s * akr;
-                    A[k][r] = A[r][k] = s * akp + c * akr;
-                }
-                A[p][p] -= t * apr;
-                A[r][r] += t * apr;
-                A[p][r] = A[r][p] = 0.0;
-                for (int k = 0; k < 4; ++k) {
-                    const double vkp = V[k][p], vkr = V[k][r];
-                    V[k][p] = c * vkp - s * vkr;
-                    V[k][r] = s * vkp + c * vkr;
-                }
-            }
-    }
-    int best = 0;
-    for (int i = 1; i < 4; ++i)
-        if (A[i][i] > A[best][best]) best = i;
-    for (int i = 0; i < 4; ++i) q[i] = V[i][best];
-}
-
-// Rigid transform (camera -> world) of three pairs by Horn's closed form
-// (unit quaternion of the largest eigenvalue), which solves the same least
-// squares problem as Kabsch's SVD construction.
-__device__ __noinline__ void kabsch3_horn(const double a[3][3], const double b[3][3], double H[12]) {
-    double ca[3], cb[3];
-    for (int k = 0; k < 3; ++k) {
-        ca[k] = (a[0][k] + a[1][k] + a[2][k]) / 3.0;
-        cb[k] = (b[0][k] + b[1][k] + b[2][k]) / 3.0;
-    }
-    double S[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    for (int i = 0; i < 3; ++i)
-        for (int r = 0; r < 3; ++r)
-            for (int c = 0; c < 3; ++c) S[r][c] += (a[i][r] - ca[r]) * (b[i][c] - cb[c]);
-    const double Sxx = S[0][0], Sxy = S[0][1], Sxz = S[0][2];
-    const double Syx = S[1][0], Syy = S[1][1], Syz = S[1][2];
-    const double Szx = S[2][0], Szy = S[2][1], Szz = S[2][2];
-    double N[4][4] = {{Sxx + Syy + Szz, Syz - Szy, Szx - Sxz, Sxy - Syx},
-                      {Syz - Szy, Sxx - Syy - Szz, Sxy + Syx, Szx + Sxz},
-                      {Szx - Sxz, Sxy + Syx, -Sxx + Syy - Szz, Syz + Szy},
-                      {Sxy - Syx, Szx + Sxz, Syz + Szy, -Sxx - Syy + Szz}};
-    double q[4];
-    jacobi4_max_eigvec(N, q);
-    const double nq = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-    const double q0 = q[0] / nq, q1 = q[1] / nq, q2 = q[2] / nq, q3 = q[3] / nq;
-    const double R[3][3] = {
-        {q0 * q0 + q1 * q1 - q2 * q2 - q3 * q3, 2 * (q1 * q2 - q0 * q3), 2 * (q1 * q3 + q0 * q2)},
-        {2 * (q1 * q2 + q0 * q3), q0 * q0 - q1 * q1 + q2 * q2 - q3 * q3, 2 * (q2 * q3 - q0 * q1)},
-        {2 * (q1 * q3 - q0 * q2), 2 * (q2 * q3 + q0 * q1), q0 * q0 - q1 * q1 - q2 * q2 + q3 * q3}};
-    for (int r = 0; r < 3; ++r) {
-        H[4 * r + 0] = R[r][0];
-        H[4 * r + 1] = R[r][1];
-        H[4 * r + 2] = R[r][2];
-        H[4 * r + 3] = cb[r] - (R[r][0] * ca[0] + R[r][1] * ca[1] + R[r][2] * ca[2]);
-    }
-}
-
-struct HypArgs {
-    const Frame *frames;
-    const uint16_t *leaves;  // [B][T][hw_max]
-    const uint16_t *mcount;  // [B][hw_max] |M(u)|
-    const uint4 *prec;       // [B][hw_max] pixel records (<= 5 trees) or null
-    int hw_max;
-    ModeView mv;
-    RParams p;
-    double *hyp_pose;        // [B][N][12]
-    int32_t *hyp_iter;       // [B][N]
-};
-
-__device__ __forceinline__ float3 backproject(const Frame &fr, int p) {
-    const float d = fr.depth[p];
-    const int u = p % fr.W, v = p / fr.W;
-    return make_float3(__fdiv_rn(__fmul_rn(__fsub_rn((float)u, fr.cx), d), fr.fx),
-                       __fdiv_rn(__fmul_rn(__fsub_rn((float)v, fr.cy), d), fr.fy), d);
-}
 
 __device__ __forceinline__ double dist2_64(float3 a, float3 b) {
     const double e0 = (double)a.x - (double)b.x, e1 = (double)a.y - (double)b.y;
@@ -119,152 +24,151 @@ __device__ __forceinline__ float dist2_32(float3 a, float3 b) {
     return __fadd_rn(__fadd_rn(__fmul_rn(e0, e0), __fmul_rn(e1, e1)), __fmul_rn(e2, e2));
 }
 
-// The draws of iteration `it` of `slot`: three pixels, the colour-check pair
-// and the three mode indices into M(u).
-struct Draw {
-    int pix[3];
-    uint32_t m[3];
-    int j;
+// Thresholds of the FP32 pre-tests: the squared spread threshold widened by
+// 2e-5 relative and rounded outwards, and the rigidity tolerance.
+struct CheckThr {
+    float sq_lo, sq_hi, tol;
 };
 
-__device__ __forceinline__ Draw draw(const HypArgs &a, const Frame &fr, int slot, int it) {
-    const uint32_t ctr1 = (TAG_HYP << 16) | (uint32_t)a.p.level;
-    const uint4 r0 = philox(make_uint4(slot, ctr1, it, 0), fr.key0, fr.key1);
-    const uint32_t WH = (uint32_t)(fr.W * fr.H);
-    Draw d;
-    d.pix[0] = (int)draw_below(r0.x, WH);
-    d.pix[1] = (int)draw_below(r0.y, WH);
-    d.pix[2] = (int)draw_below(r0.z, WH);
-    d.j = (int)draw_below(r0.w, 3);
-    return d;
-}
-
-// M(u) element through the pixel record when there is one.
-__device__ __forceinline__ void lookup(const HypArgs &a, const uint16_t *lv, const uint4 *pr, int p, int m,
-                                       uint32_t *L, int *rank) {
-    if (pr)
-        mode_at_rec(pr[p], a.p.n_trees, a.mv.leaves_per_tree, m, L, rank);
-    else
-        mode_at(a.mv, lv, a.hw_max, p, a.p.n_trees, a.p.k_top, m, L, rank);
-}
-
-// One generation attempt, evaluated cheapest-rejection first (the outcome
-// does not depend on the order): every pixel needs a non-empty M(u) (|M(u)|
-// is 0 without depth), then the colour of the checked pair, then the modes
-// of the other pairs, spread and rigidity.  The spread and rigidity tests
-// run in FP32 and are re-evaluated in FP64 whenever the FP32 value lies
-// within a margin of the threshold far wider than its rounding error, so
-// each decision equals the FP64 decision.
-__device__ bool attempt(const HypArgs &a, const Frame &fr, const uint16_t *lv, const uint16_t *mc,
-                        const uint4 *pr, int slot, int it) {
-    Draw d = draw(a, fr, slot, it);
-    int cnt[3];
-    for (int i = 0; i < 3; ++i) {
-        cnt[i] = mc[d.pix[i]];
-        if (cnt[i] == 0) return false;
-    }
+// A generation attempt is evaluated in two stages, cheapest rejection first
+// (the outcome does not depend on the order).  Stage 1: the draws, a
+// non-empty M(u) at every pixel (|M(u)| is 0 without depth) and the colour
+// of the checked pair.  Stage 2: the modes of the other pairs, spread and
+// rigidity.  The spread and rigidity tests run in FP32 (errors below 1e-6
+// relative) and are re-evaluated in FP64 whenever the FP32 value lies within
+// 2e-5 relative of the threshold, so each decision equals the FP64 decision
+// while the narrow FP64 pipe is almost never used.
+__device__ __forceinline__ bool stage1(const HypArgs &a, const Frame &fr, const uint16_t *lv,
+                                       const uint16_t *mc, const uint4 *pr, int slot, int it,
+                                       Draw &d) {
+    d = draw(a, fr, slot, it);
+    const int c0 = mc[d.pix[0]], c1 = mc[d.pix[1]], c2 = mc[d.pix[2]];
+    if (c0 == 0 || c1 == 0 || c2 == 0) return false;
     const uint32_t ctr1 = (TAG_HYP << 16) | (uint32_t)a.p.level;
     const uint4 r1 = philox(make_uint4(slot, ctr1, it, 1), fr.key0, fr.key1);
-    const uint32_t u1[3] = {r1.x, r1.y, r1.z};
+    d.m[0] = draw_below(r1.x, (uint32_t)c0);
+    d.m[1] = draw_below(r1.y, (uint32_t)c1);
+    d.m[2] = draw_below(r1.z, (uint32_t)c2);
     // check 1: colour of pair j
-    uint32_t L[3];
-    int rank[3];
-    {
-        const int j = d.j;
-        lookup(a, lv, pr, d.pix[j], (int)draw_below(u1[j], (uint32_t)cnt[j]), &L[j], &rank[j]);
-        const uchar4 mcol = a.mv.mrgb[(size_t)L[j] * a.mv.m_max + rank[j]];
-        const uint8_t *pc = fr.rgb + (size_t)d.pix[j] * 3;
-        const int dr = abs((int)pc[0] - (int)mcol.x), dg = abs((int)pc[1] - (int)mcol.y),
-                  db = abs((int)pc[2] - (int)mcol.z);
-        if (max(dr, max(dg, db)) > a.p.colour_thresh) return false;
-    }
-    for (int i = 0; i < 3; ++i)
-        if (i != d.j)
-            lookup(a, lv, pr, d.pix[i], (int)draw_below(u1[i], (uint32_t)cnt[i]), &L[i], &rank[i]);
+    const int j = d.j;
+    const int pj = j == 0 ? d.pix[0] : (j == 1 ? d.pix[1] : d.pix[2]);
+    const int mj = (int)(j == 0 ? d.m[0] : (j == 1 ? d.m[1] : d.m[2]));
+    uint32_t L;
+    int rank;
+    lookup(a, lv, pr, pj, mj, &L, &rank);
+    const uchar4 mcol = a.mv.mrgb[(size_t)L * a.mv.m_max + rank];
+    const uint8_t *pc = fr.rgb + (size_t)pj * 3;
+    const int dr = abs((int)pc[0] - (int)mcol.x), dg = abs((int)pc[1] - (int)mcol.y),
+              db = abs((int)pc[2] - (int)mcol.z);
+    return max(dr, max(dg, db)) <= a.p.colour_thresh;
+}
+
+__device__ __forceinline__ bool stage2(const HypArgs &a, const CheckThr &ct, const Frame &fr,
+                                       const uint16_t *lv, const uint4 *pr, const int pix[3],
+                                       const int m[3]) {
     float3 xw[3];
-    for (int i = 0; i < 3; ++i) xw[i] = mode_pos(a.mv, L[i], rank[i]);
+    for (int i = 0; i < 3; ++i) {
+        uint32_t L;
+        int rank;
+        lookup(a, lv, pr, pix[i], m[i], &L, &rank);
+        xw[i] = mode_pos(a.mv, L, rank);
+    }
     // check 2: scene points pairwise at least sqrt(min_sq_dist) apart
     const int PA[3] = {0, 0, 1}, PB[3] = {1, 2, 2};
-    const double thr = a.p.min_sq_dist;
     float dW2f[3];
     for (int k = 0; k < 3; ++k) {
         dW2f[k] = dist2_32(xw[PA[k]], xw[PB[k]]);
-        const double f = (double)dW2f[k];
-        if (f < thr * (1.0 - 1e-5)) return false;
-        if (!(f > thr * (1.0 + 1e-5)) && dist2_64(xw[PA[k]], xw[PB[k]]) < thr) return false;
+        if (dW2f[k] < ct.sq_lo) return false;
+        if (!(dW2f[k] > ct.sq_hi) && dist2_64(xw[PA[k]], xw[PB[k]]) < a.p.min_sq_dist) return false;
     }
     // check 3: rigidity, |d_W - d_C| <= max_trans_err for every pair
     float3 xc[3];
-    for (int i = 0; i < 3; ++i) xc[i] = backproject(fr, d.pix[i]);
-    const double tol = a.p.max_trans_err;
+    for (int i = 0; i < 3; ++i) xc[i] = backproject(fr, pix[i]);
     for (int k = 0; k < 3; ++k) {
         const float dw = sqrtf(dW2f[k]), dc = sqrtf(dist2_32(xc[PA[k]], xc[PB[k]]));
-        const double diff = fabs((double)dw - (double)dc);
-        const double margin = 1e-5 * ((double)dw + (double)dc) + 1e-6;
-        if (diff > tol + margin) return false;
-        if (diff >= tol - margin) {
+        const float diff = fabsf(__fsub_rn(dw, dc));
+        const float margin = __fadd_rn(__fmul_rn(2e-5f, __fadd_rn(dw, dc)), 2e-6f);
+        if (diff > __fadd_rn(ct.tol, margin)) return false;
+        if (diff >= __fsub_rn(ct.tol, margin)) {
             const double e = fabs(sqrt(dist2_64(xw[PA[k]], xw[PB[k]])) -
                                   sqrt(dist2_64(xc[PA[k]], xc[PB[k]])));
-            if (e > tol) return false;
+            if (e > a.p.max_trans_err) return false;
         }
     }
     return true;
 }
 
-// The accepted triple of (slot, it), re-derived exactly, and its pose.
-__device__ __noinline__ void accept_triple(const HypArgs &a, const Frame &fr, const uint16_t *lv,
-                                           const uint16_t *mc, const uint4 *pr, int slot, int it, double H[12]) {
-    const Draw d = draw(a, fr, slot, it);
-    const uint32_t ctr1 = (TAG_HYP << 16) | (uint32_t)a.p.level;
-    const uint4 r1 = philox(make_uint4(slot, ctr1, it, 1), fr.key0, fr.key1);
-    const uint32_t u1[3] = {r1.x, r1.y, r1.z};
-    double xc[3][3], xw[3][3];
-    for (int i = 0; i < 3; ++i) {
-        uint32_t L;
-        int rank;
-        lookup(a, lv, pr, d.pix[i], (int)draw_below(u1[i], (uint32_t)mc[d.pix[i]]), &L, &rank);
-        const float3 c = backproject(fr, d.pix[i]);
-        const float3 w = mode_pos(a.mv, L, rank);
-        xc[i][0] = c.x; xc[i][1] = c.y; xc[i][2] = c.z;
-        xw[i][0] = w.x; xw[i][1] = w.y; xw[i][2] = w.z;
-    }
-    kabsch3_horn(xc, xw, H);
-}
+// Warp per (frame, slot).  The 32 lanes run stage 1 on 32 consecutive
+// iterations and append the survivors, in iteration order, to a ring in
+// shared memory; whenever it holds 32 of them, the lanes run stage 2 on the
+// 32 oldest.  The first success in a drained group is the lowest successful
+// iteration, exactly as a sequential loop would find it: every lower
+// iteration failed stage 1 or was drained earlier.  Compaction keeps the
+// lanes converged on the rarely reached stage 2.
+constexpr int HG_WARPS = 4;
+constexpr int HG_RING = 64;  // < 32 pending after a drain + 32 appended
 
-// Warp per (frame, slot): the 32 lanes try 32 consecutive iterations; the
-// lowest successful iteration wins, exactly as a sequential loop would.
-// The attempt loop is latency bound (scattered loads of leaves and modes):
-// registers are capped at 64 so that 32 warps per SM hide that latency.
-__global__ void __launch_bounds__(128, 8) k_hypgen(HypArgs a) {
-    const int lane = threadIdx.x & 31;
-    const int slot = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+__global__ void __launch_bounds__(HG_WARPS * 32, 8) k_hypgen(HypArgs a) {
+    __shared__ int4 s_ring[HG_WARPS][HG_RING];   // it | j << 30, pixels of the triple
+    __shared__ uint2 s_mode[HG_WARPS][HG_RING];  // mode indices m0 | m1 << 16, m2
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int slot = blockIdx.x * HG_WARPS + w;
     const int b = blockIdx.y;
     if (slot >= a.p.n_hyp) return;
     const Frame fr = a.frames[b];
-    int32_t *iter_fail = a.hyp_iter + (size_t)b * a.p.n_hyp + slot;
+    int32_t *iter_out = a.hyp_iter + (size_t)b * a.p.n_hyp + slot;
     if (fr.W * fr.H == 0) {  // empty frame (e.g. accepted by an earlier cascade level)
-        if (lane == 0) *iter_fail = -1;
+        if (lane == 0) *iter_out = -1;
         return;
     }
     const uint16_t *lv = a.leaves + (size_t)b * a.p.n_trees * a.hw_max;
     const uint16_t *mc = a.mcount + (size_t)b * a.hw_max;
     const uint4 *pr = a.prec ? a.prec + (size_t)b * a.hw_max : nullptr;
-    int32_t *iter_out = a.hyp_iter + (size_t)b * a.p.n_hyp + slot;
-    double *pose_out = a.hyp_pose + ((size_t)b * a.p.n_hyp + slot) * 12;
+    CheckThr ct;
+    ct.sq_lo = __double2float_rd(a.p.min_sq_dist * (1.0 - 2e-5));
+    ct.sq_hi = __double2float_ru(a.p.min_sq_dist * (1.0 + 2e-5));
+    ct.tol = (float)a.p.max_trans_err;
+    int4 *ring = s_ring[w];
+    uint2 *rmode = s_mode[w];
+    unsigned head = 0, tail = 0;  // warp-uniform ring counters
+    const unsigned lt = (1u << lane) - 1u;
+    // Stage 2 on the pending entries head .. head + n - 1 (n <= 32); the
+    // winning lane stores its iteration.
+    auto drain = [&](unsigned n) -> bool {
+        bool ok = false;
+        int it = 0;
+        if ((unsigned)lane < n) {
+            const unsigned e = (head + lane) % HG_RING;
+            const int4 r = ring[e];
+            const uint2 mm = rmode[e];
+            const int pix[3] = {r.y, r.z, r.w};
+            const int m[3] = {(int)(mm.x & 0xffffu), (int)(mm.x >> 16), (int)mm.y};
+            it = r.x & 0x3fffffff;
+            ok = stage2(a, ct, fr, lv, pr, pix, m);
+        }
+        const unsigned win = __ballot_sync(0xffffffffu, ok);
+        if (win && lane == __ffs(win) - 1) *iter_out = it;
+        head += n;
+        return win != 0;
+    };
     for (int base = 0; base < a.p.max_iter; base += 32) {
         const int it = base + lane;
-        const bool ok = it < a.p.max_iter && attempt(a, fr, lv, mc, pr, slot, it);
-        const unsigned mask = __ballot_sync(0xffffffffu, ok);
-        if (mask) {
-            if (lane == __ffs(mask) - 1) {
-                double H[12];
-                accept_triple(a, fr, lv, mc, pr, slot, it, H);
-                for (int k = 0; k < 12; ++k) pose_out[k] = H[k];
-                *iter_out = it;
-            }
-            return;
+        Draw d;
+        const bool s1 = it < a.p.max_iter && stage1(a, fr, lv, mc, pr, slot, it, d);
+        const unsigned mask = __ballot_sync(0xffffffffu, s1);
+        if (s1) {
+            const unsigned e = (tail + __popc(mask & lt)) % HG_RING;
+            ring[e] = make_int4(it | (d.j << 30), d.pix[0], d.pix[1], d.pix[2]);
+            rmode[e] = make_uint2(d.m[0] | (d.m[1] << 16), d.m[2]);
+        }
+        tail += __popc(mask);
+        __syncwarp();
+        if (tail - head >= 32) {
+            if (drain(32)) return;
+            __syncwarp();
         }
     }
+    if (tail - head > 0 && drain(tail - head)) return;
     if (lane == 0) *iter_out = -1;
 }
 
@@ -334,8 +238,8 @@ rl_status launch_hypgen(const Frame *frames, const uint16_t *leaves, const uint1
                         const uint4 *prec, int hw_max, ModeView mv, const RParams &p,
                         double *hyp_pose, int32_t *hyp_iter, int n, cudaStream_t s) {
     HypArgs a{frames, leaves, mcount, prec, hw_max, mv, p, hyp_pose, hyp_iter};
-    dim3 grid((p.n_hyp + 3) / 4, n);
-    k_hypgen<<<grid, 128, 0, s>>>(a);
+    dim3 grid((p.n_hyp + HG_WARPS - 1) / HG_WARPS, n);
+    k_hypgen<<<grid, HG_WARPS * 32, 0, s>>>(a);
     RL_LAUNCH_CK();
     return RL_OK;
 }

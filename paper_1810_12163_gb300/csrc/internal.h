@@ -195,7 +195,7 @@ struct DevResult {
 // device-side work counters of the scoring kernels (off unless enabled).
 enum KernelId {
     K_LEAVES = 0, K_HYPGEN, K_COMPACT, K_SAMPLE, K_ENERGY, K_SELECT, K_LM, K_RAYCAST, K_FINALIZE,
-    K_COUNT
+    K_HYPPOSE, K_COUNT
 };
 // work counters: energy (H,px) pairs, energy (H,px,mode) triples, LM pass-1
 // (H,px) evaluations, LM (H,px,mode) triples, LM inlier accumulations, LM

@@ -93,6 +93,9 @@ rl_status launch_finalize(const QueryState &q, const RParams &p, int n_tiles, in
 rl_status launch_hypgen(const Frame *frames, const uint16_t *leaves, const uint16_t *mcount,
                         const uint4 *prec, int hw_max, ModeView mv, const RParams &p,
                         double *hyp_pose, int32_t *hyp_iter, int n, cudaStream_t s);
+rl_status launch_hyppose(const Frame *frames, const uint16_t *leaves, const uint16_t *mcount,
+                         const uint4 *prec, int hw_max, ModeView mv, const RParams &p,
+                         double *hyp_pose, int32_t *hyp_iter, int n, cudaStream_t s);
 rl_status launch_compact(const int32_t *hyp_iter, int N, int32_t *hyp_list, int32_t *n_hyp, int n,
                          cudaStream_t s);
 rl_status launch_sample_batch(const Frame *frames, const uint16_t *mcount, int hw_max,

@@ -22,7 +22,8 @@ static int rounds_for(int n_cull, int k_out, int halve_to_one) {
 static rl_status check_ransac(const rl_ransac_params *p, const rl_forest *f) {
     if (!p) return fail(RL_ERR_INVALID_ARG, "null relocaliser params");
     if (p->n_hyp < 1 || p->n_hyp > 4096) return fail(RL_ERR_INVALID_ARG, "n_hyp must be 1..4096");
-    if (p->max_iter < 1) return fail(RL_ERR_INVALID_ARG, "max_iter must be >= 1");
+    if (p->max_iter < 1 || p->max_iter > (1 << 30) - 64)
+        return fail(RL_ERR_INVALID_ARG, "max_iter must be in [1, 2^30 - 64]");
     if (p->n_cull < 1 || p->n_cull > 64) return fail(RL_ERR_INVALID_ARG, "n_cull must be 1..64");
     if (p->eta < 1 || p->eta > 4096) return fail(RL_ERR_INVALID_ARG, "eta must be 1..4096");
     if (p->k_out < 1 || p->k_out > RL_MAX_CHOSEN) return fail(RL_ERR_INVALID_ARG, "k_out must be 1..16");
@@ -136,6 +137,7 @@ rl_status run_relocalise(rl_reloc *r, int n, int level, cudaStream_t s) {
     unsigned long long *work = r->prof.on ? r->prof.work : nullptr;
     { PROF(K_LEAVES); RL_TRY(launch_leaves(f, q.frames, n, p.n_trees, hw_max, q.leaves, r->max_w, r->max_h, s, p.k_top, q.mcount, q.prec)); }
     { PROF(K_HYPGEN); RL_TRY(launch_hypgen(q.frames, q.leaves, q.mcount, q.prec, hw_max, mv, p, q.hyp_pose, q.hyp_iter, n, s)); }
+    { PROF(K_HYPPOSE); RL_TRY(launch_hyppose(q.frames, q.leaves, q.mcount, q.prec, hw_max, mv, p, q.hyp_pose, q.hyp_iter, n, s)); }
     { PROF(K_COMPACT); RL_TRY(launch_compact(q.hyp_iter, N, q.hyp_list, q.n_hyp, n, s)); }
     { PROF(K_SAMPLE); RL_TRY(launch_sample_batch(q.frames, q.mcount, hw_max, p, 0, q.pix, q.xc, n, s));
       RL_TRY(launch_build_table(q, hw_max, mv, p, 0, n, s)); }
@@ -828,7 +830,8 @@ static void prof_free(rl_reloc *r) {
 }  // namespace rl
 
 static const char *kKernelNames[K_COUNT] = {"leaves",  "hypgen", "compact", "sample_batch", "energy",
-                                             "select", "lm",     "raycast_score", "finalize"};
+                                             "select", "lm",     "raycast_score", "finalize", "hyppose"};
+static_assert(K_COUNT == RL_N_KERNELS, "kernel ids and the public count differ");
 
 extern "C" const char *rl_kernel_name(int32_t kid) {
     return (kid >= 0 && kid < K_COUNT) ? kKernelNames[kid] : "";
