@@ -183,12 +183,13 @@ struct QueryState {
     int32_t *n_rounds;       // [B]
     Frame *frames;           // [B]
     uint8_t *result_blob;    // [B] device results (DevResult)
+    int32_t *dev_err;        // [B] nonzero: a bounded device-side wait gave up
 };
 
 struct DevResult {
     double pose[12];
     float energy, energy_per_pixel, score;
-    int32_t n_hypotheses, n_chosen, n_pixels, status, best;
+    int32_t n_hypotheses, n_chosen, n_pixels, status, best, err;
 };
 
 // Per-kernel timing with CUDA events recorded on the launching stream, plus

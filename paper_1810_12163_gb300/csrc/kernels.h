@@ -64,6 +64,14 @@ constexpr size_t kLmSmemMax = 200 * 1024;
 size_t lm_tiled_smem(int maxm_pad);
 rl_status prepare_kernels();
 
+// LM with one thread-block cluster per frame (at most 64 hypotheses); its
+// shared memory grows with the padded row length, and above
+// kLmClusterSmemMax the other LM kernels are used.
+constexpr size_t kLmClusterSmemMax = 200 * 1024;
+size_t lm_cluster_smem(int mpad, bool cov);
+rl_status launch_lm_cluster(const LmArgs &a, int n, cudaStream_t s);
+rl_status prepare_lm_cluster();
+
 struct RaycastArgs {
     const Frame *frames;
     const double *poses;       // [B][pose_cap][12]

@@ -1,0 +1,432 @@
+// Levenberg-Marquardt refinement of a preemptive round (Sec. 3.2.3) with one
+// thread-block cluster per frame.
+//
+// The LMC_CTAS CTAs of a cluster share the frame's surviving hypotheses
+// (n <= 64) and split its pixel set by tiles of LMC_P pixels: CTA c takes
+// tiles c, c + LMC_CTAS, ...  Each LM iteration
+//   1. streams the CTA's tiles of the mode table (rows of decoded M(u)) into
+//      shared memory with bulk asynchronous copies on an mbarrier pipeline;
+//      thread t works for hypothesis t % HB on pixel group t / HB (HB = next
+//      power of two >= n), so the 32 lanes of a warp usually read the same
+//      staged row (broadcast) and follow the same control flow;
+//   2. finds, per (hypothesis, pixel), the nearest mode under the pixel's
+//      Mahalanobis metric, keeps it if within the inlier radius, and adds its
+//      terms to FP32 normal equations;
+//   3. reduces the normal equations over the CTA in a fixed order, then over
+//      the cluster through distributed shared memory (ranks in order), so
+//      that every CTA holds bit-identical sums;
+//   4. solves the damped 6x6 system of each hypothesis in FP64 (redundantly
+//      in every CTA, hence identical decisions everywhere and no broadcast);
+//   5. evaluates the trial pose on the same correspondences and accepts it
+//      iff the cost decreases (same two-level reduction).
+// Two cluster barriers per iteration; all CTAs take the same branches.
+//
+// Every wait on a copy is bounded: a wait that gives up marks the frame in
+// dev_err, the CTA skips the rest of its work while keeping step with the
+// cluster barriers, and waits (bounded again) for its copies in flight
+// before it exits.
+#include <cooperative_groups.h>
+
+#include "internal.h"
+#include "kernels.h"
+#include "lm_dev.cuh"
+
+namespace rl {
+
+namespace cg = cooperative_groups;
+
+constexpr int LMC_CTAS = 4;
+constexpr int LMC_THREADS = 256;
+constexpr int LMC_P = 16;        // pixels per tile (max_pix is a multiple)
+constexpr int LMC_STAGES = 2;
+constexpr int LMC_HMAX = 64;
+constexpr int LMC_NV = 29;       // 21 J^T J + 6 J^T r + cost + inlier count
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+struct LmcLayout {
+    uint32_t t0, t1, t2, xc, cnt, stage, tx;
+    uint32_t H, Hn, lambda, tot, loc, trial, state, flag, bar, total;
+};
+
+__host__ __device__ inline uint32_t lmc_a16(uint32_t x) { return (x + 15u) & ~15u; }
+
+// Shared-memory layout for rows of `stride` modes.  Region 0 holds the
+// staged tiles during the pixel pass and the per-thread partial sums during
+// the reductions (never both at once).
+__host__ __device__ inline LmcLayout lmc_layout(int stride, bool cov) {
+    LmcLayout L;
+    const uint32_t rows = (uint32_t)LMC_P * (uint32_t)stride;
+    uint32_t o = 0;
+    L.t0 = o; o += rows * 16;
+    L.t1 = o; if (cov) o += rows * 16;
+    L.t2 = o; if (cov) o += lmc_a16(rows * 4);
+    L.xc = o; o += LMC_P * 16;
+    L.cnt = o; o += lmc_a16(LMC_P * 2);
+    L.stage = o;
+    L.tx = rows * 16 + (cov ? rows * 20 : 0) + LMC_P * 16 + LMC_P * 2;
+    const uint32_t stages = LMC_STAGES * L.stage;
+    const uint32_t partials = LMC_THREADS * LMC_NV * 4;
+    o = lmc_a16(stages > partials ? stages : partials);
+    L.H = o; o += LMC_HMAX * 12 * 8;
+    L.Hn = o; o += LMC_HMAX * 12 * 8;
+    L.lambda = o; o += LMC_HMAX * 8;
+    L.tot = o; o += LMC_HMAX * LMC_NV * 4;
+    L.loc = o; o += LMC_HMAX * LMC_NV * 4;
+    L.trial = o; o += LMC_HMAX * 4;
+    L.state = o; o += LMC_HMAX * 4;
+    L.flag = o; o += 16;
+    L.bar = o; o += LMC_STAGES * 8;
+    L.total = lmc_a16(o);
+    return L;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kWaitLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+__global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k_lm_cluster(LmArgs a) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int crank = (int)cluster.block_rank();
+    const int b = blockIdx.y;
+    const int n = a.q.n_cur[b];
+    if (!round_active(n, a.p)) return;  // same n in every CTA of the cluster
+    const bool cov = a.p.use_cov;
+    const int stride = a.p.mpad;
+    const LmcLayout L = lmc_layout(stride, cov);
+    int HB = 1;
+    while (HB < n) HB <<= 1;
+    const int G = LMC_THREADS / HB;
+    const int t = threadIdx.x, hl = t % HB, g = t / HB;
+    const bool mine = hl < n;
+
+    float *s_acc = (float *)smem;
+    double(*s_H)[12] = (double(*)[12])(smem + L.H);
+    double(*s_Hn)[12] = (double(*)[12])(smem + L.Hn);
+    double *s_lambda = (double *)(smem + L.lambda);
+    float(*s_tot)[LMC_NV] = (float(*)[LMC_NV])(smem + L.tot);
+    float(*s_loc)[LMC_NV] = (float(*)[LMC_NV])(smem + L.loc);
+    float *s_tloc = (float *)(smem + L.trial);  // this CTA's trial sums
+    int *s_state = (int *)(smem + L.state);
+    volatile int *s_abort = (volatile int *)(smem + L.flag);
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
+    const uint32_t bar0 = sbase + L.bar;
+
+    const int NC = a.p.n_cull;
+    const size_t row0 = (size_t)b * a.p.max_pix;
+    const float4 *g_t0 = a.q.tab0 + row0 * stride;
+    const float4 *g_t1 = a.q.tab1 + row0 * stride;
+    const float *g_t2 = a.q.tab2 + row0 * stride;
+    const float4 *g_xc = a.q.xc + row0;
+    const int16_t *g_cnt = a.q.tab_cnt + row0;
+    int32_t *corr = a.q.corr + (size_t)b * NC * a.p.max_pix;  // [pixel][n]
+    const int n_tiles = (a.n_pix + LMC_P - 1) / LMC_P;
+    const int my_tiles = crank < n_tiles ? (n_tiles - crank + LMC_CTAS - 1) / LMC_CTAS : 0;
+    const float thr2 = (float)(a.p.lm_inlier_thresh * a.p.lm_inlier_thresh);
+
+    for (int i = t; i < n * 12; i += LMC_THREADS) s_H[i / 12][i % 12] = a.q.cur_pose[((size_t)b * NC + i / 12) * 12 + i % 12];
+    for (int i = t; i < n; i += LMC_THREADS) {
+        s_lambda[i] = a.p.lm_lambda0;
+        s_state[i] = 1;
+    }
+    if (t == 0) {
+        *s_abort = 0;
+        for (int s = 0; s < LMC_STAGES; ++s) mbar_init(bar0 + 8 * s, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    // thread 0 is the producer: my j-th tile into stage s
+    uint32_t issued[LMC_STAGES] = {}, waited[LMC_STAGES] = {};
+    auto issue = [&](int j, int s) {
+        const uint32_t bar = bar0 + 8 * s;
+        const uint32_t st = sbase + s * L.stage;
+        const size_t r = (size_t)(crank + j * LMC_CTAS) * LMC_P;  // first row of the tile
+        const uint32_t rows = (uint32_t)LMC_P * stride;
+        mbar_expect_tx(bar, L.tx);
+        bulk_g2s(st + L.t0, g_t0 + r * stride, rows * 16, bar);
+        if (cov) {
+            bulk_g2s(st + L.t1, g_t1 + r * stride, rows * 16, bar);
+            bulk_g2s(st + L.t2, g_t2 + r * stride, rows * 4, bar);
+        }
+        bulk_g2s(st + L.xc, g_xc + r, LMC_P * 16, bar);
+        bulk_g2s(st + L.cnt, g_cnt + r, LMC_P * 2, bar);
+        ++issued[s];
+    };
+
+    unsigned w_pairs = 0, w_modes = 0, w_in = 0, w_trial = 0;
+    for (int it = 0; it < a.p.lm_max_iter; ++it) {
+        if (!__syncthreads_or(mine && s_state[hl])) break;  // identical in every CTA
+        const bool act = mine && s_state[hl];
+        float r00 = 0.f, r01 = 0.f, r02 = 0.f, tx = 0.f, r10 = 0.f, r11 = 0.f, r12 = 0.f, ty = 0.f;
+        float r20 = 0.f, r21 = 0.f, r22 = 0.f, tz = 0.f;
+        if (act) {
+            const double *H = s_H[hl];
+            r00 = (float)H[0]; r01 = (float)H[1]; r02 = (float)H[2]; tx = (float)H[3];
+            r10 = (float)H[4]; r11 = (float)H[5]; r12 = (float)H[6]; ty = (float)H[7];
+            r20 = (float)H[8]; r21 = (float)H[9]; r22 = (float)H[10]; tz = (float)H[11];
+        }
+        float acc[28];
+#pragma unroll
+        for (int k = 0; k < 28; ++k) acc[k] = 0.f;
+        int nin = 0;
+        // region 0 was last written by threads (partials): order those writes
+        // before the copies that overwrite it
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (t == 0 && !*s_abort)
+            for (int j = 0; j < LMC_STAGES && j < my_tiles; ++j) issue(j, j);
+        for (int j = 0; j < my_tiles; ++j) {
+            const int s = j % LMC_STAGES;
+            const uint32_t parity = waited[s] & 1u;
+            ++waited[s];
+            if (!*s_abort && !mbar_wait_bounded(bar0 + 8 * s, parity)) {
+                *s_abort = 1;
+                a.q.dev_err[b] = 1;
+            }
+            if (act && !*s_abort) {
+                const uint8_t *st = smem + s * L.stage;
+                const float4 *s_t0 = (const float4 *)(st + L.t0);
+                const float4 *s_t1 = (const float4 *)(st + L.t1);
+                const float *s_t2 = (const float *)(st + L.t2);
+                const float4 *s_xc = (const float4 *)(st + L.xc);
+                const int16_t *s_cnt = (const int16_t *)(st + L.cnt);
+                const int i0 = (crank + j * LMC_CTAS) * LMC_P;
+                const int np = min(LMC_P, a.n_pix - i0);
+                for (int il = g; il < np; il += G) {
+                    const int cnt = s_cnt[il];
+                    int best_m = -1;
+                    if (cnt > 0) {
+                        ++w_pairs;
+                        w_modes += cnt;
+                        const float4 x = s_xc[il];
+                        const float y0 = fmaf(r00, x.x, fmaf(r01, x.y, fmaf(r02, x.z, tx)));
+                        const float y1 = fmaf(r10, x.x, fmaf(r11, x.y, fmaf(r12, x.z, ty)));
+                        const float y2 = fmaf(r20, x.x, fmaf(r21, x.y, fmaf(r22, x.z, tz)));
+                        const int base = il * stride;
+                        float best = INFINITY;
+                        if (cov) {
+                            for (int m = 0; m < cnt; ++m) {
+                                const float4 m0 = s_t0[base + m], m1 = s_t1[base + m];
+                                const float u22 = s_t2[base + m];
+                                const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+                                const float w0 = fmaf(m0.w, v0, fmaf(m1.x, v1, m1.y * v2));
+                                const float w1 = fmaf(m1.z, v1, m1.w * v2);
+                                const float w2 = u22 * v2;
+                                const float d2 = fmaf(w0, w0, fmaf(w1, w1, w2 * w2));
+                                if (d2 < best) {
+                                    best = d2;
+                                    best_m = m;
+                                }
+                            }
+                        } else {
+                            for (int m = 0; m < cnt; ++m) {
+                                const float4 m0 = s_t0[base + m];
+                                const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+                                const float d2 = fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
+                                if (d2 < best) {
+                                    best = d2;
+                                    best_m = m;
+                                }
+                            }
+                        }
+                        if (best_m >= 0) {
+                            const float4 m0 = s_t0[base + best_m];
+                            const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+                            if (fmaf(v0, v0, fmaf(v1, v1, v2 * v2)) <= thr2) {
+                                ++nin;
+                                ++w_in;
+                                if (cov) {
+                                    const float4 m1 = s_t1[base + best_m];
+                                    lm_accumulate(y0, y1, y2, v0, v1, v2, m0.w, m1.x, m1.y, m1.z, m1.w,
+                                                  s_t2[base + best_m], acc);
+                                } else {
+                                    lm_accumulate(y0, y1, y2, v0, v1, v2, 1.f, 0.f, 0.f, 1.f, 0.f, 1.f, acc);
+                                }
+                            } else {
+                                best_m = -1;
+                            }
+                        }
+                    }
+                    corr[(size_t)(i0 + il) * n + hl] = best_m;  // local mode index in the row
+                }
+            }
+            __syncthreads();  // stage s consumed by every thread
+            if (t == 0 && !*s_abort && j + LMC_STAGES < my_tiles) issue(j + LMC_STAGES, s);
+        }
+        // normal equations: CTA sums in group order, then cluster sums in rank order
+        float *mypart = s_acc + t * LMC_NV;
+#pragma unroll
+        for (int k = 0; k < 28; ++k) mypart[k] = acc[k];
+        mypart[28] = (float)nin;
+        __syncthreads();
+        for (int o = t; o < n * LMC_NV; o += LMC_THREADS) {
+            const int h = o / LMC_NV, k = o % LMC_NV;
+            float v = 0.f;
+            for (int gg = 0; gg < G; ++gg) v += s_acc[(gg * HB + h) * LMC_NV + k];
+            s_loc[h][k] = v;
+        }
+        cluster.sync();
+        for (int o = t; o < n * LMC_NV; o += LMC_THREADS) {
+            const int h = o / LMC_NV, k = o % LMC_NV;
+            float v = 0.f;
+            for (int r = 0; r < LMC_CTAS; ++r) v += cluster.map_shared_rank(&s_loc[0][0], r)[h * LMC_NV + k];
+            s_tot[h][k] = v;
+        }
+        __syncthreads();
+        // FP64 solve; hypothesis h on thread (h % 8) * 32 + h / 8, spreading
+        // the narrow FP64 pipe's work over all warps
+        {
+            const int h = (t & 31) * 8 + (t >> 5);
+            if ((t & 31) < LMC_HMAX / 8 && h < n && s_state[h]) {
+                const float *T = s_tot[h];
+                bool stop = T[28] < 3.f;
+                double step[6];
+                if (!stop) {
+                    double A[36], rhs[6];
+                    int k = 0;
+                    for (int r = 0; r < 6; ++r)
+                        for (int c = r; c < 6; ++c, ++k) A[6 * r + c] = A[6 * c + r] = (double)T[k];
+                    for (int r = 0; r < 6; ++r) {
+                        A[6 * r + r] += s_lambda[h] * (double)T[r * 6 - r * (r - 1) / 2];
+                        rhs[r] = -(double)T[21 + r];
+                    }
+                    if (!chol_solve6(A, rhs, step)) {
+                        stop = true;
+                    } else {
+                        double sn = 0.0;
+                        for (int r = 0; r < 6; ++r) sn += step[r] * step[r];
+                        stop = sqrt(sn) < a.p.lm_stop;
+                    }
+                }
+                if (stop) {
+                    s_state[h] = 0;
+                } else {
+                    double Hn[12];
+                    for (int i = 0; i < 12; ++i) Hn[i] = s_H[h][i];
+                    se3_left(step, Hn);
+                    for (int i = 0; i < 12; ++i) s_Hn[h][i] = Hn[i];
+                }
+            }
+        }
+        __syncthreads();
+        // trial cost of the new pose on the same correspondences
+        const bool act2 = mine && s_state[hl];
+        float trial = 0.f;
+        if (act2 && !*s_abort) {
+            const double *Hn = s_Hn[hl];
+            const float s00 = (float)Hn[0], s01 = (float)Hn[1], s02 = (float)Hn[2], u0 = (float)Hn[3];
+            const float s10 = (float)Hn[4], s11 = (float)Hn[5], s12 = (float)Hn[6], u1 = (float)Hn[7];
+            const float s20 = (float)Hn[8], s21 = (float)Hn[9], s22 = (float)Hn[10], u2 = (float)Hn[11];
+            for (int j = 0; j < my_tiles; ++j) {
+                const int i0 = (crank + j * LMC_CTAS) * LMC_P;
+                const int np = min(LMC_P, a.n_pix - i0);
+                for (int il = g; il < np; il += G) {
+                    const int i = i0 + il;
+                    const int m = corr[(size_t)i * n + hl];
+                    if (m < 0) continue;
+                    ++w_trial;
+                    const float4 x = g_xc[i];
+                    const size_t e = (size_t)i * stride + m;
+                    const float4 m0 = g_t0[e];
+                    const float y0 = fmaf(s00, x.x, fmaf(s01, x.y, fmaf(s02, x.z, u0)));
+                    const float y1 = fmaf(s10, x.x, fmaf(s11, x.y, fmaf(s12, x.z, u1)));
+                    const float y2 = fmaf(s20, x.x, fmaf(s21, x.y, fmaf(s22, x.z, u2)));
+                    const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+                    if (cov) {
+                        const float4 m1 = g_t1[e];
+                        const float q0 = fmaf(m0.w, v0, fmaf(m1.x, v1, m1.y * v2));
+                        const float q1 = fmaf(m1.z, v1, m1.w * v2);
+                        const float q2 = g_t2[e] * v2;
+                        trial = fmaf(q0, q0, fmaf(q1, q1, fmaf(q2, q2, trial)));
+                    } else {
+                        trial = fmaf(v0, v0, fmaf(v1, v1, fmaf(v2, v2, trial)));
+                    }
+                }
+            }
+        }
+        s_acc[t] = trial;
+        __syncthreads();
+        for (int h = t; h < n; h += LMC_THREADS) {
+            float v = 0.f;
+            for (int gg = 0; gg < G; ++gg) v += s_acc[gg * HB + h];
+            s_tloc[h] = v;
+        }
+        // Separate buffers make two barriers per iteration enough: a CTA
+        // rewrites s_loc only after the second barrier of this iteration,
+        // which every CTA reaches after reading s_loc, and rewrites s_tloc
+        // only after the first barrier of the next iteration, which every
+        // CTA reaches after reading s_tloc.
+        cluster.sync();
+        for (int h = t; h < n; h += LMC_THREADS) {
+            if (!s_state[h]) continue;
+            float v = 0.f;
+            for (int r = 0; r < LMC_CTAS; ++r) v += cluster.map_shared_rank(s_tloc, r)[h];
+            if (v < s_tot[h][27]) {
+                for (int i = 0; i < 12; ++i) s_H[h][i] = s_Hn[h][i];
+                s_lambda[h] /= 10.0;
+            } else {
+                s_lambda[h] *= 10.0;
+            }
+        }
+    }
+    __syncthreads();  // the last accept/reject updates of s_H before other threads write them out
+    if (crank == 0)
+        for (int i = t; i < n * 12; i += LMC_THREADS)
+            a.q.cur_pose[((size_t)b * NC + i / 12) * 12 + i % 12] = s_H[i / 12][i % 12];
+    if (a.work && mine) {
+        atomicAdd(&a.work[W_LM_PAIRS], (unsigned long long)w_pairs);
+        atomicAdd(&a.work[W_LM_MODES], (unsigned long long)w_modes);
+        atomicAdd(&a.work[W_LM_INLIERS], (unsigned long long)w_in);
+        atomicAdd(&a.work[W_LM_TRIAL], (unsigned long long)w_trial);
+    }
+    if (t == 0 && *s_abort)  // copies still in flight must land before the CTA exits
+        for (int s = 0; s < LMC_STAGES; ++s)
+            if (issued[s] > waited[s]) mbar_wait_bounded(bar0 + 8 * s, (issued[s] - 1) & 1u);
+    cluster.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+size_t lm_cluster_smem(int mpad, bool cov) { return lmc_layout(mpad, cov).total; }
+
+rl_status launch_lm_cluster(const LmArgs &a, int n, cudaStream_t s) {
+    dim3 grid(LMC_CTAS, n);
+    k_lm_cluster<<<grid, LMC_THREADS, lm_cluster_smem(a.p.mpad, a.p.use_cov), s>>>(a);
+    RL_LAUNCH_CK();
+    return RL_OK;
+}
+
+rl_status prepare_lm_cluster() {
+    RL_CK(cudaFuncSetAttribute(k_lm_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLmClusterSmemMax));
+    return RL_OK;
+}
+
+}  // namespace rl

@@ -1,0 +1,131 @@
+// Device helpers of the Levenberg-Marquardt refinement (Sec. 3.2.3): the
+// normal-equation terms of one correspondence, the damped 6x6 solve and the
+// SE(3) update, both in FP64.
+#pragma once
+#include <math.h>
+
+#include "internal.h"
+
+namespace rl {
+
+// A preemptive round runs while more than k_out hypotheses remain (or more
+// than one when halving continues to a single hypothesis).
+__device__ __forceinline__ bool round_active(int n, const RParams &p) {
+    return n > p.k_out || (p.halve_to_one && n > 1);
+}
+
+// Adds one correspondence to the normal equations: residual r = U (y - mu)
+// with y = H x the transformed camera point, mu the mode mean and U the
+// upper Cholesky factor of its precision (U = I without covariances); the
+// Jacobian of r with respect to a left perturbation exp(xi^) H, xi =
+// (t, w), is U [I | -[y]x].  acc: 21 entries of the upper triangle of J^T J
+// (row-major), 6 of J^T r, then the cost r^T r.
+__device__ __forceinline__ void lm_accumulate(float y0, float y1, float y2, float v0, float v1, float v2,
+                                              float U00, float U01, float U02, float U11, float U12,
+                                              float U22, float acc[28]) {
+    const float j0[6] = {U00, U01, U02, U02 * y1 - U01 * y2, U00 * y2 - U02 * y0, U01 * y0 - U00 * y1};
+    const float j1[6] = {0.f, U11, U12, U12 * y1 - U11 * y2, -U12 * y0, U11 * y0};
+    const float j2[6] = {0.f, 0.f, U22, U22 * y1, -U22 * y0, 0.f};
+    const float rr0 = fmaf(U00, v0, fmaf(U01, v1, U02 * v2));
+    const float rr1 = fmaf(U11, v1, U12 * v2);
+    const float rr2 = U22 * v2;
+    int k = 0;
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c = r; c < 6; ++c, ++k)
+            acc[k] = fmaf(j0[r], j0[c], fmaf(j1[r], j1[c], fmaf(j2[r], j2[c], acc[k])));
+#pragma unroll
+    for (int r = 0; r < 6; ++r) acc[21 + r] = fmaf(j0[r], rr0, fmaf(j1[r], rr1, fmaf(j2[r], rr2, acc[21 + r])));
+    acc[27] = fmaf(rr0, rr0, fmaf(rr1, rr1, fmaf(rr2, rr2, acc[27])));
+}
+
+// Solves A x = b for symmetric positive definite A (row-major 6x6) by
+// Cholesky, with one reciprocal per pivot instead of a division per entry.
+__device__ __forceinline__ bool chol_solve6(const double A[36], const double b[6], double x[6]) {
+    double L[36], inv[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            double s = A[6 * i + j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) s -= L[6 * i + k] * L[6 * j + k];
+            if (i == j) {
+                if (!(s > 0.0)) return false;
+                L[6 * i + i] = sqrt(s);
+                inv[i] = 1.0 / L[6 * i + i];
+            } else {
+                L[6 * i + j] = s * inv[j];
+            }
+        }
+    double y[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        double s = b[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) s -= L[6 * i + k] * y[k];
+        y[i] = s * inv[i];
+    }
+#pragma unroll
+    for (int i = 5; i >= 0; --i) {
+        double s = y[i];
+#pragma unroll
+        for (int k = i + 1; k < 6; ++k) s -= L[6 * k + i] * x[k];
+        x[i] = s * inv[i];
+    }
+    return true;
+}
+
+// H <- exp(xi^) H with xi = (t, w): R = I + A K + B K^2, V = I + B K + C K^2
+// (K = [w]x, th = |w|, A = sin th / th, B = (1 - cos th) / th^2,
+// C = (th - sin th) / th^3).  For th < 1/4 the three coefficients come from
+// their Taylor series in th^2 (seven terms: truncation below 1e-17), which
+// spares the FP64 sine and cosine on the usual small LM steps.
+__device__ __forceinline__ void se3_left(const double xi[6], double H[12]) {
+    const double w0 = xi[3], w1 = xi[4], w2 = xi[5];
+    const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
+    double A, B, C;
+    if (th2 < 0.0625) {
+        // coefficients x^k / (2k+1)!, x^k / (2k+2)!, x^k / (2k+3)! with alternating signs
+        A = 1.0 + th2 * (-1.0 / 6 + th2 * (1.0 / 120 + th2 * (-1.0 / 5040 + th2 * (1.0 / 362880 +
+            th2 * (-1.0 / 39916800 + th2 * (1.0 / 6227020800.0))))));
+        B = 0.5 + th2 * (-1.0 / 24 + th2 * (1.0 / 720 + th2 * (-1.0 / 40320 + th2 * (1.0 / 3628800 +
+            th2 * (-1.0 / 479001600 + th2 * (1.0 / 87178291200.0))))));
+        C = 1.0 / 6 + th2 * (-1.0 / 120 + th2 * (1.0 / 5040 + th2 * (-1.0 / 362880 + th2 * (1.0 / 39916800 +
+            th2 * (-1.0 / 6227020800.0 + th2 * (1.0 / 1307674368000.0))))));
+    } else {
+        const double th = sqrt(th2);
+        double s, c;
+        sincos(th, &s, &c);
+        A = s / th;
+        B = (1.0 - c) / th2;
+        C = (th - s) / (th2 * th);
+    }
+    const double K[9] = {0, -w2, w1, w2, 0, -w0, -w1, w0, 0};
+    double K2[9], Rd[9], Vd[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            K2[3 * r + c] = K[3 * r] * K[c] + K[3 * r + 1] * K[3 + c] + K[3 * r + 2] * K[6 + c];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const double I = (i % 4 == 0) ? 1.0 : 0.0;
+        Rd[i] = I + A * K[i] + B * K2[i];
+        Vd[i] = I + B * K[i] + C * K2[i];
+    }
+    double N[12];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const double td = Vd[3 * r] * xi[0] + Vd[3 * r + 1] * xi[1] + Vd[3 * r + 2] * xi[2];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            N[4 * r + c] = Rd[3 * r] * H[c] + Rd[3 * r + 1] * H[4 + c] + Rd[3 * r + 2] * H[8 + c];
+        N[4 * r + 3] = Rd[3 * r] * H[3] + Rd[3 * r + 1] * H[7] + Rd[3 * r + 2] * H[11] + td;
+    }
+#pragma unroll
+    for (int i = 0; i < 12; ++i) H[i] = N[i];
+}
+
+}  // namespace rl

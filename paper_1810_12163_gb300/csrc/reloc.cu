@@ -134,6 +134,7 @@ rl_status run_relocalise(rl_reloc *r, int n, int level, cudaStream_t s) {
     RL_CK(cudaMemsetAsync(q.n_chosen, 0xFF, sizeof(int32_t) * n, s));
     RL_CK(cudaMemsetAsync(q.n_rounds, 0, sizeof(int32_t) * n, s));
     RL_CK(cudaMemsetAsync(q.round_count, 0, sizeof(int32_t) * 16 * n, s));
+    RL_CK(cudaMemsetAsync(q.dev_err, 0, sizeof(int32_t) * n, s));
     unsigned long long *work = r->prof.on ? r->prof.work : nullptr;
     { PROF(K_LEAVES); RL_TRY(launch_leaves(f, q.frames, n, p.n_trees, hw_max, q.leaves, r->max_w, r->max_h, s, p.k_top, q.mcount, q.prec)); }
     { PROF(K_HYPGEN); RL_TRY(launch_hypgen(q.frames, q.leaves, q.mcount, q.prec, hw_max, mv, p, q.hyp_pose, q.hyp_iter, n, s)); }
@@ -321,6 +322,9 @@ static rl_status fetch_results(rl_reloc *r, int n, cudaStream_t s, rl_result *ou
             o.chosen_slot[c] = cslot[(size_t)i * 16 + c];
         }
     }
+    for (int i = 0; i < n; ++i)
+        if (r->host_results[i].err)
+            return fail(RL_ERR_TIMEOUT, "a bounded device-side wait gave up; the results of this call are invalid");
     return RL_OK;
 }
 
@@ -398,7 +402,8 @@ extern "C" rl_status rl_reloc_create(rl_forest *f, rl_scene *scene, const rl_ran
     rp.lm_lambda0 = p->lm_lambda0; rp.lm_inlier_thresh = p->lm_inlier_thresh; rp.lm_stop = p->lm_stop;
     rp.rank = p->rank; rp.halve_to_one = p->halve_to_one; rp.level = 0;
     rp.max_rounds = rounds_for(p->n_cull, p->k_out, p->halve_to_one);
-    rp.max_pix = p->eta * (rp.max_rounds + 1);
+    // rows of whole 16-pixel tiles: the LM kernel stages tiles with bulk copies
+    rp.max_pix = (p->eta * (rp.max_rounds + 1) + 15) / 16 * 16;
     const int maxm = p->n_trees_used * std::min(p->k_top, f->p.m_max);
     rp.maxm = maxm;
     rp.mpad = maxm | 1;
@@ -447,6 +452,7 @@ extern "C" rl_status rl_reloc_create(rl_forest *f, rl_scene *scene, const rl_ran
     A(n_rounds, B);
     A(frames, B);
     A(result_blob, B * sizeof(DevResult));
+    A(dev_err, B);
 #undef A
     if (s == RL_OK) s = ralloc(r, B * hw, &r->stage_depth);
     if (s == RL_OK) s = ralloc(r, B * hw * 3, &r->stage_rgb);
@@ -582,7 +588,9 @@ __global__ void k_cascade_decide(QueryState lq, CascadeOut co, LaterFrames later
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n || co.done[b]) return;
     const DevResult r = ((const DevResult *)lq.result_blob)[b];
+    const int32_t earlier_err = level > 0 ? co.res[b].err : 0;  // sticky over the levels
     co.res[b] = r;
+    co.res[b].err |= earlier_err;
     co.level[b] = level;
     const int nc = r.n_chosen > 0 ? r.n_chosen : 0;
     for (int c = 0; c < nc; ++c) {
@@ -694,6 +702,9 @@ static rl_status cascade_fetch(rl_cascade *c, int n, cudaStream_t s, rl_result *
             o.chosen_slot[k] = cslot[(size_t)i * 16 + k];
         }
     }
+    for (int i = 0; i < n; ++i)
+        if (res[i].err)
+            return fail(RL_ERR_TIMEOUT, "a bounded device-side wait gave up; the results of this call are invalid");
     return RL_OK;
 }
 

@@ -10,12 +10,9 @@
 #include "internal.h"
 #include "relocgb_dev.cuh"
 #include "kernels.h"
+#include "lm_dev.cuh"
 
 namespace rl {
-
-__device__ __forceinline__ bool round_active(int n, const RParams &p) {
-    return n > p.k_out || (p.halve_to_one && n > 1);
-}
 
 // ---------------------------------------------------------------------------
 // Eq. 5 partial energies.  Block = HT hypotheses of one frame (one per
@@ -197,69 +194,6 @@ __global__ void __launch_bounds__(1024) k_select(SelectArgs a) {
 // by an xor butterfly (every lane ends with the same bits); lane 0 solves
 // the damped normal equations in FP64 and applies exp(xi^) on the left.
 // ---------------------------------------------------------------------------
-__device__ bool chol_solve6(const double A[36], const double b[6], double x[6]) {
-    double L[36];
-    for (int i = 0; i < 36; ++i) L[i] = 0.0;
-    for (int i = 0; i < 6; ++i)
-        for (int j = 0; j <= i; ++j) {
-            double s = A[6 * i + j];
-            for (int k = 0; k < j; ++k) s -= L[6 * i + k] * L[6 * j + k];
-            if (i == j) {
-                if (!(s > 0.0)) return false;
-                L[6 * i + i] = sqrt(s);
-            } else {
-                L[6 * i + j] = s / L[6 * j + j];
-            }
-        }
-    double y[6];
-    for (int i = 0; i < 6; ++i) {
-        double s = b[i];
-        for (int k = 0; k < i; ++k) s -= L[6 * i + k] * y[k];
-        y[i] = s / L[6 * i + i];
-    }
-    for (int i = 5; i >= 0; --i) {
-        double s = y[i];
-        for (int k = i + 1; k < 6; ++k) s -= L[6 * k + i] * x[k];
-        x[i] = s / L[6 * i + i];
-    }
-    return true;
-}
-
-__device__ void se3_left(const double xi[6], double H[12]) {
-    const double w0 = xi[3], w1 = xi[4], w2 = xi[5];
-    const double th2 = w0 * w0 + w1 * w1 + w2 * w2, th = sqrt(th2);
-    double A, B, C;
-    if (th < 1e-8) {
-        A = 1.0 - th2 / 6.0;
-        B = 0.5 - th2 / 24.0;
-        C = 1.0 / 6.0 - th2 / 120.0;
-    } else {
-        double s, c;
-        sincos(th, &s, &c);
-        A = s / th;
-        B = (1.0 - c) / th2;
-        C = (th - s) / (th2 * th);
-    }
-    const double K[9] = {0, -w2, w1, w2, 0, -w0, -w1, w0, 0};
-    double K2[9], Rd[9], Vd[9];
-    for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c)
-            K2[3 * r + c] = K[3 * r] * K[c] + K[3 * r + 1] * K[3 + c] + K[3 * r + 2] * K[6 + c];
-    for (int i = 0; i < 9; ++i) {
-        const double I = (i % 4 == 0) ? 1.0 : 0.0;
-        Rd[i] = I + A * K[i] + B * K2[i];
-        Vd[i] = I + B * K[i] + C * K2[i];
-    }
-    double N[12];
-    for (int r = 0; r < 3; ++r) {
-        const double td = Vd[3 * r] * xi[0] + Vd[3 * r + 1] * xi[1] + Vd[3 * r + 2] * xi[2];
-        for (int c = 0; c < 3; ++c)
-            N[4 * r + c] = Rd[3 * r] * H[c] + Rd[3 * r + 1] * H[4 + c] + Rd[3 * r + 2] * H[8 + c];
-        N[4 * r + 3] = Rd[3 * r] * H[3] + Rd[3 * r + 1] * H[7] + Rd[3 * r + 2] * H[11] + td;
-    }
-    for (int i = 0; i < 12; ++i) H[i] = N[i];
-}
-
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -699,26 +633,6 @@ __global__ void __launch_bounds__(LM_WARPS * 32) k_lm_tiled(LmArgs a) {
 constexpr int LM3_THREADS = 256;
 constexpr int LM3_BPQ = 4;
 
-__device__ __forceinline__ void lm3_accumulate(float y0, float y1, float y2, float v0, float v1, float v2,
-                                               float U00, float U01, float U02, float U11, float U12,
-                                               float U22, float acc[28]) {
-    const float j0[6] = {U00, U01, U02, U02 * y1 - U01 * y2, U00 * y2 - U02 * y0, U01 * y0 - U00 * y1};
-    const float j1[6] = {0.f, U11, U12, U12 * y1 - U11 * y2, -U12 * y0, U11 * y0};
-    const float j2[6] = {0.f, 0.f, U22, U22 * y1, -U22 * y0, 0.f};
-    const float rr0 = fmaf(U00, v0, fmaf(U01, v1, U02 * v2));
-    const float rr1 = fmaf(U11, v1, U12 * v2);
-    const float rr2 = U22 * v2;
-    int k = 0;
-#pragma unroll
-    for (int r = 0; r < 6; ++r)
-#pragma unroll
-        for (int c = r; c < 6; ++c, ++k)
-            acc[k] = fmaf(j0[r], j0[c], fmaf(j1[r], j1[c], fmaf(j2[r], j2[c], acc[k])));
-#pragma unroll
-    for (int r = 0; r < 6; ++r) acc[21 + r] = fmaf(j0[r], rr0, fmaf(j1[r], rr1, fmaf(j2[r], rr2, acc[21 + r])));
-    acc[27] = fmaf(rr0, rr0, fmaf(rr1, rr1, fmaf(rr2, rr2, acc[27])));
-}
-
 __global__ void __launch_bounds__(LM3_THREADS, 2) k_lm_spread(LmArgs a) {
     __shared__ float s_red[LM3_THREADS * 8];         // 8 partial values per thread per pass
     __shared__ double s_H[64][12];                    // current pose per local hypothesis
@@ -816,10 +730,10 @@ __global__ void __launch_bounds__(LM3_THREADS, 2) k_lm_spread(LmArgs a) {
                             ++w_in;
                             if (cov) {
                                 const float4 m1 = __ldg(&t1[base + best_m]);
-                                lm3_accumulate(y0, y1, y2, v0, v1, v2, m0.w, m1.x, m1.y, m1.z, m1.w,
+                                lm_accumulate(y0, y1, y2, v0, v1, v2, m0.w, m1.x, m1.y, m1.z, m1.w,
                                                __ldg(&t2[base + best_m]), acc);
                             } else {
-                                lm3_accumulate(y0, y1, y2, v0, v1, v2, 1.f, 0.f, 0.f, 1.f, 0.f, 1.f, acc);
+                                lm_accumulate(y0, y1, y2, v0, v1, v2, 1.f, 0.f, 0.f, 1.f, 0.f, 1.f, acc);
                             }
                         } else {
                             best_m = -1;
@@ -1167,6 +1081,7 @@ __global__ void __launch_bounds__(256) k_finalize(QueryState q, RParams p, int n
     }
     if (threadIdx.x != 0) return;
     DevResult *out = (DevResult *)q.result_blob + b;
+    out->err = q.dev_err[b];
     out->n_hypotheses = q.n_hyp[b];
     out->n_chosen = q.n_hyp[b] > 0 ? q.n_chosen[b] : 0;
     out->n_pixels = q.n_pix[b];
@@ -1234,7 +1149,9 @@ rl_status launch_select(const SelectArgs &a, int n, cudaStream_t s) {
 
 rl_status launch_lm(const LmArgs &a, int n, cudaStream_t s) {
     const size_t sm = lm_tiled_smem(a.p.mpad);
-    if (a.p.n_cull <= 64) {
+    if (a.p.n_cull <= 64 && lm_cluster_smem(a.p.mpad, a.p.use_cov) <= kLmClusterSmemMax) {
+        return launch_lm_cluster(a, n, s);
+    } else if (a.p.n_cull <= 64) {
         dim3 grid(LM3_BPQ, n);
         k_lm_spread<<<grid, LM3_THREADS, 0, s>>>(a);
     } else if (sm <= kLmSmemMax) {
@@ -1255,6 +1172,7 @@ rl_status prepare_kernels() {
     std::lock_guard<std::mutex> g(mu);
     if (done) return RL_OK;
     RL_CK(cudaFuncSetAttribute(k_lm_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLmSmemMax));
+    RL_TRY(prepare_lm_cluster());
     done = true;
     return RL_OK;
 }
