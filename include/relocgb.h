@@ -287,7 +287,7 @@ rl_status rl_reloc_debug(rl_reloc *r, int32_t q, double *hyp_pose /* n_hyp*12 */
  * (H,px) evaluations, LM (H,px,mode) triples, LM inlier accumulations,
  * LM trial evaluations, rays cast).  Enabling resets all counters.  The
  * paper has no counterpart; its Sec. A.1 timing breakdown is per stage. */
-#define RL_N_KERNELS 10
+#define RL_N_KERNELS 11
 rl_status rl_reloc_profile(rl_reloc *r, int32_t enable);
 rl_status rl_reloc_profile_read(rl_reloc *r, double *ms /* [RL_N_KERNELS] */,
                                 int64_t *launches /* [RL_N_KERNELS] */,

@@ -34,7 +34,7 @@ STATUS_NAMES = {0: "RL_OK", 1: "RL_ERR_INVALID_ARG", 2: "RL_ERR_OOM", 3: "RL_ERR
 RL_HOST, RL_DEVICE = 0, 1
 RL_POSE_FOUND, RL_NO_POSE = 0, 1
 RL_MODES_FP32, RL_MODES_FP16_OFFSET = 0, 1
-RL_N_KERNELS = 10  # kernels the profiler reports (RL_N_KERNELS of the header)
+RL_N_KERNELS = 11  # kernels the profiler reports (RL_N_KERNELS of the header)
 
 
 class Intrinsics(ctypes.Structure):

@@ -63,6 +63,25 @@ __device__ __forceinline__ bool stage1(const HypArgs &a, const Frame &fr, const 
     return max(dr, max(dg, db)) <= a.p.colour_thresh;
 }
 
+// Stage 1 from the colour-check masks: three independent 8-byte loads give
+// every |M(u)| and the colour decision of each mode of the checked pixel.
+__device__ __forceinline__ bool stage1_mask(const HypArgs &a, const Frame &fr, const uint2 *cm, int slot,
+                                            int it, Draw &d) {
+    d = draw(a, fr, slot, it);
+    const uint2 w0 = cm[d.pix[0]], w1 = cm[d.pix[1]], w2 = cm[d.pix[2]];
+    const uint32_t c0 = w0.y >> 24, c1 = w1.y >> 24, c2 = w2.y >> 24;
+    if (c0 == 0 || c1 == 0 || c2 == 0) return false;
+    const uint32_t ctr1 = (TAG_HYP << 16) | (uint32_t)a.p.level;
+    const uint4 r1 = philox(make_uint4(slot, ctr1, it, 1), fr.key0, fr.key1);
+    d.m[0] = draw_below(r1.x, c0);
+    d.m[1] = draw_below(r1.y, c1);
+    d.m[2] = draw_below(r1.z, c2);
+    const uint2 wj = d.j == 0 ? w0 : (d.j == 1 ? w1 : w2);
+    const uint32_t mj = d.j == 0 ? d.m[0] : (d.j == 1 ? d.m[1] : d.m[2]);
+    const uint32_t bits = mj < 32 ? wj.x >> mj : wj.y >> (mj - 32);
+    return (bits & 1u) != 0;
+}
+
 __device__ __forceinline__ bool stage2(const HypArgs &a, const CheckThr &ct, const Frame &fr,
                                        const uint16_t *lv, const uint4 *pr, const int pix[3],
                                        const int m[3]) {
@@ -124,6 +143,7 @@ __global__ void __launch_bounds__(HG_WARPS * 32, 8) k_hypgen(HypArgs a) {
     const uint16_t *lv = a.leaves + (size_t)b * a.p.n_trees * a.hw_max;
     const uint16_t *mc = a.mcount + (size_t)b * a.hw_max;
     const uint4 *pr = a.prec ? a.prec + (size_t)b * a.hw_max : nullptr;
+    const uint2 *cm = a.pcm ? a.pcm + (size_t)b * a.hw_max : nullptr;
     CheckThr ct;
     ct.sq_lo = __double2float_rd(a.p.min_sq_dist * (1.0 - 2e-5));
     ct.sq_hi = __double2float_ru(a.p.min_sq_dist * (1.0 + 2e-5));
@@ -154,7 +174,8 @@ __global__ void __launch_bounds__(HG_WARPS * 32, 8) k_hypgen(HypArgs a) {
     for (int base = 0; base < a.p.max_iter; base += 32) {
         const int it = base + lane;
         Draw d;
-        const bool s1 = it < a.p.max_iter && stage1(a, fr, lv, mc, pr, slot, it, d);
+        const bool s1 = it < a.p.max_iter &&
+                        (cm ? stage1_mask(a, fr, cm, slot, it, d) : stage1(a, fr, lv, mc, pr, slot, it, d));
         const unsigned mask = __ballot_sync(0xffffffffu, s1);
         if (s1) {
             const unsigned e = (tail + __popc(mask & lt)) % HG_RING;
@@ -170,6 +191,50 @@ __global__ void __launch_bounds__(HG_WARPS * 32, 8) k_hypgen(HypArgs a) {
     }
     if (tail - head > 0 && drain(tail - head)) return;
     if (lane == 0) *iter_out = -1;
+}
+
+// Colour-check masks (Sec. 3.2.3, check 1 precomputed): bit m of pixel u is
+// set iff the m-th mode of M(u) passes the colour check against u's RGB;
+// |M(u)| (<= kMaskModes) sits in the top byte.  The same integer test as the
+// per-attempt check, so every decision is unchanged.
+__global__ void __launch_bounds__(256) k_colour_mask(const Frame *__restrict__ frames,
+                                                     const uint16_t *__restrict__ mcount,
+                                                     const uint4 *__restrict__ prec, int hw_max, ModeView mv,
+                                                     RParams p, uint2 *__restrict__ pcm) {
+    const int b = blockIdx.y;
+    const Frame fr = frames[b];
+    const int px = blockIdx.x * blockDim.x + threadIdx.x;
+    if (px >= fr.W * fr.H) return;
+    const size_t o = (size_t)b * hw_max + px;
+    const int cnt = mcount[o];
+    uint32_t lo = 0, hi = 0;
+    if (cnt > 0) {
+        const uint4 rec = prec[o];
+        const uint8_t *pc = fr.rgb + (size_t)px * 3;
+        const int pr = pc[0], pg = pc[1], pb = pc[2];
+        int m = 0;
+        for (int t = 0; t < p.n_trees; ++t) {
+            const int nm = rec_count(rec, t);
+            const uchar4 *col = mv.mrgb + (size_t)(t * mv.leaves_per_tree + rec_leaf(rec, t)) * mv.m_max;
+            for (int r = 0; r < nm; ++r, ++m) {
+                const uchar4 c = col[r];
+                const int dl = max(abs(pr - (int)c.x), max(abs(pg - (int)c.y), abs(pb - (int)c.z)));
+                if (dl <= p.colour_thresh) {
+                    if (m < 32) lo |= 1u << m;
+                    else hi |= 1u << (m - 32);
+                }
+            }
+        }
+    }
+    pcm[o] = make_uint2(lo, hi | ((uint32_t)cnt << 24));
+}
+
+rl_status launch_colour_mask(const Frame *frames, const uint16_t *mcount, const uint4 *prec, int hw_max,
+                             ModeView mv, const RParams &p, uint2 *pcm, int n, int max_hw, cudaStream_t s) {
+    dim3 grid((max_hw + 255) / 256, n);
+    k_colour_mask<<<grid, 256, 0, s>>>(frames, mcount, prec, hw_max, mv, p, pcm);
+    RL_LAUNCH_CK();
+    return RL_OK;
 }
 
 // Successful slots in slot order (block per frame).
@@ -235,9 +300,9 @@ __global__ void k_sample_batch(const Frame *__restrict__ frames, const uint16_t 
 }
 
 rl_status launch_hypgen(const Frame *frames, const uint16_t *leaves, const uint16_t *mcount,
-                        const uint4 *prec, int hw_max, ModeView mv, const RParams &p,
+                        const uint4 *prec, const uint2 *pcm, int hw_max, ModeView mv, const RParams &p,
                         double *hyp_pose, int32_t *hyp_iter, int n, cudaStream_t s) {
-    HypArgs a{frames, leaves, mcount, prec, hw_max, mv, p, hyp_pose, hyp_iter};
+    HypArgs a{frames, leaves, mcount, prec, pcm, hw_max, mv, p, hyp_pose, hyp_iter};
     dim3 grid((p.n_hyp + HG_WARPS - 1) / HG_WARPS, n);
     k_hypgen<<<grid, HG_WARPS * 32, 0, s>>>(a);
     RL_LAUNCH_CK();

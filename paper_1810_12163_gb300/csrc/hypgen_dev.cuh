@@ -13,6 +13,7 @@ struct HypArgs {
     const uint16_t *leaves;  // [B][T][hw_max]
     const uint16_t *mcount;  // [B][hw_max] |M(u)|
     const uint4 *prec;       // [B][hw_max] pixel records (<= 5 trees) or null
+    const uint2 *pcm;        // [B][hw_max] colour-check masks and |M(u)|, or null
     int hw_max;
     ModeView mv;
     RParams p;

@@ -146,6 +146,7 @@ struct QueryState {
     uint16_t *leaves;        // [B][T][HWmax]
     uint16_t *mcount;        // [B][HWmax] |M(u)| per pixel
     uint4 *prec;             // [B][HWmax] per-pixel leaves + counts (<= 5 trees), else null
+    uint2 *pcm;              // [B][HWmax] colour-check bits of M(u) | |M(u)| << 56 (|M(u)| <= 56), else null
     double *hyp_pose;        // [B][N][12]
     int32_t *hyp_iter;       // [B][N]
     int32_t *hyp_list;       // [B][N] slots of successful hypotheses
@@ -196,7 +197,7 @@ struct DevResult {
 // device-side work counters of the scoring kernels (off unless enabled).
 enum KernelId {
     K_LEAVES = 0, K_HYPGEN, K_COMPACT, K_SAMPLE, K_ENERGY, K_SELECT, K_LM, K_RAYCAST, K_FINALIZE,
-    K_HYPPOSE, K_COUNT
+    K_HYPPOSE, K_CMASK, K_COUNT
 };
 // work counters: energy (H,px) pairs, energy (H,px,mode) triples, LM pass-1
 // (H,px) evaluations, LM (H,px,mode) triples, LM inlier accumulations, LM

@@ -99,8 +99,12 @@ rl_status launch_score_poses(const RaycastArgs &a, int n_poses, int npx, float *
 rl_status launch_finalize(const QueryState &q, const RParams &p, int n_tiles, int ranked, int n,
                           cudaStream_t s);
 rl_status launch_hypgen(const Frame *frames, const uint16_t *leaves, const uint16_t *mcount,
-                        const uint4 *prec, int hw_max, ModeView mv, const RParams &p,
+                        const uint4 *prec, const uint2 *pcm, int hw_max, ModeView mv, const RParams &p,
                         double *hyp_pose, int32_t *hyp_iter, int n, cudaStream_t s);
+// Largest |M(u)| the colour-check masks cover.
+constexpr int kMaskModes = 56;
+rl_status launch_colour_mask(const Frame *frames, const uint16_t *mcount, const uint4 *prec, int hw_max,
+                             ModeView mv, const RParams &p, uint2 *pcm, int n, int max_hw, cudaStream_t s);
 rl_status launch_hyppose(const Frame *frames, const uint16_t *leaves, const uint16_t *mcount,
                          const uint4 *prec, int hw_max, ModeView mv, const RParams &p,
                          double *hyp_pose, int32_t *hyp_iter, int n, cudaStream_t s);

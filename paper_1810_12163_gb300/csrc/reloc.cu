@@ -137,7 +137,8 @@ rl_status run_relocalise(rl_reloc *r, int n, int level, cudaStream_t s) {
     RL_CK(cudaMemsetAsync(q.dev_err, 0, sizeof(int32_t) * n, s));
     unsigned long long *work = r->prof.on ? r->prof.work : nullptr;
     { PROF(K_LEAVES); RL_TRY(launch_leaves(f, q.frames, n, p.n_trees, hw_max, q.leaves, r->max_w, r->max_h, s, p.k_top, q.mcount, q.prec)); }
-    { PROF(K_HYPGEN); RL_TRY(launch_hypgen(q.frames, q.leaves, q.mcount, q.prec, hw_max, mv, p, q.hyp_pose, q.hyp_iter, n, s)); }
+    if (q.pcm) { PROF(K_CMASK); RL_TRY(launch_colour_mask(q.frames, q.mcount, q.prec, hw_max, mv, p, q.pcm, n, hw_max, s)); }
+    { PROF(K_HYPGEN); RL_TRY(launch_hypgen(q.frames, q.leaves, q.mcount, q.prec, q.pcm, hw_max, mv, p, q.hyp_pose, q.hyp_iter, n, s)); }
     { PROF(K_HYPPOSE); RL_TRY(launch_hyppose(q.frames, q.leaves, q.mcount, q.prec, hw_max, mv, p, q.hyp_pose, q.hyp_iter, n, s)); }
     { PROF(K_COMPACT); RL_TRY(launch_compact(q.hyp_iter, N, q.hyp_list, q.n_hyp, n, s)); }
     { PROF(K_SAMPLE); RL_TRY(launch_sample_batch(q.frames, q.mcount, hw_max, p, 0, q.pix, q.xc, n, s));
@@ -418,6 +419,7 @@ extern "C" rl_status rl_reloc_create(rl_forest *f, rl_scene *scene, const rl_ran
     A(leaves, B * p->n_trees_used * hw);
     A(mcount, B * hw);
     if (p->n_trees_used <= kRecTrees) A(prec, B * hw);
+    if (p->n_trees_used <= kRecTrees && maxm <= kMaskModes) A(pcm, B * hw);
     A(hyp_pose, B * N * 12);
     A(hyp_iter, B * N);
     A(hyp_list, B * N);
@@ -841,7 +843,8 @@ static void prof_free(rl_reloc *r) {
 }  // namespace rl
 
 static const char *kKernelNames[K_COUNT] = {"leaves",  "hypgen", "compact", "sample_batch", "energy",
-                                             "select", "lm",     "raycast_score", "finalize", "hyppose"};
+                                             "select", "lm",     "raycast_score", "finalize", "hyppose",
+                                             "colour_mask"};
 static_assert(K_COUNT == RL_N_KERNELS, "kernel ids and the public count differ");
 
 extern "C" const char *rl_kernel_name(int32_t kid) {
