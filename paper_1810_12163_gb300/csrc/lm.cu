@@ -3,23 +3,30 @@
 //
 // The LMC_CTAS CTAs of a cluster share the frame's surviving hypotheses
 // (n <= 64) and split its pixel set by tiles of LMC_P pixels: CTA c takes
-// tiles c, c + LMC_CTAS, ...  Each LM iteration
-//   1. streams the CTA's tiles of the mode table (rows of decoded M(u)) into
-//      shared memory with bulk asynchronous copies on an mbarrier pipeline;
-//      thread t works for hypothesis t % HB on pixel group t / HB (HB = next
-//      power of two >= n), so the 32 lanes of a warp usually read the same
-//      staged row (broadcast) and follow the same control flow;
-//   2. finds, per (hypothesis, pixel), the nearest mode under the pixel's
-//      Mahalanobis metric, keeps it if within the inlier radius, and adds its
-//      terms to FP32 normal equations;
-//   3. reduces the normal equations over the CTA in a fixed order, then over
-//      the cluster through distributed shared memory (ranks in order), so
-//      that every CTA holds bit-identical sums;
-//   4. solves the damped 6x6 system of each hypothesis in FP64 (redundantly
-//      in every CTA, hence identical decisions everywhere and no broadcast);
-//   5. evaluates the trial pose on the same correspondences and accepts it
-//      iff the cost decreases (same two-level reduction).
-// Two cluster barriers per iteration; all CTAs take the same branches.
+// tiles c, c + LMC_CTAS, ...  A pass streams the CTA's tiles of the mode
+// table (rows of decoded M(u)) into shared memory with bulk asynchronous
+// copies on an mbarrier pipeline; thread t works for hypothesis t % HB on
+// pixel group t / HB (HB = next power of two >= n), so the lanes of a warp
+// mostly read the same staged row (broadcast) and share control flow.  Per
+// (hypothesis, pixel) a pass finds the nearest mode under the pixel's
+// Mahalanobis metric, keeps it if within the inlier radius and adds its
+// terms to FP32 normal equations.
+//
+// The iterations of the method (normal equations at H, damped solve, cost
+// of the step on the same correspondences, accept iff it decreases) are
+// regrouped so that each iteration needs one pass: the pass at the trial
+// pose Hn evaluates the step's cost on the current correspondences (read
+// from the staged tile) and, in the same sweep, the correspondences and
+// normal equations at Hn, which become those of the next iteration if the
+// step is accepted; after a rejection the pose, and so its normal
+// equations, are unchanged.  Correspondences are double-buffered per
+// hypothesis (int16).  The arithmetic and its order are those of the plain
+// sequence, so the results are the same.
+//
+// Sums are reduced over the CTA in group order and over the cluster through
+// distributed shared memory in rank order, so every CTA holds bit-identical
+// values; each CTA solves every hypothesis's 6x6 system in FP64 and takes
+// the same decisions, with one cluster barrier per iteration.
 //
 // Every wait on a copy is bounded: a wait that gives up marks the frame in
 // dev_err, the CTA skips the rest of its work while keeping step with the
@@ -40,12 +47,12 @@ constexpr int LMC_THREADS = 256;
 constexpr int LMC_P = 16;        // pixels per tile (max_pix is a multiple)
 constexpr int LMC_STAGES = 2;
 constexpr int LMC_HMAX = 64;
-constexpr int LMC_NV = 29;       // 21 J^T J + 6 J^T r + cost + inlier count
+constexpr int LMC_NV = 30;       // 21 J^T J + 6 J^T r + cost, inlier count, trial cost
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 struct LmcLayout {
     uint32_t t0, t1, t2, xc, cnt, stage, tx;
-    uint32_t H, Hn, lambda, tot, loc, trial, state, flag, bar, total;
+    uint32_t H, Hn, lambda, tot, nw, loc, state, cbuf, flag, bar, total;
 };
 
 __host__ __device__ inline uint32_t lmc_a16(uint32_t x) { return (x + 15u) & ~15u; }
@@ -71,9 +78,10 @@ __host__ __device__ inline LmcLayout lmc_layout(int stride, bool cov) {
     L.Hn = o; o += LMC_HMAX * 12 * 8;
     L.lambda = o; o += LMC_HMAX * 8;
     L.tot = o; o += LMC_HMAX * LMC_NV * 4;
-    L.loc = o; o += LMC_HMAX * LMC_NV * 4;
-    L.trial = o; o += LMC_HMAX * 4;
+    L.nw = o; o += LMC_HMAX * LMC_NV * 4;
+    L.loc = o; o += 2 * LMC_HMAX * LMC_NV * 4;
     L.state = o; o += LMC_HMAX * 4;
+    L.cbuf = o; o += LMC_HMAX * 4;
     L.flag = o; o += 16;
     L.bar = o; o += LMC_STAGES * 8;
     L.total = lmc_a16(o);
@@ -113,6 +121,16 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
         : "memory");
 }
 
+// One pass over this CTA's tiles at pose P (per hypothesis, FP32 copy in
+// registers): nearest mode, inlier test and normal-equation terms for every
+// (hypothesis, pixel), correspondences written to buffer `wbuf`; with
+// `trial`, also the cost of the correspondences in buffer `rbuf` at P.
+struct LmcPass {
+    float acc[28];
+    int nin;
+    float trial;
+};
+
 __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k_lm_cluster(LmArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     cg::cluster_group cluster = cg::this_cluster();
@@ -134,9 +152,10 @@ __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 
     double(*s_Hn)[12] = (double(*)[12])(smem + L.Hn);
     double *s_lambda = (double *)(smem + L.lambda);
     float(*s_tot)[LMC_NV] = (float(*)[LMC_NV])(smem + L.tot);
-    float(*s_loc)[LMC_NV] = (float(*)[LMC_NV])(smem + L.loc);
-    float *s_tloc = (float *)(smem + L.trial);  // this CTA's trial sums
+    float(*s_new)[LMC_NV] = (float(*)[LMC_NV])(smem + L.nw);
+    float *s_loc = (float *)(smem + L.loc);  // two buffers of [LMC_HMAX][LMC_NV]
     int *s_state = (int *)(smem + L.state);
+    int *s_cbuf = (int *)(smem + L.cbuf);
     volatile int *s_abort = (volatile int *)(smem + L.flag);
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
     const uint32_t bar0 = sbase + L.bar;
@@ -148,7 +167,9 @@ __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 
     const float *g_t2 = a.q.tab2 + row0 * stride;
     const float4 *g_xc = a.q.xc + row0;
     const int16_t *g_cnt = a.q.tab_cnt + row0;
-    int32_t *corr = a.q.corr + (size_t)b * NC * a.p.max_pix;  // [pixel][n]
+    // correspondences: two int16 buffers of [pixel][n] in the frame's slice
+    int16_t *corr0 = (int16_t *)(a.q.corr + (size_t)b * NC * a.p.max_pix);
+    const size_t cstride = (size_t)NC * a.p.max_pix;
     const int n_tiles = (a.n_pix + LMC_P - 1) / LMC_P;
     const int my_tiles = crank < n_tiles ? (n_tiles - crank + LMC_CTAS - 1) / LMC_CTAS : 0;
     const float thr2 = (float)(a.p.lm_inlier_thresh * a.p.lm_inlier_thresh);
@@ -157,6 +178,7 @@ __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 
     for (int i = t; i < n; i += LMC_THREADS) {
         s_lambda[i] = a.p.lm_lambda0;
         s_state[i] = 1;
+        s_cbuf[i] = 0;
     }
     if (t == 0) {
         *s_abort = 0;
@@ -184,21 +206,22 @@ __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 
     };
 
     unsigned w_pairs = 0, w_modes = 0, w_in = 0, w_trial = 0;
-    for (int it = 0; it < a.p.lm_max_iter; ++it) {
-        if (!__syncthreads_or(mine && s_state[hl])) break;  // identical in every CTA
-        const bool act = mine && s_state[hl];
+    // The pass; act: this thread's hypothesis takes part, P: its pose.
+    auto pass = [&](bool act, const double *P, bool trial, int rbuf, int wbuf) {
+        LmcPass o;
+#pragma unroll
+        for (int k = 0; k < 28; ++k) o.acc[k] = 0.f;
+        o.nin = 0;
+        o.trial = 0.f;
         float r00 = 0.f, r01 = 0.f, r02 = 0.f, tx = 0.f, r10 = 0.f, r11 = 0.f, r12 = 0.f, ty = 0.f;
         float r20 = 0.f, r21 = 0.f, r22 = 0.f, tz = 0.f;
         if (act) {
-            const double *H = s_H[hl];
-            r00 = (float)H[0]; r01 = (float)H[1]; r02 = (float)H[2]; tx = (float)H[3];
-            r10 = (float)H[4]; r11 = (float)H[5]; r12 = (float)H[6]; ty = (float)H[7];
-            r20 = (float)H[8]; r21 = (float)H[9]; r22 = (float)H[10]; tz = (float)H[11];
+            r00 = (float)P[0]; r01 = (float)P[1]; r02 = (float)P[2]; tx = (float)P[3];
+            r10 = (float)P[4]; r11 = (float)P[5]; r12 = (float)P[6]; ty = (float)P[7];
+            r20 = (float)P[8]; r21 = (float)P[9]; r22 = (float)P[10]; tz = (float)P[11];
         }
-        float acc[28];
-#pragma unroll
-        for (int k = 0; k < 28; ++k) acc[k] = 0.f;
-        int nin = 0;
+        const int16_t *cr = corr0 + (size_t)rbuf * cstride;
+        int16_t *cw = corr0 + (size_t)wbuf * cstride;
         // region 0 was last written by threads (partials): order those writes
         // before the copies that overwrite it
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -223,6 +246,8 @@ __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 
                 const int i0 = (crank + j * LMC_CTAS) * LMC_P;
                 const int np = min(LMC_P, a.n_pix - i0);
                 for (int il = g; il < np; il += G) {
+                    const size_t ci = (size_t)(i0 + il) * n + hl;
+                    const int m_old = trial ? (int)cr[ci] : -1;
                     const int cnt = s_cnt[il];
                     int best_m = -1;
                     if (cnt > 0) {
@@ -263,48 +288,78 @@ __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 
                             const float4 m0 = s_t0[base + best_m];
                             const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
                             if (fmaf(v0, v0, fmaf(v1, v1, v2 * v2)) <= thr2) {
-                                ++nin;
+                                ++o.nin;
                                 ++w_in;
                                 if (cov) {
                                     const float4 m1 = s_t1[base + best_m];
                                     lm_accumulate(y0, y1, y2, v0, v1, v2, m0.w, m1.x, m1.y, m1.z, m1.w,
-                                                  s_t2[base + best_m], acc);
+                                                  s_t2[base + best_m], o.acc);
                                 } else {
-                                    lm_accumulate(y0, y1, y2, v0, v1, v2, 1.f, 0.f, 0.f, 1.f, 0.f, 1.f, acc);
+                                    lm_accumulate(y0, y1, y2, v0, v1, v2, 1.f, 0.f, 0.f, 1.f, 0.f, 1.f, o.acc);
                                 }
                             } else {
                                 best_m = -1;
                             }
                         }
+                        if (m_old >= 0) {  // the previous correspondence at the trial pose
+                            ++w_trial;
+                            const float4 m0 = s_t0[base + m_old];
+                            const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+                            if (cov) {
+                                const float4 m1 = s_t1[base + m_old];
+                                const float q0 = fmaf(m0.w, v0, fmaf(m1.x, v1, m1.y * v2));
+                                const float q1 = fmaf(m1.z, v1, m1.w * v2);
+                                const float q2 = s_t2[base + m_old] * v2;
+                                o.trial = fmaf(q0, q0, fmaf(q1, q1, fmaf(q2, q2, o.trial)));
+                            } else {
+                                o.trial = fmaf(v0, v0, fmaf(v1, v1, fmaf(v2, v2, o.trial)));
+                            }
+                        }
                     }
-                    corr[(size_t)(i0 + il) * n + hl] = best_m;  // local mode index in the row
+                    cw[ci] = (int16_t)best_m;  // local mode index in the row, -1: none
                 }
             }
             __syncthreads();  // stage s consumed by every thread
             if (t == 0 && !*s_abort && j + LMC_STAGES < my_tiles) issue(j + LMC_STAGES, s);
         }
-        // normal equations: CTA sums in group order, then cluster sums in rank order
+        return o;
+    };
+    // Sums of this CTA's pass over groups (fixed order) into loc buffer lb,
+    // then over the cluster's CTAs (rank order) into dst.
+    auto reduce = [&](const LmcPass &o, int lb, float (*dst)[LMC_NV]) {
         float *mypart = s_acc + t * LMC_NV;
 #pragma unroll
-        for (int k = 0; k < 28; ++k) mypart[k] = acc[k];
-        mypart[28] = (float)nin;
+        for (int k = 0; k < 28; ++k) mypart[k] = o.acc[k];
+        mypart[28] = (float)o.nin;
+        mypart[29] = o.trial;
         __syncthreads();
-        for (int o = t; o < n * LMC_NV; o += LMC_THREADS) {
-            const int h = o / LMC_NV, k = o % LMC_NV;
+        float *loc = s_loc + lb * (LMC_HMAX * LMC_NV);
+        for (int e = t; e < n * LMC_NV; e += LMC_THREADS) {
+            const int h = e / LMC_NV, k = e % LMC_NV;
             float v = 0.f;
             for (int gg = 0; gg < G; ++gg) v += s_acc[(gg * HB + h) * LMC_NV + k];
-            s_loc[h][k] = v;
+            loc[e] = v;
         }
+        // Double-buffered loc: a CTA rewrites buffer lb two reductions later,
+        // after the next barrier, which every CTA reaches only after reading
+        // buffer lb here; one barrier per reduction suffices.
         cluster.sync();
-        for (int o = t; o < n * LMC_NV; o += LMC_THREADS) {
-            const int h = o / LMC_NV, k = o % LMC_NV;
+        for (int e = t; e < n * LMC_NV; e += LMC_THREADS) {
             float v = 0.f;
-            for (int r = 0; r < LMC_CTAS; ++r) v += cluster.map_shared_rank(&s_loc[0][0], r)[h * LMC_NV + k];
-            s_tot[h][k] = v;
+            for (int r = 0; r < LMC_CTAS; ++r) v += cluster.map_shared_rank(loc, r)[e];
+            dst[e / LMC_NV][e % LMC_NV] = v;
         }
         __syncthreads();
-        // FP64 solve; hypothesis h on thread (h % 8) * 32 + h / 8, spreading
-        // the narrow FP64 pipe's work over all warps
+    };
+
+    // normal equations and correspondences at the initial poses
+    {
+        const LmcPass o = pass(mine, s_H[hl < n ? hl : 0], false, 0, 0);
+        reduce(o, 0, s_tot);
+    }
+    for (int it = 0; it < a.p.lm_max_iter; ++it) {
+        // damped FP64 solve; hypothesis h on thread (h % 8) * 32 + h / 8,
+        // spreading the narrow FP64 pipe's work over all warps
         {
             const int h = (t & 31) * 8 + (t >> 5);
             if ((t & 31) < LMC_HMAX / 8 && h < n && s_state[h]) {
@@ -338,66 +393,25 @@ __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 
                 }
             }
         }
-        __syncthreads();
-        // trial cost of the new pose on the same correspondences
-        const bool act2 = mine && s_state[hl];
-        float trial = 0.f;
-        if (act2 && !*s_abort) {
-            const double *Hn = s_Hn[hl];
-            const float s00 = (float)Hn[0], s01 = (float)Hn[1], s02 = (float)Hn[2], u0 = (float)Hn[3];
-            const float s10 = (float)Hn[4], s11 = (float)Hn[5], s12 = (float)Hn[6], u1 = (float)Hn[7];
-            const float s20 = (float)Hn[8], s21 = (float)Hn[9], s22 = (float)Hn[10], u2 = (float)Hn[11];
-            for (int j = 0; j < my_tiles; ++j) {
-                const int i0 = (crank + j * LMC_CTAS) * LMC_P;
-                const int np = min(LMC_P, a.n_pix - i0);
-                for (int il = g; il < np; il += G) {
-                    const int i = i0 + il;
-                    const int m = corr[(size_t)i * n + hl];
-                    if (m < 0) continue;
-                    ++w_trial;
-                    const float4 x = g_xc[i];
-                    const size_t e = (size_t)i * stride + m;
-                    const float4 m0 = g_t0[e];
-                    const float y0 = fmaf(s00, x.x, fmaf(s01, x.y, fmaf(s02, x.z, u0)));
-                    const float y1 = fmaf(s10, x.x, fmaf(s11, x.y, fmaf(s12, x.z, u1)));
-                    const float y2 = fmaf(s20, x.x, fmaf(s21, x.y, fmaf(s22, x.z, u2)));
-                    const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
-                    if (cov) {
-                        const float4 m1 = g_t1[e];
-                        const float q0 = fmaf(m0.w, v0, fmaf(m1.x, v1, m1.y * v2));
-                        const float q1 = fmaf(m1.z, v1, m1.w * v2);
-                        const float q2 = g_t2[e] * v2;
-                        trial = fmaf(q0, q0, fmaf(q1, q1, fmaf(q2, q2, trial)));
-                    } else {
-                        trial = fmaf(v0, v0, fmaf(v1, v1, fmaf(v2, v2, trial)));
-                    }
-                }
-            }
-        }
-        s_acc[t] = trial;
-        __syncthreads();
-        for (int h = t; h < n; h += LMC_THREADS) {
-            float v = 0.f;
-            for (int gg = 0; gg < G; ++gg) v += s_acc[gg * HB + h];
-            s_tloc[h] = v;
-        }
-        // Separate buffers make two barriers per iteration enough: a CTA
-        // rewrites s_loc only after the second barrier of this iteration,
-        // which every CTA reaches after reading s_loc, and rewrites s_tloc
-        // only after the first barrier of the next iteration, which every
-        // CTA reaches after reading s_tloc.
-        cluster.sync();
+        if (!__syncthreads_or(mine && s_state[hl])) break;  // identical in every CTA
+        // trial cost of the step on the current correspondences, and the
+        // normal equations at the trial pose (used if the step is accepted)
+        const bool act = mine && s_state[hl];
+        const int ob = act ? s_cbuf[hl] : 0;
+        const LmcPass o = pass(act, s_Hn[hl < n ? hl : 0], true, ob, ob ^ 1);
+        reduce(o, (it + 1) & 1, s_new);
         for (int h = t; h < n; h += LMC_THREADS) {
             if (!s_state[h]) continue;
-            float v = 0.f;
-            for (int r = 0; r < LMC_CTAS; ++r) v += cluster.map_shared_rank(s_tloc, r)[h];
-            if (v < s_tot[h][27]) {
+            if (s_new[h][29] < s_tot[h][27]) {
                 for (int i = 0; i < 12; ++i) s_H[h][i] = s_Hn[h][i];
+                for (int k = 0; k < 29; ++k) s_tot[h][k] = s_new[h][k];
+                s_cbuf[h] ^= 1;
                 s_lambda[h] /= 10.0;
             } else {
                 s_lambda[h] *= 10.0;
             }
         }
+        __syncthreads();
     }
     __syncthreads();  // the last accept/reject updates of s_H before other threads write them out
     if (crank == 0)
