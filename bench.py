@@ -203,6 +203,20 @@ def algorithmic_flops(kernel, work, p):
     return None
 
 
+# Hypothesis generation is integer work: per stage-1 attempt two Philox4x32-10
+# blocks (10 rounds of two 32x32->64 products = 4 ops, 4 xor, 2 key adds:
+# 100 ops each) and 3 multiply-shift draws, 3 mask loads and a bit test
+# (10 ops): 210; per stage-2 evaluation 150 (3 record decodes 30, 3 mode
+# positions 12, spread 3 x 8, 3 back-projections 3 x 12, rigidity 3 x 16).
+HYP_OPS_ATTEMPT, HYP_OPS_STAGE2 = 210, 150
+
+
+def algorithmic_int_ops(kernel, work):
+    if kernel == "hypgen":
+        return HYP_OPS_ATTEMPT * work["hyp_attempts"] + HYP_OPS_STAGE2 * work["hyp_stage2"]
+    return None
+
+
 def roofline(kernels, work, p, n_frames_profiled, w, sm_count, pk):
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     kd = kernels[dom]
@@ -221,10 +235,34 @@ def roofline(kernels, work, p, n_frames_profiled, w, sm_count, pk):
         hp = pk["hbm_gbs"] if pk else 6800.0
         out.update({"bound": "hbm", "achieved": ach, "peak": hp, "unit": "GB/s", "frac": ach / hp,
                     "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs" if pk else "fallback"})
+    elif algorithmic_int_ops(dom, work) is not None:
+        ops = algorithmic_int_ops(dom, work)
+        int_peak = fp32_peak / 2  # one 32-bit integer op per lane per clock
+        ach = ops / max(1, kd["launches"]) / avg_s / 1e12
+        out.update({"bound": "alu", "achieved": ach, "peak": int_peak, "unit": "Tops/s",
+                    "frac": ach / int_peak, "traffic": None,
+                    "peak_source": f"derived: {sm_count} SMs x 128 INT32 lanes x max SM clock"})
     else:
-        # hypothesis generation: latency/divergence bound; report issue-rate proxy
         out.update({"bound": "alu", "achieved": None, "peak": fp32_peak, "unit": "TFLOP/s",
                     "frac": None, "traffic": None})
+    return out
+
+
+def kernel_rooflines(kernels, work, p, sm_count, pk):
+    """Achieved fraction of each kernel with an algorithmic work model."""
+    fp32_peak = sm_count * FP32_LANES_PER_SM * 2 * (pk.get("sm_max_mhz", 2070.0) if pk else 2070.0) * 1e6 / 1e12
+    out = {}
+    for k, kd in kernels.items():
+        if not kd["launches"] or kd["ms"] <= 0:
+            continue
+        s = kd["ms"] / 1e3
+        f = algorithmic_flops(k, work, p)
+        if f is not None:
+            out[k] = {"achieved": f / s / 1e12, "unit": "TFLOP/s", "frac": f / s / 1e12 / fp32_peak}
+            continue
+        o = algorithmic_int_ops(k, work)
+        if o is not None:
+            out[k] = {"achieved": o / s / 1e12, "unit": "Tops/s", "frac": o / s / 1e12 / (fp32_peak / 2)}
     return out
 
 
@@ -358,6 +396,8 @@ def run_ours(args):
         "gpu_launches": int(sum(k["launches"] for k in kernels.values())),
         "kernels_ms": {k: round(v["ms"], 4) for k, v in kernels.items()},
         "roofline": roofline(kernels, work, w.ransac, B * args.steps, w, sm_count, pk),
+        "kernel_rooflines": kernel_rooflines(kernels, work, w.ransac, sm_count, pk),
+        "work_per_step": {k: v // max(1, args.steps) for k, v in work.items()},
         "clocks": clk.summary(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.profile_only:

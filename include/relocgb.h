@@ -282,16 +282,19 @@ rl_status rl_reloc_debug(rl_reloc *r, int32_t q, double *hyp_pose /* n_hyp*12 */
 /* Per-kernel timing of a relocaliser: when enabled, every kernel launch of
  * its calls is bracketed by CUDA events on the caller's stream; durations
  * and launch counts accumulate per kernel (ids 0..RL_N_KERNELS-1, names
- * from rl_kernel_name), and the scoring kernels count their work units
- * (uint64 [7]: energy (H,px) pairs, energy (H,px,mode) triples, LM pass-1
- * (H,px) evaluations, LM (H,px,mode) triples, LM inlier accumulations,
- * LM trial evaluations, rays cast).  Enabling resets all counters.  The
+ * from rl_kernel_name), and the kernels count their work units (uint64
+ * [RL_N_WORK]: energy (H,px) pairs, energy (H,px,mode) triples, LM (H,px)
+ * nearest-mode searches, LM (H,px,mode) triples, LM inlier accumulations,
+ * LM trial evaluations, rays cast, generation attempts (stage 1: draws and
+ * colour check), generation stage-2 evaluations (spread and rigidity)).
+ * Enabling resets all counters.  The
  * paper has no counterpart; its Sec. A.1 timing breakdown is per stage. */
 #define RL_N_KERNELS 11
+#define RL_N_WORK 9
 rl_status rl_reloc_profile(rl_reloc *r, int32_t enable);
 rl_status rl_reloc_profile_read(rl_reloc *r, double *ms /* [RL_N_KERNELS] */,
                                 int64_t *launches /* [RL_N_KERNELS] */,
-                                uint64_t *work /* [7] */);
+                                uint64_t *work /* [RL_N_WORK] */);
 const char *rl_kernel_name(int32_t kernel_id);
 
 /* ---- cascade (Sec. 3.2.5) -------------------------------------------- */

@@ -12,6 +12,7 @@ import numpy as np
 
 from . import binding, presets  # noqa: F401
 from .binding import RL_N_KERNELS as N_KERNELS
+from .binding import RL_N_WORK as N_WORK
 from .binding import (RL_DEVICE, RL_HOST, RL_NO_POSE, RL_POSE_FOUND,  # noqa: F401
                       ForestParams, Intrinsics, RansacParams, RelocError, Result, call, lib)
 
@@ -242,12 +243,13 @@ class Relocaliser:
     def profile_read(self):
         ms = np.zeros(N_KERNELS)
         launches = np.zeros(N_KERNELS, np.int64)
-        work = np.zeros(7, np.uint64)
+        work = np.zeros(N_WORK, np.uint64)
         call("rl_reloc_profile_read", self.h, ms.ctypes.data_as(ctypes.c_void_p),
              launches.ctypes.data_as(ctypes.c_void_p), work.ctypes.data_as(ctypes.c_void_p))
         names = [lib().rl_kernel_name(i).decode() for i in range(N_KERNELS)]
         kernels = {names[i]: dict(ms=float(ms[i]), launches=int(launches[i])) for i in range(N_KERNELS)}
-        keys = ["energy_pairs", "energy_modes", "lm_pairs", "lm_modes", "lm_inliers", "lm_trial", "rays"]
+        keys = ["energy_pairs", "energy_modes", "lm_pairs", "lm_modes", "lm_inliers", "lm_trial", "rays",
+                "hyp_attempts", "hyp_stage2"]
         return kernels, {k: int(v) for k, v in zip(keys, work)}
 
     def debug(self, q: int = 0):

@@ -154,7 +154,15 @@ __global__ void __launch_bounds__(HG_WARPS * 32, 8) k_hypgen(HypArgs a) {
     const unsigned lt = (1u << lane) - 1u;
     // Stage 2 on the pending entries head .. head + n - 1 (n <= 32); the
     // winning lane stores its iteration.
+    unsigned n_att = 0, n_s2 = 0;  // stage-1 attempts and stage-2 evaluations (profiling)
+    auto count = [&]() {
+        if (a.work && lane == 0) {
+            atomicAdd(&a.work[W_HYP_ATTEMPTS], (unsigned long long)n_att);
+            atomicAdd(&a.work[W_HYP_STAGE2], (unsigned long long)n_s2);
+        }
+    };
     auto drain = [&](unsigned n) -> bool {
+        n_s2 += n;
         bool ok = false;
         int it = 0;
         if ((unsigned)lane < n) {
@@ -177,6 +185,7 @@ __global__ void __launch_bounds__(HG_WARPS * 32, 8) k_hypgen(HypArgs a) {
         const bool s1 = it < a.p.max_iter &&
                         (cm ? stage1_mask(a, fr, cm, slot, it, d) : stage1(a, fr, lv, mc, pr, slot, it, d));
         const unsigned mask = __ballot_sync(0xffffffffu, s1);
+        n_att += (unsigned)min(32, a.p.max_iter - base);
         if (s1) {
             const unsigned e = (tail + __popc(mask & lt)) % HG_RING;
             ring[e] = make_int4(it | (d.j << 30), d.pix[0], d.pix[1], d.pix[2]);
@@ -185,12 +194,15 @@ __global__ void __launch_bounds__(HG_WARPS * 32, 8) k_hypgen(HypArgs a) {
         tail += __popc(mask);
         __syncwarp();
         if (tail - head >= 32) {
-            if (drain(32)) return;
+            if (drain(32)) {
+                count();
+                return;
+            }
             __syncwarp();
         }
     }
-    if (tail - head > 0 && drain(tail - head)) return;
-    if (lane == 0) *iter_out = -1;
+    if (!(tail - head > 0 && drain(tail - head)) && lane == 0) *iter_out = -1;
+    count();
 }
 
 // Colour-check masks (Sec. 3.2.3, check 1 precomputed): bit m of pixel u is
@@ -301,8 +313,8 @@ __global__ void k_sample_batch(const Frame *__restrict__ frames, const uint16_t 
 
 rl_status launch_hypgen(const Frame *frames, const uint16_t *leaves, const uint16_t *mcount,
                         const uint4 *prec, const uint2 *pcm, int hw_max, ModeView mv, const RParams &p,
-                        double *hyp_pose, int32_t *hyp_iter, int n, cudaStream_t s) {
-    HypArgs a{frames, leaves, mcount, prec, pcm, hw_max, mv, p, hyp_pose, hyp_iter};
+                        double *hyp_pose, int32_t *hyp_iter, unsigned long long *work, int n, cudaStream_t s) {
+    HypArgs a{frames, leaves, mcount, prec, pcm, hw_max, mv, p, hyp_pose, hyp_iter, work};
     dim3 grid((p.n_hyp + HG_WARPS - 1) / HG_WARPS, n);
     k_hypgen<<<grid, HG_WARPS * 32, 0, s>>>(a);
     RL_LAUNCH_CK();

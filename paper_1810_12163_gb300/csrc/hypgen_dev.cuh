@@ -19,6 +19,7 @@ struct HypArgs {
     RParams p;
     double *hyp_pose;        // [B][N][12]
     int32_t *hyp_iter;       // [B][N]
+    unsigned long long *work;  // profiling counters or null
 };
 
 __device__ __forceinline__ float3 backproject(const Frame &fr, int p) {

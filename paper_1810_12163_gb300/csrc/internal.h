@@ -202,7 +202,10 @@ enum KernelId {
 // work counters: energy (H,px) pairs, energy (H,px,mode) triples, LM pass-1
 // (H,px) evaluations, LM (H,px,mode) triples, LM inlier accumulations, LM
 // pass-2 evaluations, raycast rays
-enum WorkId { W_E_PAIRS = 0, W_E_MODES, W_LM_PAIRS, W_LM_MODES, W_LM_INLIERS, W_LM_TRIAL, W_RAYS, W_COUNT };
+enum WorkId {
+    W_E_PAIRS = 0, W_E_MODES, W_LM_PAIRS, W_LM_MODES, W_LM_INLIERS, W_LM_TRIAL, W_RAYS, W_HYP_ATTEMPTS,
+    W_HYP_STAGE2, W_COUNT
+};
 
 struct Profiler {
     bool on = false;

@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(128) k_hyppose(HypArgs a) {
 rl_status launch_hyppose(const Frame *frames, const uint16_t *leaves, const uint16_t *mcount,
                          const uint4 *prec, int hw_max, ModeView mv, const RParams &p,
                          double *hyp_pose, int32_t *hyp_iter, int n, cudaStream_t s) {
-    HypArgs a{frames, leaves, mcount, prec, nullptr, hw_max, mv, p, hyp_pose, hyp_iter};
+    HypArgs a{frames, leaves, mcount, prec, nullptr, hw_max, mv, p, hyp_pose, hyp_iter, nullptr};
     dim3 grid((p.n_hyp + 127) / 128, n);
     k_hyppose<<<grid, 128, 0, s>>>(a);
     RL_LAUNCH_CK();

@@ -100,7 +100,7 @@ rl_status launch_finalize(const QueryState &q, const RParams &p, int n_tiles, in
                           cudaStream_t s);
 rl_status launch_hypgen(const Frame *frames, const uint16_t *leaves, const uint16_t *mcount,
                         const uint4 *prec, const uint2 *pcm, int hw_max, ModeView mv, const RParams &p,
-                        double *hyp_pose, int32_t *hyp_iter, int n, cudaStream_t s);
+                        double *hyp_pose, int32_t *hyp_iter, unsigned long long *work, int n, cudaStream_t s);
 // Largest |M(u)| the colour-check masks cover.
 constexpr int kMaskModes = 56;
 rl_status launch_colour_mask(const Frame *frames, const uint16_t *mcount, const uint4 *prec, int hw_max,

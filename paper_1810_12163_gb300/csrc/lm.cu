@@ -48,6 +48,7 @@ constexpr int LMC_P = 16;        // pixels per tile (max_pix is a multiple)
 constexpr int LMC_STAGES = 2;
 constexpr int LMC_HMAX = 64;
 constexpr int LMC_NV = 30;       // 21 J^T J + 6 J^T r + cost, inlier count, trial cost
+constexpr int LMC_PS = 31;       // odd stride of the per-thread partials (no bank conflicts)
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 struct LmcLayout {
@@ -72,7 +73,7 @@ __host__ __device__ inline LmcLayout lmc_layout(int stride, bool cov) {
     L.stage = o;
     L.tx = rows * 16 + (cov ? rows * 20 : 0) + LMC_P * 16 + LMC_P * 2;
     const uint32_t stages = LMC_STAGES * L.stage;
-    const uint32_t partials = LMC_THREADS * LMC_NV * 4;
+    const uint32_t partials = LMC_THREADS * LMC_PS * 4;
     o = lmc_a16(stages > partials ? stages : partials);
     L.H = o; o += LMC_HMAX * 12 * 8;
     L.Hn = o; o += LMC_HMAX * 12 * 8;
@@ -259,29 +260,42 @@ __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 
                         const float y2 = fmaf(r20, x.x, fmaf(r21, x.y, fmaf(r22, x.z, tz)));
                         const int base = il * stride;
                         float best = INFINITY;
+                        // two modes per step (independent chains), compared in mode order
                         if (cov) {
-                            for (int m = 0; m < cnt; ++m) {
+                            auto d2of = [&](int m) {
                                 const float4 m0 = s_t0[base + m], m1 = s_t1[base + m];
                                 const float u22 = s_t2[base + m];
                                 const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
                                 const float w0 = fmaf(m0.w, v0, fmaf(m1.x, v1, m1.y * v2));
                                 const float w1 = fmaf(m1.z, v1, m1.w * v2);
                                 const float w2 = u22 * v2;
-                                const float d2 = fmaf(w0, w0, fmaf(w1, w1, w2 * w2));
-                                if (d2 < best) {
-                                    best = d2;
-                                    best_m = m;
-                                }
+                                return fmaf(w0, w0, fmaf(w1, w1, w2 * w2));
+                            };
+                            int m = 0;
+                            for (; m + 1 < cnt; m += 2) {
+                                const float da = d2of(m), db = d2of(m + 1);
+                                if (da < best) { best = da; best_m = m; }
+                                if (db < best) { best = db; best_m = m + 1; }
+                            }
+                            if (m < cnt) {
+                                const float da = d2of(m);
+                                if (da < best) { best = da; best_m = m; }
                             }
                         } else {
-                            for (int m = 0; m < cnt; ++m) {
+                            auto d2of = [&](int m) {
                                 const float4 m0 = s_t0[base + m];
                                 const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
-                                const float d2 = fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
-                                if (d2 < best) {
-                                    best = d2;
-                                    best_m = m;
-                                }
+                                return fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
+                            };
+                            int m = 0;
+                            for (; m + 1 < cnt; m += 2) {
+                                const float da = d2of(m), db = d2of(m + 1);
+                                if (da < best) { best = da; best_m = m; }
+                                if (db < best) { best = db; best_m = m + 1; }
+                            }
+                            if (m < cnt) {
+                                const float da = d2of(m);
+                                if (da < best) { best = da; best_m = m; }
                             }
                         }
                         if (best_m >= 0) {
@@ -327,7 +341,7 @@ __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 
     // Sums of this CTA's pass over groups (fixed order) into loc buffer lb,
     // then over the cluster's CTAs (rank order) into dst.
     auto reduce = [&](const LmcPass &o, int lb, float (*dst)[LMC_NV]) {
-        float *mypart = s_acc + t * LMC_NV;
+        float *mypart = s_acc + t * LMC_PS;
 #pragma unroll
         for (int k = 0; k < 28; ++k) mypart[k] = o.acc[k];
         mypart[28] = (float)o.nin;
@@ -337,7 +351,7 @@ __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 
         for (int e = t; e < n * LMC_NV; e += LMC_THREADS) {
             const int h = e / LMC_NV, k = e % LMC_NV;
             float v = 0.f;
-            for (int gg = 0; gg < G; ++gg) v += s_acc[(gg * HB + h) * LMC_NV + k];
+            for (int gg = 0; gg < G; ++gg) v += s_acc[(gg * HB + h) * LMC_PS + k];
             loc[e] = v;
         }
         // Double-buffered loc: a CTA rewrites buffer lb two reductions later,
