@@ -63,16 +63,15 @@ __device__ __forceinline__ bool stage1(const HypArgs &a, const Frame &fr, const 
     return max(dr, max(dg, db)) <= a.p.colour_thresh;
 }
 
-// Stage 1 from the colour-check masks: three independent 8-byte loads give
-// every |M(u)| and the colour decision of each mode of the checked pixel.
-__device__ __forceinline__ bool stage1_mask(const HypArgs &a, const Frame &fr, const uint2 *cm, int slot,
-                                            int it, Draw &d) {
-    d = draw(a, fr, slot, it);
-    const uint2 w0 = cm[d.pix[0]], w1 = cm[d.pix[1]], w2 = cm[d.pix[2]];
+// Stage 1 from the colour-check masks: per attempt three independent 8-byte
+// loads give every |M(u)| and the colour decision of each mode of the
+// checked pixel.  Two attempts run together, with every load issued before
+// the second Philox block of either attempt, which then hides the latency.
+// Draws are valid pixel indices for any counter, so the loads need no guard.
+__device__ __forceinline__ bool mask_decide(const uint2 w0, const uint2 w1, const uint2 w2, const uint4 r1,
+                                            Draw &d) {
     const uint32_t c0 = w0.y >> 24, c1 = w1.y >> 24, c2 = w2.y >> 24;
     if (c0 == 0 || c1 == 0 || c2 == 0) return false;
-    const uint32_t ctr1 = (TAG_HYP << 16) | (uint32_t)a.p.level;
-    const uint4 r1 = philox(make_uint4(slot, ctr1, it, 1), fr.key0, fr.key1);
     d.m[0] = draw_below(r1.x, c0);
     d.m[1] = draw_below(r1.y, c1);
     d.m[2] = draw_below(r1.z, c2);
@@ -80,6 +79,19 @@ __device__ __forceinline__ bool stage1_mask(const HypArgs &a, const Frame &fr, c
     const uint32_t mj = d.j == 0 ? d.m[0] : (d.j == 1 ? d.m[1] : d.m[2]);
     const uint32_t bits = mj < 32 ? wj.x >> mj : wj.y >> (mj - 32);
     return (bits & 1u) != 0;
+}
+
+__device__ __forceinline__ void stage1_mask2(const HypArgs &a, const Frame &fr, const uint2 *cm, int slot,
+                                             int itA, int itB, Draw &dA, Draw &dB, bool &sA, bool &sB) {
+    dA = draw(a, fr, slot, itA);
+    dB = draw(a, fr, slot, itB);
+    const uint2 a0 = cm[dA.pix[0]], a1 = cm[dA.pix[1]], a2 = cm[dA.pix[2]];
+    const uint2 b0 = cm[dB.pix[0]], b1 = cm[dB.pix[1]], b2 = cm[dB.pix[2]];
+    const uint32_t ctr1 = (TAG_HYP << 16) | (uint32_t)a.p.level;
+    const uint4 rA = philox(make_uint4(slot, ctr1, itA, 1), fr.key0, fr.key1);
+    const uint4 rB = philox(make_uint4(slot, ctr1, itB, 1), fr.key0, fr.key1);
+    sA = mask_decide(a0, a1, a2, rA, dA);
+    sB = mask_decide(b0, b1, b2, rB, dB);
 }
 
 __device__ __forceinline__ bool stage2(const HypArgs &a, const CheckThr &ct, const Frame &fr,
@@ -117,15 +129,15 @@ __device__ __forceinline__ bool stage2(const HypArgs &a, const CheckThr &ct, con
     return true;
 }
 
-// Warp per (frame, slot).  The 32 lanes run stage 1 on 32 consecutive
-// iterations and append the survivors, in iteration order, to a ring in
-// shared memory; whenever it holds 32 of them, the lanes run stage 2 on the
-// 32 oldest.  The first success in a drained group is the lowest successful
+// Warp per (frame, slot).  The 32 lanes run stage 1 on 64 (with masks) or
+// 32 consecutive iterations and append the survivors, in iteration order, to
+// a ring in shared memory; whenever it holds 32 of them, the lanes run
+// stage 2 on the 32 oldest.  The first success in a drained group is the lowest successful
 // iteration, exactly as a sequential loop would find it: every lower
 // iteration failed stage 1 or was drained earlier.  Compaction keeps the
 // lanes converged on the rarely reached stage 2.
 constexpr int HG_WARPS = 4;
-constexpr int HG_RING = 64;  // < 32 pending after a drain + 32 appended
+constexpr int HG_RING = 128;  // < 32 pending after a drain + 64 appended
 
 __global__ void __launch_bounds__(HG_WARPS * 32, 8) k_hypgen(HypArgs a) {
     __shared__ int4 s_ring[HG_WARPS][HG_RING];   // it | j << 30, pixels of the triple
@@ -179,21 +191,35 @@ __global__ void __launch_bounds__(HG_WARPS * 32, 8) k_hypgen(HypArgs a) {
         head += n;
         return win != 0;
     };
-    for (int base = 0; base < a.p.max_iter; base += 32) {
-        const int it = base + lane;
-        Draw d;
-        const bool s1 = it < a.p.max_iter &&
-                        (cm ? stage1_mask(a, fr, cm, slot, it, d) : stage1(a, fr, lv, mc, pr, slot, it, d));
+    auto append = [&](bool s1, int it, const Draw &d) {
         const unsigned mask = __ballot_sync(0xffffffffu, s1);
-        n_att += (unsigned)min(32, a.p.max_iter - base);
         if (s1) {
             const unsigned e = (tail + __popc(mask & lt)) % HG_RING;
             ring[e] = make_int4(it | (d.j << 30), d.pix[0], d.pix[1], d.pix[2]);
             rmode[e] = make_uint2(d.m[0] | (d.m[1] << 16), d.m[2]);
         }
         tail += __popc(mask);
+    };
+    // iterations in groups of 64 (masks: two per lane) or 32; survivors are
+    // appended in iteration order
+    const int step = cm ? 64 : 32;
+    for (int base = 0; base < a.p.max_iter; base += step) {
+        if (cm) {
+            Draw dA, dB;
+            bool sA, sB;
+            const int itA = base + lane, itB = base + 32 + lane;
+            stage1_mask2(a, fr, cm, slot, itA, itB, dA, dB, sA, sB);
+            append(sA && itA < a.p.max_iter, itA, dA);
+            append(sB && itB < a.p.max_iter, itB, dB);
+        } else {
+            const int it = base + lane;
+            Draw d;
+            const bool s1 = it < a.p.max_iter && stage1(a, fr, lv, mc, pr, slot, it, d);
+            append(s1, it, d);
+        }
+        n_att += (unsigned)min(step, a.p.max_iter - base);
         __syncwarp();
-        if (tail - head >= 32) {
+        while (tail - head >= 32) {
             if (drain(32)) {
                 count();
                 return;
