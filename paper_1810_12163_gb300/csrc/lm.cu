@@ -407,6 +407,12 @@ __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 
                 }
             }
         }
+        // The stop flags were just written by the solving threads: the
+        // predicate below is evaluated before its barrier, so it must see them
+        // through one of its own.  Every CTA then takes the same exit decision
+        // and the cluster barriers stay paired (a CTA that left the loop alone
+        // would be read through distributed shared memory after it exits).
+        __syncthreads();
         if (!__syncthreads_or(mine && s_state[hl])) break;  // identical in every CTA
         // trial cost of the step on the current correspondences, and the
         // normal equations at the trial pose (used if the step is accepted)
