@@ -17,6 +17,7 @@ slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -217,7 +218,27 @@ def algorithmic_int_ops(kernel, work):
     return None
 
 
-def roofline(kernels, work, p, n_frames_profiled, w, sm_count, pk):
+# DRAM traffic (read + write) of a kernel from one ncu capture, per frame
+# and launch (profiles/k_lm_cluster_config2_b32_round0.md: mean over the six
+# rounds of a 32-frame call), valid only for the source it was measured on:
+# when the file's hash differs, traffic is reported as null.
+PROFILED_TRAFFIC = {
+    "lm": {"bytes_per_frame_launch": 13.02e6, "source": "paper_1810_12163_gb300/csrc/lm.cu",
+           "sha256_16": "cf0ecf162b015e09"},
+}
+
+
+def profiled_traffic(kernel, frames):
+    e = PROFILED_TRAFFIC.get(kernel)
+    if not e:
+        return None
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), e["source"])
+    with open(path, "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()[:16]
+    return e["bytes_per_frame_launch"] * frames if h == e["sha256_16"] else None
+
+
+def roofline(kernels, work, p, n_frames_profiled, w, sm_count, pk, batch=1):
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     kd = kernels[dom]
     fp32_peak = sm_count * FP32_LANES_PER_SM * 2 * (pk.get("sm_max_mhz", 2070.0) if pk else 2070.0) * 1e6 / 1e12
@@ -227,7 +248,7 @@ def roofline(kernels, work, p, n_frames_profiled, w, sm_count, pk):
     if flops is not None:
         ach = flops / max(1, kd["launches"]) / avg_s / 1e12
         out.update({"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                    "frac": ach / fp32_peak, "traffic": None,
+                    "frac": ach / fp32_peak, "traffic": profiled_traffic(dom, batch),
                     "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x max SM clock"})
     elif dom == "leaves":
         bpf = w.width * w.height * (4 + 3 + 2 * p["n_trees_used"])
@@ -395,7 +416,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(sum(k["launches"] for k in kernels.values())),
         "kernels_ms": {k: round(v["ms"], 4) for k, v in kernels.items()},
-        "roofline": roofline(kernels, work, w.ransac, B * args.steps, w, sm_count, pk),
+        "roofline": roofline(kernels, work, w.ransac, B * args.steps, w, sm_count, pk, batch=B),
         "kernel_rooflines": kernel_rooflines(kernels, work, w.ransac, sm_count, pk),
         "work_per_step": {k: v // max(1, args.steps) for k, v in work.items()},
         "clocks": clk.summary(),
