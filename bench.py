@@ -101,6 +101,79 @@ def oracle_step(w, nodes, modes, q):
                              1 << w.forest["depth"])
 
 
+
+def cpu_model_name():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+# Oracle workers for the all-cores baseline: spawned processes (the parent
+# already holds a CUDA context), each running the single-threaded oracle on
+# whole queries.
+_ORACLE_MODEL = None
+
+
+def _oracle_worker_init(path):
+    global _ORACLE_MODEL
+    import pickle
+    import oracle
+    oracle.set_threads(1)
+    with open(path, "rb") as f:
+        _ORACLE_MODEL = pickle.load(f)
+
+
+def _oracle_worker_idle(_):
+    time.sleep(0.2)
+    return os.getpid()
+
+
+def _oracle_worker_run(q):
+    w, nodes, modes = _ORACLE_MODEL
+    oracle_step(w, nodes, modes, q)
+    return 1
+
+
+def oracle_all_cores(w, nodes, modes, queries):
+    """Wall-clock frames/s of the oracle on every host core: one single-threaded
+    oracle per core, queries spread over them."""
+    import multiprocessing
+    import pickle
+    ncores = os.cpu_count() or 1
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "model.pkl")
+        with open(path, "wb") as f:
+            pickle.dump((w, nodes, modes), f, protocol=pickle.HIGHEST_PROTOCOL)
+        ctx = multiprocessing.get_context("spawn")
+        with ctx.Pool(ncores, initializer=_oracle_worker_init, initargs=(path,)) as pool:
+            pool.map(_oracle_worker_idle, range(2 * ncores), chunksize=1)
+            t0 = time.perf_counter()
+            pool.map(_oracle_worker_run, queries, chunksize=1)
+            dt = time.perf_counter() - t0
+    return len(queries) / dt, ncores, dt
+
+
+def pose_err(A, B):
+    A = np.asarray(A, np.float64).reshape(4, 4)
+    B = np.asarray(B, np.float64).reshape(4, 4)
+    dt = float(np.linalg.norm(A[:3, 3] - B[:3, 3]))
+    c = (np.trace(A[:3, :3].T @ B[:3, :3]) - 1.0) / 2.0
+    return dt, float(np.degrees(np.arccos(np.clip(c, -1.0, 1.0))))
+
+
 def oracle_threads():
     return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
@@ -109,9 +182,11 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    import oracle
     w = workloads.CONFIG2
     frames = training_set(w, args.train_frames or w.n_train)
     nodes, modes = oracle_model(w, frames)
+    oracle.set_threads(1)  # one core, as the line states
     qs = w.queries(max(1, min(8, args.steps + args.warmup)))
     for i in range(args.warmup):
         oracle_step(w, nodes, modes, qs[i % len(qs)])
@@ -129,7 +204,8 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": w.name, "global_batch": 1, "seq_len": 640 * 480,
                                         "parallelism": "replicas"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "cpu": cpu_model_name()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -422,15 +498,39 @@ def run_ours(args):
         "clocks": clk.summary(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.profile_only:
+        import oracle
         nodes, modes = oracle_model(w, frames)
         oq = [w.query(i) for i in range(args.cpu_sample)]
+        oracle.set_threads(1)
         t0 = time.perf_counter()
-        for q in oq:
-            oracle_step(w, nodes, modes, q)
+        ores = [oracle_step(w, nodes, modes, q) for q in oq]
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": len(oq) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{len(oq)} config-2 queries relocalised one at a time "
-                                          f"(single thread, {dt:.1f} s)"}
+                                          f"(one thread, {dt:.1f} s)", "cpu": cpu_model_name()}
+        # the oracle on every host core, one query per process at a time
+        allq = [w.query(i) for i in range(2 * (os.cpu_count() or 1))]
+        v, ncores, dta = oracle_all_cores(w, nodes, modes, allq)
+        line["cpu_baseline_all_cores"] = {
+            "value": v, "unit": UNIT, "cores": ncores, "kind": "oracle", "cpu": cpu_model_name(),
+            "sample": f"{len(allq)} config-2 queries, {ncores} single-threaded oracle processes ({dta:.1f} s)"}
+        # error of the GPU results against the FP64 oracle on the same queries and seeds
+        Dq = torch.from_numpy(np.stack([q[0] for q in oq])).cuda()
+        Cq = torch.from_numpy(np.stack([q[1] for q in oq])).cuda()
+        gres = rel.relocalise_batch(Dq, Cq, w.K, [q[3] for q in oq], stream=stream)
+        torch.cuda.synchronize()
+        errs = []
+        for g, o in zip(gres, ores):
+            dtp, drp = pose_err(g["pose"], o["pose"])
+            e_rel = abs(g["energy"] - o["energy"]) / max(abs(o["energy"]), 1e-30)
+            s_rel = (abs(g["score"] - o["score"]) / max(abs(o["score"]), 1e-30)
+                     if np.isfinite(o["score"]) and np.isfinite(g["score"]) else 0.0)
+            errs.append((dtp, drp, e_rel, s_rel))
+        e = np.array(errs)
+        line["oracle_error"] = {
+            "queries": len(errs), "max_pose_m": float(e[:, 0].max()), "max_pose_deg": float(e[:, 1].max()),
+            "max_energy_rel": float(e[:, 2].max()), "max_score_rel": float(e[:, 3].max()),
+            "within_1mm_0.05deg": int(((e[:, 0] <= 1e-3) & (e[:, 1] <= 0.05)).sum())}
     if rank == 0:
         print(json.dumps(line), flush=True)
     rel1.close()

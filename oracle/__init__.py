@@ -89,6 +89,8 @@ class Debug(ctypes.Structure):
 
 def _declare(L):
     L.orc_philox4x32_10.argtypes = [P, P, P]
+    L.orc_set_threads.argtypes = [I32]
+    L.orc_set_threads.restype = None
     L.orc_forest_random.argtypes = [I32, I32, F32, F32, F32, F32, F32, F32, F32, I32, U64,
                                     P, P, P, P, P]
     L.orc_forest_leaves.argtypes = [P, P, P, P, P, I32, I32, P, P, I32, I32, F32, P]
@@ -232,6 +234,11 @@ def update_modes(res: Reservoirs, modes: Modes, sigma, tau_c, min_cluster_size,
                            int(fp16_offsets), _p(modes.nmodes), _p(modes.centroid), _p(modes.pos),
                            _p(modes.rgb), _p(modes.U), _p(modes.size))
     return modes
+
+
+def set_threads(n: int):
+    """Threads of the oracle's OpenMP loops (results do not depend on it)."""
+    lib().orc_set_threads(int(n))
 
 
 def kabsch(a, b):

@@ -72,6 +72,10 @@
  */
 #include "oracle.h"
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 #include <math.h>
 #include <string.h>
 
@@ -281,3 +285,15 @@ void orc_reservoir_add_frame(const float *dx, const float *dy, const float *tau,
         }
     }
 }
+
+/* Threads of the OpenMP loops (pixel rows, leaves); the arithmetic does not
+ * depend on it.  Test and timing infrastructure only. */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
+

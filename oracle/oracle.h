@@ -196,4 +196,6 @@ int orc_cascade(int n_levels, const orc_params *levels, const double *thresholds
 #ifdef __cplusplus
 }
 #endif
+void orc_set_threads(int n);
+
 #endif
