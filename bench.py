@@ -61,6 +61,28 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def replica_seeds(rank, step, batch):
+    """Seeds of one step's queries on one replica: disjoint across ranks
+    (high bits) and steps."""
+    return [(rank << 40) + (step + 1) * batch + i for i in range(batch)]
+
+
+def max_over_ranks(x, device):
+    """Largest value over the ranks: the slowest replica sets the job's time."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(frames_per_rank, world, seconds):
+    """Whole-job frames/s: every rank's frames over the slowest rank's time."""
+    return frames_per_rank * world / seconds
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -398,7 +420,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def seeds(step):
-        return [(rank << 40) + (step + 1) * B + i for i in range(B)]
+        return replica_seeds(rank, step, B)
 
     for k in range(args.warmup):
         rel.relocalise_batch(D, C, w.K, seeds(500_000 + k), stream=stream, raw=True)
@@ -425,10 +447,9 @@ def run_ours(args):
     rel.profile(False)
     total_s = sum(step_ms) / 1e3
     if world > 1:
-        t = torch.tensor([total_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = B * args.steps * world / total_s
+        torch.distributed.barrier()
+    total_s = max_over_ranks(total_s, "cuda")
+    value = job_throughput(B * args.steps, world, total_s)
 
     # accuracy of the last step's poses (5 cm / 5 deg)
     ok = 0
@@ -452,10 +473,7 @@ def run_ours(args):
         rel.relocalise_batch(Dn, Cn, w.K, seeds(20_000 + k), stream=stream, raw=True)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, "cuda")
     h2d = int(Dn.nbytes + Cn.nbytes)
     d2h = B * (128 + 16 * 12 * 8 + 3 * 16 * 4)
 
@@ -488,7 +506,7 @@ def run_ours(args):
                           "frames_per_s": 1000.0 / float(np.mean(lat1))},
         },
         "success_5cm_5deg": ok / B,
-        "e2e": {"value": B * e2e_steps * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_throughput(B * e2e_steps, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(sum(k["launches"] for k in kernels.values())),
         "kernels_ms": {k: round(v["ms"], 4) for k, v in kernels.items()},
