@@ -186,6 +186,13 @@ rl_status rl_forest_export(rl_forest *f, float *node_dx, float *node_dy, float *
                            uint8_t *nmodes /* L */, float *mode_pos /* L*m_max*3 */,
                            uint8_t *mode_rgb /* L*m_max*3 */, float *mode_U /* L*m_max*6 */,
                            int32_t *mode_size /* L*m_max */);
+/* Overwrites the positions of the stored modes (HOST float [L][m_max][3];
+ * ranks at or beyond a leaf's mode count are ignored), re-encoded in the
+ * forest's precision: FP16 offsets from the leaf's FP32 centroid (which is
+ * kept; the difference is rounded once to half) or FP32.  The paper has no
+ * counterpart: it injects outlier modes for precision and stress studies.
+ * Synchronises the device. */
+rl_status rl_forest_set_mode_positions(rl_forest *f, const float *mode_pos);
 /* Binary checkpoint of nodes, reservoirs, modes and the round-robin cursor. */
 rl_status rl_forest_save(rl_forest *f, const char *path);
 rl_status rl_forest_load(rl_ctx *ctx, const char *path, rl_forest **out);

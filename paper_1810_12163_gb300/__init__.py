@@ -164,6 +164,14 @@ class Forest:
         out["channel"] = (out["meta"] >> 8).astype(np.uint8)
         return out
 
+    def set_mode_positions(self, mode_pos):
+        """Overwrites the stored modes' positions ([L][m_max][3] FP32), re-encoded
+        in the forest's precision (see rl_forest_set_mode_positions)."""
+        pos = np.ascontiguousarray(mode_pos, np.float32)
+        if pos.shape != (self.n_leaves, self.params["m_max"], 3):
+            raise ValueError(f"mode_pos must have shape {(self.n_leaves, self.params['m_max'], 3)}")
+        call("rl_forest_set_mode_positions", self.h, pos.ctypes.data_as(ctypes.c_void_p))
+
     def close(self):
         if self.h:
             call("rl_forest_destroy", self.h)

@@ -94,6 +94,7 @@ _SIGS = {
     "rl_forest_update_modes": [P, I32, P],
     "rl_forest_leaves": [P, P, P, P, I32, P, I32, P],
     "rl_forest_export": [P] + [P] * 12,
+    "rl_forest_set_mode_positions": [P, P],
     "rl_forest_save": [P, ctypes.c_char_p],
     "rl_forest_load": [P, ctypes.c_char_p, P],
     "rl_scene_box": [P, P, P, P],

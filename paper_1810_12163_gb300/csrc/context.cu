@@ -4,6 +4,8 @@
 
 #include <algorithm>
 
+#include <cuda_fp16.h>
+
 #include "internal.h"
 
 namespace rl {
@@ -301,6 +303,55 @@ extern "C" rl_status rl_forest_leaves(rl_forest *f, const float *depth, const ui
 }
 
 // Decodes the mode store to host buffers.
+// Re-encodes the positions of leaves [l0, l0 + n): FP16 offsets from the
+// stored FP32 centroid (difference exact in FP64, one rounding to half) or
+// FP32 positions.  Ranks at or beyond the leaf's mode count are untouched.
+__global__ void k_set_mode_positions(const float *__restrict__ pos, int l0, int n, int m_max,
+                                     const uint8_t *__restrict__ nmodes, const float4 *__restrict__ centroid,
+                                     ushort4 *mpos_h, float4 *mpos_f) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * m_max) return;
+    const int l = l0 + e / m_max, r = e % m_max;
+    if (r >= nmodes[l]) return;
+    const float x = pos[3 * e], y = pos[3 * e + 1], z = pos[3 * e + 2];
+    const size_t o = (size_t)l * m_max + r;
+    if (mpos_h) {
+        const float4 c = centroid[l];
+        mpos_h[o] = make_ushort4(__half_as_ushort(__double2half((double)x - (double)c.x)),
+                                 __half_as_ushort(__double2half((double)y - (double)c.y)),
+                                 __half_as_ushort(__double2half((double)z - (double)c.z)), 0);
+    } else {
+        mpos_f[o] = make_float4(x, y, z, 0.f);
+    }
+}
+
+extern "C" rl_status rl_forest_set_mode_positions(rl_forest *f, const float *mode_pos) {
+    if (!f || !mode_pos) return fail(RL_ERR_INVALID_ARG, "null argument");
+    RL_CK(cudaSetDevice(f->ctx->device));
+    RL_CK(cudaDeviceSynchronize());
+    const int M = f->p.m_max;
+    const int chunk = std::max(1, (1 << 20) / (M * 3));  // leaves per staged chunk (<= 12 MB)
+    float *stage = nullptr;
+    RL_TRY(alloc_n(f->ctx, (uint64_t)chunk * M * 3, &stage));
+    rl_status st = RL_OK;
+    for (int l0 = 0; l0 < f->n_leaves && st == RL_OK; l0 += chunk) {
+        const int n = std::min(chunk, f->n_leaves - l0);
+        cudaError_t e = cudaMemcpy(stage, mode_pos + (size_t)l0 * M * 3, sizeof(float) * n * M * 3,
+                                   cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            st = cuda_fail(e, "cudaMemcpy", __FILE__, __LINE__);
+            break;
+        }
+        k_set_mode_positions<<<(n * M + 255) / 256, 256>>>(stage, l0, n, M, f->nmodes, f->centroid,
+                                                           f->mpos_h, f->mpos_f);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) st = cuda_fail(e, "k_set_mode_positions", __FILE__, __LINE__);
+    }
+    arena_free(f->ctx, stage);
+    return st;
+}
+
 extern "C" rl_status rl_forest_export(rl_forest *f, float *node_dx, float *node_dy,
                                       float *node_tau, int32_t *node_meta, float *res_pos,
                                       uint8_t *res_rgb, uint32_t *res_count, uint8_t *nmodes,

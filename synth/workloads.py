@@ -96,6 +96,27 @@ CONFIG2 = Workload(
     n_queries=16,
 )
 
+# Config 5: precision and stress on the config-2 room and forest training:
+# 4096 hypotheses, every stored mode of a leaf used (K_top = M_max = 50),
+# 60% of the stored modes replaced by outliers uniform in the room
+# (synth.outliers, seed 13), FP16-offset vs FP32 mode storage, 200 queries.
+CONFIG5_OUTLIER_FRACTION = 0.6
+CONFIG5_OUTLIER_SEED = 13
+
+
+def config5(mode_precision: int) -> Workload:
+    """mode_precision: 1 = FP16 offsets from FP32 leaf centroids, 0 = FP32."""
+    tag = "fp16" if mode_precision else "fp32"
+    return Workload(
+        name=f"room4x3x2.5_640x480_5trees_d15_outliers60_{tag}", room_size=(4.0, 3.0, 2.5), room_seed=5,
+        width=640, height=480,
+        forest=dict(FOREST_DEFAULT, mode_precision=mode_precision),
+        forest_seed=2, n_train=200,
+        ransac=dict(RANSAC_DEFAULT, n_hyp=4096, n_cull=64, eta=500, k_out=16, halve_to_one=1, k_top=50),
+        n_queries=200,
+    )
+
+
 # Config 3 levels (shared config-2 forest): subsample, relocaliser parameters.
 CASCADE_LEVELS = [
     (4, dict(RANSAC_DEFAULT, n_hyp=64, n_trees_used=1, k_out=1, eta=100)),

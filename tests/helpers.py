@@ -138,3 +138,68 @@ def compare_survivors(gpu_slots, gpu_E, ora_slots, ora_E, what):
         e = gpu_E[gs.index(s)] if s in gs else ora_E[os_.index(s)]
         assert abs(e - cut) <= SWAP_RTOL * abs(cut) + 1e-6, f"{what}: survivor {s} differs, E={e} cut={cut}"
     return False
+
+
+def compare_results(rg, gr, dbg, orr, params, what):
+    """GPU result and debug record of one query against the oracle's, with
+    the bars stated in the module docstring."""
+    od = orr["debug"]
+    # generation: identical winning iteration for every slot (bit-exact choices)
+    assert np.array_equal(dbg["hyp_iter"], od["hyp_iter"])
+    ok = dbg["hyp_iter"] >= 0
+    for s in np.nonzero(ok)[0]:
+        dt, dr = pose_err(as44(dbg["hyp_pose"][s]), as44(od["hyp_pose"][s]))
+        assert dt < 1e-6 and dr < 1e-4, (what, s, dt, dr)
+    assert gr["n_hypotheses"] == orr["n_hypotheses"]
+    if orr["n_hypotheses"] == 0:
+        assert gr["status"] == rg.RL_NO_POSE and orr["status"] == 1
+        return
+    # batch pixels: bit-exact
+    nb = min(16, dbg["n_rounds"] + 1)
+    assert np.array_equal(dbg["batch_pix"][:nb], od["batch_pix"][:nb])
+    # cull survivors
+    nc = min(params["n_cull"], orr["n_hypotheses"])
+    same = compare_survivors(dbg["cull_slot"][:nc], dbg["cull_energy"][:nc],
+                             od["cull_slot"][:nc], od["cull_energy"][:nc], f"{what} cull")
+    if not same:
+        return
+    # preemptive rounds
+    assert dbg["n_rounds"] == od["n_rounds"]
+    off = 0
+    for r in range(dbg["n_rounds"]):
+        k = od["round_count"][r]
+        assert dbg["round_count"][r] == k
+        gs, ge = dbg["round_slot"][r][:k], dbg["round_energy"][r][:k]
+        os_, oe = od["round_slot"][off:off + k], od["round_energy"][off:off + k]
+        if not compare_survivors(gs, ge, os_, oe, f"{what} round {r}"):
+            return
+        for i in range(k):
+            dt, dr = pose_err(as44(dbg["round_pose"][r][i]), as44(od["round_pose"][off + i]))
+            check_refined_pose(dt, dr, ge[i], oe[i], f"{what} round {r} survivor {i}")
+        off += k
+    # ranking scores of the chosen set, then the output pose
+    assert gr["n_chosen"] == orr["n_chosen"]
+    if params["rank"]:
+        tol = score_tolerances(gr["chosen_pose"], orr["chosen_pose"], orr["chosen_score"])
+        check_scores(gr["chosen_score"], orr["chosen_score"], tol, what)
+        if gr["best"] != orr["best"]:
+            # argmin between near-tied scores: either choice is valid
+            a, b = gr["best"], orr["best"]
+            assert abs(orr["chosen_score"][a] - orr["chosen_score"][b]) <= tol[a] + tol[b], (what, a, b)
+            return
+    dt, dr = pose_err(gr["pose"], orr["pose"])
+    np.testing.assert_allclose(gr["energy"], orr["energy"], rtol=ENERGY_RTOL)
+    check_refined_pose(dt, dr, gr["energy"], orr["energy"], f"{what} output")
+
+
+def oracle_modes_from_export(ex, m_max):
+    """Oracle mode store holding exactly the library's decoded modes (both
+    sides then score the same mode positions)."""
+    L = ex["nmodes"].shape[0]
+    m = oracle.Modes(L, m_max)
+    m.nmodes[:] = ex["nmodes"]
+    m.pos[:] = ex["mode_pos"]
+    m.rgb[:] = ex["mode_rgb"]
+    m.U[:] = ex["mode_U"]
+    m.size[:] = ex["mode_size"]
+    return m

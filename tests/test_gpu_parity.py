@@ -94,55 +94,8 @@ def test_reservoirs_and_modes_bitexact(rg, small):
 def _compare_query(rg, rel, w, q, params):
     d, c, T, seed = w.query(q)
     gr = rel.relocalise(d, c, w.K, seed)
-    dbg = rel.debug(0)
     orr, _ = H.oracle_query(w.name, q, params)
-    od = orr["debug"]
-    # generation: identical winning iteration for every slot (bit-exact choices)
-    assert np.array_equal(dbg["hyp_iter"], od["hyp_iter"])
-    ok = dbg["hyp_iter"] >= 0
-    for s in np.nonzero(ok)[0]:
-        dt, dr = H.pose_err(H.as44(dbg["hyp_pose"][s]), H.as44(od["hyp_pose"][s]))
-        assert dt < 1e-6 and dr < 1e-4, (s, dt, dr)
-    assert gr["n_hypotheses"] == orr["n_hypotheses"]
-    if orr["n_hypotheses"] == 0:
-        assert gr["status"] == rg.RL_NO_POSE and orr["status"] == 1
-        return
-    # batch pixels: bit-exact
-    nb = min(16, dbg["n_rounds"] + 1)
-    assert np.array_equal(dbg["batch_pix"][:nb], od["batch_pix"][:nb])
-    # cull survivors
-    nc = min(params["n_cull"], orr["n_hypotheses"])
-    same = H.compare_survivors(dbg["cull_slot"][:nc], dbg["cull_energy"][:nc],
-                               od["cull_slot"][:nc], od["cull_energy"][:nc], f"q{q} cull")
-    if not same:
-        return
-    # preemptive rounds
-    assert dbg["n_rounds"] == od["n_rounds"]
-    off = 0
-    for r in range(dbg["n_rounds"]):
-        k = od["round_count"][r]
-        assert dbg["round_count"][r] == k
-        gs, ge = dbg["round_slot"][r][:k], dbg["round_energy"][r][:k]
-        os_, oe = od["round_slot"][off:off + k], od["round_energy"][off:off + k]
-        if not H.compare_survivors(gs, ge, os_, oe, f"q{q} round {r}"):
-            return
-        for i in range(k):
-            dt, dr = H.pose_err(H.as44(dbg["round_pose"][r][i]), H.as44(od["round_pose"][off + i]))
-            H.check_refined_pose(dt, dr, ge[i], oe[i], f"q{q} round {r} survivor {i}")
-        off += k
-    # ranking scores of the chosen set, then the output pose
-    assert gr["n_chosen"] == orr["n_chosen"]
-    if params["rank"]:
-        tol = H.score_tolerances(gr["chosen_pose"], orr["chosen_pose"], orr["chosen_score"])
-        H.check_scores(gr["chosen_score"], orr["chosen_score"], tol, f"q{q}")
-        if gr["best"] != orr["best"]:
-            # argmin between near-tied scores: either choice is valid
-            a, b = gr["best"], orr["best"]
-            assert abs(orr["chosen_score"][a] - orr["chosen_score"][b]) <= tol[a] + tol[b], (q, a, b)
-            return
-    dt, dr = H.pose_err(gr["pose"], orr["pose"])
-    np.testing.assert_allclose(gr["energy"], orr["energy"], rtol=H.ENERGY_RTOL)
-    H.check_refined_pose(dt, dr, gr["energy"], orr["energy"], f"q{q} output")
+    H.compare_results(rg, gr, rel.debug(0), orr, params, f"q{q}")
 
 
 def test_relocalise_parity_small(rg, ctx, small):
