@@ -360,6 +360,14 @@ rl_status rl_server_create(rl_ctx *ctx, const rl_server_params *p, rl_server **o
 rl_status rl_server_add_model(rl_server *s, rl_forest *f, rl_scene *scene,
                               const rl_ransac_params *p, int32_t max_width, int32_t max_height,
                               int32_t *model_id);
+/* Adds a cascade model (Sec. 3.2.5): per slot, one relocaliser per level
+ * (levels[l] parameters, input subsampled by subsample[l], the last level at
+ * full resolution) chained as by rl_cascade_create with thresholds [L-1];
+ * requests to it return the cascade's result (level = the accepting level). */
+rl_status rl_server_add_cascade_model(rl_server *s, rl_forest *f, rl_scene *scene,
+                                      const rl_ransac_params *levels, const int32_t *subsample,
+                                      const double *thresholds, int32_t n_levels, int32_t max_width,
+                                      int32_t max_height, int32_t *model_id);
 /* Copies the HOST frame and enqueues it; *ticket identifies the request. */
 rl_status rl_server_submit(rl_server *s, int32_t model, const float *depth, const uint8_t *rgb,
                            const rl_intrinsics *K, uint64_t query_seed, uint64_t *ticket);

@@ -329,6 +329,20 @@ class Server:
              ctypes.byref(_struct(RansacParams, full)), max_w, max_h, ctypes.byref(mid))
         return mid.value
 
+    def add_cascade_model(self, forest: Forest, scene: Scene | None, levels: list, subsample,
+                          thresholds, max_w: int, max_h: int) -> int:
+        """A cascade (Sec. 3.2.5) served like a single relocaliser: levels are
+        parameter dicts, subsample[l] the level's input subsampling (last 1)."""
+        mid = ctypes.c_int32()
+        L = len(levels)
+        arr = (RansacParams * L)(*[_struct(RansacParams, dict(presets.DEFAULT, **p)) for p in levels])
+        ss = np.ascontiguousarray(subsample, np.int32)
+        th = np.ascontiguousarray(list(thresholds) + [0.0], np.float64)
+        call("rl_server_add_cascade_model", self.h, forest.h, scene.h if scene else None,
+             ctypes.cast(arr, ctypes.c_void_p), ss.ctypes.data_as(ctypes.c_void_p),
+             th.ctypes.data_as(ctypes.c_void_p), L, max_w, max_h, ctypes.byref(mid))
+        return mid.value
+
     def submit(self, model: int, depth, rgb, K, seed: int) -> int:
         d = np.ascontiguousarray(depth, np.float32)
         c = np.ascontiguousarray(rgb, np.uint8)

@@ -327,5 +327,8 @@ rl_status run_relocalise(rl_reloc *r, int n, int level, cudaStream_t s);
 // launch sequence is enqueued on s (graph replay when enabled).
 rl_status reloc_enqueue_frames(rl_reloc *r, int n, const Frame *frames, cudaStream_t s);
 // Copies the results of the last n frames back and waits for s.
+// Cascade counterparts: frames in the last level's host_frames.
+rl_status cascade_enqueue_frames(rl_cascade *c, int n, cudaStream_t s);
+rl_status cascade_fetch_results(rl_cascade *c, int n, cudaStream_t s, rl_result *out);
 rl_status reloc_fetch_results(rl_reloc *r, int n, cudaStream_t s, rl_result *out);
 }  // namespace rl

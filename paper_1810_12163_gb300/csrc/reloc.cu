@@ -780,6 +780,54 @@ extern "C" rl_status rl_cascade_destroy(rl_cascade *c) {
     return RL_OK;
 }
 
+namespace rl {
+
+// Enqueues a cascade call on n full-resolution frames whose descriptors are
+// in the last level's host_frames (images already on the device): each
+// earlier level gets its subsampled copy of every frame (its own size and
+// intrinsics / s), then all levels run as one graph.
+rl_status cascade_enqueue_frames(rl_cascade *c, int n, cudaStream_t s) {
+    rl_reloc *top = c->levels.back();
+    const Frame *full = top->host_frames;
+    RL_CK(cudaMemcpyAsync(top->q.frames, full, sizeof(Frame) * n, cudaMemcpyHostToDevice, s));
+    RL_CK(cudaMemcpyAsync(c->full_dev, full, sizeof(Frame) * n, cudaMemcpyHostToDevice, s));
+    const int L = (int)c->levels.size();
+    for (int l = 0; l < L - 1; ++l) {
+        rl_reloc *r = c->levels[l];
+        const int sf = c->subsample[l];
+        const int hw = r->max_w * r->max_h;
+        for (int i = 0; i < n; ++i) {
+            Frame &f = r->host_frames[i];
+            f = full[i];
+            if (sf > 1) {
+                const int W = (full[i].W + sf - 1) / sf, H = (full[i].H + sf - 1) / sf;
+                if (W > r->max_w || H > r->max_h)
+                    return fail(RL_ERR_INVALID_ARG, "level input larger than the level's maximum size");
+                f.depth = r->stage_depth + (size_t)hw * i;
+                f.rgb = r->stage_rgb + (size_t)hw * 3 * i;
+                f.fx = (float)((double)full[i].fx / sf);
+                f.fy = (float)((double)full[i].fy / sf);
+                f.cx = (float)((double)full[i].cx / sf);
+                f.cy = (float)((double)full[i].cy / sf);
+                f.W = W;
+                f.H = H;
+            }
+        }
+        RL_CK(cudaMemcpyAsync(r->q.frames, r->host_frames, sizeof(Frame) * n, cudaMemcpyHostToDevice, s));
+    }
+    RL_TRY(cascade_launch(c, n, s));
+    for (rl_reloc *r : c->levels) r->last_batch = n;
+    return RL_OK;
+}
+
+rl_status cascade_fetch_results(rl_cascade *c, int n, cudaStream_t s, rl_result *out) {
+    return cascade_fetch(c, n, s, out);
+}
+
+}  // namespace rl
+
+using namespace rl;
+
 extern "C" rl_status rl_cascade_relocalise_batch(rl_cascade *c, int32_t n, const float *depth,
                                                  const uint8_t *rgb, const rl_intrinsics *K,
                                                  const uint64_t *seeds, rl_mem mem, void *stream,
@@ -792,36 +840,7 @@ extern "C" rl_status rl_cascade_relocalise_batch(rl_cascade *c, int32_t n, const
     cudaStream_t s = (cudaStream_t)stream;
     // full-resolution frames: staged into (or pointing at) the last level's inputs
     RL_TRY(stage_inputs(top, n, depth, rgb, K, seeds, mem, s));
-    std::vector<Frame> full(top->host_frames, top->host_frames + n);
-    RL_CK(cudaMemcpyAsync(c->full_dev, full.data(), sizeof(Frame) * n, cudaMemcpyHostToDevice, s));
-    const int L = (int)c->levels.size();
-    for (int l = 0; l < L - 1; ++l) {
-        rl_reloc *r = c->levels[l];
-        const int sf = c->subsample[l];
-        rl_intrinsics Kl = *K;
-        Kl.width = (K->width + sf - 1) / sf;
-        Kl.height = (K->height + sf - 1) / sf;
-        Kl.fx = (float)((double)K->fx / sf);
-        Kl.fy = (float)((double)K->fy / sf);
-        Kl.cx = (float)((double)K->cx / sf);
-        Kl.cy = (float)((double)K->cy / sf);
-        if (Kl.width > r->max_w || Kl.height > r->max_h)
-            return fail(RL_ERR_INVALID_ARG, "level input larger than the level's maximum size");
-        const int hw = r->max_w * r->max_h;
-        for (int i = 0; i < n; ++i) {
-            Frame &f = r->host_frames[i];
-            f = full[i];
-            if (sf > 1) {
-                f.depth = r->stage_depth + (size_t)hw * i;
-                f.rgb = r->stage_rgb + (size_t)hw * 3 * i;
-                f.fx = Kl.fx; f.fy = Kl.fy; f.cx = Kl.cx; f.cy = Kl.cy;
-                f.W = Kl.width; f.H = Kl.height;
-            }
-        }
-        RL_CK(cudaMemcpyAsync(r->q.frames, r->host_frames, sizeof(Frame) * n, cudaMemcpyHostToDevice, s));
-    }
-    RL_TRY(cascade_launch(c, n, s));
-    for (rl_reloc *r : c->levels) r->last_batch = n;
+    RL_TRY(cascade_enqueue_frames(c, n, s));
     return cascade_fetch(c, n, s, out);
 }
 

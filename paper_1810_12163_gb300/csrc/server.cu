@@ -47,7 +47,9 @@ struct Ticket {
 };
 
 struct Slot {
-    rl_reloc *r = nullptr;
+    rl_reloc *r = nullptr;          // single relocaliser, or
+    rl_cascade *c = nullptr;        // a cascade over `levels`
+    std::vector<rl_reloc *> levels;
     cudaStream_t stream = nullptr;
     cudaEvent_t done_ev = nullptr;
     float *pin_depth = nullptr;     // pinned staging [max_batch][hw]
@@ -107,8 +109,9 @@ rl_status launch_slot(Model *m, Slot &sl) {
         const size_t px = (size_t)rq.K.width * rq.K.height;
         memcpy(sl.pin_depth + (size_t)hw * i, rq.depth.data(), px * sizeof(float));
         memcpy(sl.pin_rgb + (size_t)hw * 3 * i, rq.rgb.data(), px * 3);
-        float *dd = sl.r->stage_depth + (size_t)hw * i;
-        uint8_t *dc = sl.r->stage_rgb + (size_t)hw * 3 * i;
+        rl_reloc *owner = sl.c ? sl.c->levels.back() : sl.r;  // full-resolution inputs
+        float *dd = owner->stage_depth + (size_t)hw * i;
+        uint8_t *dc = owner->stage_rgb + (size_t)hw * 3 * i;
         RL_CK(cudaMemcpyAsync(dd, sl.pin_depth + (size_t)hw * i, px * sizeof(float), cudaMemcpyHostToDevice, sl.stream));
         RL_CK(cudaMemcpyAsync(dc, sl.pin_rgb + (size_t)hw * 3 * i, px * 3, cudaMemcpyHostToDevice, sl.stream));
         Frame &f = fr[i];
@@ -119,7 +122,13 @@ rl_status launch_slot(Model *m, Slot &sl) {
         f.key0 = (uint32_t)rq.seed;
         f.key1 = (uint32_t)(rq.seed >> 32);
     }
-    RL_TRY(reloc_enqueue_frames(sl.r, n, fr.data(), sl.stream));
+    if (sl.c) {
+        rl_reloc *top = sl.c->levels.back();
+        for (int i = 0; i < n; ++i) top->host_frames[i] = fr[i];
+        RL_TRY(cascade_enqueue_frames(sl.c, n, sl.stream));
+    } else {
+        RL_TRY(reloc_enqueue_frames(sl.r, n, fr.data(), sl.stream));
+    }
     RL_CK(cudaEventRecord(sl.done_ev, sl.stream));
     sl.busy = true;
     return RL_OK;
@@ -128,7 +137,8 @@ rl_status launch_slot(Model *m, Slot &sl) {
 void complete_slot(rl_server *s, Model *m, Slot &sl) {
     const int n = (int)sl.batch.size();
     std::vector<rl_result> res(n);
-    const rl_status st = reloc_fetch_results(sl.r, n, sl.stream, res.data());
+    const rl_status st = sl.c ? cascade_fetch_results(sl.c, n, sl.stream, res.data())
+                              : reloc_fetch_results(sl.r, n, sl.stream, res.data());
     const double t = now_ms();
     std::lock_guard<std::mutex> g(s->mu);
     for (int i = 0; i < n; ++i) {
@@ -224,36 +234,63 @@ extern "C" rl_status rl_server_create(rl_ctx *ctx, const rl_server_params *p, rl
     return RL_OK;
 }
 
-extern "C" rl_status rl_server_add_model(rl_server *s, rl_forest *f, rl_scene *scene,
-                                         const rl_ransac_params *rp, int32_t max_w, int32_t max_h,
-                                         int32_t *model_id) {
-    if (!s || !f || !rp || !model_id) return fail(RL_ERR_INVALID_ARG, "null argument");
+namespace rl {
+namespace {
+
+struct CascadeSpec {
+    const rl_ransac_params *levels;
+    const int32_t *subsample;
+    const double *thresholds;
+    int n;
+};
+
+void release_slot(Slot &sl) {
+    if (sl.c) rl_cascade_destroy(sl.c);
+    for (rl_reloc *r : sl.levels) rl_reloc_destroy(r);
+    if (sl.r) rl_reloc_destroy(sl.r);
+    if (sl.stream) cudaStreamDestroy(sl.stream);
+    if (sl.done_ev) cudaEventDestroy(sl.done_ev);
+    if (sl.pin_depth) cudaFreeHost(sl.pin_depth);
+    if (sl.pin_rgb) cudaFreeHost(sl.pin_rgb);
+    sl = Slot();
+}
+
+// Two slots (relocaliser or cascade, stream, event, pinned staging) and the
+// model's worker thread.
+rl_status add_model(rl_server *s, rl_forest *f, rl_scene *scene, const rl_ransac_params *rp,
+                    const CascadeSpec *cs, int32_t max_w, int32_t max_h, int32_t *model_id) {
     RL_CK(cudaSetDevice(s->ctx->device));
     Model *m = new Model();
     m->max_w = max_w;
     m->max_h = max_h;
     const size_t hw = (size_t)max_w * max_h;
+    const int B = s->p.max_batch;
     rl_status st = RL_OK;
     for (int k = 0; k < 2 && st == RL_OK; ++k) {
         Slot &sl = m->slot[k];
-        st = rl_reloc_create(f, scene, rp, max_w, max_h, s->p.max_batch, &sl.r);
+        if (!cs) {
+            st = rl_reloc_create(f, scene, rp, max_w, max_h, B, &sl.r);
+        } else {
+            for (int l = 0; l < cs->n && st == RL_OK; ++l) {
+                const int sf = cs->subsample[l];
+                rl_reloc *r = nullptr;
+                st = rl_reloc_create(f, scene, &cs->levels[l], (max_w + sf - 1) / sf, (max_h + sf - 1) / sf, B, &r);
+                if (st == RL_OK) sl.levels.push_back(r);
+            }
+            if (st == RL_OK)
+                st = rl_cascade_create(sl.levels.data(), cs->thresholds, cs->subsample, cs->n, &sl.c);
+        }
         if (st == RL_OK && cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess)
             st = fail(RL_ERR_CUDA, "stream creation failed");
         if (st == RL_OK && cudaEventCreateWithFlags(&sl.done_ev, cudaEventDisableTiming) != cudaSuccess)
             st = fail(RL_ERR_CUDA, "event creation failed");
-        if (st == RL_OK && cudaMallocHost(&sl.pin_depth, hw * s->p.max_batch * sizeof(float)) != cudaSuccess)
+        if (st == RL_OK && cudaMallocHost(&sl.pin_depth, hw * B * sizeof(float)) != cudaSuccess)
             st = fail(RL_ERR_CUDA, "pinned allocation failed");
-        if (st == RL_OK && cudaMallocHost(&sl.pin_rgb, hw * 3 * s->p.max_batch) != cudaSuccess)
+        if (st == RL_OK && cudaMallocHost(&sl.pin_rgb, hw * 3 * B) != cudaSuccess)
             st = fail(RL_ERR_CUDA, "pinned allocation failed");
     }
     if (st != RL_OK) {
-        for (auto &sl : m->slot) {
-            if (sl.r) rl_reloc_destroy(sl.r);
-            if (sl.stream) cudaStreamDestroy(sl.stream);
-            if (sl.done_ev) cudaEventDestroy(sl.done_ev);
-            if (sl.pin_depth) cudaFreeHost(sl.pin_depth);
-            if (sl.pin_rgb) cudaFreeHost(sl.pin_rgb);
-        }
+        for (auto &sl : m->slot) release_slot(sl);
         delete m;
         return st;
     }
@@ -263,6 +300,28 @@ extern "C" rl_status rl_server_add_model(rl_server *s, rl_forest *f, rl_scene *s
     m->worker = std::thread(worker, s, m);
     *model_id = m->id;
     return RL_OK;
+}
+
+}  // namespace
+}  // namespace rl
+
+extern "C" rl_status rl_server_add_model(rl_server *s, rl_forest *f, rl_scene *scene,
+                                         const rl_ransac_params *rp, int32_t max_w, int32_t max_h,
+                                         int32_t *model_id) {
+    if (!s || !f || !rp || !model_id) return fail(RL_ERR_INVALID_ARG, "null argument");
+    return add_model(s, f, scene, rp, nullptr, max_w, max_h, model_id);
+}
+
+extern "C" rl_status rl_server_add_cascade_model(rl_server *s, rl_forest *f, rl_scene *scene,
+                                                 const rl_ransac_params *levels, const int32_t *subsample,
+                                                 const double *thresholds, int32_t n_levels, int32_t max_w,
+                                                 int32_t max_h, int32_t *model_id) {
+    if (!s || !f || !levels || !subsample || !model_id || (n_levels > 1 && !thresholds))
+        return fail(RL_ERR_INVALID_ARG, "null argument");
+    if (n_levels < 1 || n_levels > 8) return fail(RL_ERR_INVALID_ARG, "n_levels must be 1..8");
+    if (subsample[n_levels - 1] != 1) return fail(RL_ERR_INVALID_ARG, "the last level must run at full resolution");
+    const CascadeSpec cs{levels, subsample, thresholds, n_levels};
+    return add_model(s, f, scene, nullptr, &cs, max_w, max_h, model_id);
 }
 
 extern "C" rl_status rl_server_submit(rl_server *s, int32_t model, const float *depth, const uint8_t *rgb,
@@ -367,11 +426,7 @@ extern "C" rl_status rl_server_destroy(rl_server *s) {
     for (Model *m : s->models) {
         for (auto &sl : m->slot) {
             if (sl.stream) cudaStreamSynchronize(sl.stream);
-            rl_reloc_destroy(sl.r);
-            cudaStreamDestroy(sl.stream);
-            cudaEventDestroy(sl.done_ev);
-            cudaFreeHost(sl.pin_depth);
-            cudaFreeHost(sl.pin_rgb);
+            release_slot(sl);
         }
         delete m;
     }

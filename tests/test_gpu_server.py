@@ -105,3 +105,35 @@ def test_wait_times_out_then_completes(setup):
     results = [srv.wait(t, 60_000) for t in tickets]
     assert len(results) == 12
     srv.close()
+
+
+def test_cascade_model_matches_the_cascade_alone(setup):
+    """A cascade served among other requests (two resolutions) returns what
+    the same cascade returns for the frame alone."""
+    rg, ctx, w, g, scene = setup
+    levels = [dict(w.ransac, n_hyp=48, n_trees_used=1, k_out=1), dict(w.ransac)]
+    subsample, thresholds = [2, 1], [0.06]
+    srv = rg.Server(ctx, max_batch=4, memory_budget=1 << 26)
+    mc = srv.add_cascade_model(g, scene, levels, subsample, thresholds, w.width, w.height)
+    mp = srv.add_model(g, scene, w.ransac, w.width, w.height)
+    frames = _frames(w)
+    tickets = [(srv.submit(mc, d, c, K, seed), srv.submit(mp, d, c, K, seed + 1)) for d, c, K, seed in frames]
+    got = [srv.wait(tc, 60_000) for tc, _ in tickets]
+    for _, tp in tickets:
+        srv.wait(tp, 60_000)
+    srv.close()
+    used = set()
+    for (d, c, K, seed), r in zip(frames, got):
+        lv = [rg.Relocaliser(g, scene, p, (K.width + s - 1) // s, (K.height + s - 1) // s, 1)
+              for p, s in zip(levels, subsample)]
+        cas = rg.Cascade(lv, thresholds, subsample)
+        alone = cas.relocalise_batch(d[None], c[None], K, [seed])[0]
+        cas.close()
+        for x in lv:
+            x.close()
+        used.add(alone["level"])
+        assert r["level"] == alone["level"]
+        assert np.array_equal(alone["pose"], r["pose"])
+        assert alone["energy"] == r["energy"] and alone["n_hypotheses"] == r["n_hypotheses"]
+        assert (alone["score"] == r["score"]) or (np.isinf(alone["score"]) and np.isinf(r["score"]))
+    assert used  # at least one level produced the results
