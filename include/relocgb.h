@@ -377,6 +377,9 @@ rl_status rl_server_poll(rl_server *s, uint64_t ticket, int32_t *done, rl_result
  * (the ticket stays valid). */
 rl_status rl_server_wait(rl_server *s, uint64_t ticket, uint32_t timeout_ms, rl_result *out);
 rl_status rl_server_get_stats(rl_server *s, rl_server_stats *out);
+/* Clears the counters and latencies of rl_server_get_stats (requests in
+ * flight and tickets are unaffected), e.g. after a warm-up. */
+rl_status rl_server_reset_stats(rl_server *s);
 /* Finishes queued work, stops the workers and releases the models. */
 rl_status rl_server_destroy(rl_server *s);
 

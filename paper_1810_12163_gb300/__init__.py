@@ -362,6 +362,9 @@ class Server:
         call("rl_server_wait", self.h, ticket, timeout_ms, ctypes.byref(r))
         return result_dict(r)
 
+    def reset_stats(self):
+        call("rl_server_reset_stats", self.h)
+
     def stats(self) -> dict:
         from .binding import ServerStats
         st = ServerStats()

@@ -118,6 +118,7 @@ _SIGS = {
     "rl_server_create": [P, P, P],
     "rl_server_add_model": [P, P, P, P, I32, I32, P],
     "rl_server_add_cascade_model": [P, P, P, P, P, P, I32, I32, I32, P],
+    "rl_server_reset_stats": [P],
     "rl_server_submit": [P, I32, P, P, P, U64, P],
     "rl_server_poll": [P, U64, P, P],
     "rl_server_wait": [P, U64, ctypes.c_uint32, P],

@@ -413,6 +413,16 @@ extern "C" rl_status rl_server_get_stats(rl_server *s, rl_server_stats *out) {
     return RL_OK;
 }
 
+extern "C" rl_status rl_server_reset_stats(rl_server *s) {
+    if (!s) return fail(RL_ERR_INVALID_ARG, "null server");
+    std::lock_guard<std::mutex> g(s->mu);
+    s->submitted = s->completed = s->refused = 0;
+    s->peak_bytes = s->bytes_admitted;
+    s->latencies.clear();
+    s->t_first = s->t_last = -1.0;
+    return RL_OK;
+}
+
 extern "C" rl_status rl_server_destroy(rl_server *s) {
     if (!s) return fail(RL_ERR_INVALID_ARG, "null server");
     {

@@ -117,6 +117,37 @@ def config5(mode_precision: int) -> Workload:
     )
 
 
+# Config 4: serving over three rooms, each with its own five-tree forest;
+# 8 camera streams (room = stream mod 3; even streams 640x480, odd 320x240)
+# with Poisson arrivals at 30 Hz per stream (seed 11 + stream).
+SERVING_ROOMS = [
+    CONFIG2,
+    Workload(name="room6x5x3_640x480_5trees_d15", room_size=(6.0, 5.0, 3.0), room_seed=17,
+             width=640, height=480, forest=dict(FOREST_DEFAULT), forest_seed=3, n_train=200,
+             ransac=dict(CONFIG2.ransac), n_queries=16),
+    Workload(name="room10x8x3_640x480_5trees_d15", room_size=(10.0, 8.0, 3.0), room_seed=29,
+             width=640, height=480, forest=dict(FOREST_DEFAULT), forest_seed=4, n_train=200,
+             ransac=dict(CONFIG2.ransac), n_queries=16),
+]
+SERVING_STREAMS = 8
+SERVING_RATE_HZ = 30.0
+
+
+def serving_arrivals(seconds: float, rate_scale: float = 1.0, streams: int = SERVING_STREAMS,
+                     seed: int = 11):
+    """Sorted (time in s, stream) of Poisson arrivals at SERVING_RATE_HZ x
+    rate_scale per stream over [0, seconds)."""
+    out = []
+    for s in range(streams):
+        rng = np.random.default_rng(seed + s)
+        t = rng.exponential(1.0 / (SERVING_RATE_HZ * rate_scale))
+        while t < seconds:
+            out.append((t, s))
+            t += rng.exponential(1.0 / (SERVING_RATE_HZ * rate_scale))
+    out.sort()
+    return out
+
+
 # Config 3 levels (shared config-2 forest): subsample, relocaliser parameters.
 CASCADE_LEVELS = [
     (4, dict(RANSAC_DEFAULT, n_hyp=64, n_trees_used=1, k_out=1, eta=100)),
