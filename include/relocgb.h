@@ -285,6 +285,41 @@ rl_status rl_reloc_debug(rl_reloc *r, int32_t q, double *hyp_pose /* n_hyp*12 */
                          double *round_pose /* 16*n_cull*12 */, int32_t *batch_pix /* 16*eta */,
                          int32_t *n_rounds);
 
+/* ---- launch-shape tuning ---------------------------------------------- */
+/* Launch shapes of the relocaliser's kernels that do not change any result
+ * (every kernel computes the same values in the same order for each of
+ * them).  Defaults: {4, 128, 128, 256}. */
+typedef struct {
+    int32_t hypgen_warps;     /* warps (slots) per block of generation: 2, 4 or 8 */
+    int32_t energy_threads;   /* at most this many hypotheses per block of Eq. 5: 32, 64, 128 or 256 */
+    int32_t leaves_threads;   /* pixels per block of the forest walk: 64, 128, 256 or 512 */
+    int32_t mask_threads;     /* pixels per block of the colour-check masks: 64, 128 or 256 */
+} rl_tuning;
+
+rl_status rl_reloc_get_tuning(rl_reloc *r, rl_tuning *out);
+/* RL_ERR_INVALID_ARG for a value outside the lists above.  Drops the
+ * relocaliser's captured CUDA graphs (they hold the old launch shapes). */
+rl_status rl_reloc_set_tuning(rl_reloc *r, const rl_tuning *t);
+/* Autotuner.  If cache_path (may be NULL) holds an entry for this
+ * relocaliser's key (rl_tuning_key), applies it.  Otherwise times every
+ * candidate of each knob in turn on n given frames (calls of
+ * rl_relocalise_batch with per-kernel CUDA-event timing, two per
+ * candidate), keeps the fastest (ties: the current value), applies the
+ * result and, with a cache_path, records it there.  *out (may be NULL)
+ * receives the tuning in use.  The paper has no counterpart. */
+rl_status rl_reloc_autotune(rl_reloc *r, int32_t n, const float *depth, const uint8_t *rgb,
+                            const rl_intrinsics *K, const uint64_t *seeds, rl_mem mem, void *stream,
+                            const char *cache_path, rl_tuning *out);
+/* Cache key of a relocaliser: device name and SM count, maximum frame size
+ * and batch, and the parameters that shape its kernels.  RL_ERR_INVALID_ARG
+ * if buf (len bytes) is too small. */
+rl_status rl_tuning_key(rl_reloc *r, char *buf, int32_t len);
+/* Tuning cache (text file, one "key = w e l m" line per key).  Host only.
+ * read: *found = 0 if the file or the key is absent (RL_OK).  write:
+ * replaces the key's line or appends it; RL_ERR_IO on file errors. */
+rl_status rl_tuning_cache_read(const char *path, const char *key, rl_tuning *out, int32_t *found);
+rl_status rl_tuning_cache_write(const char *path, const char *key, const rl_tuning *t);
+
 /* ---- tracing ---------------------------------------------------------- */
 /* Per-kernel timing of a relocaliser: when enabled, every kernel launch of
  * its calls is bracketed by CUDA events on the caller's stream; durations

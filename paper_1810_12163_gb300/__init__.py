@@ -240,6 +240,34 @@ class Relocaliser:
     def relocalise(self, depth, rgb, K, seed, stream=None):
         return self.relocalise_batch(depth, rgb, K, [seed], stream)[0]
 
+    @property
+    def tuning(self) -> dict:
+        """Launch shapes in use (they never change a result)."""
+        t = binding.Tuning()
+        call("rl_reloc_get_tuning", self.h, ctypes.byref(t))
+        return {f: getattr(t, f) for f, _ in binding.Tuning._fields_}
+
+    def set_tuning(self, tuning: dict):
+        t = binding.Tuning(**dict(self.tuning, **tuning))
+        call("rl_reloc_set_tuning", self.h, ctypes.byref(t))
+
+    def tuning_key(self) -> str:
+        buf = ctypes.create_string_buffer(512)
+        call("rl_tuning_key", self.h, buf, 512)
+        return buf.value.decode()
+
+    def autotune(self, depth, rgb, K, seeds, cache_path=None, stream=None) -> dict:
+        """Times the candidate launch shapes on these frames (or takes them from
+        cache_path) and applies the fastest; returns the tuning in use."""
+        d = _Image(depth, np.float32)
+        c = _Image(rgb, np.uint8)
+        seeds = np.ascontiguousarray(seeds, np.uint64)
+        t = binding.Tuning()
+        call("rl_reloc_autotune", self.h, len(seeds), d.ptr, c.ptr, ctypes.byref(intrinsics(K)),
+             seeds.ctypes.data_as(ctypes.c_void_p), d.mem, _stream_ptr(stream),
+             cache_path.encode() if cache_path else None, ctypes.byref(t))
+        return {f: getattr(t, f) for f, _ in binding.Tuning._fields_}
+
     def set_graphs(self, enable: bool = True):
         """Replay captured CUDA graphs (default) or launch kernels one by one."""
         call("rl_reloc_set_graphs", self.h, int(enable))
@@ -375,3 +403,17 @@ class Server:
         if self.h:
             call("rl_server_destroy", self.h)
             self.h = ctypes.c_void_p()
+
+
+def tuning_cache_read(path: str, key: str):
+    """Tuning recorded under key in the cache file, or None."""
+    t = binding.Tuning()
+    found = ctypes.c_int32()
+    call("rl_tuning_cache_read", path.encode(), key.encode(), ctypes.byref(t), ctypes.byref(found))
+    return {f: getattr(t, f) for f, _ in binding.Tuning._fields_} if found.value else None
+
+
+def tuning_cache_write(path: str, key: str, tuning: dict):
+    t = binding.Tuning(**tuning)
+    call("rl_tuning_cache_write", path.encode(), key.encode(), ctypes.byref(t))
+

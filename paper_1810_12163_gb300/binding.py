@@ -67,6 +67,11 @@ class ServerParams(ctypes.Structure):
     _fields_ = [("max_batch", I32), ("queue_when_full", I32), ("memory_budget", U64)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("hypgen_warps", ctypes.c_int32), ("energy_threads", ctypes.c_int32),
+                ("leaves_threads", ctypes.c_int32), ("mask_threads", ctypes.c_int32)]
+
+
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", U64), ("completed", U64), ("refused", U64),
                 ("peak_admitted_bytes", U64), ("p50_ms", ctypes.c_double),
@@ -119,6 +124,12 @@ _SIGS = {
     "rl_server_add_model": [P, P, P, P, I32, I32, P],
     "rl_server_add_cascade_model": [P, P, P, P, P, P, I32, I32, I32, P],
     "rl_server_reset_stats": [P],
+    "rl_reloc_get_tuning": [P, P],
+    "rl_reloc_set_tuning": [P, P],
+    "rl_reloc_autotune": [P, I32, P, P, P, P, I32, P, ctypes.c_char_p, P],
+    "rl_tuning_key": [P, ctypes.c_char_p, I32],
+    "rl_tuning_cache_read": [ctypes.c_char_p, ctypes.c_char_p, P, P],
+    "rl_tuning_cache_write": [ctypes.c_char_p, ctypes.c_char_p, P],
     "rl_server_submit": [P, I32, P, P, P, U64, P],
     "rl_server_poll": [P, U64, P, P],
     "rl_server_wait": [P, U64, ctypes.c_uint32, P],

@@ -185,10 +185,10 @@ __global__ void k_leaves(const float4 *__restrict__ nodes, int n_branch, int dep
 
 rl_status launch_leaves(const rl_forest *f, const Frame *frames_dev, int n_frames, int n_trees,
                         int hw_max, uint16_t *out, int max_w, int max_h, cudaStream_t s,
-                        int k_top, uint16_t *mcount, uint4 *prec) {
+                        int k_top, uint16_t *mcount, uint4 *prec, int threads) {
     const int npx = max_w * max_h;
-    dim3 grid((npx + 127) / 128, n_frames);
-    k_leaves<<<grid, 128, 0, s>>>(f->nodes, f->n_branch, f->p.depth, n_trees, frames_dev, hw_max, out,
+    dim3 grid((npx + threads - 1) / threads, n_frames);
+    k_leaves<<<grid, threads, 0, s>>>(f->nodes, f->n_branch, f->p.depth, n_trees, frames_dev, hw_max, out,
                                   f->nmodes, f->leaves_per_tree, k_top, mcount,
                                   n_trees <= kRecTrees ? prec : nullptr);
     RL_LAUNCH_CK();

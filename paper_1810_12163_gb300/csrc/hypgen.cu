@@ -136,10 +136,12 @@ __device__ __forceinline__ bool stage2(const HypArgs &a, const CheckThr &ct, con
 // iteration, exactly as a sequential loop would find it: every lower
 // iteration failed stage 1 or was drained earlier.  Compaction keeps the
 // lanes converged on the rarely reached stage 2.
-constexpr int HG_WARPS = 4;
 constexpr int HG_RING = 128;  // < 32 pending after a drain + 64 appended
 
-__global__ void __launch_bounds__(HG_WARPS * 32, 8) k_hypgen(HypArgs a) {
+// WARPS slots per block; registers stay capped at 64 (32 warps per SM).
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_hypgen(HypArgs a) {
+    constexpr int HG_WARPS = WARPS;
     __shared__ int4 s_ring[HG_WARPS][HG_RING];   // it | j << 30, pixels of the triple
     __shared__ uint2 s_mode[HG_WARPS][HG_RING];  // mode indices m0 | m1 << 16, m2
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -268,9 +270,10 @@ __global__ void __launch_bounds__(256) k_colour_mask(const Frame *__restrict__ f
 }
 
 rl_status launch_colour_mask(const Frame *frames, const uint16_t *mcount, const uint4 *prec, int hw_max,
-                             ModeView mv, const RParams &p, uint2 *pcm, int n, int max_hw, cudaStream_t s) {
-    dim3 grid((max_hw + 255) / 256, n);
-    k_colour_mask<<<grid, 256, 0, s>>>(frames, mcount, prec, hw_max, mv, p, pcm);
+                             ModeView mv, const RParams &p, uint2 *pcm, int n, int max_hw, cudaStream_t s,
+                             int threads) {
+    dim3 grid((max_hw + threads - 1) / threads, n);
+    k_colour_mask<<<grid, threads, 0, s>>>(frames, mcount, prec, hw_max, mv, p, pcm);
     RL_LAUNCH_CK();
     return RL_OK;
 }
@@ -339,10 +342,14 @@ __global__ void k_sample_batch(const Frame *__restrict__ frames, const uint16_t 
 
 rl_status launch_hypgen(const Frame *frames, const uint16_t *leaves, const uint16_t *mcount,
                         const uint4 *prec, const uint2 *pcm, int hw_max, ModeView mv, const RParams &p,
-                        double *hyp_pose, int32_t *hyp_iter, unsigned long long *work, int n, cudaStream_t s) {
+                        double *hyp_pose, int32_t *hyp_iter, unsigned long long *work, int n, cudaStream_t s,
+                        int warps) {
     HypArgs a{frames, leaves, mcount, prec, pcm, hw_max, mv, p, hyp_pose, hyp_iter, work};
-    dim3 grid((p.n_hyp + HG_WARPS - 1) / HG_WARPS, n);
-    k_hypgen<<<grid, HG_WARPS * 32, 0, s>>>(a);
+    switch (warps) {
+    case 2: k_hypgen<2><<<dim3((p.n_hyp + 1) / 2, n), 64, 0, s>>>(a); break;
+    case 8: k_hypgen<8><<<dim3((p.n_hyp + 7) / 8, n), 256, 0, s>>>(a); break;
+    default: k_hypgen<4><<<dim3((p.n_hyp + 3) / 4, n), 128, 0, s>>>(a); break;
+    }
     RL_LAUNCH_CK();
     return RL_OK;
 }

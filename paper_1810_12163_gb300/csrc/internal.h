@@ -247,6 +247,7 @@ struct rl_reloc {
     cudaStream_t capture_stream = nullptr;
     bool use_graphs = true;
     uint64_t calls = 0;
+    rl_tuning tune{4, 128, 128, 256};  // launch shapes (results do not depend on them)
 };
 
 // Per-frame output of a cascade, written on the device by each level's
@@ -315,7 +316,8 @@ namespace rl {
 rl_status launch_forest_random(rl_forest *f, cudaStream_t s);
 rl_status launch_leaves(const rl_forest *f, const Frame *frames_dev, int n_frames, int n_trees,
                         int hw_max, uint16_t *out, int max_w, int max_h, cudaStream_t s,
-                        int k_top = 0, uint16_t *mcount = nullptr, uint4 *prec = nullptr);
+                        int k_top = 0, uint16_t *mcount = nullptr, uint4 *prec = nullptr,
+                        int threads = 128);
 rl_status adapt_frame(rl_forest *f, const float *depth, const uint8_t *rgb,
                       const rl_intrinsics *K, const double T[16], cudaStream_t s);
 rl_status update_modes(rl_forest *f, int64_t begin, int64_t count, cudaStream_t s);

@@ -90,7 +90,7 @@ struct RaycastArgs {
 };
 
 size_t energy_smem(int chunk, int maxm);
-rl_status launch_energy(const EnergyArgs &a, int max_count, int n, cudaStream_t s);
+rl_status launch_energy(const EnergyArgs &a, int max_count, int n, cudaStream_t s, int max_threads = 128);
 rl_status launch_select(const SelectArgs &a, int n, cudaStream_t s);
 rl_status launch_lm(const LmArgs &a, int n, cudaStream_t s);
 rl_status launch_raycast(const RaycastArgs &a, int n, int max_hw, cudaStream_t s);
@@ -100,11 +100,13 @@ rl_status launch_finalize(const QueryState &q, const RParams &p, int n_tiles, in
                           cudaStream_t s);
 rl_status launch_hypgen(const Frame *frames, const uint16_t *leaves, const uint16_t *mcount,
                         const uint4 *prec, const uint2 *pcm, int hw_max, ModeView mv, const RParams &p,
-                        double *hyp_pose, int32_t *hyp_iter, unsigned long long *work, int n, cudaStream_t s);
+                        double *hyp_pose, int32_t *hyp_iter, unsigned long long *work, int n, cudaStream_t s,
+                        int warps = 4);
 // Largest |M(u)| the colour-check masks cover.
 constexpr int kMaskModes = 56;
 rl_status launch_colour_mask(const Frame *frames, const uint16_t *mcount, const uint4 *prec, int hw_max,
-                             ModeView mv, const RParams &p, uint2 *pcm, int n, int max_hw, cudaStream_t s);
+                             ModeView mv, const RParams &p, uint2 *pcm, int n, int max_hw, cudaStream_t s,
+                             int threads = 256);
 rl_status launch_hyppose(const Frame *frames, const uint16_t *leaves, const uint16_t *mcount,
                          const uint4 *prec, int hw_max, ModeView mv, const RParams &p,
                          double *hyp_pose, int32_t *hyp_iter, int n, cudaStream_t s);

@@ -136,9 +136,9 @@ rl_status run_relocalise(rl_reloc *r, int n, int level, cudaStream_t s) {
     RL_CK(cudaMemsetAsync(q.round_count, 0, sizeof(int32_t) * 16 * n, s));
     RL_CK(cudaMemsetAsync(q.dev_err, 0, sizeof(int32_t) * n, s));
     unsigned long long *work = r->prof.on ? r->prof.work : nullptr;
-    { PROF(K_LEAVES); RL_TRY(launch_leaves(f, q.frames, n, p.n_trees, hw_max, q.leaves, r->max_w, r->max_h, s, p.k_top, q.mcount, q.prec)); }
-    if (q.pcm) { PROF(K_CMASK); RL_TRY(launch_colour_mask(q.frames, q.mcount, q.prec, hw_max, mv, p, q.pcm, n, hw_max, s)); }
-    { PROF(K_HYPGEN); RL_TRY(launch_hypgen(q.frames, q.leaves, q.mcount, q.prec, q.pcm, hw_max, mv, p, q.hyp_pose, q.hyp_iter, work, n, s)); }
+    { PROF(K_LEAVES); RL_TRY(launch_leaves(f, q.frames, n, p.n_trees, hw_max, q.leaves, r->max_w, r->max_h, s, p.k_top, q.mcount, q.prec, r->tune.leaves_threads)); }
+    if (q.pcm) { PROF(K_CMASK); RL_TRY(launch_colour_mask(q.frames, q.mcount, q.prec, hw_max, mv, p, q.pcm, n, hw_max, s, r->tune.mask_threads)); }
+    { PROF(K_HYPGEN); RL_TRY(launch_hypgen(q.frames, q.leaves, q.mcount, q.prec, q.pcm, hw_max, mv, p, q.hyp_pose, q.hyp_iter, work, n, s, r->tune.hypgen_warps)); }
     { PROF(K_HYPPOSE); RL_TRY(launch_hyppose(q.frames, q.leaves, q.mcount, q.prec, hw_max, mv, p, q.hyp_pose, q.hyp_iter, n, s)); }
     { PROF(K_COMPACT); RL_TRY(launch_compact(q.hyp_iter, N, q.hyp_list, q.n_hyp, n, s)); }
     { PROF(K_SAMPLE); RL_TRY(launch_sample_batch(q.frames, q.mcount, hw_max, p, 0, q.pix, q.xc, n, s));
@@ -174,7 +174,7 @@ rl_status run_relocalise(rl_reloc *r, int n, int level, cudaStream_t s) {
     ea.n_pix = p.eta;
     ea.round_gate = 0;
     ea.work = work;
-    { PROF(K_ENERGY); RL_TRY(launch_energy(ea, N, n, s)); }
+    { PROF(K_ENERGY); RL_TRY(launch_energy(ea, N, n, s, r->tune.energy_threads)); }
     SelectArgs sa{};
     sa.phase = 0;
     sa.round = 0;
@@ -206,7 +206,7 @@ rl_status run_relocalise(rl_reloc *r, int n, int level, cudaStream_t s) {
         ea.count = q.n_cur;
         ea.n_pix = n_pix;
         ea.round_gate = 1;
-        { PROF(K_ENERGY); RL_TRY(launch_energy(ea, NC, n, s)); }
+        { PROF(K_ENERGY); RL_TRY(launch_energy(ea, NC, n, s, r->tune.energy_threads)); }
         sa.phase = 1;
         sa.round = round;
         sa.count = q.n_cur;
@@ -980,4 +980,176 @@ extern "C" rl_status rl_score_poses(rl_scene *sc, const float *depth, const rl_i
     void *ptrs[] = {fr, pd, psum, pcnt, sd, dd};
     for (void *p : ptrs) arena_free(ctx, p);
     return st;
+}
+
+// ---------------------------------------------------------------------------
+// Launch-shape tuning and the autotuner.  Every tunable shape leaves each
+// kernel's arithmetic and its order unchanged, so tuning never changes a
+// result; only the time to get it.
+// ---------------------------------------------------------------------------
+namespace rl {
+
+static bool one_of(int v, std::initializer_list<int> l) {
+    for (int x : l)
+        if (v == x) return true;
+    return false;
+}
+
+static bool valid_tuning(const rl_tuning &t) {
+    return one_of(t.hypgen_warps, {2, 4, 8}) && one_of(t.energy_threads, {32, 64, 128, 256}) &&
+           one_of(t.leaves_threads, {64, 128, 256, 512}) && one_of(t.mask_threads, {64, 128, 256});
+}
+
+static std::string trim(const std::string &x) {
+    size_t a = x.find_first_not_of(" \t\r\n"), b = x.find_last_not_of(" \t\r\n");
+    return a == std::string::npos ? std::string() : x.substr(a, b - a + 1);
+}
+
+}  // namespace rl
+
+extern "C" rl_status rl_reloc_get_tuning(rl_reloc *r, rl_tuning *out) {
+    if (!r || !out) return fail(RL_ERR_INVALID_ARG, "null argument");
+    *out = r->tune;
+    return RL_OK;
+}
+
+extern "C" rl_status rl_reloc_set_tuning(rl_reloc *r, const rl_tuning *t) {
+    if (!r || !t) return fail(RL_ERR_INVALID_ARG, "null argument");
+    if (!valid_tuning(*t)) return fail(RL_ERR_INVALID_ARG, "tuning value outside its list");
+    RL_CK(cudaSetDevice(r->forest->ctx->device));
+    RL_CK(cudaDeviceSynchronize());
+    graphs_free(r);
+    r->tune = *t;
+    return RL_OK;
+}
+
+extern "C" rl_status rl_tuning_key(rl_reloc *r, char *buf, int32_t len) {
+    if (!r || !buf || len < 1) return fail(RL_ERR_INVALID_ARG, "null argument");
+    cudaDeviceProp prop;
+    RL_CK(cudaGetDeviceProperties(&prop, r->forest->ctx->device));
+    std::string name = prop.name;
+    for (char &ch : name)
+        if (ch == ' ' || ch == '=' || ch == '\t') ch = '_';
+    const RParams &p = r->rp;
+    char tmp[512];
+    const int w = snprintf(tmp, sizeof(tmp), "%s|sm%d|%dx%d|b%d|T%d|d%d|ktop%d|mpad%d|N%d|C%d|eta%d|cov%d|mask%d",
+                           name.c_str(), prop.multiProcessorCount, r->max_w, r->max_h, r->max_batch, p.n_trees,
+                           r->forest->p.depth, p.k_top, p.mpad, p.n_hyp, p.n_cull, p.eta, p.use_cov ? 1 : 0,
+                           r->q.pcm ? 1 : 0);
+    if (w < 0 || w >= len) return fail(RL_ERR_INVALID_ARG, "key buffer too small");
+    memcpy(buf, tmp, (size_t)w + 1);
+    return RL_OK;
+}
+
+extern "C" rl_status rl_tuning_cache_read(const char *path, const char *key, rl_tuning *out, int32_t *found) {
+    if (!path || !key || !out || !found) return fail(RL_ERR_INVALID_ARG, "null argument");
+    *found = 0;
+    FILE *fp = fopen(path, "r");
+    if (!fp) return RL_OK;
+    char line[1024];
+    while (fgets(line, sizeof(line), fp)) {
+        std::string l(line);
+        const size_t eq = l.find('=');
+        if (eq == std::string::npos || trim(l.substr(0, eq)) != key) continue;
+        rl_tuning t{};
+        if (sscanf(l.c_str() + eq + 1, "%d %d %d %d", &t.hypgen_warps, &t.energy_threads, &t.leaves_threads,
+                   &t.mask_threads) == 4 && valid_tuning(t)) {
+            *out = t;
+            *found = 1;
+        }
+    }
+    fclose(fp);
+    return RL_OK;
+}
+
+extern "C" rl_status rl_tuning_cache_write(const char *path, const char *key, const rl_tuning *t) {
+    if (!path || !key || !t) return fail(RL_ERR_INVALID_ARG, "null argument");
+    if (!valid_tuning(*t)) return fail(RL_ERR_INVALID_ARG, "tuning value outside its list");
+    std::vector<std::string> lines;
+    if (FILE *fp = fopen(path, "r")) {
+        char line[1024];
+        while (fgets(line, sizeof(line), fp)) {
+            std::string l(line);
+            const size_t eq = l.find('=');
+            if (eq != std::string::npos && trim(l.substr(0, eq)) == key) continue;  // replaced below
+            if (!trim(l).empty()) lines.push_back(trim(l));
+        }
+        fclose(fp);
+    }
+    char entry[1100];
+    snprintf(entry, sizeof(entry), "%s = %d %d %d %d", key, t->hypgen_warps, t->energy_threads,
+             t->leaves_threads, t->mask_threads);
+    lines.push_back(entry);
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *fp = fopen(tmp.c_str(), "w");
+    if (!fp) return fail(RL_ERR_IO, "cannot write the tuning cache");
+    bool ok = true;
+    for (auto &l : lines) ok = ok && fprintf(fp, "%s\n", l.c_str()) > 0;
+    ok = (fclose(fp) == 0) && ok;
+    if (!ok || rename(tmp.c_str(), path) != 0) return fail(RL_ERR_IO, "cannot write the tuning cache");
+    return RL_OK;
+}
+
+extern "C" rl_status rl_reloc_autotune(rl_reloc *r, int32_t n, const float *depth, const uint8_t *rgb,
+                                       const rl_intrinsics *K, const uint64_t *seeds, rl_mem mem, void *stream,
+                                       const char *cache_path, rl_tuning *out) {
+    if (!r) return fail(RL_ERR_INVALID_ARG, "null relocaliser");
+    char key[512];
+    RL_TRY(rl_tuning_key(r, key, (int32_t)sizeof(key)));
+    if (cache_path) {
+        rl_tuning t{};
+        int32_t found = 0;
+        RL_TRY(rl_tuning_cache_read(cache_path, key, &t, &found));
+        if (found) {
+            RL_TRY(rl_reloc_set_tuning(r, &t));
+            if (out) *out = t;
+            return RL_OK;
+        }
+    }
+    RL_TRY(check_call(r, n, depth, rgb, K, seeds));
+    const bool was_on = r->prof.on;
+    std::vector<rl_result> res((size_t)n);
+    struct Knob {
+        int32_t rl_tuning::*field;
+        std::vector<int> values;
+        int kid;
+    };
+    std::vector<Knob> knobs = {{&rl_tuning::hypgen_warps, {2, 4, 8}, K_HYPGEN},
+                               {&rl_tuning::energy_threads, {32, 64, 128, 256}, K_ENERGY},
+                               {&rl_tuning::leaves_threads, {64, 128, 256, 512}, K_LEAVES}};
+    if (r->q.pcm) knobs.push_back({&rl_tuning::mask_threads, {64, 128, 256}, K_CMASK});
+    rl_tuning t = r->tune;
+    rl_status st = RL_OK;
+    for (const Knob &k : knobs) {
+        int best = t.*k.field;
+        double best_ms = INFINITY, cur_ms = INFINITY;
+        for (int v : k.values) {
+            rl_tuning c = t;
+            c.*k.field = v;
+            r->tune = c;
+            double ms[RL_N_KERNELS];
+            if ((st = rl_reloc_profile(r, 1)) != RL_OK) break;      // resets the counters; launches bypass graphs
+            for (int rep = 0; rep < 2 && st == RL_OK; ++rep)
+                st = rl_relocalise_batch(r, n, depth, rgb, K, seeds, mem, stream, res.data());
+            if (st == RL_OK) st = rl_reloc_profile_read(r, ms, nullptr, nullptr);
+            if (st != RL_OK) break;
+            if (v == t.*k.field) cur_ms = ms[k.kid];
+            if (ms[k.kid] < best_ms) {
+                best_ms = ms[k.kid];
+                best = v;
+            }
+        }
+        if (st != RL_OK) break;
+        // keep the current value unless another is at least 2% faster
+        t.*k.field = best_ms < 0.98 * cur_ms ? best : t.*k.field;
+    }
+    rl_reloc_profile(r, was_on ? 1 : 0);
+    if (st != RL_OK) {
+        r->tune = t;
+        return st;
+    }
+    RL_TRY(rl_reloc_set_tuning(r, &t));
+    if (cache_path) RL_TRY(rl_tuning_cache_write(cache_path, key, &t));
+    if (out) *out = t;
+    return RL_OK;
 }

@@ -20,7 +20,7 @@ namespace rl {
 // (decoded to FP32) are staged in shared memory and read by broadcast.
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(128) k_energy(EnergyArgs a) {
+__global__ void __launch_bounds__(256) k_energy(EnergyArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
     float4 *s_xc = (float4 *)smem;                         // [chunk]
     float4 *s_m0 = s_xc + a.chunk;                         // [chunk*maxm] mu.xyz, U00
@@ -1123,9 +1123,10 @@ __global__ void __launch_bounds__(256) k_finalize(QueryState q, RParams p, int n
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-rl_status launch_energy(const EnergyArgs &a0, int max_count, int n, cudaStream_t s) {
+rl_status launch_energy(const EnergyArgs &a0, int max_count, int n, cudaStream_t s, int max_threads) {
     EnergyArgs a = a0;
-    const int ht = max_count <= 32 ? 32 : (max_count <= 64 ? 64 : 128);
+    int ht = 32;  // hypotheses per block: the smallest power of two covering them, capped
+    while (ht < max_count && ht < max_threads) ht <<= 1;
     const size_t sm = (size_t)a.chunk * sizeof(float4) + (size_t)a.chunk * a.maxm * (2 * sizeof(float4) + sizeof(float)) +
                       (size_t)a.chunk * sizeof(int);
     dim3 grid((max_count + ht - 1) / ht, (a.n_pix + a.chunk - 1) / a.chunk, n);

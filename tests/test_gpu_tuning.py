@@ -1,0 +1,66 @@
+"""Autotuner: tuned and extreme launch shapes give bit-identical results
+(each kernel computes the same values in the same order), the tuning is
+recorded in and reused from the cache, and bad values are refused."""
+import numpy as np
+import pytest
+
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1810_12163_gb300 as rg
+    ctx = rg.Context(0, arena_bytes=4 << 30)
+    w = H.WORKLOADS[H.SMALL]
+    g = H.gpu_model(ctx, w)
+    scene = rg.Scene(ctx, w.room().lo, w.room().hi)
+    return rg, ctx, w, g, scene
+
+
+def _run(rel, qs, w):
+    D = np.stack([q[0] for q in qs])
+    C = np.stack([q[1] for q in qs])
+    return rel.relocalise_batch(D, C, w.K, [q[3] for q in qs])
+
+
+def _same(a, b):
+    for x, y in zip(a, b):
+        assert np.array_equal(x["pose"], y["pose"]) and x["energy"] == y["energy"]
+        assert x["n_hypotheses"] == y["n_hypotheses"] and x["best"] == y["best"]
+        assert np.array_equal(x["chosen_score"], y["chosen_score"])
+
+
+def test_tuning_never_changes_results(setup, tmp_path):
+    rg, ctx, w, g, scene = setup
+    rel = rg.Relocaliser(g, scene, w.ransac, w.width, w.height, 4)
+    qs = [w.query(q) for q in range(4)]
+    base = _run(rel, qs, w)
+    for t in (dict(hypgen_warps=2, energy_threads=32, leaves_threads=64, mask_threads=64),
+              dict(hypgen_warps=8, energy_threads=256, leaves_threads=512, mask_threads=256)):
+        rel.set_tuning(t)
+        assert rel.tuning == t
+        _same(_run(rel, qs, w), base)
+    cache = str(tmp_path / "tuning.txt")
+    tuned = rel.autotune(np.stack([q[0] for q in qs]), np.stack([q[1] for q in qs]), w.K,
+                         [q[3] for q in qs], cache_path=cache)
+    assert rel.tuning == tuned
+    _same(_run(rel, qs, w), base)
+    assert rg.tuning_cache_read(cache, rel.tuning_key()) == tuned
+    # a second relocaliser of the same shape takes the cached tuning without timing
+    rel2 = rg.Relocaliser(g, scene, w.ransac, w.width, w.height, 4)
+    assert rel2.tuning_key() == rel.tuning_key()
+    rg.tuning_cache_write(cache, rel2.tuning_key(), dict(hypgen_warps=2, energy_threads=64,
+                                                         leaves_threads=256, mask_threads=128))
+    got = rel2.autotune(np.stack([q[0] for q in qs]), np.stack([q[1] for q in qs]), w.K,
+                        [q[3] for q in qs], cache_path=cache)
+    assert got == dict(hypgen_warps=2, energy_threads=64, leaves_threads=256, mask_threads=128)
+    _same(_run(rel2, qs, w), base)
+    with pytest.raises(rg.RelocError):
+        rel.set_tuning(dict(hypgen_warps=5))
+    rel.close()
+    rel2.close()
