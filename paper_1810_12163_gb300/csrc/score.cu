@@ -920,102 +920,123 @@ __device__ bool ray_depth64(const double *P, int u, int v, float fx, float fy, f
     return false;
 }
 
-// The hit test runs in FP32; a ray whose decision lies within a relative
-// margin of 1e-4 of changing (near-parallel faces, grazing edges, a face
-// through the camera) is re-evaluated in FP64, so the valid mask of Eq. 7
-// is the FP64 one.
+// One thread per pixel of a 256-pixel tile, all poses of the frame in turn
+// (staged in shared memory, RC_CHUNK at a time): the pixel's live depth and
+// viewing direction are read once.  The hit test runs in FP32; a ray whose
+// decision lies within a relative margin of 1e-4 of changing (near-parallel
+// faces, grazing edges, a face through the camera) is re-evaluated in FP64,
+// so the valid mask of Eq. 7 is the FP64 one.  Per pose the tile's sums are
+// reduced over lanes, then over warps in order, one partial per (pose, tile).
+constexpr int RC_CHUNK = 16;
+
 __global__ void __launch_bounds__(256) k_raycast_score(RaycastArgs a) {
-    __shared__ float s_sum[8];
-    __shared__ int s_syn[8], s_both[8];
-    const int b = blockIdx.z, c = blockIdx.y;
-    if (c >= a.n_poses_of(b)) return;
+    __shared__ float sPf[RC_CHUNK][12];
+    __shared__ float s_sum[RC_CHUNK][8];
+    __shared__ int s_syn[RC_CHUNK][8], s_both[RC_CHUNK][8];
+    const int b = blockIdx.y;
+    const int n_poses = a.n_poses_of(b);
+    if (n_poses <= 0) return;
     const Frame fr = a.frames[b];
+    const int npx = fr.W * fr.H;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    const double *P = a.pose_of(b, c);
-    __shared__ float sPf[12];
-    if (threadIdx.x < 12) sPf[threadIdx.x] = (float)P[threadIdx.x];
-    __syncthreads();
-    float sum = 0.f;
-    int syn = 0, both = 0;
-    if (p < fr.W * fr.H) {
-        const int u = p % fr.W, v = p / fr.W;
+    const bool in = p < npx;
+    int u = 0, v = 0;
+    float dc0 = 0.f, dc1 = 0.f, dl = 0.f;
+    if (in) {
+        u = p % fr.W;
+        v = p / fr.W;
         // fast approximate divisions: their few-ulp error is far inside the
         // margin that sends a ray to the FP64 path
-        const float dc0 = __fdividef((float)u - fr.cx, fr.fx), dc1 = __fdividef((float)v - fr.cy, fr.fy);
-        float d[3], o[3];
-        for (int r = 0; r < 3; ++r) {
-            d[r] = fmaf(sPf[4 * r], dc0, fmaf(sPf[4 * r + 1], dc1, sPf[4 * r + 2]));
-            o[r] = sPf[4 * r + 3];
-        }
-        const float dn = fabsf(d[0]) + fabsf(d[1]) + fabsf(d[2]);
-        float tn = -INFINITY, tf = INFINITY;
-        bool ok = true, unsure = false;
-        for (int ax = 0; ax < 3; ++ax) {
-            if (fabsf(d[ax]) <= 1e-5f * dn) {
-                unsure = true;
-                continue;
-            }
-            const float inv = __fdividef(1.0f, d[ax]);
-            const float ta = (a.lo[ax] - o[ax]) * inv, tb = (a.hi[ax] - o[ax]) * inv;
-            tn = fmaxf(tn, fminf(ta, tb));
-            tf = fminf(tf, fmaxf(ta, tb));
-        }
-        float depth = 0.f;
-        if (!unsure) {
-            const float scale = fmaxf(fabsf(tn), fabsf(tf));
-            if (fabsf(tf - tn) <= 1e-4f * scale || fabsf(tn) <= 1e-4f * scale ||
-                fabsf(tf) <= 1e-4f * scale)
-                unsure = true;
-        }
-        if (unsure) {
-            double dd;
-            ok = ray_depth64(P, u, v, fr.fx, fr.fy, fr.cx, fr.cy, a.lo64, a.hi64, &dd);
-            depth = (float)dd;
-        } else if (tn <= tf && tn > 0.f) {
-            depth = tn;
-        } else if (tn <= tf && tf > 0.f) {
-            depth = tf;
-        } else {
-            ok = false;
-        }
-        if (ok) {
-            syn = 1;
-            const float dl = fr.depth[p];
-            if (dl > 0.f) {
-                both = 1;
-                sum = fabsf(dl - depth);
-            }
-        }
+        dc0 = __fdividef((float)u - fr.cx, fr.fx);
+        dc1 = __fdividef((float)v - fr.cy, fr.fy);
+        dl = fr.depth[p];
     }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int c0 = 0; c0 < n_poses; c0 += RC_CHUNK) {
+        const int cnt = min(RC_CHUNK, n_poses - c0);
+        __syncthreads();  // the previous chunk's poses and partials are consumed
+        for (int e = threadIdx.x; e < cnt * 12; e += blockDim.x) sPf[e / 12][e % 12] = (float)a.pose_of(b, c0 + e / 12)[e % 12];
+        __syncthreads();
+        for (int k = 0; k < cnt; ++k) {
+            float sum = 0.f;
+            int syn = 0, both = 0;
+            if (in) {
+                const float *P = sPf[k];
+                float d[3], o[3];
+                for (int r = 0; r < 3; ++r) {
+                    d[r] = fmaf(P[4 * r], dc0, fmaf(P[4 * r + 1], dc1, P[4 * r + 2]));
+                    o[r] = P[4 * r + 3];
+                }
+                const float dn = fabsf(d[0]) + fabsf(d[1]) + fabsf(d[2]);
+                float tn = -INFINITY, tf = INFINITY;
+                bool ok = true, unsure = false;
+                for (int ax = 0; ax < 3; ++ax) {
+                    if (fabsf(d[ax]) <= 1e-5f * dn) {
+                        unsure = true;
+                        continue;
+                    }
+                    const float inv = __fdividef(1.0f, d[ax]);
+                    const float ta = (a.lo[ax] - o[ax]) * inv, tb = (a.hi[ax] - o[ax]) * inv;
+                    tn = fmaxf(tn, fminf(ta, tb));
+                    tf = fminf(tf, fmaxf(ta, tb));
+                }
+                float depth = 0.f;
+                if (!unsure) {
+                    const float scale = fmaxf(fabsf(tn), fabsf(tf));
+                    if (fabsf(tf - tn) <= 1e-4f * scale || fabsf(tn) <= 1e-4f * scale ||
+                        fabsf(tf) <= 1e-4f * scale)
+                        unsure = true;
+                }
+                if (unsure) {
+                    double dd;
+                    ok = ray_depth64(a.pose_of(b, c0 + k), u, v, fr.fx, fr.fy, fr.cx, fr.cy, a.lo64, a.hi64, &dd);
+                    depth = (float)dd;
+                } else if (tn <= tf && tn > 0.f) {
+                    depth = tn;
+                } else if (tn <= tf && tf > 0.f) {
+                    depth = tf;
+                } else {
+                    ok = false;
+                }
+                if (ok) {
+                    syn = 1;
+                    if (dl > 0.f) {
+                        both = 1;
+                        sum = fabsf(dl - depth);
+                    }
+                }
+            }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        sum += __shfl_down_sync(0xffffffffu, sum, o);
-        syn += __shfl_down_sync(0xffffffffu, syn, o);
-        both += __shfl_down_sync(0xffffffffu, both, o);
-    }
-    const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) {
-        s_sum[w] = sum;
-        s_syn[w] = syn;
-        s_both[w] = both;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float ts = 0.f;
-        int tsyn = 0, tb = 0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-            ts += s_sum[k];
-            tsyn += s_syn[k];
-            tb += s_both[k];
+            for (int o = 16; o > 0; o >>= 1) {
+                sum += __shfl_down_sync(0xffffffffu, sum, o);
+                syn += __shfl_down_sync(0xffffffffu, syn, o);
+                both += __shfl_down_sync(0xffffffffu, both, o);
+            }
+            if (lane == 0) {
+                s_sum[k][w] = sum;
+                s_syn[k][w] = syn;
+                s_both[k][w] = both;
+            }
         }
-        const size_t o = ((size_t)b * a.pose_cap + c) * a.n_tiles + blockIdx.x;
-        a.part_sum[o] = (double)ts;
-        a.part_cnt[2 * o] = tsyn;
-        a.part_cnt[2 * o + 1] = tb;
-        if (a.work)
-            atomicAdd(&a.work[W_RAYS],
-                      (unsigned long long)min((int)blockDim.x, fr.W * fr.H - (int)(blockIdx.x * blockDim.x)));
+        __syncthreads();
+        if (threadIdx.x < cnt) {
+            const int k = threadIdx.x;
+            float ts = 0.f;
+            int tsyn = 0, tb = 0;
+            for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) {
+                ts += s_sum[k][ww];
+                tsyn += s_syn[k][ww];
+                tb += s_both[k][ww];
+            }
+            const size_t o = ((size_t)b * a.pose_cap + c0 + k) * a.n_tiles + blockIdx.x;
+            a.part_sum[o] = (double)ts;
+            a.part_cnt[2 * o] = tsyn;
+            a.part_cnt[2 * o + 1] = tb;
+        }
     }
+    if (a.work && threadIdx.x == 0)
+        atomicAdd(&a.work[W_RAYS], (unsigned long long)n_poses *
+                                       (unsigned long long)min((int)blockDim.x, npx - (int)(blockIdx.x * blockDim.x)));
 }
 
 // Eq. 7 from the tile partials of one (frame, pose): FP64 sums in tile order.
@@ -1179,7 +1200,7 @@ rl_status prepare_kernels() {
 }
 
 rl_status launch_raycast(const RaycastArgs &a, int n, int max_hw, cudaStream_t s) {
-    dim3 grid(a.n_tiles, a.pose_cap, n);
+    dim3 grid(a.n_tiles, n);
     k_raycast_score<<<grid, 256, 0, s>>>(a);
     RL_LAUNCH_CK();
     return RL_OK;
@@ -1207,7 +1228,7 @@ __global__ void k_scores_final(const double *part_sum, const int32_t *part_cnt, 
 
 rl_status launch_score_poses(const RaycastArgs &a, int n_poses, int npx, float *scores,
                              float *valid_frac, cudaStream_t s) {
-    dim3 grid(a.n_tiles, n_poses, 1);
+    dim3 grid(a.n_tiles, 1);
     k_raycast_score<<<grid, 256, 0, s>>>(a);
     RL_LAUNCH_CK();
     k_scores_final<<<(n_poses + 63) / 64, 64, 0, s>>>(a.part_sum, a.part_cnt, a.n_tiles, n_poses,
