@@ -16,7 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
-_SOURCES = ["oracle.c", "adapt.c", "ransac.c"]
+_SOURCES = ["oracle.c", "adapt.c", "ransac.c", "icp.c"]
 _lock = threading.Lock()
 _lib = None
 
@@ -54,6 +54,13 @@ F64 = ctypes.c_double
 U64 = ctypes.c_uint64
 
 
+class IcpParams(ctypes.Structure):
+    _fields_ = [
+        ("levels", ctypes.c_int32), ("stride", ctypes.c_int32 * 3), ("iters", ctypes.c_int32 * 3),
+        ("pad", ctypes.c_int32), ("dist", F64 * 3), ("min_frac", F64), ("ridge", F64),
+    ]
+
+
 class Params(ctypes.Structure):
     _fields_ = [
         ("n_hyp", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("n_cull", ctypes.c_int32),
@@ -64,7 +71,7 @@ class Params(ctypes.Structure):
         ("lm_max_iter", ctypes.c_int32), ("batch_attempts", ctypes.c_int32),
         ("lm_lambda0", F64), ("lm_inlier_thresh", F64), ("lm_stop", F64),
         ("rank", ctypes.c_int32), ("halve_to_one", ctypes.c_int32), ("level", ctypes.c_int32),
-        ("pad0", ctypes.c_int32), ("pad1", ctypes.c_int32),
+        ("icp", ctypes.c_int32), ("icp_p", IcpParams),
     ]
 
 
@@ -75,7 +82,7 @@ class Result(ctypes.Structure):
         ("n_pixels", ctypes.c_int32), ("status", ctypes.c_int32),
         ("chosen_pose", (F64 * 16) * 16), ("chosen_energy", F64 * 16),
         ("chosen_score", F64 * 16), ("chosen_slot", ctypes.c_int32 * 16),
-        ("best", ctypes.c_int32), ("pad", ctypes.c_int32),
+        ("best", ctypes.c_int32), ("icp_mask", ctypes.c_int32), ("chosen_icp_frac", F64 * 16),
     ]
 
 
@@ -118,6 +125,8 @@ def _declare(L):
     L.orc_cascade.argtypes = [I32, ctypes.POINTER(Params), P, P, P, P, P, P, P, P, P, P,
                               I32, I32, P, P, P, P, I32, P, P, U64, ctypes.POINTER(Result)]
     L.orc_cascade.restype = I32
+    L.orc_icp_refine.argtypes = [P, P, I32, I32, F32, F32, F32, F32, P, P, ctypes.POINTER(IcpParams), P]
+    L.orc_icp_refine.restype = I32
 
 
 def _p(a):
@@ -255,7 +264,22 @@ PARAM_DEFAULTS = dict(
     colour_thresh=30, min_sq_dist=0.09, max_trans_err=0.05, k_top=10, n_trees_used=5,
     lm_max_iter=10, batch_attempts=32, lm_lambda0=1e-3, lm_inlier_thresh=0.1, lm_stop=1e-6,
     rank=1, halve_to_one=0, level=0,
+    icp=0, icp_levels=3, icp_stride=(4, 2, 1), icp_iters=(6, 3, 2), icp_dist=(0.1, 0.05, 0.025),
+    icp_min_frac=0.5, icp_ridge=1e-4,
 )
+
+
+def make_icp_params(levels=3, stride=(4, 2, 1), iters=(6, 3, 2), dist=(0.1, 0.05, 0.025),
+                    min_frac=0.5, ridge=1e-4):
+    ip = IcpParams()
+    ip.levels = levels
+    for i in range(3):
+        ip.stride[i] = stride[i] if i < len(stride) else 1
+        ip.iters[i] = iters[i] if i < len(iters) else 0
+        ip.dist[i] = dist[i] if i < len(dist) else 0.0
+    ip.min_frac = min_frac
+    ip.ridge = ridge
+    return ip
 
 
 def make_params(**kw):
@@ -265,8 +289,27 @@ def make_params(**kw):
             d[k] = v
     p = Params()
     for k, v in d.items():
-        setattr(p, k, v)
+        if not k.startswith("icp_"):
+            setattr(p, k, v)
+    p.icp_p = make_icp_params(d["icp_levels"], d["icp_stride"], d["icp_iters"], d["icp_dist"],
+                              d["icp_min_frac"], d["icp_ridge"])
     return p
+
+
+def icp_refine(pose, depth_img, K, lo, hi, **icp):
+    """ICP of one pose against the box (R21): (refined 4x4, ok, last-iteration
+    inlier fraction).  Keyword arguments as make_icp_params."""
+    H12 = _pose12(pose).copy()
+    d = _c(depth_img, np.float32)
+    H, W = d.shape
+    lo = _c(lo, np.float64); hi = _c(hi, np.float64)
+    ip = make_icp_params(**icp)
+    frac = ctypes.c_double()
+    ok = lib().orc_icp_refine(_p(H12), _p(d), W, H, K.fx, K.fy, K.cx, K.cy, _p(lo), _p(hi),
+                              ctypes.byref(ip), ctypes.byref(frac))
+    out = np.eye(4)
+    out[:3, :4] = H12.reshape(3, 4)
+    return out, bool(ok), frac.value
 
 
 def _pose12(pose):
@@ -329,7 +372,8 @@ def _result_dict(r: Result):
         status=r.status, best=r.best,
         chosen_pose=np.array([np.array(r.chosen_pose[i]).reshape(4, 4) for i in range(nc)]),
         chosen_energy=np.array(r.chosen_energy[:nc]), chosen_score=np.array(r.chosen_score[:nc]),
-        chosen_slot=np.array(r.chosen_slot[:nc]),
+        chosen_slot=np.array(r.chosen_slot[:nc]), icp_mask=r.icp_mask,
+        chosen_icp_frac=np.array(r.chosen_icp_frac[:max(nc, 1)]),
     )
 
 

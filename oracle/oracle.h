@@ -86,6 +86,17 @@ void orc_update_modes(const float *res_pos, const uint8_t *res_rgb, const uint32
 /* Rigid transform (R,t) minimising sum |R a_i + t - b_i|^2 over 3D pairs. */
 void orc_kabsch(const double *a, const double *b, int n, double R[9], double t[3]);
 
+/* ICP refinement against the box model (Sec. 3.2.4, reading R21). */
+typedef struct {
+    int32_t levels;           /* coarse-to-fine levels, 1..3 */
+    int32_t stride[3];        /* pixel stride of each level */
+    int32_t iters[3];         /* Gauss-Newton iterations of each level */
+    int32_t pad;
+    double  dist[3];          /* inlier distance |q - p| of each level, m */
+    double  min_frac;         /* success: last-iteration inliers >= min_frac x valid pixels */
+    double  ridge;            /* lambda = ridge * trace(J^T J) / 6 */
+} orc_icp_params;
+
 typedef struct {
     int32_t n_hyp;            /* N_max */
     int32_t max_iter;         /* maxCandidateGenerationIterations */
@@ -107,7 +118,8 @@ typedef struct {
     int32_t rank;             /* model-based ranking of the chosen set */
     int32_t halve_to_one;     /* keep halving to 1 after the chosen set */
     int32_t level;            /* cascade level, part of the random stream */
-    int32_t pad0, pad1;
+    int32_t icp;              /* ICP of the chosen set (ranked) or output pose (R21) */
+    orc_icp_params icp_p;
 } orc_params;
 
 typedef struct {
@@ -124,7 +136,8 @@ typedef struct {
     double chosen_score[16];
     int32_t chosen_slot[16];
     int32_t best;             /* index into chosen of xi* */
-    int32_t pad;
+    int32_t icp_mask;         /* bit c: ICP refined chosen pose c (ranked) / the output (bit 0, unranked) */
+    double chosen_icp_frac[16]; /* last-iteration inlier fraction of each ICP run, -1 if not run */
 } orc_result;
 
 /* Optional diagnostics; any pointer may be NULL.  hyp_*: per slot of the
@@ -180,6 +193,18 @@ double orc_depth_score(const double pose12[12], const float *depth_img, int W, i
                        float fx, float fy, float cx, float cy,
                        const double box_lo[3], const double box_hi[3],
                        double *mean_abs, double *valid_frac);
+
+/* ICP of one pose against the box (R21); H is updated in place.  Returns 1
+ * on success, 0 on failure; *frac_out = inliers / valid pixels of the last
+ * iteration run. */
+int orc_icp_refine(double pose12[12], const float *depth_img, int W, int H,
+                   float fx, float fy, float cx, float cy,
+                   const double box_lo[3], const double box_hi[3], const orc_icp_params *ip,
+                   double *frac_out);
+
+/* Oracle-internal FP64 helpers shared by the LM and ICP parts. */
+int orc_chol_solve6(const double A[36], const double b[6], double x[6]);
+void orc_se3_left_update(const double xi[6], double H[12]);
 
 /* Sec. 3.2.5: cascade.  levels[l] describes level l; level_depth[l] etc.
  * are that level's (possibly subsampled) inputs and leaf maps.  Returns the

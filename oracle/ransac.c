@@ -141,7 +141,7 @@ void orc_kabsch(const double *a, const double *b, int n, double R[9], double t[3
 }
 
 /* Cholesky solve of a symmetric positive-definite 6x6 system; 0 on failure. */
-static int chol_solve6(const double A[36], const double b[6], double x[6])
+int orc_chol_solve6(const double A[36], const double b[6], double x[6])
 {
     double L[36] = {0};
     for (int i = 0; i < 6; ++i) {
@@ -175,7 +175,7 @@ static int chol_solve6(const double A[36], const double b[6], double x[6])
 }
 
 /* SE(3) exponential of xi = (v, w) applied on the left: H <- exp(xi^) H. */
-static void se3_left_update(const double xi[6], double H[12])
+void orc_se3_left_update(const double xi[6], double H[12])
 {
     const double w0 = xi[3], w1 = xi[4], w2 = xi[5];
     const double th2 = w0 * w0 + w1 * w1 + w2 * w2, th = sqrt(th2);
@@ -384,7 +384,7 @@ int orc_lm_refine(double H[12], const int32_t *pix, int n_pix,
             A[6 * a + a] += lambda * JtJ[6 * a + a];
             rhs[a] = -g[a];
         }
-        if (!chol_solve6(A, rhs, step))
+        if (!orc_chol_solve6(A, rhs, step))
             break;
         double sn = 0.0;
         for (int a = 0; a < 6; ++a)
@@ -393,7 +393,7 @@ int orc_lm_refine(double H[12], const int32_t *pix, int n_pix,
             break;
         double Hn[12];
         memcpy(Hn, H, sizeof(Hn));
-        se3_left_update(step, Hn);
+        orc_se3_left_update(step, Hn);
         /* cost at the trial pose with the same correspondences */
         double trial = 0.0;
         for (int i = 0; i < n_pix; ++i) {
@@ -609,8 +609,10 @@ void orc_relocalise(const orc_params *p,
     memset(out, 0, sizeof(*out));
     out->score = INFINITY;
     out->best = -1;
-    for (int i = 0; i < 16; ++i)
+    for (int i = 0; i < 16; ++i) {
         out->pose[i] = (i % 5 == 0) ? 1.0 : 0.0;
+        out->chosen_icp_frac[i] = -1.0;
+    }
 
     /* 1. hypothesis generation: one independent attempt loop per slot */
     hyp_t *hyp = (hyp_t *)malloc(sizeof(hyp_t) * (size_t)p->n_hyp);
@@ -725,7 +727,28 @@ void orc_relocalise(const orc_params *p,
         out->chosen_score[c] = INFINITY;
     }
 
-    /* 4. model-based ranking of the chosen set (Eq. 6-8) */
+    /* 4. ICP against the model (R21): each chosen pose when ranking, else the
+     * output pose; a pose is replaced by its refinement only when ICP
+     * succeeds, and a chosen pose whose ICP failed is not ranked. */
+    int icp_ok[16] = {0};
+    if (p->icp) {
+        const int n_icp = p->rank ? n_chosen : 1;
+        for (int c = 0; c < n_icp; ++c) {
+            double Hc[12], frac;
+            memcpy(Hc, p->rank ? chosen[c].H : hyp[0].H, sizeof(Hc));
+            icp_ok[c] = orc_icp_refine(Hc, depth_img, W, Himg, fx, fy, cx, cy, box_lo, box_hi, &p->icp_p, &frac);
+            out->chosen_icp_frac[c] = frac;
+            if (icp_ok[c]) {
+                out->icp_mask |= 1 << c;
+                memcpy(p->rank ? chosen[c].H : hyp[0].H, Hc, sizeof(Hc));
+                if (p->rank)
+                    for (int k = 0; k < 12; ++k)
+                        out->chosen_pose[c][k] = Hc[k];
+            }
+        }
+    }
+
+    /* 5. model-based ranking of the chosen set (Eq. 6-8) */
     int best = 0;
     double best_E = hyp[0].E;
     const double *best_H = hyp[0].H;
@@ -734,6 +757,8 @@ void orc_relocalise(const orc_params *p,
         double bs = INFINITY;
         int bi = -1;
         for (int c = 0; c < n_chosen; ++c) {
+            if (p->icp && !icp_ok[c])
+                continue; /* discarded: score stays +inf */
             out->chosen_score[c] = orc_depth_score(chosen[c].H, depth_img, W, Himg, fx, fy, cx, cy,
                                                    box_lo, box_hi, NULL, NULL);
             if (out->chosen_score[c] < bs) {

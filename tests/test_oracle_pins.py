@@ -437,6 +437,90 @@ def test_depth_score_of_ground_truth_is_noise_mean():
     assert abs(s2 - sigma * math.sqrt(2 / math.pi)) < 0.05 * sigma
 
 
+# ---------------------------------------------------------------- ICP before ranking (R21)
+_ICP_K = rooms.Intrinsics(292.5, 292.5, 160.0, 120.0, 320, 240)
+_ICP_ROOM = rooms.Room((4.0, 3.0, 2.5), 5)
+
+
+def _rot_deg(axis, deg):
+    return rooms._rodrigues(axis, math.radians(deg))
+
+
+def _corner_view():
+    """Camera near one corner looking at the opposite lower corner: two walls
+    and the floor in view, so every pose direction is constrained."""
+    pos = np.array([1.0, 0.8, 1.6])
+    tgt = np.array([4.0, 3.0, 0.0]) - pos
+    return rooms.look_pose(pos, math.atan2(tgt[1], tgt[0]), math.atan2(tgt[2], math.hypot(tgt[0], tgt[1])))
+
+
+def test_icp_recovers_exact_pose_of_corner_view():
+    """Noise-free depth: the true pose zeroes every residual, so ICP started a
+    few cm / degrees away must land on it (a wrong sign, index or transposed
+    Jacobian block would not converge there), and started on it stays."""
+    T = _corner_view()
+    d, _ = rooms.render(_ICP_ROOM, _ICP_K, T, noise_sigma=0.0)
+    rng = np.random.default_rng(1)
+    for _ in range(4):
+        P = T.copy()
+        P[:3, :3] = _rot_deg(rng.normal(size=3), 2.5) @ T[:3, :3]
+        P[:3, 3] += rng.normal(size=3) * 0.03
+        R, ok, frac = oracle.icp_refine(P, d, _ICP_K, _ICP_ROOM.lo, _ICP_ROOM.hi)
+        dt, dr = H.pose_err(R, T)
+        assert ok and frac == 1.0
+        assert dt < 1e-6 and dr < 1e-4, (dt, dr)
+    R, ok, _ = oracle.icp_refine(T, d, _ICP_K, _ICP_ROOM.lo, _ICP_ROOM.hi)
+    assert ok and H.pose_err(R, T)[0] < 1e-6
+    # pure rotation and pure translation errors separately
+    for P in (T @ np.block([[_rot_deg([1, 0, 0], 3.0), np.zeros((3, 1))], [np.zeros((1, 3)), np.ones((1, 1))]]),
+              T + np.block([[np.zeros((3, 3)), np.array([[0.04], [-0.03], [0.02]])], [np.zeros((1, 4))]])):
+        R, ok, _ = oracle.icp_refine(P, d, _ICP_K, _ICP_ROOM.lo, _ICP_ROOM.hi)
+        assert ok and H.pose_err(R, T)[0] < 1e-6 and H.pose_err(R, T)[1] < 1e-4
+
+
+def test_icp_single_wall_keeps_unconstrained_directions():
+    """A wall seen alone fixes only the distance to it and the two tilts.
+    ICP must correct those exactly and leave the camera centre's offset along
+    the wall and the turn about the wall normal where they started."""
+    T = rooms.look_pose([2.5, 1.5, 1.25], 0.0, 0.0)          # 1.5 m from the wall x = 4
+    d, _ = rooms.render(_ICP_ROOM, _ICP_K, T, noise_sigma=0.0)
+    P = T.copy()
+    P[:3, :3] = _rot_deg([0, 0, 1], 1.5) @ _rot_deg([0, 1, 0], -1.0) @ _rot_deg([1, 0, 0], 2.0) @ T[:3, :3]
+    P[:3, 3] += [0.04, 0.05, 0.03]
+    R, ok, frac = oracle.icp_refine(P, d, _ICP_K, _ICP_ROOM.lo, _ICP_ROOM.hi)
+    assert ok and frac == 1.0
+    assert abs(R[0, 3] - T[0, 3]) < 1e-6                      # distance to the wall
+    assert np.abs(R[:3, 2] - np.array([1.0, 0.0, 0.0])).max() < 1e-6   # view direction = wall normal
+    # offset along the wall kept: only a second-order coupling remains (the
+    # first steps move along the still-tilted normal: 4 cm x 2 deg ~ 1.4 mm),
+    # where a turn about any point but the camera centre would shift it by
+    # distance x angle (1.5 m x 2 deg ~ 5 cm)
+    assert np.abs(R[1:3, 3] - P[1:3, 3]).max() < 2e-3
+    roll = lambda M: math.degrees(math.atan2(M[2, 0], -M[1, 0]))       # turn about the normal
+    assert abs(roll(R) - roll(P)) < 0.02, (roll(R), roll(P))
+
+
+def test_icp_failure_cases():
+    T = _corner_view()
+    d, _ = rooms.render(_ICP_ROOM, _ICP_K, T, noise_sigma=0.0)
+    lo, hi = _ICP_ROOM.lo, _ICP_ROOM.hi
+    R, ok, frac = oracle.icp_refine(T, np.zeros_like(d), _ICP_K, lo, hi)       # no valid depth
+    assert not ok and frac == 0.0 and np.array_equal(R, T)
+    Tout = rooms.look_pose([-1.0, 1.5, 1.25], math.pi, 0.0)                     # outside, facing away
+    assert not oracle.icp_refine(Tout, d, _ICP_K, lo, hi)[1]
+    P = T.copy()
+    P[:3, 3] += T[:3, 2] * 0.3                                 # 30 cm along the view: no pair within 10 cm
+    R, ok, frac = oracle.icp_refine(P, d, _ICP_K, lo, hi)
+    assert not ok and frac == 0.0
+    # the inlier-fraction rule: half the image without a model counterpart
+    d2 = d.copy()
+    d2[(np.arange(d.shape[0]) // 4) % 2 == 0] += 0.5    # every other band of 4 rows
+    _, ok, frac = oracle.icp_refine(T, d2, _ICP_K, lo, hi, min_frac=0.6)
+    assert not ok and abs(frac - 0.5) < 0.01
+    _, ok, frac = oracle.icp_refine(T, d2, _ICP_K, lo, hi, min_frac=0.4)
+    assert ok and abs(frac - 0.5) < 0.01
+
+
 def _numpy_box_depth(P, K, lo, hi):
     """Vectorised slab test: z-depth of the exit point from inside the box,
     of the entry point from outside, NaN when the ray misses."""
@@ -587,6 +671,39 @@ def test_halving_and_chosen_set(small_run):
         np.testing.assert_allclose(r["chosen_score"], sc, rtol=1e-6)
         assert r["best"] == int(np.argmin(sc))
         assert np.array_equal(r["pose"], r["chosen_pose"][r["best"]])
+
+
+def test_icp_in_relocaliser_refines_and_discards(small_run):
+    """With ICP on, the chosen set is the one RANSAC gives without it; each
+    chosen pose is replaced by its ICP result iff ICP succeeds, a failed pose
+    is not ranked (score +inf), and the output is the argmin over the
+    rest.  Unranked, ICP refines the output pose alone."""
+    w, f, modes, runs = small_run
+    room = w.room()
+    for d, c, T, seed, lv, r in runs:
+        p = dict(w.ransac, icp=1)
+        ri = oracle.relocalise(p, d, c, w.K, lv, modes, room.lo, room.hi, seed, 1 << w.forest["depth"])
+        assert ri["n_chosen"] == r["n_chosen"]
+        assert np.array_equal(ri["chosen_slot"], r["chosen_slot"])
+        scores = []
+        for k, P0 in enumerate(r["chosen_pose"]):
+            Pk, ok, frac = oracle.icp_refine(P0, d, w.K, room.lo, room.hi)
+            assert bool(ri["icp_mask"] >> k & 1) == ok
+            assert ri["chosen_icp_frac"][k] == frac
+            assert np.array_equal(ri["chosen_pose"][k], Pk if ok else P0)
+            scores.append(oracle.depth_score(Pk, d, w.K, room.lo, room.hi)[0] if ok else np.inf)
+        assert np.array_equal(ri["chosen_score"], scores)
+        if np.isfinite(scores).any():
+            assert ri["best"] == int(np.argmin(scores))
+        assert np.array_equal(ri["pose"], ri["chosen_pose"][ri["best"]])
+        # unranked: the output pose alone
+        pu = dict(w.ransac, icp=1, rank=0)
+        r0 = oracle.relocalise(dict(pu, icp=0), d, c, w.K, lv, modes, room.lo, room.hi, seed,
+                               1 << w.forest["depth"])
+        ru = oracle.relocalise(pu, d, c, w.K, lv, modes, room.lo, room.hi, seed, 1 << w.forest["depth"])
+        Pk, ok, frac = oracle.icp_refine(r0["pose"], d, w.K, room.lo, room.hi)
+        assert ru["icp_mask"] == int(ok) and ru["chosen_icp_frac"][0] == frac
+        assert np.array_equal(ru["pose"], Pk if ok else r0["pose"])
 
 
 def test_cascade_fall_back_rule():
