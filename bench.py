@@ -294,7 +294,9 @@ def algorithmic_flops(kernel, work, p):
     squared norm 5, min 1) or 9 Euclidean.  LM: pass 1 as the energy per
     (H, pixel, mode) plus 18 per (H, pixel) transform and 190 per inlier
     (J rows 12, J^T J 126, J^T r 36, cost 6, residual 10); trial pass 34 per
-    inlier.  Raycast: 45 per ray."""
+    inlier.  Raycast: 45 per ray.  ICP: 100 per valid-pixel evaluation
+    (ray 16, slab test 15, gap and inlier test 8, residual and camera point
+    3, Jacobian 9, normal equations 27 FMAs = 54)."""
     per_mode = 18 if p["use_cov"] else 9
     if kernel == "energy":
         return 20 * work["energy_pairs"] + per_mode * work["energy_modes"]
@@ -303,6 +305,8 @@ def algorithmic_flops(kernel, work, p):
                 + 34 * work["lm_trial"])
     if kernel == "raycast_score":
         return 45 * work["rays"]
+    if kernel == "icp":
+        return 100 * work["icp_pixels"]
     return None
 
 
@@ -387,6 +391,65 @@ def kernel_rooflines(kernels, work, p, sm_count, pk):
         if o is not None:
             out[k] = {"achieved": o / s / 1e12, "unit": "Tops/s", "frac": o / s / 1e12 / (fp32_peak / 2)}
     return out
+
+
+def _success(P, T):
+    P = np.asarray(P).reshape(4, 4)
+    dt, dr = pose_err(P, T)
+    return dt <= 0.05 and dr <= 5.0
+
+
+def run_icp_variant(rg, forest, scene, w, D, C, B, qs, stream, seeds, args, sm_count, pk, tuning):
+    """The same workload with ICP before ranking (Sec. 3.2.4): throughput,
+    the ICP kernel's share and roofline, and the 5 cm / 5 deg success rate
+    with and without ICP on the same distinct queries and seeds."""
+    import torch
+    p = dict(w.ransac, **workloads.ICP_ON)
+    rel = rg.Relocaliser(forest, scene, p, w.width, w.height, B)
+    rel.set_tuning(tuning)
+    for k in range(2):
+        rel.relocalise_batch(D, C, w.K, seeds(600_000 + k), stream=stream, raw=True)
+    torch.cuda.synchronize()
+    steps = max(3, args.steps // 2)
+    rel.profile(True)
+    ms = []
+    for k in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rel.relocalise_batch(D, C, w.K, seeds(k), stream=stream, raw=True)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    kernels, work = rel.profile_read()
+    rel.profile(False)
+    # success with and without ICP over the distinct queries, same seeds
+    n = len(qs)
+    Dq = D[:n]
+    Cq = C[:n]
+    sd = [q[3] for q in qs]
+    with_icp = rel.relocalise_batch(Dq, Cq, w.K, sd, stream=stream)
+    rel0 = rg.Relocaliser(forest, scene, w.ransac, w.width, w.height, B)
+    without = rel0.relocalise_batch(Dq, Cq, w.K, sd, stream=stream)
+    rel0.close()
+    rel.close()
+    err = lambda rs: [pose_err(r["pose"], q[2]) for r, q in zip(rs, qs)]
+    e1, e0 = np.array(err(with_icp)), np.array(err(without))
+    kr = kernel_rooflines(kernels, work, p, sm_count, pk)
+    return {
+        "frames_per_s": B * steps / (sum(ms) / 1e3), "ms_per_step": float(np.mean(ms)),
+        "icp_ms_per_step": kernels["icp"]["ms"] / steps, "icp_roofline": kr.get("icp"),
+        "icp_pixel_evals_per_step": work["icp_pixels"] // steps,
+        "queries": n,
+        "success_5cm_5deg": {"icp": float(np.mean([_success(r["pose"], q[2]) for r, q in zip(with_icp, qs)])),
+                             "no_icp": float(np.mean([_success(r["pose"], q[2]) for r, q in zip(without, qs)]))},
+        "median_error": {"icp": [float(np.median(e1[:, 0])), float(np.median(e1[:, 1]))],
+                         "no_icp": [float(np.median(e0[:, 0])), float(np.median(e0[:, 1]))],
+                         "unit": ["m", "deg"]},
+        "icp_success_fraction": float(np.mean([bin(r["icp_mask"]).count("1") / max(1, r["n_chosen"])
+                                               for r in with_icp])),
+        "params": {k: (list(v) if isinstance(v, tuple) else v) for k, v in workloads.ICP_ON.items()},
+    }
 
 
 # --------------------------------------------------------------------------- ours
@@ -496,6 +559,8 @@ def run_ours(args):
         lat1.append(e0.elapsed_time(e1))
     lat1 = lat1[2:]
 
+    icp = run_icp_variant(rg, forest, scene, w, D, C, B, qs, stream, seeds, args, sm_count, pk, tuning)
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000 * total_s / args.steps, "higher_is_better": True,
@@ -520,6 +585,7 @@ def run_ours(args):
         "kernel_rooflines": kernel_rooflines(kernels, work, w.ransac, sm_count, pk),
         "work_per_step": {k: v // max(1, args.steps) for k, v in work.items()},
         "clocks": clk.summary(),
+        "icp_variant": icp,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.profile_only:
         import oracle

@@ -89,6 +89,30 @@ typedef struct {
     int32_t grid_origin;      /* first grid row/column (0) */
 } rl_forest_params;
 
+/* ICP refinement against the scene model before ranking (Sec. 3.2.4: the
+ * paper refines each chosen pose by ICP and drops it when ICP fails, with
+ * the ICP of its host reconstruction system).  Point-to-plane ICP with
+ * projective association: pixel u's live point under the current pose
+ * against the first model face hit by the same pixel ray; pairs farther
+ * apart than dist[l] are outliers.  Gauss-Newton on a camera-frame update
+ * H exp(xi), xi = (v, w), with a ridge lambda = ridge * trace(J^T J) / 6 on
+ * the normal equations, so that directions the visible faces leave
+ * unconstrained keep their value.  Level l uses the pixels whose column and
+ * row are multiples of stride[l], for iters[l] iterations.  ICP fails when
+ * an iteration has fewer than 6 inliers or a system that is not positive
+ * definite, or when the last iteration's inliers are fewer than
+ * min_frac x its valid pixels.  Sums are FP32 per thread, FP64 across
+ * threads; the solve and the pose are FP64. */
+typedef struct {
+    int32_t levels;           /* coarse-to-fine levels, 1..3 */
+    int32_t stride[3];        /* pixel stride of each level, 1..16 */
+    int32_t iters[3];         /* Gauss-Newton iterations of each level, 1..50 */
+    int32_t pad;
+    double dist[3];           /* inlier distance of each level, metres, > 0 */
+    double min_frac;          /* success threshold on the inlier fraction, 0..1 */
+    double ridge;             /* relative ridge, >= 0 */
+} rl_icp_params;
+
 /* Relocaliser parameters (Sec. 3.2.3-3.2.4; names follow the parameter
  * table of Appendix B). */
 typedef struct {
@@ -111,6 +135,10 @@ typedef struct {
     double lm_stop;           /* LM stops when |step| < lm_stop */
     int32_t rank;             /* score the chosen set by Eq. 6-8 */
     int32_t halve_to_one;     /* keep halving after the chosen set is taken */
+    int32_t icp;              /* 1: ICP before ranking (each chosen pose; the
+                                 output pose alone when rank == 0); needs a scene */
+    int32_t pad;
+    rl_icp_params icp_p;
 } rl_ransac_params;
 
 #define RL_MAX_CHOSEN 16
@@ -130,7 +158,11 @@ typedef struct {
     float chosen_score[RL_MAX_CHOSEN];
     int32_t chosen_slot[RL_MAX_CHOSEN];
     int32_t best;             /* index of xi* in chosen_pose */
-    int32_t pad;
+    int32_t icp_mask;         /* ICP on: bit c set iff ICP refined chosen pose c
+                                 (ranked) / the output pose (bit 0, unranked);
+                                 chosen_pose holds the refined poses, a failed
+                                 pose stays as RANSAC left it with score +inf */
+    float chosen_icp_frac[RL_MAX_CHOSEN]; /* last-iteration inlier fraction, -1 if ICP did not run */
 } rl_result;
 
 /* ---- context --------------------------------------------------------- */
@@ -213,6 +245,16 @@ rl_status rl_scene_destroy(rl_scene *s);
 rl_status rl_score_poses(rl_scene *s, const float *depth, const rl_intrinsics *K,
                          const double *poses, int32_t n, rl_mem mem, void *stream,
                          float *scores, float *valid_frac);
+
+/* ICP of n given camera->world poses (HOST [n][16] row-major) against one
+ * live depth frame and the box model, with the rl_icp_params rules above.
+ * refined: HOST [n][16], the refined pose, or the input pose where ICP
+ * failed; ok: HOST [n] 1/0; frac: HOST [n] last-iteration inlier fraction
+ * (may be NULL).  Scratch comes from the context arena (RL_ERR_OOM if it
+ * does not fit).  Synchronises `stream`. */
+rl_status rl_icp_poses(rl_scene *s, const float *depth, const rl_intrinsics *K,
+                       const double *poses, int32_t n, const rl_icp_params *p, rl_mem mem,
+                       void *stream, double *refined, int32_t *ok, float *frac);
 
 /* Same score as rl_score_poses, for callers that cannot allocate device
  * memory (a real-time loop whose memory is fixed at start-up, a host
@@ -328,11 +370,12 @@ rl_status rl_tuning_cache_write(const char *path, const char *key, const rl_tuni
  * [RL_N_WORK]: energy (H,px) pairs, energy (H,px,mode) triples, LM (H,px)
  * nearest-mode searches, LM (H,px,mode) triples, LM inlier accumulations,
  * LM trial evaluations, rays cast, generation attempts (stage 1: draws and
- * colour check), generation stage-2 evaluations (spread and rigidity)).
+ * colour check), generation stage-2 evaluations (spread and rigidity), ICP
+ * pixel evaluations (valid pixels visited, over all iterations)).
  * Enabling resets all counters.  The
  * paper has no counterpart; its Sec. A.1 timing breakdown is per stage. */
-#define RL_N_KERNELS 11
-#define RL_N_WORK 9
+#define RL_N_KERNELS 12
+#define RL_N_WORK 10
 rl_status rl_reloc_profile(rl_reloc *r, int32_t enable);
 rl_status rl_reloc_profile_read(rl_reloc *r, double *ms /* [RL_N_KERNELS] */,
                                 int64_t *launches /* [RL_N_KERNELS] */,

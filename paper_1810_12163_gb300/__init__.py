@@ -14,7 +14,7 @@ from . import binding, presets  # noqa: F401
 from .binding import RL_N_KERNELS as N_KERNELS
 from .binding import RL_N_WORK as N_WORK
 from .binding import (RL_DEVICE, RL_HOST, RL_NO_POSE, RL_POSE_FOUND,  # noqa: F401
-                      ForestParams, Intrinsics, RansacParams, RelocError, Result, call, lib)
+                      ForestParams, IcpParams, Intrinsics, RansacParams, RelocError, Result, call, lib)
 
 __all__ = ["Context", "Forest", "Scene", "Relocaliser", "Cascade", "intrinsics", "presets",
            "RelocError", "lib"]
@@ -45,6 +45,26 @@ def _struct(cls, d: dict):
     for k, v in d.items():
         if k in names:
             setattr(s, k, v)
+    return s
+
+
+def icp_struct(d: dict) -> IcpParams:
+    """rl_icp_params from icp_* keys (missing keys take presets.ICP_DEFAULT)."""
+    d = dict(presets.ICP_DEFAULT, **{k: v for k, v in d.items() if k.startswith("icp_")})
+    ip = IcpParams()
+    ip.levels = int(d["icp_levels"])
+    for l in range(3):
+        ip.stride[l] = int(d["icp_stride"][l]) if l < len(d["icp_stride"]) else 1
+        ip.iters[l] = int(d["icp_iters"][l]) if l < len(d["icp_iters"]) else 1
+        ip.dist[l] = float(d["icp_dist"][l]) if l < len(d["icp_dist"]) else 1.0
+    ip.min_frac = float(d["icp_min_frac"])
+    ip.ridge = float(d["icp_ridge"])
+    return ip
+
+
+def ransac_struct(d: dict) -> RansacParams:
+    s = _struct(RansacParams, {k: v for k, v in d.items() if not k.startswith("icp_")})
+    s.icp_p = icp_struct(d)
     return s
 
 
@@ -198,6 +218,24 @@ class Scene:
              scores.ctypes.data_as(ctypes.c_void_p), frac.ctypes.data_as(ctypes.c_void_p))
         return scores, frac
 
+    def icp_poses(self, depth, K, poses, stream=None, **icp):
+        """ICP (Sec. 3.2.4) of the given camera->world poses against `depth`
+        and the box: (refined [n][4][4], ok [n] bool, inlier fraction [n]).
+        Keyword arguments: icp_levels, icp_stride, icp_iters, icp_dist,
+        icp_min_frac, icp_ridge (defaults: presets.ICP_DEFAULT)."""
+        d = _Image(depth, np.float32)
+        P = np.ascontiguousarray(np.asarray(poses, np.float64).reshape(-1, 16))
+        n = P.shape[0]
+        out = np.zeros((n, 16), np.float64)
+        ok = np.zeros(n, np.int32)
+        frac = np.zeros(n, np.float32)
+        ip = icp_struct(icp)
+        call("rl_icp_poses", self.h, d.ptr, ctypes.byref(intrinsics(K)),
+             P.ctypes.data_as(ctypes.c_void_p), n, ctypes.byref(ip), d.mem, _stream_ptr(stream),
+             out.ctypes.data_as(ctypes.c_void_p), ok.ctypes.data_as(ctypes.c_void_p),
+             frac.ctypes.data_as(ctypes.c_void_p))
+        return out.reshape(n, 4, 4), ok.astype(bool), frac
+
     def close(self):
         if self.h:
             call("rl_scene_destroy", self.h)
@@ -212,7 +250,8 @@ def result_dict(r: Result) -> dict:
         n_pixels=r.n_pixels, status=r.status, best=r.best,
         chosen_pose=np.array([np.array(r.chosen_pose[i]).reshape(4, 4) for i in range(nc)]),
         chosen_energy=np.array(r.chosen_energy[:nc]), chosen_score=np.array(r.chosen_score[:nc]),
-        chosen_slot=np.array(r.chosen_slot[:nc]),
+        chosen_slot=np.array(r.chosen_slot[:nc]), icp_mask=r.icp_mask,
+        chosen_icp_frac=np.array(r.chosen_icp_frac[:max(nc, 1)]),
     )
 
 
@@ -224,7 +263,7 @@ class Relocaliser:
         self.max_batch = max_batch
         self.h = ctypes.c_void_p()
         call("rl_reloc_create", forest.h, scene.h if scene else None,
-             ctypes.byref(_struct(RansacParams, self.params)), max_w, max_h, max_batch,
+             ctypes.byref(ransac_struct(self.params)), max_w, max_h, max_batch,
              ctypes.byref(self.h))
 
     def relocalise_batch(self, depth, rgb, K, seeds, stream=None, raw=False):
@@ -285,7 +324,7 @@ class Relocaliser:
         names = [lib().rl_kernel_name(i).decode() for i in range(N_KERNELS)]
         kernels = {names[i]: dict(ms=float(ms[i]), launches=int(launches[i])) for i in range(N_KERNELS)}
         keys = ["energy_pairs", "energy_modes", "lm_pairs", "lm_modes", "lm_inliers", "lm_trial", "rays",
-                "hyp_attempts", "hyp_stage2"]
+                "hyp_attempts", "hyp_stage2", "icp_pixels"]
         return kernels, {k: int(v) for k, v in zip(keys, work)}
 
     def debug(self, q: int = 0):
@@ -354,7 +393,7 @@ class Server:
         mid = ctypes.c_int32()
         full = dict(presets.DEFAULT, **params)
         call("rl_server_add_model", self.h, forest.h, scene.h if scene else None,
-             ctypes.byref(_struct(RansacParams, full)), max_w, max_h, ctypes.byref(mid))
+             ctypes.byref(ransac_struct(full)), max_w, max_h, ctypes.byref(mid))
         return mid.value
 
     def add_cascade_model(self, forest: Forest, scene: Scene | None, levels: list, subsample,
@@ -363,7 +402,7 @@ class Server:
         parameter dicts, subsample[l] the level's input subsampling (last 1)."""
         mid = ctypes.c_int32()
         L = len(levels)
-        arr = (RansacParams * L)(*[_struct(RansacParams, dict(presets.DEFAULT, **p)) for p in levels])
+        arr = (RansacParams * L)(*[ransac_struct(dict(presets.DEFAULT, **p)) for p in levels])
         ss = np.ascontiguousarray(subsample, np.int32)
         th = np.ascontiguousarray(list(thresholds) + [0.0], np.float64)
         call("rl_server_add_cascade_model", self.h, forest.h, scene.h if scene else None,

@@ -34,8 +34,8 @@ STATUS_NAMES = {0: "RL_OK", 1: "RL_ERR_INVALID_ARG", 2: "RL_ERR_OOM", 3: "RL_ERR
 RL_HOST, RL_DEVICE = 0, 1
 RL_POSE_FOUND, RL_NO_POSE = 0, 1
 RL_MODES_FP32, RL_MODES_FP16_OFFSET = 0, 1
-RL_N_KERNELS = 11  # kernels the profiler reports (RL_N_KERNELS of the header)
-RL_N_WORK = 9      # work counters (RL_N_WORK of the header)
+RL_N_KERNELS = 12  # kernels the profiler reports (RL_N_KERNELS of the header)
+RL_N_WORK = 10     # work counters (RL_N_WORK of the header)
 
 
 class Intrinsics(ctypes.Structure):
@@ -53,6 +53,11 @@ class ForestParams(ctypes.Structure):
                 ("mode_precision", I32), ("grid_step", I32), ("grid_origin", I32)]
 
 
+class IcpParams(ctypes.Structure):
+    _fields_ = [("levels", I32), ("stride", I32 * 3), ("iters", I32 * 3), ("pad", I32),
+                ("dist", ctypes.c_double * 3), ("min_frac", ctypes.c_double), ("ridge", ctypes.c_double)]
+
+
 class RansacParams(ctypes.Structure):
     _fields_ = [("n_hyp", I32), ("max_iter", I32), ("n_cull", I32), ("eta", I32), ("k_out", I32),
                 ("pose_update", I32), ("use_cov", I32), ("colour_thresh", I32),
@@ -60,7 +65,8 @@ class RansacParams(ctypes.Structure):
                 ("k_top", I32), ("n_trees_used", I32), ("lm_max_iter", I32),
                 ("batch_attempts", I32), ("lm_lambda0", ctypes.c_double),
                 ("lm_inlier_thresh", ctypes.c_double), ("lm_stop", ctypes.c_double),
-                ("rank", I32), ("halve_to_one", I32)]
+                ("rank", I32), ("halve_to_one", I32), ("icp", I32), ("pad", I32),
+                ("icp_p", IcpParams)]
 
 
 class ServerParams(ctypes.Structure):
@@ -85,7 +91,7 @@ class Result(ctypes.Structure):
                 ("n_hypotheses", I32), ("n_chosen", I32), ("n_pixels", I32), ("status", I32),
                 ("chosen_pose", (ctypes.c_double * 16) * 16), ("chosen_energy", ctypes.c_float * 16),
                 ("chosen_score", ctypes.c_float * 16), ("chosen_slot", I32 * 16), ("best", I32),
-                ("pad", I32)]
+                ("icp_mask", I32), ("chosen_icp_frac", ctypes.c_float * 16)]
 
 
 _SIGS = {
@@ -106,6 +112,7 @@ _SIGS = {
     "rl_scene_destroy": [P],
     "rl_score_poses": [P, P, P, P, I32, I32, P, P, P],
     "rl_score_poses_noalloc": [P, P, P, P, P, I32, P, P, P],
+    "rl_icp_poses": [P, P, P, P, I32, P, I32, P, P, P, P],
     "rl_reloc_create": [P, P, P, I32, I32, I32, P],
     "rl_reloc_destroy": [P],
     "rl_relocalise": [P, P, P, P, U64, I32, P, P],

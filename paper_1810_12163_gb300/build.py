@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librelocgb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 EXACT = {"forest.cu", "rqs.cu", "hypgen.cu"}
-SOURCES = ["context.cu", "forest.cu", "rqs.cu", "hypgen.cu", "kabsch.cu", "score.cu", "lm.cu", "reloc.cu",
+SOURCES = ["context.cu", "forest.cu", "rqs.cu", "hypgen.cu", "kabsch.cu", "score.cu", "lm.cu", "icp.cu", "reloc.cu",
            "score_static.cu", "server.cu"]
 
 

@@ -119,6 +119,13 @@ struct ModeView {
 };
 
 // Relocaliser parameters as passed to kernels.
+// ICP settings of Sec. 3.2.4 (see rl_icp_params), as the kernels read them.
+struct IcpParams {
+    int levels, stride[3], iters[3];
+    float dist[3];
+    double min_frac, ridge;
+};
+
 struct RParams {
     int n_hyp, max_iter, n_cull, eta, k_out, pose_update, use_cov, colour_thresh;
     double min_sq_dist, max_trans_err;
@@ -130,6 +137,8 @@ struct RParams {
     int max_pix;      // eta * (max_rounds + 1)
     int maxm;         // bound on |M(u)|: trees x min(k_top, m_max)
     int mpad;         // maxm rounded up to an odd count (mode-table row stride)
+    int icp;          // ICP before ranking (or of the output pose when unranked)
+    IcpParams icp_p;
 };
 
 // Per-frame description used by batched kernels.
@@ -177,6 +186,8 @@ struct QueryState {
     double *score_part;      // [B][16][n_score_tiles][2] sum, counts
     int32_t *score_cnt;      // [B][16][n_score_tiles][2]
     float *chosen_score;     // [B][16]
+    int32_t *icp_ok;         // [B][16] ICP succeeded (ranked: chosen pose c; unranked: slot 0)
+    float *icp_frac;         // [B][16] last-iteration inlier fraction, -1 if ICP did not run
     int32_t *round_count;    // [B][16]
     int32_t *round_slot;     // [B][16][n_cull]
     float *round_energy;     // [B][16][n_cull]
@@ -190,21 +201,22 @@ struct QueryState {
 struct DevResult {
     double pose[12];
     float energy, energy_per_pixel, score;
-    int32_t n_hypotheses, n_chosen, n_pixels, status, best, err;
+    int32_t n_hypotheses, n_chosen, n_pixels, status, best, err, icp_mask, pad;
 };
 
 // Per-kernel timing with CUDA events recorded on the launching stream, plus
 // device-side work counters of the scoring kernels (off unless enabled).
 enum KernelId {
     K_LEAVES = 0, K_HYPGEN, K_COMPACT, K_SAMPLE, K_ENERGY, K_SELECT, K_LM, K_RAYCAST, K_FINALIZE,
-    K_HYPPOSE, K_CMASK, K_COUNT
+    K_HYPPOSE, K_CMASK, K_ICP, K_COUNT
 };
 // work counters: energy (H,px) pairs, energy (H,px,mode) triples, LM pass-1
 // (H,px) evaluations, LM (H,px,mode) triples, LM inlier accumulations, LM
-// pass-2 evaluations, raycast rays
+// pass-2 evaluations, raycast rays, generation attempts and stage-2
+// evaluations, ICP valid-pixel evaluations
 enum WorkId {
     W_E_PAIRS = 0, W_E_MODES, W_LM_PAIRS, W_LM_MODES, W_LM_INLIERS, W_LM_TRIAL, W_RAYS, W_HYP_ATTEMPTS,
-    W_HYP_STAGE2, W_COUNT
+    W_HYP_STAGE2, W_ICP_PIX, W_COUNT
 };
 
 struct Profiler {
@@ -257,6 +269,7 @@ struct CascadeOut {
     double *chosen_pose;     // [B][16][12]
     float *chosen_energy;    // [B][16]
     float *chosen_score;     // [B][16]
+    float *icp_frac;         // [B][16] ICP inlier fractions of the level that produced the result
     int32_t *chosen_slot;    // [B][16]
     int32_t *level;          // [B]
     int32_t *done;           // [B] accepted by some level

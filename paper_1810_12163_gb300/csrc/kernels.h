@@ -89,6 +89,24 @@ struct RaycastArgs {
     }
 };
 
+// ICP of Sec. 3.2.4 (one thread block per pose): pose c of frame b is
+// poses[(b * pose_stride + c) * 12], refined in place when ICP succeeds.
+struct IcpArgs {
+    const Frame *frames;
+    double *poses;             // [B][pose_stride][12]
+    int pose_stride;
+    const int32_t *counts;     // poses per frame, or null: `cap` for every frame
+    const int32_t *gate;       // frames with gate[b] <= 0 are skipped, or null
+    int cap;                   // poses per frame when counts is null / grid width
+    int32_t *ok;               // [B][out_stride]
+    float *frac;               // [B][out_stride]
+    int out_stride;
+    float lo[3], hi[3];
+    IcpParams ip;
+    unsigned long long *work;  // profiling counters or null
+};
+rl_status launch_icp(const IcpArgs &a, int n, cudaStream_t s);
+
 size_t energy_smem(int chunk, int maxm);
 rl_status launch_energy(const EnergyArgs &a, int max_count, int n, cudaStream_t s, int max_threads = 128);
 rl_status launch_select(const SelectArgs &a, int n, cudaStream_t s);

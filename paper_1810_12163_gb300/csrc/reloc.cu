@@ -33,7 +33,34 @@ static rl_status check_ransac(const rl_ransac_params *p, const rl_forest *f) {
     if (p->batch_attempts < 1) return fail(RL_ERR_INVALID_ARG, "batch_attempts must be >= 1");
     if (p->lm_max_iter < 0) return fail(RL_ERR_INVALID_ARG, "lm_max_iter must be >= 0");
     if (p->colour_thresh < 0) return fail(RL_ERR_INVALID_ARG, "colour_thresh must be >= 0");
+    if (p->icp != 0 && p->icp != 1) return fail(RL_ERR_INVALID_ARG, "icp must be 0 or 1");
     return RL_OK;
+}
+
+static rl_status check_icp(const rl_icp_params *ip) {
+    if (!ip) return fail(RL_ERR_INVALID_ARG, "null ICP params");
+    if (ip->levels < 1 || ip->levels > 3) return fail(RL_ERR_INVALID_ARG, "icp levels must be 1..3");
+    for (int l = 0; l < ip->levels; ++l) {
+        if (ip->stride[l] < 1 || ip->stride[l] > 16) return fail(RL_ERR_INVALID_ARG, "icp stride must be 1..16");
+        if (ip->iters[l] < 1 || ip->iters[l] > 50) return fail(RL_ERR_INVALID_ARG, "icp iters must be 1..50");
+        if (!(ip->dist[l] > 0.0) || !(ip->dist[l] < 1e6)) return fail(RL_ERR_INVALID_ARG, "icp dist must be > 0");
+    }
+    if (!(ip->min_frac >= 0.0 && ip->min_frac <= 1.0)) return fail(RL_ERR_INVALID_ARG, "icp min_frac must be 0..1");
+    if (!(ip->ridge >= 0.0 && ip->ridge < 1e6)) return fail(RL_ERR_INVALID_ARG, "icp ridge must be >= 0");
+    return RL_OK;
+}
+
+static IcpParams icp_device_params(const rl_icp_params &ip) {
+    IcpParams d{};
+    d.levels = ip.levels;
+    for (int l = 0; l < 3; ++l) {
+        d.stride[l] = ip.stride[l];
+        d.iters[l] = ip.iters[l];
+        d.dist[l] = (float)ip.dist[l];
+    }
+    d.min_frac = ip.min_frac;
+    d.ridge = ip.ridge;
+    return d;
 }
 
 template <class T>
@@ -215,6 +242,27 @@ rl_status run_relocalise(rl_reloc *r, int n, int level, cudaStream_t s) {
         { PROF(K_SELECT); RL_TRY(launch_select(sa, n, s)); }
     }
     const int ranked = p.rank && r->scene != nullptr;
+    if (p.icp && r->scene) {
+        // ICP before ranking: each chosen pose, or the output pose when unranked
+        IcpArgs ia{};
+        ia.frames = q.frames;
+        ia.poses = ranked ? q.chosen_pose : q.cur_pose;
+        ia.pose_stride = ranked ? 16 : NC;
+        ia.counts = ranked ? q.n_chosen : nullptr;
+        ia.gate = q.n_hyp;
+        ia.cap = ranked ? p.k_out : 1;
+        ia.ok = q.icp_ok;
+        ia.frac = q.icp_frac;
+        ia.out_stride = 16;
+        for (int a = 0; a < 3; ++a) {
+            ia.lo[a] = (float)r->scene->lo[a];
+            ia.hi[a] = (float)r->scene->hi[a];
+        }
+        ia.ip = p.icp_p;
+        ia.work = work;
+        PROF(K_ICP);
+        RL_TRY(launch_icp(ia, n, s));
+    }
     if (ranked) {
         RaycastArgs ra{};
         ra.frames = q.frames;
@@ -288,12 +336,25 @@ rl_status launch_relocalise(rl_reloc *r, int n, int level, cudaStream_t s) {
     return RL_OK;
 }
 
+// ICP outputs of one result: the mask, and each ICP run's inlier fraction
+// (-1 where ICP did not run).
+static void fill_icp(rl_result &o, const DevResult &d, const rl_reloc *r, const float *frac16) {
+    o.icp_mask = d.icp_mask;
+    for (int c = 0; c < RL_MAX_CHOSEN; ++c) o.chosen_icp_frac[c] = -1.f;
+    if (!frac16 || !r->rp.icp || d.n_hypotheses <= 0) return;
+    const int ranked = r->rp.rank && r->scene != nullptr;
+    const int n_icp = ranked ? std::max(0, d.n_chosen) : 1;
+    for (int c = 0; c < n_icp && c < RL_MAX_CHOSEN; ++c) o.chosen_icp_frac[c] = frac16[c];
+}
+
 static rl_status fetch_results(rl_reloc *r, int n, cudaStream_t s, rl_result *out, int level) {
     QueryState &q = r->q;
     std::vector<double> cp((size_t)n * 16 * 12);
     std::vector<float> ce((size_t)n * 16), cs((size_t)n * 16);
     std::vector<int32_t> cslot((size_t)n * 16);
+    std::vector<float> icpf(r->rp.icp ? (size_t)n * 16 : 0);
     RL_CK(cudaMemcpyAsync(r->host_results, q.result_blob, sizeof(DevResult) * n, cudaMemcpyDeviceToHost, s));
+    if (r->rp.icp) RL_CK(cudaMemcpyAsync(icpf.data(), q.icp_frac, icpf.size() * 4, cudaMemcpyDeviceToHost, s));
     RL_CK(cudaMemcpyAsync(cp.data(), q.chosen_pose, cp.size() * 8, cudaMemcpyDeviceToHost, s));
     RL_CK(cudaMemcpyAsync(ce.data(), q.chosen_energy, ce.size() * 4, cudaMemcpyDeviceToHost, s));
     RL_CK(cudaMemcpyAsync(cs.data(), q.chosen_score, cs.size() * 4, cudaMemcpyDeviceToHost, s));
@@ -315,6 +376,7 @@ static rl_status fetch_results(rl_reloc *r, int n, cudaStream_t s, rl_result *ou
         o.n_pixels = d.n_pixels;
         o.status = d.status;
         o.best = d.best;
+        fill_icp(o, d, r, icpf.empty() ? nullptr : &icpf[(size_t)i * 16]);
         for (int c = 0; c < o.n_chosen && c < RL_MAX_CHOSEN; ++c) {
             for (int k = 0; k < 12; ++k) o.chosen_pose[c][k] = cp[((size_t)i * 16 + c) * 12 + k];
             o.chosen_pose[c][15] = 1.0;
@@ -385,6 +447,8 @@ extern "C" rl_status rl_reloc_create(rl_forest *f, rl_scene *scene, const rl_ran
         return fail(RL_ERR_INVALID_ARG, "bad maximum frame size");
     if (max_batch < 1 || max_batch > 65535) return fail(RL_ERR_INVALID_ARG, "max_batch must be 1..65535");
     if (p->rank && !scene) return fail(RL_ERR_INVALID_ARG, "ranking needs a scene model");
+    if (p->icp && !scene) return fail(RL_ERR_INVALID_ARG, "ICP needs a scene model");
+    if (p->icp) RL_TRY(check_icp(&p->icp_p));
     RL_CK(cudaSetDevice(f->ctx->device));
     RL_TRY(prepare_kernels());
     rl_reloc *r = new rl_reloc();
@@ -402,6 +466,8 @@ extern "C" rl_status rl_reloc_create(rl_forest *f, rl_scene *scene, const rl_ran
     rp.lm_max_iter = p->lm_max_iter; rp.batch_attempts = p->batch_attempts;
     rp.lm_lambda0 = p->lm_lambda0; rp.lm_inlier_thresh = p->lm_inlier_thresh; rp.lm_stop = p->lm_stop;
     rp.rank = p->rank; rp.halve_to_one = p->halve_to_one; rp.level = 0;
+    rp.icp = p->icp;
+    if (p->icp) rp.icp_p = icp_device_params(p->icp_p);
     rp.max_rounds = rounds_for(p->n_cull, p->k_out, p->halve_to_one);
     // rows of whole 16-pixel tiles: the LM kernel stages tiles with bulk copies
     rp.max_pix = (p->eta * (rp.max_rounds + 1) + 15) / 16 * 16;
@@ -447,6 +513,8 @@ extern "C" rl_status rl_reloc_create(rl_forest *f, rl_scene *scene, const rl_ran
     A(score_part, B * 16 * (uint64_t)r->n_score_tiles);
     A(score_cnt, B * 16 * 2 * (uint64_t)r->n_score_tiles);
     A(chosen_score, B * 16);
+    A(icp_ok, B * 16);
+    A(icp_frac, B * 16);
     A(round_count, B * 16);
     A(round_slot, B * 16 * NC);
     A(round_energy, B * 16 * NC);
@@ -602,6 +670,7 @@ __global__ void k_cascade_decide(QueryState lq, CascadeOut co, LaterFrames later
         co.chosen_score[(size_t)b * 16 + c] = lq.chosen_score[(size_t)b * 16 + c];
         co.chosen_slot[(size_t)b * 16 + c] = lq.chosen_slot[(size_t)b * 16 + c];
     }
+    for (int c = 0; c < 16; ++c) co.icp_frac[(size_t)b * 16 + c] = lq.icp_frac[(size_t)b * 16 + c];
     // fall back iff the output pose's score exceeds tau (Sec. 3.2.5)
     const bool accept = last || (r.status == RL_POSE_FOUND && r.score <= tau);
     if (!accept) return;
@@ -672,7 +741,9 @@ static rl_status cascade_fetch(rl_cascade *c, int n, cudaStream_t s, rl_result *
     std::vector<double> cp((size_t)n * 16 * 12);
     std::vector<float> ce((size_t)n * 16), cs((size_t)n * 16);
     std::vector<int32_t> cslot((size_t)n * 16), lvl(n);
+    std::vector<float> icpf((size_t)n * 16);
     RL_CK(cudaMemcpyAsync(res.data(), c->out.res, sizeof(DevResult) * n, cudaMemcpyDeviceToHost, s));
+    RL_CK(cudaMemcpyAsync(icpf.data(), c->out.icp_frac, icpf.size() * 4, cudaMemcpyDeviceToHost, s));
     RL_CK(cudaMemcpyAsync(cp.data(), c->out.chosen_pose, cp.size() * 8, cudaMemcpyDeviceToHost, s));
     RL_CK(cudaMemcpyAsync(ce.data(), c->out.chosen_energy, ce.size() * 4, cudaMemcpyDeviceToHost, s));
     RL_CK(cudaMemcpyAsync(cs.data(), c->out.chosen_score, cs.size() * 4, cudaMemcpyDeviceToHost, s));
@@ -696,6 +767,7 @@ static rl_status cascade_fetch(rl_cascade *c, int n, cudaStream_t s, rl_result *
         o.n_pixels = d.n_pixels;
         o.status = d.status;
         o.best = d.best;
+        fill_icp(o, d, c->levels[lvl[i]], &icpf[(size_t)i * 16]);
         for (int k = 0; k < o.n_chosen && k < RL_MAX_CHOSEN; ++k) {
             for (int j = 0; j < 12; ++j) o.chosen_pose[k][j] = cp[((size_t)i * 16 + k) * 12 + j];
             o.chosen_pose[k][15] = 1.0;
@@ -756,6 +828,7 @@ extern "C" rl_status rl_cascade_create(rl_reloc *const *levels, const double *th
     A(&c->out.chosen_pose, B * 16 * 12);
     A(&c->out.chosen_energy, B * 16);
     A(&c->out.chosen_score, B * 16);
+    A(&c->out.icp_frac, B * 16);
     A(&c->out.chosen_slot, B * 16);
     A(&c->out.level, B);
     A(&c->out.done, B);
@@ -863,7 +936,7 @@ static void prof_free(rl_reloc *r) {
 
 static const char *kKernelNames[K_COUNT] = {"leaves",  "hypgen", "compact", "sample_batch", "energy",
                                              "select", "lm",     "raycast_score", "finalize", "hyppose",
-                                             "colour_mask"};
+                                             "colour_mask", "icp"};
 static_assert(K_COUNT == RL_N_KERNELS, "kernel ids and the public count differ");
 
 extern "C" const char *rl_kernel_name(int32_t kid) {
@@ -978,6 +1051,80 @@ extern "C" rl_status rl_score_poses(rl_scene *sc, const float *depth, const rl_i
             if (valid_frac) valid_frac[i] = hs[n + i];
         }
     void *ptrs[] = {fr, pd, psum, pcnt, sd, dd};
+    for (void *p : ptrs) arena_free(ctx, p);
+    return st;
+}
+
+// ---------------------------------------------------------------------------
+// Standalone ICP (Sec. 3.2.4) of given poses against the box model.
+// ---------------------------------------------------------------------------
+extern "C" rl_status rl_icp_poses(rl_scene *sc, const float *depth, const rl_intrinsics *K,
+                                  const double *poses, int32_t n, const rl_icp_params *ip, rl_mem mem,
+                                  void *stream, double *refined, int32_t *ok, float *frac) {
+    if (!sc || !depth || !K || !poses || !ip || !refined || !ok) return fail(RL_ERR_INVALID_ARG, "null argument");
+    if (n < 1 || n > 65535) return fail(RL_ERR_INVALID_ARG, "n must be 1..65535");
+    if (K->width < 1 || K->height < 1 || K->width > 8192 || K->height > 8192 || !(K->fx > 0) || !(K->fy > 0))
+        return fail(RL_ERR_INVALID_ARG, "bad intrinsics");
+    if (mem != RL_HOST && mem != RL_DEVICE) return fail(RL_ERR_INVALID_ARG, "bad rl_mem");
+    RL_TRY(check_icp(ip));
+    rl_ctx *ctx = sc->ctx;
+    RL_CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int npx = K->width * K->height;
+    Frame *fr = nullptr;
+    double *pd = nullptr;
+    int32_t *okd = nullptr;
+    float *fd = nullptr, *dd = nullptr;
+    rl_status st = alloc_n(ctx, 1, &fr);
+    if (st == RL_OK) st = alloc_n(ctx, (uint64_t)n * 12, &pd);
+    if (st == RL_OK) st = alloc_n(ctx, (uint64_t)n, &okd);
+    if (st == RL_OK) st = alloc_n(ctx, (uint64_t)n, &fd);
+    if (st == RL_OK && mem == RL_HOST) st = alloc_n(ctx, (uint64_t)npx, &dd);
+    std::vector<double> p12((size_t)n * 12);
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < 12; ++k) p12[(size_t)i * 12 + k] = poses[(size_t)i * 16 + k];
+    Frame h{};
+    h.depth = mem == RL_HOST ? dd : depth;
+    h.rgb = nullptr;
+    h.fx = K->fx; h.fy = K->fy; h.cx = K->cx; h.cy = K->cy;
+    h.W = K->width; h.H = K->height;
+    std::vector<int32_t> hok(n);
+    std::vector<float> hfrac(n);
+    if (st == RL_OK && mem == RL_HOST &&
+        cudaMemcpyAsync(dd, depth, sizeof(float) * npx, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        st = fail(RL_ERR_CUDA, "depth copy failed");
+    if (st == RL_OK && cudaMemcpyAsync(fr, &h, sizeof(Frame), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        st = fail(RL_ERR_CUDA, "frame copy failed");
+    if (st == RL_OK && cudaMemcpyAsync(pd, p12.data(), p12.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        st = fail(RL_ERR_CUDA, "pose copy failed");
+    if (st == RL_OK) {
+        IcpArgs ia{};
+        ia.frames = fr;
+        ia.poses = pd;
+        ia.pose_stride = n;
+        ia.cap = n;
+        ia.ok = okd;
+        ia.frac = fd;
+        ia.out_stride = n;
+        for (int a = 0; a < 3; ++a) {
+            ia.lo[a] = (float)sc->lo[a];
+            ia.hi[a] = (float)sc->hi[a];
+        }
+        ia.ip = icp_device_params(*ip);
+        st = launch_icp(ia, 1, s);
+    }
+    if (st == RL_OK && (cudaMemcpyAsync(p12.data(), pd, p12.size() * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                        cudaMemcpyAsync(hok.data(), okd, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                        cudaMemcpyAsync(hfrac.data(), fd, sizeof(float) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess))
+        st = fail(RL_ERR_CUDA, "result copy failed");
+    if (st == RL_OK && cudaStreamSynchronize(s) != cudaSuccess) st = fail(RL_ERR_CUDA, "ICP failed");
+    if (st == RL_OK)
+        for (int i = 0; i < n; ++i) {
+            for (int k = 0; k < 16; ++k) refined[(size_t)i * 16 + k] = k < 12 ? p12[(size_t)i * 12 + k] : (k == 15 ? 1.0 : 0.0);
+            ok[i] = hok[i];
+            if (frac) frac[i] = hfrac[i];
+        }
+    void *ptrs[] = {fr, pd, okd, fd, dd};
     for (void *p : ptrs) arena_free(ctx, p);
     return st;
 }

@@ -1094,8 +1094,10 @@ __global__ void __launch_bounds__(256) k_finalize(QueryState q, RParams p, int n
                     tb += s_both[k];
                 }
                 const double frac = (double)tsyn / npx;
+                // a pose whose ICP failed is discarded (Sec. 3.2.4)
+                const bool kept = !p.icp || q.icp_ok[(size_t)b * 16 + c];
                 q.chosen_score[(size_t)b * 16 + c] =
-                    (frac >= 0.1 && tb > 0) ? (float)(ts / (double)tb) : INFINITY;
+                    (kept && frac >= 0.1 && tb > 0) ? (float)(ts / (double)tb) : INFINITY;
             }
             __syncthreads();
         }
@@ -1108,6 +1110,12 @@ __global__ void __launch_bounds__(256) k_finalize(QueryState q, RParams p, int n
     out->n_pixels = q.n_pix[b];
     out->score = INFINITY;
     out->best = -1;
+    out->icp_mask = 0;
+    if (p.icp && q.n_hyp[b] > 0) {
+        const int n_icp = ranked ? q.n_chosen[b] : 1;
+        for (int c = 0; c < n_icp; ++c)
+            if (q.icp_ok[(size_t)b * 16 + c]) out->icp_mask |= 1 << c;
+    }
     if (q.n_hyp[b] == 0) {
         out->status = RL_NO_POSE;
         for (int k = 0; k < 12; ++k) out->pose[k] = (k % 5 == 0) ? 1.0 : 0.0;

@@ -14,8 +14,15 @@ FOREST_DEFAULT = dict(
 # clustererTau 0.2, minClusterSize 5, reservoirCapacity 2048 for the cascade relocalisers
 FOREST_CASCADE = dict(FOREST_DEFAULT, kappa=2048, min_cluster_size=5, tau_c=0.2)
 
+# ICP before ranking (Sec. 3.2.4; this library's reading of an ICP the paper
+# leaves to its host system): off by default; strides, iterations and inlier
+# distances per coarse-to-fine level, success threshold, relative ridge.
+ICP_DEFAULT = dict(icp=0, icp_levels=3, icp_stride=(4, 2, 1), icp_iters=(6, 3, 2),
+                   icp_dist=(0.1, 0.05, 0.025), icp_min_frac=0.5, icp_ridge=1e-4)
+
 _COMMON = dict(colour_thresh=30, k_top=10, n_trees_used=5, lm_max_iter=10, batch_attempts=32,
-               lm_lambda0=1e-3, lm_inlier_thresh=0.1, lm_stop=1e-6, rank=1, halve_to_one=0)
+               lm_lambda0=1e-3, lm_inlier_thresh=0.1, lm_stop=1e-6, rank=1, halve_to_one=0,
+               **ICP_DEFAULT)
 
 DEFAULT = dict(_COMMON, n_hyp=1024, max_iter=6000, n_cull=64, max_trans_err=0.05,
                min_sq_dist=0.09, pose_update=1, eta=512, use_cov=1, k_out=16)

@@ -21,6 +21,9 @@ RANSAC_DEFAULT = dict(
     lm_max_iter=10, batch_attempts=32, lm_lambda0=1e-3, lm_inlier_thresh=0.1, lm_stop=1e-6,
     rank=1, halve_to_one=0,
 )
+# ICP before ranking (Sec. 3.2.4, the library's reading R21), switched on.
+ICP_ON = dict(icp=1, icp_levels=3, icp_stride=(4, 2, 1), icp_iters=(6, 3, 2),
+              icp_dist=(0.1, 0.05, 0.025), icp_min_frac=0.5, icp_ridge=1e-4)
 FOREST_DEFAULT = dict(
     n_trees=5, depth=15, p_depth=0.4, delta_lo=-130.0, delta_hi=130.0, tau_depth_lo=-0.2,
     tau_depth_hi=0.2, tau_rgb_lo=-50.0, tau_rgb_hi=50.0, tau_zero=0, kappa=1024, m_max=50,

@@ -179,6 +179,8 @@ def compare_results(rg, gr, dbg, orr, params, what):
         off += k
     # ranking scores of the chosen set, then the output pose
     assert gr["n_chosen"] == orr["n_chosen"]
+    if params.get("icp") and not check_icp(gr, orr, params, what):
+        return
     if params["rank"]:
         tol = score_tolerances(gr["chosen_pose"], orr["chosen_pose"], orr["chosen_score"])
         check_scores(gr["chosen_score"], orr["chosen_score"], tol, what)
@@ -190,6 +192,46 @@ def compare_results(rg, gr, dbg, orr, params, what):
     dt, dr = pose_err(gr["pose"], orr["pose"])
     np.testing.assert_allclose(gr["energy"], orr["energy"], rtol=ENERGY_RTOL)
     check_refined_pose(dt, dr, gr["energy"], orr["energy"], f"{what} output")
+
+
+ICP_FRAC_TOL = 1e-3   # inlier fractions: a few pixels at the inlier radius flip in FP32
+
+
+def oracle_icp_kwargs(p: dict) -> dict:
+    """oracle.icp_refine keywords from icp_* parameters."""
+    d = dict(oracle.PARAM_DEFAULTS, **p)
+    return dict(levels=d["icp_levels"], stride=d["icp_stride"], iters=d["icp_iters"],
+                dist=d["icp_dist"], min_frac=d["icp_min_frac"], ridge=d["icp_ridge"])
+
+
+def check_icp_one(ok_g, frac_g, P_g, ok_o, frac_o, P_o, min_frac, what):
+    """One ICP run, GPU vs oracle: inlier fractions within ICP_FRAC_TOL; the
+    success decision equal unless the oracle's fraction lies within that
+    tolerance of the threshold; refined poses within 1 mm / 0.05 deg.
+    Returns True when both sides took the same decision."""
+    assert abs(frac_g - frac_o) <= ICP_FRAC_TOL, (what, frac_g, frac_o)
+    if ok_g != ok_o:
+        assert abs(frac_o - min_frac) <= ICP_FRAC_TOL, (what, ok_g, ok_o, frac_o)
+        return False
+    dt, dr = pose_err(P_g, P_o)
+    assert dt <= POSE_T_TOL and dr <= POSE_R_TOL, (what, dt, dr)
+    return True
+
+
+def check_icp(gr, orr, params, what):
+    """ICP outputs of a relocalisation (ranked: every chosen pose;
+    unranked: the output pose).  False when a success decision differs at
+    the threshold (what follows from it then differs legitimately)."""
+    mf = dict(oracle.PARAM_DEFAULTS, **params)["icp_min_frac"]
+    if params["rank"]:
+        same = True
+        for c in range(gr["n_chosen"]):
+            same &= check_icp_one(bool(gr["icp_mask"] >> c & 1), gr["chosen_icp_frac"][c], gr["chosen_pose"][c],
+                                  bool(orr["icp_mask"] >> c & 1), orr["chosen_icp_frac"][c], orr["chosen_pose"][c],
+                                  mf, f"{what} chosen {c}")
+        return same
+    return check_icp_one(bool(gr["icp_mask"] & 1), gr["chosen_icp_frac"][0], gr["pose"],
+                         bool(orr["icp_mask"] & 1), orr["chosen_icp_frac"][0], orr["pose"], mf, f"{what} output")
 
 
 def oracle_modes_from_export(ex, m_max):

@@ -55,3 +55,34 @@ def test_error_path_without_gpu():
     assert b"null" in L.rl_last_error()
     assert L.rl_forest_destroy(None) == 1
     assert L.rl_reloc_destroy(None) == 1
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of the public structs have the C compiler's sizes
+    and field offsets (gcc on the header itself)."""
+    import ctypes
+    import subprocess
+
+    from paper_1810_12163_gb300 import binding as B
+    structs = {"rl_intrinsics": B.Intrinsics, "rl_forest_params": B.ForestParams,
+               "rl_icp_params": B.IcpParams, "rl_ransac_params": B.RansacParams,
+               "rl_result": B.Result, "rl_tuning": B.Tuning, "rl_server_params": B.ServerParams,
+               "rl_server_stats": B.ServerStats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "relocgb.h"', 'int main(void) {']
+    for cname, cls in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in cls._fields_:
+            lines.append(f'printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        name, field, v = ln.split()
+        got[(name, field)] = int(v)
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for f in cls._fields_:
+            assert got[(cname, f[0])] == getattr(cls, f[0]).offset, (cname, f[0])

@@ -1,0 +1,179 @@
+"""ICP before ranking (Sec. 3.2.4, reading R21): the CUDA kernel against the
+FP64 oracle, through the C ABI.
+
+Standalone ICP of given poses: inlier fractions within 1e-3, success
+decisions equal (they may differ only where the oracle's fraction is within
+1e-3 of the threshold), refined poses within 1 mm / 0.05 deg.  Inside the
+relocaliser: each chosen pose refined or discarded as the oracle does, then
+ranking on the refined poses with the usual bars; results unchanged by
+batching."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import rooms, workloads
+from tests import helpers as H
+from tests.test_gpu_parity import _compare_query
+
+pytestmark = pytest.mark.gpu
+ICP = workloads.ICP_ON
+W2 = workloads.CONFIG2
+
+
+@pytest.fixture(scope="module")
+def rg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1810_12163_gb300 as rg
+    rg.lib()
+    return rg
+
+
+@pytest.fixture(scope="module")
+def ctx(rg):
+    return rg.Context(0, arena_bytes=16 << 30)
+
+
+def _perturb(T, dt, dr, rng):
+    P = T.copy()
+    P[:3, :3] = rooms._rodrigues(rng.normal(size=3), math.radians(dr)) @ T[:3, :3]
+    v = rng.normal(size=3)
+    P[:3, 3] += v / np.linalg.norm(v) * dt
+    return P
+
+
+def _check_poses(rg, scene, d, K, room, poses, what, icp=ICP):
+    out, ok, frac = scene.icp_poses(d, K, np.stack(poses), **icp)
+    kw = H.oracle_icp_kwargs(icp)
+    for i, P in enumerate(poses):
+        Po, oko, fo = oracle.icp_refine(P, d, K, room.lo, room.hi, **kw)
+        # the oracle hands back where a failed run stopped; the library
+        # returns a failed pose unchanged
+        H.check_icp_one(bool(ok[i]), float(frac[i]), out[i], oko, fo, Po if oko else P, kw["min_frac"],
+                        f"{what} pose {i}")
+        if not ok[i]:
+            assert np.array_equal(out[i], P)      # a failed pose comes back unchanged
+    return out, ok, frac
+
+
+def test_icp_poses_config2_queries(rg, ctx):
+    """640x480 noisy queries: the true pose and starts 3 cm / 2 deg, 8 cm /
+    5 deg and 30 cm / 20 deg away."""
+    room = W2.room()
+    scene = rg.Scene(ctx, room.lo, room.hi)
+    rng = np.random.default_rng(3)
+    for q in range(6):
+        d, c, T, seed = W2.query(q)
+        poses = [T] + [_perturb(T, dt, dr, rng) for dt, dr in ((0.03, 2.0), (0.08, 5.0), (0.3, 20.0))]
+        _check_poses(rg, scene, d, W2.K, room, poses, f"query {q}")
+    scene.close()
+
+
+def test_icp_poses_noise_free_views(rg, ctx):
+    """The oracle pins' views: the corner view converges to the true pose on
+    the GPU too (FP32 sums: within 1e-5 m / 1e-3 deg); a wall seen alone."""
+    K = rooms.Intrinsics(292.5, 292.5, 160.0, 120.0, 320, 240)
+    room = rooms.Room((4.0, 3.0, 2.5), 5)
+    scene = rg.Scene(ctx, room.lo, room.hi)
+    pos = np.array([1.0, 0.8, 1.6])
+    tgt = np.array([4.0, 3.0, 0.0]) - pos
+    T = rooms.look_pose(pos, math.atan2(tgt[1], tgt[0]), math.atan2(tgt[2], math.hypot(tgt[0], tgt[1])))
+    d, _ = rooms.render(room, K, T, noise_sigma=0.0)
+    rng = np.random.default_rng(1)
+    poses = [T] + [_perturb(T, 0.03, 2.5, rng) for _ in range(7)]
+    out, ok, _ = _check_poses(rg, scene, d, K, room, poses, "corner")
+    assert ok.all()
+    for P in out:
+        dt, dr = H.pose_err(P, T)
+        assert dt < 1e-5 and dr < 1e-3, (dt, dr)
+    Tw = rooms.look_pose([2.5, 1.5, 1.25], 0.0, 0.0)
+    dw, _ = rooms.render(room, K, Tw, noise_sigma=0.0)
+    _check_poses(rg, scene, dw, K, room, [_perturb(Tw, 0.05, 2.0, rng) for _ in range(4)], "wall")
+    scene.close()
+
+
+def test_icp_ragged_sizes_and_many_poses(rg, ctx):
+    """333 x 250 pixels with strides (5, 3, 1): ragged tails at every level;
+    40 poses in one call equal the same poses one per call, bit for bit."""
+    room = W2.room()
+    scene = rg.Scene(ctx, room.lo, room.hi)
+    K = rooms.Intrinsics(304.0, 304.0, 166.0, 124.5, 333, 250)
+    T = rooms.look_pose([1.2, 1.0, 1.4], 0.7, -0.2)
+    d, _ = rooms.render(room, K, T, noise_sigma=0.002, noise_seed=4)
+    d = rooms.mask_depth(d, 0.3, seed=6)
+    icp = dict(ICP, icp_stride=(5, 3, 1))
+    rng = np.random.default_rng(8)
+    poses = [_perturb(T, rng.uniform(0, 0.1), rng.uniform(0, 6), rng) for _ in range(40)]
+    out, ok, frac = _check_poses(rg, scene, d, K, room, poses, "ragged", icp)
+    for i in (0, 17, 39):
+        o1, k1, f1 = scene.icp_poses(d, K, poses[i][None], **icp)
+        assert np.array_equal(o1[0], out[i]) and k1[0] == ok[i] and f1[0] == frac[i]
+    scene.close()
+
+
+def test_icp_failure_cases(rg, ctx):
+    K = rooms.Intrinsics(292.5, 292.5, 160.0, 120.0, 320, 240)
+    room = rooms.Room((4.0, 3.0, 2.5), 5)
+    scene = rg.Scene(ctx, room.lo, room.hi)
+    T = rooms.look_pose([1.0, 0.8, 1.6], 0.6, -0.3)
+    d, _ = rooms.render(room, K, T, noise_sigma=0.0)
+    push = T.copy()
+    push[:3, 3] += T[:3, 2] * 0.3
+    outside = rooms.look_pose([-1.0, 1.5, 1.25], math.pi, 0.0)
+    out, ok, frac = _check_poses(rg, scene, d, K, room, [push, outside], "fail")
+    assert not ok.any()
+    out, ok, frac = scene.icp_poses(np.zeros_like(d), K, T[None], **ICP)
+    assert not ok[0] and frac[0] == 0.0 and np.array_equal(out[0], T)
+    d2 = d.copy()
+    d2[(np.arange(d.shape[0]) // 4) % 2 == 0] += 0.5
+    for mf, want in ((0.6, False), (0.4, True)):
+        _, ok, frac = scene.icp_poses(d2, K, T[None], **dict(ICP, icp_min_frac=mf))
+        assert ok[0] == want and abs(frac[0] - 0.5) < 0.01
+    with pytest.raises(rg.RelocError):
+        scene.icp_poses(d, K, T[None], **dict(ICP, icp_levels=4))
+    with pytest.raises(rg.RelocError):
+        scene.icp_poses(d, K, T[None], **dict(ICP, icp_iters=(0, 1, 1)))
+    scene.close()
+
+
+@pytest.fixture(scope="module")
+def config2_model(rg, ctx):
+    return H.gpu_model(ctx, W2)
+
+
+def test_relocalise_with_icp_config2(rg, ctx, config2_model):
+    room = W2.room()
+    scene = rg.Scene(ctx, room.lo, room.hi)
+    p = dict(W2.ransac, **ICP)
+    rel = rg.Relocaliser(config2_model, scene, p, W2.width, W2.height, 1)
+    for q in range(2):
+        _compare_query(rg, rel, W2, q, p)
+    rel.close()
+    scene.close()
+
+
+def test_relocalise_with_icp_small_variants_and_batch(rg, ctx):
+    """Ranked and unranked ICP on the small workload, and each frame's result
+    identical alone and in a batch of 4."""
+    w = H.WORKLOADS[H.SMALL]
+    g = H.gpu_model(ctx, w)
+    scene = rg.Scene(ctx, w.room().lo, w.room().hi)
+    for extra in (dict(), dict(rank=0, k_out=1, halve_to_one=0)):
+        p = dict(w.ransac, **ICP, **extra)
+        rel = rg.Relocaliser(g, scene, p, w.width, w.height, 4)
+        for q in range(3):
+            _compare_query(rg, rel, w, q, p)
+        qs = [w.query(q) for q in range(4)]
+        batch = rel.relocalise_batch(np.stack([x[0] for x in qs]), np.stack([x[1] for x in qs]), w.K,
+                                     [x[3] for x in qs])
+        for i in range(4):
+            alone = rel.relocalise(qs[i][0], qs[i][1], w.K, qs[i][3])
+            assert np.array_equal(alone["pose"], batch[i]["pose"])
+            assert alone["icp_mask"] == batch[i]["icp_mask"]
+            assert np.array_equal(alone["chosen_icp_frac"], batch[i]["chosen_icp_frac"])
+        rel.close()
+    scene.close()
+    g.close()
