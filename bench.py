@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--sweep-seconds", type=float, default=4.0, help="length of each saturation point")
     ap.add_argument("--profile-only", action="store_true",
                     help="short run for an external profiler (no baselines)")
+    ap.add_argument("--icp-poses", type=int, default=0,
+                    help="standalone ICP: refine this many poses against one 640x480 frame "
+                         "(1 GB of device memory; the small case for profiling the ICP kernel)")
     return ap.parse_args()
 
 
@@ -294,9 +297,10 @@ def algorithmic_flops(kernel, work, p):
     squared norm 5, min 1) or 9 Euclidean.  LM: pass 1 as the energy per
     (H, pixel, mode) plus 18 per (H, pixel) transform and 190 per inlier
     (J rows 12, J^T J 126, J^T r 36, cost 6, residual 10); trial pass 34 per
-    inlier.  Raycast: 45 per ray.  ICP: 100 per valid-pixel evaluation
-    (ray 16, slab test 15, gap and inlier test 8, residual and camera point
-    3, Jacobian 9, normal equations 27 FMAs = 54)."""
+    inlier.  Raycast: 45 per ray.  ICP: 50 per valid-pixel evaluation in the
+    face-binned world-frame form (camera ray 4, rotation 12, exit face 6,
+    gap and inlier test 9, rotated point and residual 4, nine normal-equation
+    terms 15)."""
     per_mode = 18 if p["use_cov"] else 9
     if kernel == "energy":
         return 20 * work["energy_pairs"] + per_mode * work["energy_modes"]
@@ -306,7 +310,7 @@ def algorithmic_flops(kernel, work, p):
     if kernel == "raycast_score":
         return 45 * work["rays"]
     if kernel == "icp":
-        return 100 * work["icp_pixels"]
+        return 50 * work["icp_pixels"]
     return None
 
 
@@ -772,10 +776,51 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+def run_icp_poses(args):
+    """ICP (Sec. 3.2.4) of N poses, 3 cm / 2 deg around the true pose of a
+    640x480 query of the config-2 room, in one rl_icp_poses call per step."""
+    import torch
+    import paper_1810_12163_gb300 as rg
+    w = workloads.CONFIG2
+    room = w.room()
+    ctx = rg.Context(0, arena_bytes=1 << 30)
+    scene = rg.Scene(ctx, room.lo, room.hi)
+    d, c, T, seed = w.query(0)
+    rng = np.random.default_rng(0)
+    poses = []
+    for _ in range(args.icp_poses):
+        P = T.copy()
+        axis = rng.normal(size=3)
+        P[:3, :3] = rodrigues(axis / np.linalg.norm(axis), math.radians(2.0)) @ T[:3, :3]
+        v = rng.normal(size=3)
+        P[:3, 3] += v / np.linalg.norm(v) * 0.03
+        poses.append(P)
+    poses = np.stack(poses)
+    dd = torch.from_numpy(d).cuda()
+    for _ in range(args.warmup):
+        scene.icp_poses(dd, w.K, poses, **workloads.ICP_ON)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        out, ok, frac = scene.icp_poses(dd, w.K, poses, **workloads.ICP_ON)
+    dt = time.perf_counter() - t0
+    print(json.dumps({"metric": "ICP pose refinements/s (640x480, 3 levels)", "value": args.icp_poses * args.steps / dt,
+                      "unit": "poses/s", "poses": args.icp_poses, "steps": args.steps, "ok": float(ok.mean()),
+                      "note": "host-timed through rl_icp_poses, pose copies included"}), flush=True)
+    scene.close()
+
+
+def rodrigues(axis, angle):
+    K = np.array([[0, -axis[2], axis[1]], [axis[2], 0, -axis[0]], [-axis[1], axis[0], 0]])
+    return np.eye(3) + math.sin(angle) * K + (1 - math.cos(angle)) * (K @ K)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.icp_poses:
+        run_icp_poses(args)
     elif args.serving:
         run_serving(args)
     else:
