@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--sweep-seconds", type=float, default=4.0, help="length of each saturation point")
     ap.add_argument("--profile-only", action="store_true",
                     help="short run for an external profiler (no baselines)")
+    ap.add_argument("--robustness", action="store_true",
+                    help="success vs missing depth and depth-dependent noise (training and queries corrupted), "
+                         "without and with ICP")
+    ap.add_argument("--robust-queries", type=int, default=64)
     ap.add_argument("--icp-poses", type=int, default=0,
                     help="standalone ICP: refine this many poses against one 640x480 frame "
                          "(1 GB of device memory; the small case for profiling the ICP kernel)")
@@ -810,6 +814,64 @@ def run_icp_poses(args):
     scene.close()
 
 
+def run_robustness(args):
+    """Robustness sweeps (reading R22): per corruption level, a config-2
+    forest adapted from the corrupted training frames, then the corrupted
+    queries relocalised in one batch without and with ICP before ranking;
+    5 cm / 5 deg success and median error against the true poses."""
+    import torch
+    import paper_1810_12163_gb300 as rg
+    w = workloads.CONFIG2
+    nq = args.robust_queries
+    train = list(w.training_frames())
+    queries = w.queries(nq)
+    ctx = rg.Context(0, arena_bytes=24 << 30)
+    room = w.room()
+    scene = rg.Scene(ctx, room.lo, room.hi)
+    t0 = time.perf_counter()
+    out = {}
+    arms = (("missing", "missing", workloads.MISSING_LEVELS, True),
+            ("missing_queries_only", "missing", workloads.MISSING_LEVELS, False),
+            ("noise", "noise", workloads.NOISE_LEVELS, True))
+    clean = None
+    for arm, kind, levels, train_corrupted in arms:
+        rows = []
+        for lvl in levels:
+            if train_corrupted or clean is None:
+                forest = rg.Forest.random(ctx, w.forest, w.forest_seed)
+                for i, (d, c, T) in enumerate(train):
+                    forest.adapt(workloads.corrupt(d, kind, lvl, i) if train_corrupted else d, c, w.K, T)
+                forest.update_modes(-1)
+                if not train_corrupted:
+                    clean = forest
+            else:
+                forest = clean
+            D = torch.from_numpy(np.stack([workloads.corrupt(q[0], kind, lvl, 10000 + i)
+                                           for i, q in enumerate(queries)])).cuda()
+            C = torch.from_numpy(np.stack([q[1] for q in queries])).cuda()
+            row = {"level": lvl, "valid_depth": float((D > 0).float().mean())}
+            for name, p in (("no_icp", w.ransac), ("icp", dict(w.ransac, **workloads.ICP_ON))):
+                rel = rg.Relocaliser(forest, scene, p, w.width, w.height, nq)
+                rs = rel.relocalise_batch(D, C, w.K, [q[3] for q in queries])
+                rel.close()
+                e = np.array([pose_err(r["pose"], q[2]) for r, q in zip(rs, queries)])
+                row[name] = {"success": float(np.mean((e[:, 0] <= 0.05) & (e[:, 1] <= 5.0))),
+                             "median_m": float(np.median(e[:, 0])), "median_deg": float(np.median(e[:, 1])),
+                             "mean_hypotheses": float(np.mean([r["n_hypotheses"] for r in rs]))}
+            if forest is not clean:
+                forest.close()
+            rows.append(row)
+        out[arm] = rows
+    line = {"metric": "5 cm / 5 deg success vs depth corruption", "workload": w.name, "queries": nq,
+            "arms": {"missing": "training frames and queries masked",
+                     "missing_queries_only": "queries masked, forest adapted from clean frames",
+                     "noise": "training frames and queries noisy"}, **out,
+            "icp": {k: (list(v) if isinstance(v, tuple) else v) for k, v in workloads.ICP_ON.items()},
+            "seconds": time.perf_counter() - t0}
+    print(json.dumps(line), flush=True)
+    scene.close()
+
+
 def rodrigues(axis, angle):
     K = np.array([[0, -axis[2], axis[1]], [axis[2], 0, -axis[0]], [-axis[1], axis[0], 0]])
     return np.eye(3) + math.sin(angle) * K + (1 - math.cos(angle)) * (K @ K)
@@ -821,6 +883,8 @@ def main():
         run_reference(args)
     elif args.icp_poses:
         run_icp_poses(args)
+    elif args.robustness:
+        run_robustness(args)
     elif args.serving:
         run_serving(args)
     else:

@@ -11,7 +11,7 @@ import dataclasses
 
 import numpy as np
 
-from .rooms import Room, intrinsics_for, query_poses, render, training_trajectory
+from .rooms import Room, intrinsics_for, mask_depth, noisy_depth, query_poses, render, training_trajectory
 
 # Default relocaliser of the paper's parameter table (Appendix B) with the
 # open values filled in.
@@ -149,6 +149,28 @@ def serving_arrivals(seconds: float, rate_scale: float = 1.0, streams: int = SER
             t += rng.exponential(1.0 / (SERVING_RATE_HZ * rate_scale))
     out.sort()
     return out
+
+
+# Robustness sweeps (missing and noisy depth; reading R22: the corruption is
+# applied to every depth image, training frames and queries alike).
+MISSING_LEVELS = (0.0, 0.1, 0.2, 0.3, 0.5, 0.7, 0.8, 0.9, 0.95)
+NOISE_LEVELS = (0.0, 0.025, 0.05, 0.075, 0.1)
+_CORRUPT_SEED = {"missing": 70000, "noise": 90000}
+
+
+def corrupt(depth, kind: str, level: float, index: int):
+    """Depth image `index` of a sweep corrupted at `level`: missing depth
+    (zero iff r <= p, r ~ U[0,1] per pixel) or depth-dependent noise
+    (d + n d, n ~ N(0, sigma^2) per pixel); training frames use indices
+    0.., queries 10000 + q.  Level 0 returns the image unchanged."""
+    if level == 0:
+        return depth
+    seed = _CORRUPT_SEED[kind] + index
+    if kind == "missing":
+        return mask_depth(depth, level, seed)
+    if kind == "noise":
+        return noisy_depth(depth, level, seed)
+    raise ValueError(kind)
 
 
 # Config 3 levels (shared config-2 forest): subsample, relocaliser parameters.
