@@ -202,6 +202,25 @@ rl_status rl_forest_adapt(rl_forest *f, const float *depth, const uint8_t *rgb,
  * round-robin order (n_leaves < 0: every leaf); keeps the largest M_max
  * clusters per leaf with centroid, colour, covariance. */
 rl_status rl_forest_update_modes(rl_forest *f, int32_t n_leaves, void *stream);
+/* Streaming adaptation (Sec. 3.2.2: leaves are re-clustered a few hundred
+ * per frame while the relocaliser keeps running): enable = 1 gives the
+ * forest a second mode store.  Relocalisation launches then read a complete
+ * snapshot, the front store, while rl_forest_update_modes writes the back
+ * store on its own stream and swaps the two.  Each launch sees the modes
+ * after the last update enqueued (in host order) before it, never a leaf
+ * halfway through re-clustering.
+ *   Ordering is by CUDA events, with no host waits: a launch waits on its
+ * stream for the last update; an update waits on its stream for every
+ * launch that read the store it overwrites.  rl_forest_adapt writes only the
+ * reservoirs, which relocalisation never reads, so it needs no ordering
+ * against launches.  Enqueueing from several host threads is safe (the
+ * forest serialises its bookkeeping); export, save, set_mode_positions and
+ * reset_leaves act on the front store and belong between updates.
+ *   Costs: a second mode store (L x M_max x 34 bytes + L x 17 bytes) and,
+ * per update, a device copy of the previous update's leaves.  Must be set
+ * before any relocaliser of the forest exists (RL_ERR_BUSY otherwise).
+ * enable = 0 frees the second store. */
+rl_status rl_forest_set_streaming(rl_forest *f, int32_t enable);
 /* Eq. 1-3 for every pixel: out_leaves is a DEVICE uint16 [n_trees][H][W]
  * buffer (0xFFFF where depth is invalid).  Bit-exact FP32 arithmetic. */
 rl_status rl_forest_leaves(rl_forest *f, const float *depth, const uint8_t *rgb,

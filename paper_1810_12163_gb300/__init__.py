@@ -153,6 +153,12 @@ class Forest:
     def update_modes(self, n_leaves: int = -1, stream=None):
         call("rl_forest_update_modes", self.h, n_leaves, _stream_ptr(stream))
 
+    def set_streaming(self, enable: bool = True):
+        """Double-buffered modes: relocalisation reads a complete snapshot
+        while update_modes re-clusters leaves on another stream (call before
+        creating relocalisers of this forest)."""
+        call("rl_forest_set_streaming", self.h, int(enable))
+
     def leaves(self, depth, rgb, K, n_trees=None, stream=None):
         torch = _torch()
         Ki = intrinsics(K)
@@ -278,6 +284,24 @@ class Relocaliser:
 
     def relocalise(self, depth, rgb, K, seed, stream=None):
         return self.relocalise_batch(depth, rgb, K, [seed], stream)[0]
+
+    def relocalise_batch_async(self, depth, rgb, K, seeds, stream=None):
+        """Enqueues a batch (inputs in device memory) and returns at once;
+        fetch() waits for the stream and returns the results."""
+        d = _Image(depth, np.float32)
+        c = _Image(rgb, np.uint8)
+        if d.mem != RL_DEVICE or c.mem != RL_DEVICE:
+            raise ValueError("relocalise_batch_async takes device tensors")
+        seeds = np.ascontiguousarray(seeds, np.uint64)
+        call("rl_relocalise_batch_async", self.h, len(seeds), d.ptr, c.ptr, ctypes.byref(intrinsics(K)),
+             seeds.ctypes.data_as(ctypes.c_void_p), _stream_ptr(stream))
+        self._pending = len(seeds)
+
+    def fetch(self, stream=None, raw=False):
+        n = self._pending
+        out = (Result * n)()
+        call("rl_reloc_fetch", self.h, n, _stream_ptr(stream), out)
+        return out if raw else [result_dict(out[i]) for i in range(n)]
 
     @property
     def tuning(self) -> dict:

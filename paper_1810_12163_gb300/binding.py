@@ -103,6 +103,7 @@ _SIGS = {
     "rl_forest_reset_leaves": [P, P],
     "rl_forest_adapt": [P, P, P, P, P, I32, P],
     "rl_forest_update_modes": [P, I32, P],
+    "rl_forest_set_streaming": [P, I32],
     "rl_forest_leaves": [P, P, P, P, I32, P, I32, P],
     "rl_forest_export": [P] + [P] * 12,
     "rl_forest_set_mode_positions": [P, P],

@@ -75,6 +75,105 @@ ModeView mode_view(const rl_forest *f) {
     return v;
 }
 
+// ---------------------------------------------------------------------------
+// Streaming adaptation: two mode stores.  Relocalisers read the front store
+// (the forest's mode arrays); a mode update first waits for every launch
+// that read the back store, swaps the two, brings the new front up to date
+// on the leaves the previous update wrote (a device copy of that range from
+// the old front), clusters its own range into it and records `ready`, which
+// later relocalisation launches wait for.  A launch thus sees one complete
+// snapshot: the modes after the last update enqueued before it.
+// ---------------------------------------------------------------------------
+static ModeStore front_store(const rl_forest *f) {
+    ModeStore m;
+    m.nmodes = f->nmodes;
+    m.centroid = f->centroid;
+    m.mpos_h = f->mpos_h;
+    m.mpos_f = f->mpos_f;
+    m.mrgb = f->mrgb;
+    m.mU = f->mU;
+    m.msize = f->msize;
+    return m;
+}
+
+static void set_front_store(rl_forest *f, const ModeStore &m) {
+    f->nmodes = m.nmodes;
+    f->centroid = m.centroid;
+    f->mpos_h = m.mpos_h;
+    f->mpos_f = m.mpos_f;
+    f->mrgb = m.mrgb;
+    f->mU = m.mU;
+    f->msize = m.msize;
+}
+
+void free_store(rl_ctx *c, ModeStore &m) {
+    void *ptrs[] = {m.nmodes, m.centroid, m.mpos_h, m.mpos_f, m.mrgb, m.mU, m.msize};
+    for (void *p : ptrs) arena_free(c, p);
+    m = ModeStore{};
+}
+
+static rl_status alloc_store(rl_forest *f, ModeStore &m) {
+    const uint64_t L = (uint64_t)f->n_leaves, M = (uint64_t)f->p.m_max;
+    rl_status s = alloc_n(f->ctx, L, &m.nmodes);
+    if (s == RL_OK) s = alloc_n(f->ctx, L, &m.centroid);
+    if (s == RL_OK && f->p.mode_precision == RL_MODES_FP16_OFFSET) s = alloc_n(f->ctx, L * M, &m.mpos_h);
+    if (s == RL_OK && f->p.mode_precision == RL_MODES_FP32) s = alloc_n(f->ctx, L * M, &m.mpos_f);
+    if (s == RL_OK) s = alloc_n(f->ctx, L * M, &m.mrgb);
+    if (s == RL_OK) s = alloc_n(f->ctx, L * M * 2, &m.mU);
+    if (s == RL_OK) s = alloc_n(f->ctx, L * M, &m.msize);
+    if (s != RL_OK) free_store(f->ctx, m);
+    return s;
+}
+
+template <class T>
+static rl_status copy_rows(T *dst, const T *src, int64_t row, int64_t b, int64_t n, cudaStream_t s) {
+    if (!dst || !src || n <= 0) return RL_OK;
+    RL_CK(cudaMemcpyAsync(dst + b * row, src + b * row, sizeof(T) * (size_t)(n * row), cudaMemcpyDeviceToDevice, s));
+    return RL_OK;
+}
+
+// Leaves [begin, begin + count) mod L of every mode array, src -> dst.
+static rl_status copy_store_range(const rl_forest *f, const ModeStore &src, const ModeStore &dst, int64_t begin,
+                                  int64_t count, cudaStream_t s) {
+    const int64_t L = f->n_leaves, M = f->p.m_max;
+    count = std::min<int64_t>(count, L);
+    const int64_t b0 = begin % L, n0 = std::min<int64_t>(count, L - b0), n1 = count - n0;
+    const int64_t segs[2][2] = {{b0, n0}, {0, n1}};
+    for (const auto &g : segs) {
+        RL_TRY(copy_rows(dst.nmodes, src.nmodes, 1, g[0], g[1], s));
+        RL_TRY(copy_rows(dst.centroid, src.centroid, 1, g[0], g[1], s));
+        RL_TRY(copy_rows(dst.mpos_h, src.mpos_h, M, g[0], g[1], s));
+        RL_TRY(copy_rows(dst.mpos_f, src.mpos_f, M, g[0], g[1], s));
+        RL_TRY(copy_rows(dst.mrgb, src.mrgb, M, g[0], g[1], s));
+        RL_TRY(copy_rows(dst.mU, src.mU, 2 * M, g[0], g[1], s));
+        RL_TRY(copy_rows(dst.msize, src.msize, M, g[0], g[1], s));
+    }
+    return RL_OK;
+}
+
+// Stream s waits for every launch that read mode store b.
+static rl_status wait_readers(rl_forest *f, int b, cudaStream_t s) {
+    for (rl_reloc *r : f->readers)
+        if (r->read_valid[b]) RL_CK(cudaStreamWaitEvent(s, r->read_done[b], 0));
+    return RL_OK;
+}
+
+static rl_status streaming_update(rl_forest *f, int64_t begin, int64_t count, cudaStream_t s) {
+    std::lock_guard<std::mutex> g(f->mu);
+    const int back = 1 - f->mode_buf;
+    RL_TRY(wait_readers(f, back, s));
+    const ModeStore old_front = front_store(f);
+    set_front_store(f, f->alt);  // the back store becomes the front
+    f->alt = old_front;
+    RL_TRY(copy_store_range(f, old_front, front_store(f), f->last_begin, f->last_count, s));
+    RL_TRY(update_modes(f, begin, count, s));
+    RL_CK(cudaEventRecord(f->ready, s));
+    f->mode_buf = back;
+    f->last_begin = begin;
+    f->last_count = count;
+    return RL_OK;
+}
+
 }  // namespace rl
 
 using namespace rl;
@@ -140,6 +239,9 @@ static void forest_release(rl_forest *f) {
                     f->mrgb, f->mU, f->msize, f->ex_leaf, f->ex_pt, f->ex_rank, f->frame_cnt,
                     f->stage_depth, f->stage_rgb};
     for (void *p : ptrs) arena_free(c, p);
+    free_store(c, f->alt);
+    if (f->ready) cudaEventDestroy(f->ready);
+    f->ready = nullptr;
 }
 
 static rl_status forest_alloc(rl_ctx *ctx, const rl_forest_params *p, uint64_t seed,
@@ -209,7 +311,18 @@ extern "C" rl_status rl_forest_destroy(rl_forest *f) {
 extern "C" rl_status rl_forest_reset_leaves(rl_forest *f, void *stream) {
     if (!f) return fail(RL_ERR_INVALID_ARG, "null forest");
     RL_CK(cudaSetDevice(f->ctx->device));
-    return reset_leaves(f, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!f->streaming) return reset_leaves(f, s);
+    // both stores emptied once no launch reads either
+    std::lock_guard<std::mutex> g(f->mu);
+    RL_TRY(wait_readers(f, 0, s));
+    RL_TRY(wait_readers(f, 1, s));
+    RL_TRY(reset_leaves(f, s));
+    RL_CK(cudaMemsetAsync(f->alt.nmodes, 0, f->n_leaves, s));
+    RL_CK(cudaMemsetAsync(f->alt.centroid, 0, sizeof(float4) * f->n_leaves, s));
+    RL_CK(cudaEventRecord(f->ready, s));
+    f->last_count = 0;
+    return RL_OK;
 }
 
 static rl_status check_intrinsics(const rl_intrinsics *K) {
@@ -256,8 +369,43 @@ extern "C" rl_status rl_forest_update_modes(rl_forest *f, int32_t n_leaves, void
     RL_CK(cudaSetDevice(f->ctx->device));
     int64_t count = n_leaves < 0 ? f->n_leaves : std::min<int64_t>(n_leaves, f->n_leaves);
     int64_t begin = n_leaves < 0 ? 0 : f->cursor;
-    RL_TRY(update_modes(f, begin, count, (cudaStream_t)stream));
+    if (f->streaming)
+        RL_TRY(streaming_update(f, begin, count, (cudaStream_t)stream));
+    else
+        RL_TRY(update_modes(f, begin, count, (cudaStream_t)stream));
     if (n_leaves >= 0) f->cursor = (f->cursor + count) % f->n_leaves;
+    return RL_OK;
+}
+
+extern "C" rl_status rl_forest_set_streaming(rl_forest *f, int32_t enable) {
+    if (!f) return fail(RL_ERR_INVALID_ARG, "null forest");
+    if (enable != 0 && enable != 1) return fail(RL_ERR_INVALID_ARG, "enable must be 0 or 1");
+    if ((enable != 0) == f->streaming) return RL_OK;
+    if (f->refcount > 0) return fail(RL_ERR_BUSY, "set streaming before creating relocalisers of the forest");
+    RL_CK(cudaSetDevice(f->ctx->device));
+    RL_CK(cudaDeviceSynchronize());
+    std::lock_guard<std::mutex> g(f->mu);
+    if (enable) {
+        RL_TRY(alloc_store(f, f->alt));
+        rl_status s = copy_store_range(f, front_store(f), f->alt, 0, f->n_leaves, 0);
+        if (s == RL_OK && cudaEventCreateWithFlags(&f->ready, cudaEventDisableTiming) != cudaSuccess)
+            s = fail(RL_ERR_CUDA, "event creation failed");
+        if (s == RL_OK && (cudaEventRecord(f->ready, 0) != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess))
+            s = fail(RL_ERR_CUDA, "initial mode copy failed");
+        if (s != RL_OK) {
+            free_store(f->ctx, f->alt);
+            if (f->ready) cudaEventDestroy(f->ready);
+            f->ready = nullptr;
+            return s;
+        }
+        f->last_count = 0;
+        f->streaming = true;
+    } else {
+        free_store(f->ctx, f->alt);
+        cudaEventDestroy(f->ready);
+        f->ready = nullptr;
+        f->streaming = false;
+    }
     return RL_OK;
 }
 
@@ -349,6 +497,10 @@ extern "C" rl_status rl_forest_set_mode_positions(rl_forest *f, const float *mod
         if (e != cudaSuccess) st = cuda_fail(e, "k_set_mode_positions", __FILE__, __LINE__);
     }
     arena_free(f->ctx, stage);
+    if (f->streaming) {  // the back store lacks the new positions everywhere
+        f->last_begin = 0;
+        f->last_count = f->n_leaves;
+    }
     return st;
 }
 

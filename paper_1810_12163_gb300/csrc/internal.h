@@ -64,6 +64,19 @@ rl_status alloc_n(rl_ctx *c, uint64_t n, T **out) {
 // ---------------------------------------------------------------------------
 // Forest and its leaf models.
 // ---------------------------------------------------------------------------
+// The arrays of one mode store (a streaming forest keeps two of them).
+struct ModeStore {
+    uint8_t *nmodes = nullptr;
+    float4 *centroid = nullptr;
+    ushort4 *mpos_h = nullptr;
+    float4 *mpos_f = nullptr;
+    uchar4 *mrgb = nullptr;
+    float4 *mU = nullptr;
+    int32_t *msize = nullptr;
+};
+
+struct rl_reloc;
+
 struct rl_forest {
     rl_ctx *ctx = nullptr;
     rl_forest_params p{};
@@ -95,6 +108,16 @@ struct rl_forest {
     int stage_pixels = 0;
     int64_t cursor = 0;             // round-robin mode update
     int refcount = 0;
+    // Streaming adaptation: the mode arrays above are the front store that
+    // relocalisers read; `alt` is the back store that the next mode update
+    // writes before the two are swapped (see rl_forest_set_streaming).
+    bool streaming = false;
+    ModeStore alt{};
+    int mode_buf = 0;                          // id of the front store (0/1): part of graph keys
+    int64_t last_begin = 0, last_count = 0;    // leaves the back store lacks (written by the last update)
+    cudaEvent_t ready = nullptr;               // recorded after the last update on its stream
+    std::vector<rl_reloc *> readers;           // relocalisers of this forest
+    std::mutex mu;                             // front/back bookkeeping against concurrent launches
 };
 
 struct rl_scene {
@@ -118,7 +141,6 @@ struct ModeView {
     int leaves_per_tree;
 };
 
-// Relocaliser parameters as passed to kernels.
 // ICP settings of Sec. 3.2.4 (see rl_icp_params), as the kernels read them.
 struct IcpParams {
     int levels, stride[3], iters[3];
@@ -126,6 +148,7 @@ struct IcpParams {
     double min_frac, ridge;
 };
 
+// Relocaliser parameters as passed to kernels.
 struct RParams {
     int n_hyp, max_iter, n_cull, eta, k_out, pose_update, use_cov, colour_thresh;
     double min_sq_dist, max_trans_err;
@@ -249,9 +272,10 @@ struct rl_reloc {
     int last_batch = 0;
     int refcount = 0;
     Profiler prof;
-    // Captured launch sequences keyed by (batch size, cascade level).
+    // Captured launch sequences keyed by (batch size, cascade level, front
+    // mode store of the forest).
     struct Graph {
-        int n, level;
+        int n, level, buf;
         cudaGraphExec_t exec;
         uint64_t last_use;
     };
@@ -260,6 +284,9 @@ struct rl_reloc {
     bool use_graphs = true;
     uint64_t calls = 0;
     rl_tuning tune{4, 128, 128, 256};  // launch shapes (results do not depend on them)
+    // streaming forests: recorded after the last launch that read mode store b
+    cudaEvent_t read_done[2] = {nullptr, nullptr};
+    bool read_valid[2] = {false, false};
 };
 
 // Per-frame output of a cascade, written on the device by each level's
@@ -285,7 +312,7 @@ struct rl_cascade {
     Frame *full_dev = nullptr;            // [B] full-resolution frames
     std::vector<void *> allocs;
     struct Graph {
-        int n;
+        int n, buf;
         cudaGraphExec_t exec;
     };
     std::vector<Graph> graphs;

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <memory>
 
 #include "kernels.h"
 
@@ -299,11 +300,44 @@ static void graphs_free(rl_reloc *r) {
     r->capture_stream = nullptr;
 }
 
+// Reader side of a streaming forest (see rl_forest_set_streaming): under the
+// forest's lock, the launch waits for the last mode update and records, after
+// its own work, the event that the next update of the store it read waits
+// for.  A non-streaming forest has one store and no events.
+struct ModeReadScope {
+    rl_forest *f;
+    std::unique_lock<std::mutex> lk;
+    int buf = 0;
+    ModeReadScope(rl_forest *forest, cudaStream_t s, rl_status *st) : f(forest), lk(forest->mu) {
+        buf = f->mode_buf;
+        *st = RL_OK;
+        if (f->streaming && cudaStreamWaitEvent(s, f->ready, 0) != cudaSuccess)
+            *st = fail(RL_ERR_CUDA, "waiting for the mode snapshot failed");
+    }
+    rl_status done(rl_reloc *r, cudaStream_t s) {
+        if (!f->streaming) return RL_OK;
+        if (!r->read_done[buf]) RL_CK(cudaEventCreateWithFlags(&r->read_done[buf], cudaEventDisableTiming));
+        RL_CK(cudaEventRecord(r->read_done[buf], s));
+        r->read_valid[buf] = true;
+        return RL_OK;
+    }
+};
+
+static rl_status launch_relocalise_snapshot(rl_reloc *r, int n, int level, int buf, cudaStream_t s);
+
 rl_status launch_relocalise(rl_reloc *r, int n, int level, cudaStream_t s) {
+    rl_status st;
+    ModeReadScope scope(r->forest, s, &st);
+    RL_TRY(st);
+    RL_TRY(launch_relocalise_snapshot(r, n, level, scope.buf, s));
+    return scope.done(r, s);
+}
+
+static rl_status launch_relocalise_snapshot(rl_reloc *r, int n, int level, int buf, cudaStream_t s) {
     ++r->calls;
     if (r->prof.on || !r->use_graphs) return run_relocalise(r, n, level, s);
     for (auto &g : r->graphs)
-        if (g.n == n && g.level == level) {
+        if (g.n == n && g.level == level && g.buf == buf) {
             g.last_use = r->calls;
             RL_CK(cudaGraphLaunch(g.exec, s));
             return RL_OK;
@@ -331,7 +365,7 @@ rl_status launch_relocalise(rl_reloc *r, int n, int level, cudaStream_t s) {
         cudaGraphExecDestroy(r->graphs[lru].exec);
         r->graphs.erase(r->graphs.begin() + lru);
     }
-    r->graphs.push_back({n, level, exec, r->calls});
+    r->graphs.push_back({n, level, buf, exec, r->calls});
     RL_CK(cudaGraphLaunch(exec, s));
     return RL_OK;
 }
@@ -541,6 +575,10 @@ extern "C" rl_status rl_reloc_create(rl_forest *f, rl_scene *scene, const rl_ran
         return s;
     }
     f->refcount++;
+    {
+        std::lock_guard<std::mutex> g(f->mu);
+        f->readers.push_back(r);
+    }
     *out = r;
     return RL_OK;
 }
@@ -551,6 +589,17 @@ extern "C" rl_status rl_reloc_destroy(rl_reloc *r) {
     cudaSetDevice(r->forest->ctx->device);
     cudaDeviceSynchronize();
     r->forest->refcount--;
+    {
+        rl_forest *f = r->forest;
+        std::lock_guard<std::mutex> g(f->mu);
+        for (size_t i = 0; i < f->readers.size(); ++i)
+            if (f->readers[i] == r) {
+                f->readers.erase(f->readers.begin() + i);
+                break;
+            }
+    }
+    for (cudaEvent_t &e : r->read_done)
+        if (e) cudaEventDestroy(e);
     reloc_release(r);
     delete r;
     return RL_OK;
@@ -704,12 +753,37 @@ static rl_status cascade_enqueue(rl_cascade *c, int n, cudaStream_t s) {
     return RL_OK;
 }
 
+static rl_status cascade_launch_snapshot(rl_cascade *c, int n, int buf, cudaStream_t s);
+
+// The levels' forests are read under the reader protocol of launch_relocalise
+// (each distinct forest locked, in address order); the graph cache is keyed
+// by the forests' front stores.
 static rl_status cascade_launch(rl_cascade *c, int n, cudaStream_t s) {
+    std::vector<rl_forest *> fs;
+    for (rl_reloc *r : c->levels)
+        if (std::find(fs.begin(), fs.end(), r->forest) == fs.end()) fs.push_back(r->forest);
+    std::sort(fs.begin(), fs.end());
+    std::vector<std::unique_ptr<ModeReadScope>> scopes;
+    int buf = 0;
+    for (size_t k = 0; k < fs.size(); ++k) {
+        rl_status st;
+        scopes.emplace_back(new ModeReadScope(fs[k], s, &st));
+        RL_TRY(st);
+        buf |= scopes.back()->buf << k;
+    }
+    RL_TRY(cascade_launch_snapshot(c, n, buf, s));
+    for (rl_reloc *r : c->levels)
+        for (auto &sc : scopes)
+            if (sc->f == r->forest) RL_TRY(sc->done(r, s));
+    return RL_OK;
+}
+
+static rl_status cascade_launch_snapshot(rl_cascade *c, int n, int buf, cudaStream_t s) {
     bool prof = false;
     for (rl_reloc *r : c->levels) prof = prof || r->prof.on;
     if (prof || !c->use_graphs) return cascade_enqueue(c, n, s);
     for (auto &g : c->graphs)
-        if (g.n == n) {
+        if (g.n == n && g.buf == buf) {
             RL_CK(cudaGraphLaunch(g.exec, s));
             return RL_OK;
         }
@@ -731,7 +805,7 @@ static rl_status cascade_launch(rl_cascade *c, int n, cudaStream_t s) {
         cudaGraphExecDestroy(c->graphs.front().exec);
         c->graphs.erase(c->graphs.begin());
     }
-    c->graphs.push_back({n, exec});
+    c->graphs.push_back({n, buf, exec});
     RL_CK(cudaGraphLaunch(exec, s));
     return RL_OK;
 }
