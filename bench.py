@@ -61,6 +61,13 @@ def parse():
                     help="success vs missing depth and depth-dependent noise (training and queries corrupted), "
                          "without and with ICP")
     ap.add_argument("--robust-queries", type=int, default=64)
+    ap.add_argument("--tracking-loss", action="store_true",
+                    help="tracking-loss recovery along a fresh trajectory from empty leaves")
+    ap.add_argument("--track-frames", type=int, default=120)
+    ap.add_argument("--rqs-leaves", type=int, default=0,
+                    help="time Really Quick Shift on this many leaves of the trained config-2 forest")
+    ap.add_argument("--streaming", action="store_true",
+                    help="relocalisation throughput with adaptation running on a second stream")
     ap.add_argument("--icp-poses", type=int, default=0,
                     help="standalone ICP: refine this many poses against one 640x480 frame "
                          "(1 GB of device memory; the small case for profiling the ICP kernel)")
@@ -872,6 +879,170 @@ def run_robustness(args):
     scene.close()
 
 
+def _device_frames(frames):
+    import torch
+    return [(torch.from_numpy(d).cuda(), torch.from_numpy(c).cuda(), T) for d, c, T in frames]
+
+
+def run_tracking_loss(args):
+    """Tracking-loss recovery (Sec. 4): along a fresh 640x480 trajectory of
+    the config-2 room, starting from a random forest with empty leaves,
+    frame t is relocalised with the forest as it stands (stream R), then
+    added with its true pose: reservoir adaptation and a round-robin
+    re-clustering of k leaves (stream T, double-buffered modes).  Success
+    per frame, first success, per-frame training time (CUDA events on T)
+    and relocalisation latency (events on R), for k = 256 (the paper's
+    budget) and larger GB300 budgets."""
+    import torch
+    import paper_1810_12163_gb300 as rg
+    from synth import rooms
+    w = workloads.CONFIG2
+    room = w.room()
+    n = args.track_frames
+    poses = rooms.training_trajectory(room, n, seed=21)
+    frames = []
+    for t, T in enumerate(poses):
+        d, c = rooms.render(room, w.K, T, w.noise_sigma, noise_seed=60000 + t)
+        frames.append((d, c, T))
+    dev = _device_frames(frames)
+    ctx = rg.Context(0, arena_bytes=24 << 30)
+    scene = rg.Scene(ctx, room.lo, room.hi)
+    out = []
+    for k in (256, 8192, 65536):
+        forest = rg.Forest.random(ctx, w.forest, w.forest_seed)
+        forest.set_streaming(True)
+        rel = rg.Relocaliser(forest, scene, w.ransac, w.width, w.height, 1)
+        sR, sT = torch.cuda.Stream(), torch.cuda.Stream()
+        ok, train_ms, reloc_ms = [], [], []
+        for t, (dd, cc, T) in enumerate(dev):
+            eR = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            eT = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            if t >= 1:
+                eR[0].record(sR)
+                rel.relocalise_batch_async(dd[None], cc[None], w.K, [80000 + t], stream=sR)
+                eR[1].record(sR)
+            eT[0].record(sT)
+            forest.adapt(dd, cc, w.K, T, stream=sT)
+            forest.update_modes(k, stream=sT)
+            eT[1].record(sT)
+            if t >= 1:
+                r = rel.fetch(stream=sR)[0]
+                ok.append(bool(_success(r["pose"], T)))
+                reloc_ms.append(eR[0].elapsed_time(eR[1]))
+            eT[1].synchronize()
+            train_ms.append(eT[0].elapsed_time(eT[1]))
+        rel.close()
+        forest.close()
+        first = next((i + 1 for i, v in enumerate(ok) if v), None)
+        out.append({"leaves_per_frame": k, "first_success_frame": first,
+                    "success_frames_1_10": float(np.mean(ok[:10])),
+                    "success_frames_11_end": float(np.mean(ok[10:])) if len(ok) > 10 else None,
+                    "success_curve_by_10": [float(np.mean(ok[i:i + 10])) for i in range(0, len(ok), 10)],
+                    "train_ms_per_frame": {"median": float(np.median(train_ms[1:])),
+                                           "p99": float(np.percentile(train_ms[1:], 99))},
+                    "reloc_ms": {"median": float(np.median(reloc_ms)), "p99": float(np.percentile(reloc_ms, 99))}})
+    line = {"metric": "tracking-loss recovery: 5 cm / 5 deg success per frame", "workload": w.name,
+            "frames": n, "forest_leaves": int(w.forest["n_trees"] << w.forest["depth"]),
+            "sequence": "seeded trajectory (seed 21) of the config-2 room, 2 mm depth noise", "arms": out}
+    print(json.dumps(line), flush=True)
+    scene.close()
+
+
+def run_streaming(args):
+    """Adaptation concurrent with relocalisation (Sec. 3.2.2): the config-2
+    batched relocalisation (64 frames per launch) runs back to back on one
+    stream; a second stream adapts the forest from one posed frame and
+    re-clusters 256 leaves (round robin) per relocalisation launch.
+    Relocalisation frames/s without and with the training stream, training
+    time per frame under load (CUDA events on the training stream)."""
+    import torch
+    import paper_1810_12163_gb300 as rg
+    w = workloads.CONFIG2
+    B = args.batch
+    frames = training_set(w, w.n_train)
+    ctx = rg.Context(0, arena_bytes=24 << 30)
+    forest = rg.Forest.random(ctx, w.forest, w.forest_seed)
+    for d, c, T in frames:
+        forest.adapt(d, c, w.K, T)
+    forest.update_modes(-1)
+    forest.set_streaming(True)
+    scene = rg.Scene(ctx, w.room().lo, w.room().hi)
+    rel = rg.Relocaliser(forest, scene, w.ransac, w.width, w.height, B)
+    qs = [w.query(i) for i in range(min(B, 32))]
+    D = torch.from_numpy(np.stack([qs[i % len(qs)][0] for i in range(B)])).cuda()
+    C = torch.from_numpy(np.stack([qs[i % len(qs)][1] for i in range(B)])).cuda()
+    dev = _device_frames(frames)
+    sR, sT = torch.cuda.Stream(), torch.cuda.Stream()
+    steps = max(args.steps, 4)
+    for k in range(args.warmup):
+        rel.relocalise_batch_async(D, C, w.K, list(range(k * B, k * B + B)), stream=sR)
+        rel.fetch(stream=sR, raw=True)
+        forest.adapt(dev[k][0], dev[k][1], w.K, dev[k][2], stream=sT)
+        forest.update_modes(256, stream=sT)
+    torch.cuda.synchronize()
+
+    def phase(train):
+        t_ms = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(steps):
+            rel.relocalise_batch_async(D, C, w.K, list(range(10_000 + k * B, 10_000 + k * B + B)), stream=sR)
+            if train:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                dd, cc, T = dev[(args.warmup + k) % len(dev)]
+                e0.record(sT)
+                forest.adapt(dd, cc, w.K, T, stream=sT)
+                forest.update_modes(256, stream=sT)
+                e1.record(sT)
+                t_ms.append((e0, e1))
+            rel.fetch(stream=sR, raw=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        return B * steps / dt, [a.elapsed_time(b) for a, b in t_ms]
+
+    alone, _ = phase(False)
+    mixed, tms = phase(True)
+    line = {"metric": "relocalisation frames/s with concurrent adaptation", "workload": w.name, "batch": B,
+            "steps": steps, "frames_per_s_alone": alone, "frames_per_s_with_training": mixed,
+            "training_ms_per_frame_under_load": {"median": float(np.median(tms)), "p99": float(np.percentile(tms, 99))},
+            "leaves_per_frame": 256, "note": "host-timed, results fetched every launch"}
+    print(json.dumps(line), flush=True)
+    rel.close()
+    scene.close()
+
+
+def run_rqs(args):
+    """Really Quick Shift (Sec. 3.2.2 step 3) on N consecutive leaves of the
+    config-2 forest adapted from its 200 training frames: CUDA-event time per
+    launch and per leaf, and the leaves' reservoir fill."""
+    import torch
+    import paper_1810_12163_gb300 as rg
+    w = workloads.CONFIG2
+    frames = training_set(w, args.train_frames or w.n_train)
+    ctx = rg.Context(0, arena_bytes=16 << 30)
+    forest = rg.Forest.random(ctx, w.forest, w.forest_seed)
+    for d, c, T in frames:
+        forest.adapt(d, c, w.K, T)
+    s = torch.cuda.current_stream()
+    ms = []
+    for k in range(args.warmup + args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        forest.update_modes(args.rqs_leaves, stream=s)
+        e1.record(s)
+        e1.synchronize()
+        if k >= args.warmup:
+            ms.append(e0.elapsed_time(e1))
+    count = forest.export(reservoirs=True)["res_count"]
+    kappa = w.forest["kappa"]
+    print(json.dumps({"metric": "Really Quick Shift time per leaf", "leaves_per_launch": args.rqs_leaves,
+                      "ms_per_launch": float(np.median(ms)), "us_per_leaf": 1000 * float(np.median(ms)) / args.rqs_leaves,
+                      "reservoir_fill": {"mean": float(np.minimum(count, kappa).mean()),
+                                         "full_fraction": float((count >= kappa).mean()),
+                                         "empty_fraction": float((count == 0).mean())}}), flush=True)
+    forest.close()
+
+
 def rodrigues(axis, angle):
     K = np.array([[0, -axis[2], axis[1]], [axis[2], 0, -axis[0]], [-axis[1], axis[0], 0]])
     return np.eye(3) + math.sin(angle) * K + (1 - math.cos(angle)) * (K @ K)
@@ -885,6 +1056,12 @@ def main():
         run_icp_poses(args)
     elif args.robustness:
         run_robustness(args)
+    elif args.tracking_loss:
+        run_tracking_loss(args)
+    elif args.streaming:
+        run_streaming(args)
+    elif args.rqs_leaves:
+        run_rqs(args)
     elif args.serving:
         run_serving(args)
     else:

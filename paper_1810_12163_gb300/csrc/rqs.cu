@@ -1,8 +1,24 @@
 // Really Quick Shift clustering of leaf reservoirs and the leaf mode store
 // (Sec. 3.2.2, step 3).  One block per leaf; the leaf's reservoir is staged
-// in shared memory.  Compiled with --fmad=false: densities, parents, cluster
-// statistics and the covariance factor are FP64 IEEE operations in a fixed
-// order, so cluster membership decisions do not depend on the launch shape.
+// in shared memory.  Compiled with --fmad=false.
+//
+// The clustering decisions (density order, parent within tau_c, nearest
+// parent) are those of the FP64 definition: densities summed in index order
+// from FP64 exp, squared distances in FP64.  GB300 runs FP64 at about 1/64 of
+// its FP32 rate, so the O(n^2) loops run in FP32 with a certified error bound
+// and fall back to the FP64 value only where the bound cannot decide:
+//  - densities: FP32 expf of an FP32 argument, FP32 partial sums of 32 terms
+//    added in FP64; |rho32 - rho64| <= n 8e-7 + 1e-5 rho (expf within 4 ulp,
+//    the argument within 8 ulp relative, partial sums within 31 ulp: each
+//    bound doubled);
+//  - a density comparison whose difference lies within the two bounds marks
+//    both points; their FP64 densities are then computed exactly as the
+//    definition does and the parents of the affected points are recomputed;
+//  - squared distances in FP32 are within 5e-7 relative of the FP64 value;
+//    tests against tau_c^2 or against the current nearest candidate closer
+//    than 1e-6 relative are redone in FP64.
+// Cluster statistics and the covariance factor are FP64, members in index
+// order, so the modes are identical to the FP64 definition's.
 #include "internal.h"
 
 namespace rl {
@@ -46,8 +62,61 @@ __device__ __forceinline__ double dist2(const float4 a, const float4 b) {
     return (ex * ex + ey * ey) + ez * ez;
 }
 
+__device__ __forceinline__ float dist2f(const float4 a, const float4 b) {
+    const float ex = a.x - b.x, ey = a.y - b.y, ez = a.z - b.z;
+    return (ex * ex + ey * ey) + ez * ez;
+}
+
+// Parent of point i: the nearest point j of higher density (equal density:
+// lower index) with squared distance <= tau2.  Densities come with error
+// bounds err (0 for exact FP64 values): a pair the bounds cannot order is
+// decided exactly when both points have FP64 densities (exact != null marks
+// them), otherwise both points are marked in need64 and *any64 is set.
+__device__ int rqs_parent(const RqsArgs &a, const float4 *pts, const double *rho, const float *rhof,
+                          const float *err, int *need64, const int *exact, int n, int i, int *any64) {
+    const float4 pi = pts[i];
+    const float ri = rhof[i], ei = err[i];
+    const float tau2f = (float)a.tau2;
+    int best = -1;
+    float bd = 0.f;
+    for (int j = 0; j < n; ++j) {
+        if (j == i) continue;
+        // FP32 density order: err covers the FP32 sum and its rounding to
+        // float; the factor covers the FP32 subtraction and addition
+        const float rj = rhof[j];
+        bool higher;
+        if (fabsf(rj - ri) > (ei + err[j]) * 1.0001f) {
+            higher = rj > ri;
+        } else if (exact && exact[j]) {
+            higher = rho[j] > rho[i] || (rho[j] == rho[i] && j < i);
+        } else {
+            need64[i] = 1;
+            need64[j] = 1;
+            if (any64) *any64 = 1;
+            continue;
+        }
+        if (!higher) continue;
+        const float d2 = dist2f(pi, pts[j]);
+        // FP32 squared distances are within 5e-7 relative of FP64
+        if (fabsf(d2 - tau2f) <= 1e-6f * tau2f) {
+            if (dist2(pi, pts[j]) > a.tau2) continue;
+        } else if (d2 > tau2f) {
+            continue;
+        }
+        if (best < 0 || d2 < bd * (1.f - 1e-6f)) {
+            best = j;
+            bd = d2;
+        } else if (d2 <= bd * (1.f + 1e-6f) && dist2(pi, pts[j]) < dist2(pi, pts[best])) {
+            best = j;
+            bd = d2;
+        }
+    }
+    return best;
+}
+
 // Shared memory: pts[kappa] float4, rho[kappa] double, parent/root/csize/
-// crank[kappa] int, cl_root[64], mu[64][3] double.
+// crank/need64[kappa] int, err/rhof[kappa] float, cl_root[64], mu[64][3]
+// double.
 __global__ void __launch_bounds__(256) k_rqs(RqsArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int K = a.kappa;
@@ -57,9 +126,12 @@ __global__ void __launch_bounds__(256) k_rqs(RqsArgs a) {
     int *root = parent + K;
     int *csize = root + K;
     int *crank = csize + K;
-    int *cl_root = crank + K;            // [64]
+    int *need64 = crank + K;
+    float *err = (float *)(need64 + K);
+    float *rhof = err + K;
+    int *cl_root = (int *)(rhof + K + (K & 1));  // [64]; keeps mu 8-byte aligned for odd kappa
     double *mu = (double *)(cl_root + 64);  // [64][3]
-    __shared__ int n_qual;
+    __shared__ int n_qual, any64;
 
     const int L = (int)((a.begin + blockIdx.x) % a.n_leaves);
     const uint32_t cnt = a.res_count[L];
@@ -72,34 +144,49 @@ __global__ void __launch_bounds__(256) k_rqs(RqsArgs a) {
     }
     if (tid == 0) n_qual = 0;
     __syncthreads();
-    // Parzen density, summed over every point in index order.
+    // Parzen density in FP32 with its error bound (see the file comment).
+    const float c32 = (float)a.inv2s2;
     for (int i = tid; i < n; i += nt) {
         const float4 pi = pts[i];
         double r = 0.0;
-        for (int j = 0; j < n; ++j) r += exp(-(dist2(pi, pts[j]) * a.inv2s2));
-        rho[i] = r;
-    }
-    __syncthreads();
-    // Parent: nearest point of higher density within tau_c (ties: lower index).
-    for (int i = tid; i < n; i += nt) {
-        const float4 pi = pts[i];
-        const double ri = rho[i];
-        int best = -1;
-        double bd = 0.0;
+        float part = 0.f;
         for (int j = 0; j < n; ++j) {
-            if (j == i) continue;
-            const double rj = rho[j];
-            if (!(rj > ri || (rj == ri && j < i))) continue;
-            const double d2 = dist2(pi, pts[j]);
-            if (d2 > a.tau2) continue;
-            if (best < 0 || d2 < bd) {
-                best = j;
-                bd = d2;
+            part += expf(-(dist2f(pi, pts[j]) * c32));
+            if ((j & 31) == 31) {
+                r += (double)part;
+                part = 0.f;
             }
         }
-        parent[i] = best;
+        r += (double)part;
+        rho[i] = r;
+        rhof[i] = (float)r;
+        err[i] = (float)((double)n * 8e-7 + 1.02e-5 * r);  // + 2^-23 r for the rounding to float
+        need64[i] = 0;
     }
+    if (tid == 0) any64 = 0;
     __syncthreads();
+    // Parent: nearest point of higher density within tau_c (ties: lower
+    // index).  Density pairs the bounds cannot order are left to the FP64
+    // pass below.
+    for (int i = tid; i < n; i += nt) parent[i] = rqs_parent(a, pts, rho, rhof, err, need64, nullptr, n, i, &any64);
+    __syncthreads();
+    if (any64) {
+        // exact FP64 densities of the marked points, as the definition sums them
+        for (int i = tid; i < n; i += nt) {
+            if (!need64[i]) continue;
+            const float4 pi = pts[i];
+            double r = 0.0;
+            for (int j = 0; j < n; ++j) r += exp(-(dist2(pi, pts[j]) * a.inv2s2));
+            rho[i] = r;
+            rhof[i] = (float)r;
+            err[i] = (float)(1.2e-7 * r);  // the rounding to float only
+        }
+        __syncthreads();
+        // parents of the points that took part in an undecided comparison
+        for (int i = tid; i < n; i += nt)
+            if (need64[i]) parent[i] = rqs_parent(a, pts, rho, rhof, err, need64, need64, n, i, nullptr);
+        __syncthreads();
+    }
     for (int i = tid; i < n; i += nt) {
         int r = i;
         while (parent[r] >= 0) r = parent[r];
@@ -204,7 +291,8 @@ __global__ void __launch_bounds__(256) k_rqs(RqsArgs a) {
 }
 
 static size_t rqs_smem(int kappa) {
-    return (size_t)kappa * (sizeof(float4) + sizeof(double) + 4 * sizeof(int)) + 64 * sizeof(int) +
+    return (size_t)kappa * (sizeof(float4) + sizeof(double) + 5 * sizeof(int) + 2 * sizeof(float)) +
+           (size_t)(kappa & 1) * sizeof(float) + 64 * sizeof(int) +
            64 * 3 * sizeof(double);
 }
 

@@ -123,3 +123,47 @@ def test_streaming_must_be_set_before_relocalisers(rg, ctx):
     g.set_streaming(True)
     g.set_streaming(False)
     g.close()
+
+
+def test_tracking_loss_protocol_parity(rg, ctx):
+    """Tracking-loss recovery (Sec. 4): from empty leaves, frame t is
+    relocalised with the forest adapted from frames < t (round-robin modes),
+    then frame t is added with its true pose.  Each relocalisation against
+    the oracle run on the same forest state."""
+    import torch
+    w = H.WORKLOADS[H.SMALL]
+    frames = list(w.training_frames())[:8]
+    step_leaves = 200
+    g = rg.Forest.random(ctx, w.forest, w.forest_seed)
+    g.set_streaming(True)
+    room = w.room()
+    scene = rg.Scene(ctx, room.lo, room.hi)
+    rel = rg.Relocaliser(g, scene, w.ransac, w.width, w.height, 1)
+    f = H.oracle_forest_nodes(w)
+    res = oracle.Reservoirs(f, w.forest["kappa"], w.forest_seed)
+    modes = oracle.Modes(res.n_leaves, w.forest["m_max"])
+    kw = dict(cov_eps=w.forest["cov_eps"], fp16_offsets=bool(w.forest["mode_precision"]))
+    sR, sT = torch.cuda.Stream(), torch.cuda.Stream()
+    cursor, found = 0, 0
+    for t, (d, c, T) in enumerate(frames):
+        dd, cc = torch.from_numpy(d).cuda(), torch.from_numpy(c).cuda()
+        if t >= 1:
+            seed = 7000 + t
+            rel.relocalise_batch_async(dd[None], cc[None], w.K, [seed], stream=sR)
+        g.adapt(dd, cc, w.K, T, stream=sT)
+        g.update_modes(step_leaves, stream=sT)
+        if t >= 1:
+            gr = rel.fetch(stream=sR)[0]
+            lv = oracle.forest_leaves(f, d, c, w.K.fx, n_trees=w.ransac["n_trees_used"])
+            orr = oracle.relocalise(w.ransac, d, c, w.K, lv, modes, room.lo, room.hi, seed,
+                                    1 << w.forest["depth"], debug=True)
+            H.compare_results(rg, gr, rel.debug(0), orr, w.ransac, f"tracking loss frame {t}")
+            found += gr["status"] == rg.RL_POSE_FOUND
+        res.add_frame(d, c, w.K, T, w.forest["grid_step"], w.forest["grid_origin"])
+        oracle.update_modes(res, modes, w.forest["sigma"], w.forest["tau_c"], w.forest["min_cluster_size"],
+                            leaf_begin=cursor, leaf_count=step_leaves, **kw)
+        cursor = (cursor + step_leaves) % res.n_leaves
+    assert found >= 3
+    rel.close()
+    scene.close()
+    g.close()
