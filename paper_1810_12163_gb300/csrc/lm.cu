@@ -145,7 +145,13 @@ __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 
     int HB = 1;
     while (HB < n) HB <<= 1;
     const int G = LMC_THREADS / HB;
-    const int t = threadIdx.x, hl = t % HB, g = t / HB;
+    // With fewer than 16 hypotheses a tile has fewer (hypothesis, pixel)
+    // pairs than threads: S adjacent lanes then share a pair and split its
+    // mode scan (every S-th mode), and the nearest mode is found by a
+    // shuffle reduction (ties: lower index, as a sequential scan finds it).
+    const int S = G > LMC_P ? G / LMC_P : 1;
+    const int Gp = G / S;  // pixel groups
+    const int t = threadIdx.x, sub = t % S, hl = (t / S) % HB, g = (t / S) / HB;
     const bool mine = hl < n;
 
     float *s_acc = (float *)smem;
@@ -207,6 +213,118 @@ __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 
     };
 
     unsigned w_pairs = 0, w_modes = 0, w_in = 0, w_trial = 0;
+    // One tile of a pass with S > 1: pixel g of the tile for hypothesis hl,
+    // modes sub, sub + S, ... on this lane; every lane reaches the shuffles.
+    auto split_tile = [&](bool live, int s, int j, bool trial, const int16_t *cr, int16_t *cw, LmcPass &o,
+                          float r00, float r01, float r02, float tx, float r10, float r11, float r12, float ty,
+                          float r20, float r21, float r22, float tz) {
+        const uint8_t *st = smem + s * L.stage;
+        const float4 *s_t0 = (const float4 *)(st + L.t0);
+        const float4 *s_t1 = (const float4 *)(st + L.t1);
+        const float *s_t2 = (const float *)(st + L.t2);
+        const float4 *s_xc = (const float4 *)(st + L.xc);
+        const int16_t *s_cnt = (const int16_t *)(st + L.cnt);
+        const int i0 = (crank + j * LMC_CTAS) * LMC_P;
+        const int il = g;
+        const bool on = live && il < min(LMC_P, a.n_pix - i0);
+        const int cnt = on ? (int)s_cnt[il] : 0;
+        const int base = il * stride;
+        float y0 = 0.f, y1 = 0.f, y2 = 0.f;
+        if (cnt > 0) {
+            const float4 x = s_xc[il];
+            y0 = fmaf(r00, x.x, fmaf(r01, x.y, fmaf(r02, x.z, tx)));
+            y1 = fmaf(r10, x.x, fmaf(r11, x.y, fmaf(r12, x.z, ty)));
+            y2 = fmaf(r20, x.x, fmaf(r21, x.y, fmaf(r22, x.z, tz)));
+        }
+        float best = INFINITY;
+        int best_m = -1;
+        if (cov) {
+            auto d2of = [&](int m) {
+                const float4 m0 = s_t0[base + m], m1 = s_t1[base + m];
+                const float u22 = s_t2[base + m];
+                const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+                const float w0 = fmaf(m0.w, v0, fmaf(m1.x, v1, m1.y * v2));
+                const float w1 = fmaf(m1.z, v1, m1.w * v2);
+                const float w2 = u22 * v2;
+                return fmaf(w0, w0, fmaf(w1, w1, w2 * w2));
+            };
+            int m = sub;
+            for (; m + S < cnt; m += 2 * S) {
+                const float da = d2of(m), db = d2of(m + S);
+                if (da < best) { best = da; best_m = m; }
+                if (db < best) { best = db; best_m = m + S; }
+            }
+            if (m < cnt) {
+                const float da = d2of(m);
+                if (da < best) { best = da; best_m = m; }
+            }
+        } else {
+            auto d2of = [&](int m) {
+                const float4 m0 = s_t0[base + m];
+                const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+                return fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
+            };
+            int m = sub;
+            for (; m + S < cnt; m += 2 * S) {
+                const float da = d2of(m), db = d2of(m + S);
+                if (da < best) { best = da; best_m = m; }
+                if (db < best) { best = db; best_m = m + S; }
+            }
+            if (m < cnt) {
+                const float da = d2of(m);
+                if (da < best) { best = da; best_m = m; }
+            }
+        }
+        for (int off = 1; off < S; off <<= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+            const int om = __shfl_xor_sync(0xffffffffu, best_m, off);
+            if (om >= 0 && (best_m < 0 || ob < best || (ob == best && om < best_m))) {
+                best = ob;
+                best_m = om;
+            }
+        }
+        if (sub != 0 || !on) return;
+        const size_t ci = (size_t)(i0 + il) * n + hl;
+        const int m_old = trial ? (int)cr[ci] : -1;
+        if (cnt > 0) {
+            ++w_pairs;
+            w_modes += cnt;
+            if (best_m >= 0) {
+                const float4 m0 = s_t0[base + best_m];
+                const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+                if (fmaf(v0, v0, fmaf(v1, v1, v2 * v2)) <= thr2) {
+                    ++o.nin;
+                    ++w_in;
+                    if (cov) {
+                        const float4 m1 = s_t1[base + best_m];
+                        lm_accumulate(y0, y1, y2, v0, v1, v2, m0.w, m1.x, m1.y, m1.z, m1.w, s_t2[base + best_m],
+                                      o.acc);
+                    } else {
+                        lm_accumulate(y0, y1, y2, v0, v1, v2, 1.f, 0.f, 0.f, 1.f, 0.f, 1.f, o.acc);
+                    }
+                } else {
+                    best_m = -1;
+                }
+            }
+            if (m_old >= 0) {  // the previous correspondence at the trial pose
+                ++w_trial;
+                const float4 m0 = s_t0[base + m_old];
+                const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+                if (cov) {
+                    const float4 m1 = s_t1[base + m_old];
+                    const float q0 = fmaf(m0.w, v0, fmaf(m1.x, v1, m1.y * v2));
+                    const float q1 = fmaf(m1.z, v1, m1.w * v2);
+                    const float q2 = s_t2[base + m_old] * v2;
+                    o.trial = fmaf(q0, q0, fmaf(q1, q1, fmaf(q2, q2, o.trial)));
+                } else {
+                    o.trial = fmaf(v0, v0, fmaf(v1, v1, fmaf(v2, v2, o.trial)));
+                }
+            }
+        } else {
+            best_m = -1;
+        }
+        cw[ci] = (int16_t)best_m;  // local mode index in the row, -1: none
+    };
     // The pass; act: this thread's hypothesis takes part, P: its pose.
     auto pass = [&](bool act, const double *P, bool trial, int rbuf, int wbuf) {
         LmcPass o;
@@ -237,7 +355,10 @@ __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 
                 *s_abort = 1;
                 a.q.dev_err[b] = 1;
             }
-            if (act && !*s_abort) {
+            if (S > 1) {
+                split_tile(act && !*s_abort, s, j, trial, cr, cw, o, r00, r01, r02, tx, r10, r11, r12, ty, r20, r21,
+                           r22, tz);
+            } else if (act && !*s_abort) {
                 const uint8_t *st = smem + s * L.stage;
                 const float4 *s_t0 = (const float4 *)(st + L.t0);
                 const float4 *s_t1 = (const float4 *)(st + L.t1);
@@ -246,7 +367,7 @@ __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 
                 const int16_t *s_cnt = (const int16_t *)(st + L.cnt);
                 const int i0 = (crank + j * LMC_CTAS) * LMC_P;
                 const int np = min(LMC_P, a.n_pix - i0);
-                for (int il = g; il < np; il += G) {
+                for (int il = g; il < np; il += Gp) {
                     const size_t ci = (size_t)(i0 + il) * n + hl;
                     const int m_old = trial ? (int)cr[ci] : -1;
                     const int cnt = s_cnt[il];
@@ -351,7 +472,8 @@ __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 
         for (int e = t; e < n * LMC_NV; e += LMC_THREADS) {
             const int h = e / LMC_NV, k = e % LMC_NV;
             float v = 0.f;
-            for (int gg = 0; gg < G; ++gg) v += s_acc[(gg * HB + h) * LMC_PS + k];
+            // the lanes holding hypothesis h's partials, in group order
+            for (int gg = 0; gg < Gp; ++gg) v += s_acc[(S * (gg * HB + h)) * LMC_PS + k];
             loc[e] = v;
         }
         // Double-buffered loc: a CTA rewrites buffer lb two reductions later,
