@@ -344,8 +344,8 @@ def algorithmic_int_ops(kernel, work):
 # rounds of a 32-frame call), valid only for the source it was measured on:
 # when the file's hash differs, traffic is reported as null.
 PROFILED_TRAFFIC = {
-    "lm": {"bytes_per_frame_launch": 13.02e6, "source": "paper_1810_12163_gb300/csrc/lm.cu",
-           "sha256_16": "cf0ecf162b015e09"},
+    "lm": {"bytes_per_frame_launch": 12.57e6, "source": "paper_1810_12163_gb300/csrc/lm.cu",
+           "sha256_16": "99c84ba4c352e039"},
 }
 
 
@@ -522,7 +522,9 @@ def run_ours(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
+            torch.cuda.nvtx.range_push("timed_step")  # lets an external profiler select these launches
             results = rel.relocalise_batch(D, C, w.K, seeds(k), stream=stream, raw=True)
+            torch.cuda.nvtx.range_pop()
             e1.record(stream)
             e1.synchronize()
             step_ms.append(e0.elapsed_time(e1))
@@ -574,7 +576,8 @@ def run_ours(args):
         lat1.append(e0.elapsed_time(e1))
     lat1 = lat1[2:]
 
-    icp = run_icp_variant(rg, forest, scene, w, D, C, B, qs, stream, seeds, args, sm_count, pk, tuning)
+    icp = None if args.profile_only else run_icp_variant(rg, forest, scene, w, D, C, B, qs, stream, seeds, args,
+                                                          sm_count, pk, tuning)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
