@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--sweep-seconds", type=float, default=4.0, help="length of each saturation point")
     ap.add_argument("--profile-only", action="store_true",
                     help="short run for an external profiler (no baselines)")
+    ap.add_argument("--arena-gb", type=float, default=24.0,
+                    help="device memory handed to the library (smaller for profiler captures)")
     ap.add_argument("--robustness", action="store_true",
                     help="success vs missing depth and depth-dependent noise (training and queries corrupted), "
                          "without and with ICP")
@@ -340,7 +342,7 @@ def algorithmic_int_ops(kernel, work):
 
 
 # DRAM traffic (read + write) of a kernel from one ncu capture, per frame
-# and launch (profiles/k_lm_cluster_config2_b32_round0.md: mean over the six
+# and launch (profiles/launches_relocalise_config2_b64.md: mean over the six
 # rounds of a 32-frame call), valid only for the source it was measured on:
 # when the file's hash differs, traffic is reported as null.
 PROFILED_TRAFFIC = {
@@ -484,7 +486,7 @@ def run_ours(args):
 
     n_train = args.train_frames or w.n_train
     frames = training_set(w, n_train)
-    ctx = rg.Context(local, arena_bytes=24 << 30)
+    ctx = rg.Context(local, arena_bytes=int(args.arena_gb * (1 << 30)))
     forest = rg.Forest.random(ctx, w.forest, w.forest_seed)
     for d, c, T in frames:
         forest.adapt(d, c, w.K, T)
@@ -639,6 +641,7 @@ def run_ours(args):
             "queries": len(errs), "max_pose_m": float(e[:, 0].max()), "max_pose_deg": float(e[:, 1].max()),
             "max_energy_rel": float(e[:, 2].max()), "max_score_rel": float(e[:, 3].max()),
             "within_1mm_0.05deg": int(((e[:, 0] <= 1e-3) & (e[:, 1] <= 0.05)).sum())}
+    line["arena_peak_gb"] = ctx.usage()[1] / (1 << 30)
     if rank == 0:
         print(json.dumps(line), flush=True)
     rel1.close()

@@ -236,10 +236,10 @@ enum KernelId {
 // work counters: energy (H,px) pairs, energy (H,px,mode) triples, LM pass-1
 // (H,px) evaluations, LM (H,px,mode) triples, LM inlier accumulations, LM
 // pass-2 evaluations, raycast rays, generation attempts and stage-2
-// evaluations, ICP valid-pixel evaluations
+// evaluations, ICP valid-pixel evaluations, raycast rays re-evaluated in FP64
 enum WorkId {
     W_E_PAIRS = 0, W_E_MODES, W_LM_PAIRS, W_LM_MODES, W_LM_INLIERS, W_LM_TRIAL, W_RAYS, W_HYP_ATTEMPTS,
-    W_HYP_STAGE2, W_ICP_PIX, W_COUNT
+    W_HYP_STAGE2, W_ICP_PIX, W_RAY64, W_COUNT
 };
 
 struct Profiler {

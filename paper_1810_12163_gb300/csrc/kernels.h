@@ -72,6 +72,11 @@ size_t lm_cluster_smem(int mpad, bool cov);
 rl_status launch_lm_cluster(const LmArgs &a, int n, cudaStream_t s);
 rl_status prepare_lm_cluster();
 
+// Ranking raycast tiles: 256 threads x RC_PIX pixels; one partial record
+// per (frame, pose, tile).
+constexpr int RC_PIX = 2;
+constexpr int RC_TILE = 256 * RC_PIX;
+
 struct RaycastArgs {
     const Frame *frames;
     const double *poses;       // [B][pose_cap][12]

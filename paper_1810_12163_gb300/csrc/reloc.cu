@@ -511,7 +511,7 @@ extern "C" rl_status rl_reloc_create(rl_forest *f, rl_scene *scene, const rl_ran
     const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(32, 40960 / (rp.mpad * 36)));
     r->n_chunks = (rp.max_pix + chunk - 1) / chunk;
     const size_t hw = (size_t)max_w * max_h;
-    r->n_score_tiles = (int)((hw + 255) / 256);
+    r->n_score_tiles = (int)((hw + RC_TILE - 1) / RC_TILE);
     const uint64_t B = max_batch, N = p->n_hyp, NC = p->n_cull, MP = rp.max_pix;
     QueryState &q = r->q;
     rl_status s = RL_OK;
@@ -1012,6 +1012,7 @@ static const char *kKernelNames[K_COUNT] = {"leaves",  "hypgen", "compact", "sam
                                              "select", "lm",     "raycast_score", "finalize", "hyppose",
                                              "colour_mask", "icp"};
 static_assert(K_COUNT == RL_N_KERNELS, "kernel ids and the public count differ");
+static_assert(W_COUNT == RL_N_WORK, "work counters and the public count differ");
 
 extern "C" const char *rl_kernel_name(int32_t kid) {
     return (kid >= 0 && kid < K_COUNT) ? kKernelNames[kid] : "";
@@ -1071,7 +1072,7 @@ extern "C" rl_status rl_score_poses(rl_scene *sc, const float *depth, const rl_i
     RL_CK(cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
     const int npx = K->width * K->height;
-    const int tiles = (npx + 255) / 256;
+    const int tiles = (npx + RC_TILE - 1) / RC_TILE;
     Frame *fr = nullptr;
     double *pd = nullptr, *psum = nullptr;
     int32_t *pcnt = nullptr;

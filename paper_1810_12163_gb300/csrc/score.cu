@@ -920,13 +920,25 @@ __device__ bool ray_depth64(const double *P, int u, int v, float fx, float fy, f
     return false;
 }
 
-// One thread per pixel of a 256-pixel tile, all poses of the frame in turn
-// (staged in shared memory, RC_CHUNK at a time): the pixel's live depth and
-// viewing direction are read once.  The hit test runs in FP32; a ray whose
-// decision lies within a relative margin of 1e-4 of changing (near-parallel
-// faces, grazing edges, a face through the camera) is re-evaluated in FP64,
-// so the valid mask of Eq. 7 is the FP64 one.  Per pose the tile's sums are
-// reduced over lanes, then over warps in order, one partial per (pose, tile).
+// The FP64 re-evaluation of one ray, kept out of line so that none of its
+// FP64 work is scheduled into the FP32 loop that rarely needs it.
+__device__ __noinline__ bool ray_depth_fp64(const double *P, int u, int v, float fx, float fy, float cx, float cy,
+                                            const double lo[3], const double hi[3], float *depth) {
+    double dd = 0.0;
+    const bool ok = ray_depth64(P, u, v, fx, fy, cx, cy, lo, hi, &dd);
+    *depth = (float)dd;
+    return ok;
+}
+
+// Each thread owns RC_PIX pixels of an RC_TILE-pixel tile and runs all poses
+// of the frame over them in turn (poses staged in shared memory, RC_CHUNK at a
+// time), so each pixel's live depth and viewing direction are read once.  The
+// hit test runs in FP32; a ray whose decision lies within a relative margin
+// of 1e-4 of changing (near-parallel faces, grazing edges, a face through the
+// camera) is re-evaluated in FP64, so the valid mask of Eq. 7 is the FP64
+// one.  Per pose the tile's sums are reduced over the thread's pixels in
+// order, then over lanes, then over warps in order, one partial per (pose,
+// tile).
 constexpr int RC_CHUNK = 16;
 
 __global__ void __launch_bounds__(256) k_raycast_score(RaycastArgs a) {
@@ -938,33 +950,42 @@ __global__ void __launch_bounds__(256) k_raycast_score(RaycastArgs a) {
     if (n_poses <= 0) return;
     const Frame fr = a.frames[b];
     const int npx = fr.W * fr.H;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool in = p < npx;
-    int u = 0, v = 0;
-    float dc0 = 0.f, dc1 = 0.f, dl = 0.f;
-    if (in) {
-        u = p % fr.W;
-        v = p / fr.W;
-        // fast approximate divisions: their few-ulp error is far inside the
-        // margin that sends a ray to the FP64 path
-        dc0 = __fdividef((float)u - fr.cx, fr.fx);
-        dc1 = __fdividef((float)v - fr.cy, fr.fy);
-        dl = fr.depth[p];
+    int u[RC_PIX], v[RC_PIX];
+    float dc0[RC_PIX], dc1[RC_PIX], dl[RC_PIX];
+    bool in[RC_PIX];
+#pragma unroll
+    for (int q = 0; q < RC_PIX; ++q) {
+        const int p = blockIdx.x * RC_TILE + q * 256 + threadIdx.x;
+        in[q] = p < npx;
+        u[q] = 0; v[q] = 0;
+        dc0[q] = 0.f; dc1[q] = 0.f; dl[q] = 0.f;
+        if (in[q]) {
+            u[q] = p % fr.W;
+            v[q] = p / fr.W;
+            // fast approximate divisions: their few-ulp error is far inside
+            // the margin that sends a ray to the FP64 path
+            dc0[q] = __fdividef((float)u[q] - fr.cx, fr.fx);
+            dc1[q] = __fdividef((float)v[q] - fr.cy, fr.fy);
+            dl[q] = fr.depth[p];
+        }
     }
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned n64 = 0;  // rays re-evaluated in FP64 (profiling counter)
     for (int c0 = 0; c0 < n_poses; c0 += RC_CHUNK) {
         const int cnt = min(RC_CHUNK, n_poses - c0);
         __syncthreads();  // the previous chunk's poses and partials are consumed
         for (int e = threadIdx.x; e < cnt * 12; e += blockDim.x) sPf[e / 12][e % 12] = (float)a.pose_of(b, c0 + e / 12)[e % 12];
         __syncthreads();
         for (int k = 0; k < cnt; ++k) {
+            const float *P = sPf[k];
             float sum = 0.f;
             int syn = 0, both = 0;
-            if (in) {
-                const float *P = sPf[k];
+#pragma unroll
+            for (int q = 0; q < RC_PIX; ++q) {
+                if (!in[q]) continue;
                 float d[3], o[3];
                 for (int r = 0; r < 3; ++r) {
-                    d[r] = fmaf(P[4 * r], dc0, fmaf(P[4 * r + 1], dc1, P[4 * r + 2]));
+                    d[r] = fmaf(P[4 * r], dc0[q], fmaf(P[4 * r + 1], dc1[q], P[4 * r + 2]));
                     o[r] = P[4 * r + 3];
                 }
                 const float dn = fabsf(d[0]) + fabsf(d[1]) + fabsf(d[2]);
@@ -988,9 +1009,9 @@ __global__ void __launch_bounds__(256) k_raycast_score(RaycastArgs a) {
                         unsure = true;
                 }
                 if (unsure) {
-                    double dd;
-                    ok = ray_depth64(a.pose_of(b, c0 + k), u, v, fr.fx, fr.fy, fr.cx, fr.cy, a.lo64, a.hi64, &dd);
-                    depth = (float)dd;
+                    ++n64;
+                    ok = ray_depth_fp64(a.pose_of(b, c0 + k), u[q], v[q], fr.fx, fr.fy, fr.cx, fr.cy, a.lo64,
+                                        a.hi64, &depth);
                 } else if (tn <= tf && tn > 0.f) {
                     depth = tn;
                 } else if (tn <= tf && tf > 0.f) {
@@ -999,19 +1020,17 @@ __global__ void __launch_bounds__(256) k_raycast_score(RaycastArgs a) {
                     ok = false;
                 }
                 if (ok) {
-                    syn = 1;
-                    if (dl > 0.f) {
-                        both = 1;
-                        sum = fabsf(dl - depth);
+                    ++syn;
+                    if (dl[q] > 0.f) {
+                        ++both;
+                        sum += fabsf(dl[q] - depth);
                     }
                 }
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                sum += __shfl_down_sync(0xffffffffu, sum, o);
-                syn += __shfl_down_sync(0xffffffffu, syn, o);
-                both += __shfl_down_sync(0xffffffffu, both, o);
-            }
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+            syn = __reduce_add_sync(0xffffffffu, syn);
+            both = __reduce_add_sync(0xffffffffu, both);
             if (lane == 0) {
                 s_sum[k][w] = sum;
                 s_syn[k][w] = syn;
@@ -1034,9 +1053,12 @@ __global__ void __launch_bounds__(256) k_raycast_score(RaycastArgs a) {
             a.part_cnt[2 * o + 1] = tb;
         }
     }
-    if (a.work && threadIdx.x == 0)
-        atomicAdd(&a.work[W_RAYS], (unsigned long long)n_poses *
-                                       (unsigned long long)min((int)blockDim.x, npx - (int)(blockIdx.x * blockDim.x)));
+    if (a.work) {
+        if (threadIdx.x == 0)
+            atomicAdd(&a.work[W_RAYS], (unsigned long long)n_poses *
+                                           (unsigned long long)min(RC_TILE, npx - (int)(blockIdx.x * RC_TILE)));
+        if (n64) atomicAdd(&a.work[W_RAY64], (unsigned long long)n64);
+    }
 }
 
 // Eq. 7 from the tile partials of one (frame, pose): FP64 sums in tile order.
