@@ -20,6 +20,57 @@ namespace rl {
 // (decoded to FP32) are staged in shared memory and read by broadcast.
 // ---------------------------------------------------------------------------
 
+// Partial energy with S lanes per hypothesis (S a power of two <= 32): lane
+// t serves hypothesis h0 + t / S and scans modes t % S, t % S + S, ...  Every
+// lane runs every pixel, so the shuffles see the whole warp.
+__device__ __noinline__ void energy_split(const EnergyArgs &a, int b, int h0, int nb, int S, int np,
+                                          const float4 *s_xc, const float4 *s_m0, const float4 *s_m1,
+                                          const float *s_m2, const int *s_cnt) {
+    const int hl = threadIdx.x / S, sub = threadIdx.x % S;
+    const bool act = hl < nb;
+    float r00 = 0.f, r01 = 0.f, r02 = 0.f, t0 = 0.f, r10 = 0.f, r11 = 0.f, r12 = 0.f, t1 = 0.f;
+    float r20 = 0.f, r21 = 0.f, r22 = 0.f, t2 = 0.f;
+    if (act) {
+        const int h = h0 + hl;
+        const int id = a.idx ? a.idx[(size_t)b * a.idx_stride + h] : h;
+        const double *P = a.pose + ((size_t)b * a.pose_stride + id) * 12;
+        r00 = (float)P[0]; r01 = (float)P[1]; r02 = (float)P[2]; t0 = (float)P[3];
+        r10 = (float)P[4]; r11 = (float)P[5]; r12 = (float)P[6]; t1 = (float)P[7];
+        r20 = (float)P[8]; r21 = (float)P[9]; r22 = (float)P[10]; t2 = (float)P[11];
+    }
+    float acc = 0.f;
+    for (int i = 0; i < np; ++i) {
+        const int cnt = s_cnt[i];
+        if (cnt == 0) continue;  // the same for every lane
+        const float4 x = s_xc[i];
+        const float y0 = fmaf(r00, x.x, fmaf(r01, x.y, fmaf(r02, x.z, t0)));
+        const float y1 = fmaf(r10, x.x, fmaf(r11, x.y, fmaf(r12, x.z, t1)));
+        const float y2 = fmaf(r20, x.x, fmaf(r21, x.y, fmaf(r22, x.z, t2)));
+        const int base = i * a.maxm;
+        float best = INFINITY;
+        if (a.p.use_cov) {
+            for (int m = sub; m < cnt; m += S) {
+                const float4 m0 = s_m0[base + m], m1 = s_m1[base + m];
+                const float u22 = s_m2[base + m];
+                const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+                const float w0 = fmaf(m0.w, v0, fmaf(m1.x, v1, m1.y * v2));
+                const float w1 = fmaf(m1.z, v1, m1.w * v2);
+                const float w2 = u22 * v2;
+                best = fminf(best, fmaf(w0, w0, fmaf(w1, w1, w2 * w2)));
+            }
+        } else {
+            for (int m = sub; m < cnt; m += S) {
+                const float4 m0 = s_m0[base + m];
+                const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+                best = fminf(best, fmaf(v0, v0, fmaf(v1, v1, v2 * v2)));
+            }
+        }
+        for (int off = 1; off < S; off <<= 1) best = fminf(best, __shfl_xor_sync(0xffffffffu, best, off));
+        acc += sqrtf(best);
+    }
+    if (act && sub == 0) a.part[((size_t)b * a.part_h + h0 + hl) * a.n_chunks + blockIdx.y] = acc;
+}
+
 __global__ void __launch_bounds__(256) k_energy(EnergyArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
     float4 *s_xc = (float4 *)smem;                         // [chunk]
@@ -65,6 +116,17 @@ __global__ void __launch_bounds__(256) k_energy(EnergyArgs a) {
         const unsigned long long nh = (unsigned long long)min((int)blockDim.x, n - h0);
         atomicAdd(&a.work[W_E_PAIRS], nh * pairs);
         atomicAdd(&a.work[W_E_MODES], nh * modes);
+    }
+    // With fewer hypotheses than threads, S adjacent lanes share one and
+    // split each pixel's mode scan (every S-th mode); the minimum is exact in
+    // any order, so the partial energy is the same as with one lane.
+    const int nb = min((int)blockDim.x, n - h0);
+    int hb = 1;
+    while (hb < nb) hb <<= 1;
+    const int S = min(32, (int)blockDim.x / hb);
+    if (S > 1) {
+        energy_split(a, b, h0, nb, S, np, s_xc, s_m0, s_m1, s_m2, s_cnt);
+        return;
     }
     const int h = h0 + threadIdx.x;
     if (h >= n) return;
