@@ -392,10 +392,35 @@ def roofline(kernels, work, p, n_frames_profiled, w, sm_count, pk, batch=1):
     return out
 
 
-def kernel_rooflines(kernels, work, p, sm_count, pk):
+# Forest walk (Eq. 1-3): per pixel with depth, 4 B of depth, 3 B of colour
+# and 2 B of leaf index per tree are the algorithmic HBM bytes; each node test
+# is about 8 FP32 operations (offset scale, probe rounding, feature, compare).
+LEAF_OPS_PER_TEST = 8
+
+
+def leaves_roofline(kernels, n_frames, w, pk, fp32_peak):
+    kd = kernels.get("leaves")
+    if not kd or kd["ms"] <= 0:
+        return None
+    s = kd["ms"] / 1e3
+    px = n_frames * w.width * w.height
+    T, depth = w.ransac["n_trees_used"], w.forest["depth"]
+    hbm = (pk["hbm_gbs"] if pk else 6800.0)
+    bytes_ = px * (4 + 3 + 2 * T)
+    flops = px * T * depth * LEAF_OPS_PER_TEST
+    return {"hbm": {"achieved": bytes_ / s / 1e9, "unit": "GB/s", "frac": bytes_ / s / 1e9 / hbm},
+            "fp32": {"achieved": flops / s / 1e12, "unit": "TFLOP/s", "frac": flops / s / 1e12 / fp32_peak},
+            "note": "a gather-latency kernel: neither fraction is its bound"}
+
+
+def kernel_rooflines(kernels, work, p, sm_count, pk, n_frames=None, w=None, accepted=None):
     """Achieved fraction of each kernel with an algorithmic work model."""
     fp32_peak = sm_count * FP32_LANES_PER_SM * 2 * (pk.get("sm_max_mhz", 2070.0) if pk else 2070.0) * 1e6 / 1e12
     out = {}
+    if n_frames and w is not None:
+        lr = leaves_roofline(kernels, n_frames, w, pk, fp32_peak)
+        if lr:
+            out["leaves"] = lr
     for k, kd in kernels.items():
         if not kd["launches"] or kd["ms"] <= 0:
             continue
@@ -407,7 +432,26 @@ def kernel_rooflines(kernels, work, p, sm_count, pk):
         o = algorithmic_int_ops(k, work)
         if o is not None:
             out[k] = {"achieved": o / s / 1e12, "unit": "Tops/s", "frac": o / s / 1e12 / (fp32_peak / 2)}
+            if k == "hypgen":
+                out[k]["attempts_per_s"] = work["hyp_attempts"] / s
+                if accepted is not None:
+                    out[k]["accepted_per_s"] = accepted / s
     return out
+
+
+def end_to_end_roofline(work, p, frames, seconds, sm_count, pk):
+    """FP32 work of the scoring kernels per frame (energy, LM, raycast; the
+    models of algorithmic_flops) against the FP32 peak: the frames/s the
+    device would reach if those flops ran at peak, and the fraction of it
+    achieved.  Generation is integer work and the forest walk a gather, both
+    outside this figure."""
+    fp32_peak = sm_count * FP32_LANES_PER_SM * 2 * (pk.get("sm_max_mhz", 2070.0) if pk else 2070.0) * 1e6
+    flops = sum(algorithmic_flops(k, work, p) or 0.0 for k in ("energy", "lm", "raycast_score"))
+    per_frame = flops / frames
+    roof = fp32_peak / per_frame
+    achieved = frames / seconds
+    return {"flops_per_frame": per_frame, "roofline_frames_per_s": roof, "achieved_frames_per_s": achieved,
+            "frac": achieved / roof}
 
 
 def _success(P, T):
@@ -602,7 +646,9 @@ def run_ours(args):
         "gpu_launches": int(sum(k["launches"] for k in kernels.values())),
         "kernels_ms": {k: round(v["ms"], 4) for k, v in kernels.items()},
         "roofline": roofline(kernels, work, w.ransac, B * args.steps, w, sm_count, pk, batch=B),
-        "kernel_rooflines": kernel_rooflines(kernels, work, w.ransac, sm_count, pk),
+        "kernel_rooflines": kernel_rooflines(kernels, work, w.ransac, sm_count, pk, n_frames=B * args.steps, w=w,
+                                             accepted=args.steps * sum(int(r.n_hypotheses) for r in results)),
+        "roofline_end_to_end": end_to_end_roofline(work, w.ransac, B * args.steps, total_s, sm_count, pk),
         "work_per_step": {k: v // max(1, args.steps) for k, v in work.items()},
         "clocks": clk.summary(),
         "icp_variant": icp,
