@@ -177,3 +177,64 @@ def test_relocalise_with_icp_small_variants_and_batch(rg, ctx):
         rel.close()
     scene.close()
     g.close()
+
+
+def test_cascade_with_icp_levels(rg, ctx):
+    """Sec. 3.2.5 with ICP before ranking on every level: the level that
+    answers, its ICP outputs and its pose match the oracle's cascade (a
+    different level only where a score lies within its tolerance of the
+    threshold)."""
+    w = H.WORKLOADS[H.SMALL]
+    g = H.gpu_model(ctx, w)
+    f, res, modes = H.oracle_model(w.name)
+    room = w.room()
+    scene = rg.Scene(ctx, room.lo, room.hi)
+    lv_params = [(2, dict(w.ransac, **ICP, n_hyp=48, k_out=2)), (1, dict(w.ransac, **ICP))]
+    th = [0.004]
+    levels = [rg.Relocaliser(g, scene, p, w.width // s, w.height // s, 4) for s, p in lv_params]
+    cas = rg.Cascade(levels, th, [s for s, _ in lv_params])
+    qs = [w.query(q) for q in range(4)]
+    out = cas.relocalise_batch(np.stack([q[0] for q in qs]), np.stack([q[1] for q in qs]), w.K, [q[3] for q in qs])
+    lpt = 1 << w.forest["depth"]
+    seen = set()
+    for i, (d, c, T, seed) in enumerate(qs):
+        frames, maps, params = [], [], []
+        for lvl, (s, p) in enumerate(lv_params):
+            ds, cs, Ks = rooms.subsample(d, c, w.K, s) if s > 1 else (d, c, w.K)
+            frames.append((ds, cs, Ks))
+            maps.append(oracle.forest_leaves(f, ds, cs, Ks.fx, n_trees=p["n_trees_used"]))
+            params.append(dict(p, level=lvl))
+        o = oracle.cascade(params, th, frames, maps, modes, room.lo, room.hi, seed, lpt)
+        seen.add(o["level"])
+        if out[i]["level"] != o["level"]:
+            lvl = min(out[i]["level"], o["level"])
+            assert abs(min(out[i]["score"], o["score"]) - th[lvl]) <= 1e-4 + 1e-3 * th[lvl], i
+            continue
+        p = params[o["level"]]
+        # chosen hypotheses compared by slot: a swap at a cut between energies
+        # within 1e-5 can put a different hypothesis in the chosen set
+        gs, os_ = list(out[i]["chosen_slot"]), list(o["chosen_slot"])
+        same = True
+        for gi, sl in enumerate(gs):
+            if sl not in os_:
+                continue
+            oi = os_.index(sl)
+            same &= H.check_icp_one(bool(out[i]["icp_mask"] >> gi & 1), out[i]["chosen_icp_frac"][gi],
+                                    out[i]["chosen_pose"][gi], bool(o["icp_mask"] >> oi & 1),
+                                    o["chosen_icp_frac"][oi], o["chosen_pose"][oi], p["icp_min_frac"],
+                                    f"cascade frame {i} slot {sl}")
+        if gs != os_ or not same:
+            continue
+        tol = H.score_tolerances(out[i]["chosen_pose"], o["chosen_pose"], o["chosen_score"])
+        H.check_scores(out[i]["chosen_score"], o["chosen_score"], tol, f"cascade frame {i}")
+        if out[i]["best"] != o["best"]:  # argmin between near-tied scores
+            a, b = out[i]["best"], o["best"]
+            assert abs(o["chosen_score"][a] - o["chosen_score"][b]) <= tol[a] + tol[b], i
+            continue
+        dt, dr = H.pose_err(out[i]["pose"], o["pose"])
+        assert dt <= H.POSE_T_TOL and dr <= H.POSE_R_TOL, (i, dt, dr)
+    cas.close()
+    for lv in levels:
+        lv.close()
+    scene.close()
+    g.close()
