@@ -238,3 +238,28 @@ def test_cascade_with_icp_levels(rg, ctx):
         lv.close()
     scene.close()
     g.close()
+
+
+def test_every_icp_failing_keeps_the_ransac_pose(rg, ctx):
+    """An inlier radius of 1 um leaves no pair: every chosen pose is
+    discarded (score +inf), the output is the RANSAC pose of chosen index 0
+    with score +inf, and the oracle agrees."""
+    w = H.WORKLOADS[H.SMALL]
+    g = H.gpu_model(ctx, w)
+    scene = rg.Scene(ctx, w.room().lo, w.room().hi)
+    p = dict(w.ransac, **dict(ICP, icp_dist=(1e-6, 1e-6, 1e-6)))
+    rel = rg.Relocaliser(g, scene, p, w.width, w.height, 1)
+    plain = rg.Relocaliser(g, scene, w.ransac, w.width, w.height, 1)
+    for q in range(2):
+        d, c, T, seed = w.query(q)
+        r = rel.relocalise(d, c, w.K, seed)
+        r0 = plain.relocalise(d, c, w.K, seed)
+        assert r["status"] == rg.RL_POSE_FOUND and r["icp_mask"] == 0
+        assert np.isinf(r["score"]) and np.isinf(r["chosen_score"]).all()
+        assert np.array_equal(r["chosen_pose"], r0["chosen_pose"])     # nothing refined
+        assert np.array_equal(r["pose"], r0["chosen_pose"][0])
+        _compare_query(rg, rel, w, q, p)
+    rel.close()
+    plain.close()
+    scene.close()
+    g.close()
