@@ -162,12 +162,17 @@ static rl_status streaming_update(rl_forest *f, int64_t begin, int64_t count, cu
     std::lock_guard<std::mutex> g(f->mu);
     const int back = 1 - f->mode_buf;
     RL_TRY(wait_readers(f, back, s));
-    const ModeStore old_front = front_store(f);
-    set_front_store(f, f->alt);  // the back store becomes the front
+    const ModeStore old_front = front_store(f), old_back = f->alt;
+    set_front_store(f, old_back);  // the back store becomes the front
     f->alt = old_front;
-    RL_TRY(copy_store_range(f, old_front, front_store(f), f->last_begin, f->last_count, s));
-    RL_TRY(update_modes(f, begin, count, s));
-    RL_CK(cudaEventRecord(f->ready, s));
+    rl_status st = copy_store_range(f, old_front, old_back, f->last_begin, f->last_count, s);
+    if (st == RL_OK) st = update_modes(f, begin, count, s);
+    if (st == RL_OK && cudaEventRecord(f->ready, s) != cudaSuccess) st = fail(RL_ERR_CUDA, "event record failed");
+    if (st != RL_OK) {  // keep the previous snapshot in front
+        set_front_store(f, old_front);
+        f->alt = old_back;
+        return st;
+    }
     f->mode_buf = back;
     f->last_begin = begin;
     f->last_count = count;
