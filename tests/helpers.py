@@ -101,6 +101,31 @@ def check_refined_pose(dt, dr, e_gpu, e_ora, what):
     assert len(LM_SEPARATIONS) <= 3, LM_SEPARATIONS
 
 
+SEP_ENERGY_RTOL = 1e-3
+
+
+def lm_separated(gpu_poses, ora_poses, gpu_slots, ora_slots, gpu_E, ora_E, what):
+    """True when a survivor's LM trajectory separated from the oracle's: the
+    same hypothesis at the same rank ends more than 1 mm / 0.05 deg away.
+    After an accept/reject decision falls within FP32 rounding of its
+    threshold, the two trajectories continue from different points of a flat
+    valley of Eq. 5 and end at different poses, so their energies are no
+    longer those of one pose: they must agree within SEP_ENERGY_RTOL, the
+    separation counts toward the session's limit and the comparison of this
+    query stops (what follows from it differs legitimately)."""
+    for i, (sg, so) in enumerate(zip(gpu_slots, ora_slots)):
+        if sg != so:
+            continue
+        dt, dr = pose_err(as44(gpu_poses[i]), as44(ora_poses[i]))
+        if dt <= POSE_T_TOL and dr <= POSE_R_TOL:
+            continue
+        assert abs(gpu_E[i] - ora_E[i]) <= SEP_ENERGY_RTOL * abs(ora_E[i]), (what, i, dt, dr, gpu_E[i], ora_E[i])
+        LM_SEPARATIONS.append((what, dt, dr))
+        assert len(LM_SEPARATIONS) <= 3, LM_SEPARATIONS
+        return True
+    return False
+
+
 def score_tolerances(gpu_poses, ora_poses, ora_scores, max_range=6.0, incidence=10.0):
     """Tolerance of each Eq. 6 score given how far the two sides' poses are
     apart.  The masked mean |D_l - D_synth| is 1-Lipschitz in D_synth, and a
@@ -171,6 +196,9 @@ def compare_results(rg, gr, dbg, orr, params, what):
         assert dbg["round_count"][r] == k
         gs, ge = dbg["round_slot"][r][:k], dbg["round_energy"][r][:k]
         os_, oe = od["round_slot"][off:off + k], od["round_energy"][off:off + k]
+        if lm_separated(dbg["round_pose"][r][:k], od["round_pose"][off:off + k], gs, os_, ge, oe,
+                        f"{what} round {r}"):
+            return
         if not compare_survivors(gs, ge, os_, oe, f"{what} round {r}"):
             return
         for i in range(k):

@@ -263,3 +263,34 @@ def test_every_icp_failing_keeps_the_ransac_pose(rg, ctx):
     plain.close()
     scene.close()
     g.close()
+
+
+def test_config2_batch_of_64_with_icp_sampled(rg, ctx, config2_model):
+    """The launch shape the benchmark's ICP variant times: 64 frames per call
+    with ICP before ranking; frames 5 and 40 recomputed by the oracle."""
+    room = W2.room()
+    scene = rg.Scene(ctx, room.lo, room.hi)
+    p = dict(W2.ransac, **ICP)
+    rel = rg.Relocaliser(config2_model, scene, p, W2.width, W2.height, 64)
+    qs = [W2.query(q) for q in range(16)]
+    seeds = [qs[i % 16][3] + 1000 * (i // 16) for i in range(64)]
+    out = rel.relocalise_batch(np.stack([qs[i % 16][0] for i in range(64)]),
+                               np.stack([qs[i % 16][1] for i in range(64)]), W2.K, seeds)
+    f, res, modes = H.oracle_model(W2.name)
+    for i in (5, 40):
+        d, c, T, _ = qs[i % 16]
+        lv = oracle.forest_leaves(f, d, c, W2.K.fx)
+        o = oracle.relocalise(p, d, c, W2.K, lv, modes, room.lo, room.hi, seeds[i], 1 << W2.forest["depth"])
+        assert out[i]["n_hypotheses"] == o["n_hypotheses"]
+        gs, os_ = list(out[i]["chosen_slot"]), list(o["chosen_slot"])
+        for gi, sl in enumerate(gs):
+            if sl in os_:
+                oi = os_.index(sl)
+                H.check_icp_one(bool(out[i]["icp_mask"] >> gi & 1), out[i]["chosen_icp_frac"][gi],
+                                out[i]["chosen_pose"][gi], bool(o["icp_mask"] >> oi & 1), o["chosen_icp_frac"][oi],
+                                o["chosen_pose"][oi], p["icp_min_frac"], f"frame {i} slot {sl}")
+        if gs == os_ and out[i]["best"] == o["best"]:
+            dt, dr = H.pose_err(out[i]["pose"], o["pose"])
+            assert dt <= H.POSE_T_TOL and dr <= H.POSE_R_TOL, (i, dt, dr)
+    rel.close()
+    scene.close()

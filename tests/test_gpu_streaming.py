@@ -167,3 +167,50 @@ def test_tracking_loss_protocol_parity(rg, ctx):
     rel.close()
     scene.close()
     g.close()
+
+
+def test_tracking_loss_step_config2(rg, ctx):
+    """Paper-sized tracking-loss step: a five-tree depth-15 forest from
+    empty leaves adapts three frames of a fresh trajectory (65,536 leaves
+    re-clustered per frame, double-buffered), then relocalises the fourth;
+    modes and the relocalisation against the oracle on the same state."""
+    import math
+    import torch
+    from synth import rooms, workloads
+    w = workloads.CONFIG2
+    room = w.room()
+    poses = rooms.training_trajectory(room, 4, seed=21)
+    frames = [rooms.render(room, w.K, T, w.noise_sigma, noise_seed=60000 + t) + (T,) for t, T in enumerate(poses)]
+    step = 65536
+    g = rg.Forest.random(ctx, w.forest, w.forest_seed)
+    g.set_streaming(True)
+    scene = rg.Scene(ctx, room.lo, room.hi)
+    rel = rg.Relocaliser(g, scene, w.ransac, w.width, w.height, 1)
+    f = H.oracle_forest_nodes(w)
+    res = oracle.Reservoirs(f, w.forest["kappa"], w.forest_seed)
+    modes = oracle.Modes(res.n_leaves, w.forest["m_max"])
+    kw = dict(cov_eps=w.forest["cov_eps"], fp16_offsets=bool(w.forest["mode_precision"]))
+    sT = torch.cuda.Stream()
+    cursor = 0
+    for d, c, T in frames[:3]:
+        g.adapt(torch.from_numpy(d).cuda(), torch.from_numpy(c).cuda(), w.K, T, stream=sT)
+        g.update_modes(step, stream=sT)
+        res.add_frame(d, c, w.K, T, w.forest["grid_step"], w.forest["grid_origin"])
+        oracle.update_modes(res, modes, w.forest["sigma"], w.forest["tau_c"], w.forest["min_cluster_size"],
+                            leaf_begin=cursor, leaf_count=step, **kw)
+        cursor = (cursor + step) % res.n_leaves
+    torch.cuda.synchronize()
+    e = g.export()
+    assert np.array_equal(e["nmodes"], modes.nmodes)
+    mm = np.arange(w.forest["m_max"])[None, :] < modes.nmodes[:, None]
+    assert np.array_equal(e["mode_pos"][mm].view(np.uint32), modes.pos[mm].view(np.uint32))
+    d, c, T = frames[3]
+    seed = 123457
+    gr = rel.relocalise(d, c, w.K, seed)
+    lv = oracle.forest_leaves(f, d, c, w.K.fx)
+    orr = oracle.relocalise(w.ransac, d, c, w.K, lv, modes, room.lo, room.hi, seed, 1 << w.forest["depth"],
+                            debug=True)
+    H.compare_results(rg, gr, rel.debug(0), orr, w.ransac, "config2 tracking-loss frame 3")
+    rel.close()
+    scene.close()
+    g.close()
