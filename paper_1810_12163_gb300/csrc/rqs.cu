@@ -7,10 +7,12 @@
 // from FP64 exp, squared distances in FP64.  GB300 runs FP64 at about 1/64 of
 // its FP32 rate, so the O(n^2) loops run in FP32 with a certified error bound
 // and fall back to the FP64 value only where the bound cannot decide:
-//  - densities: FP32 expf of an FP32 argument, FP32 partial sums of 32 terms
-//    added in FP64; |rho32 - rho64| <= n 8e-7 + 1e-5 rho (expf within 4 ulp,
-//    the argument within 8 ulp relative, partial sums within 31 ulp: each
-//    bound doubled);
+//  - densities: FP32 expf of an FP32 argument x, each row summed with
+//    Kahan compensation; with t = exp(x), S = sum of t |x| (summed alongside)
+//    and rho the density, |rho32 - rho64| <= 9.6e-7 S + 1.32e-6 rho: expf
+//    within 4 ulp (4.8e-7 relative) and x within 8 ulp relative (4.8e-7 |x|,
+//    so 4.8e-7 t |x| per term), the compensated sum within 2 ulp of rho and
+//    the final rounding to float within 0.5 ulp, all doubled;
 //  - a density comparison whose difference lies within the two bounds marks
 //    both points; their FP64 densities are then computed exactly as the
 //    definition does and the parents of the affected points are recomputed;
@@ -148,19 +150,19 @@ __global__ void __launch_bounds__(256) k_rqs(RqsArgs a) {
     const float c32 = (float)a.inv2s2;
     for (int i = tid; i < n; i += nt) {
         const float4 pi = pts[i];
-        double r = 0.0;
-        float part = 0.f;
+        float sum = 0.f, comp = 0.f, sx = 0.f;  // Kahan sum of t, plain sum of t |x|
         for (int j = 0; j < n; ++j) {
-            part += expf(-(dist2f(pi, pts[j]) * c32));
-            if ((j & 31) == 31) {
-                r += (double)part;
-                part = 0.f;
-            }
+            const float x = dist2f(pi, pts[j]) * c32;
+            const float t = expf(-x);
+            sx += t * x;
+            const float yk = t - comp;
+            const float tk = sum + yk;
+            comp = (tk - sum) - yk;
+            sum = tk;
         }
-        r += (double)part;
-        rho[i] = r;
-        rhof[i] = (float)r;
-        err[i] = (float)((double)n * 8e-7 + 1.02e-5 * r);  // + 2^-23 r for the rounding to float
+        rho[i] = (double)sum;
+        rhof[i] = sum;
+        err[i] = 9.6e-7f * sx + 1.32e-6f * sum + 1e-30f * (float)n;
         need64[i] = 0;
     }
     if (tid == 0) any64 = 0;
