@@ -53,7 +53,7 @@ constexpr uint32_t kWaitLimit = 1u << 22;
 
 struct LmcLayout {
     uint32_t t0, t1, t2, xc, cnt, stage, tx;
-    uint32_t H, Hn, lambda, tot, nw, loc, state, cbuf, flag, bar, total;
+    uint32_t H, Hn, Pf, lambda, tot, nw, loc, state, cbuf, flag, bar, total;
 };
 
 __host__ __device__ inline uint32_t lmc_a16(uint32_t x) { return (x + 15u) & ~15u; }
@@ -77,6 +77,7 @@ __host__ __device__ inline LmcLayout lmc_layout(int stride, bool cov) {
     o = lmc_a16(stages > partials ? stages : partials);
     L.H = o; o += LMC_HMAX * 12 * 8;
     L.Hn = o; o += LMC_HMAX * 12 * 8;
+    L.Pf = o; o += LMC_HMAX * 12 * 4;
     L.lambda = o; o += LMC_HMAX * 8;
     L.tot = o; o += LMC_HMAX * LMC_NV * 4;
     L.nw = o; o += LMC_HMAX * LMC_NV * 4;
@@ -157,6 +158,7 @@ __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 
     float *s_acc = (float *)smem;
     double(*s_H)[12] = (double(*)[12])(smem + L.H);
     double(*s_Hn)[12] = (double(*)[12])(smem + L.Hn);
+    float(*s_Pf)[12] = (float(*)[12])(smem + L.Pf);  // FP32 copy of the pose of the next pass
     double *s_lambda = (double *)(smem + L.lambda);
     float(*s_tot)[LMC_NV] = (float(*)[LMC_NV])(smem + L.tot);
     float(*s_new)[LMC_NV] = (float(*)[LMC_NV])(smem + L.nw);
@@ -181,7 +183,11 @@ __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 
     const int my_tiles = crank < n_tiles ? (n_tiles - crank + LMC_CTAS - 1) / LMC_CTAS : 0;
     const float thr2 = (float)(a.p.lm_inlier_thresh * a.p.lm_inlier_thresh);
 
-    for (int i = t; i < n * 12; i += LMC_THREADS) s_H[i / 12][i % 12] = a.q.cur_pose[((size_t)b * NC + i / 12) * 12 + i % 12];
+    for (int i = t; i < n * 12; i += LMC_THREADS) {
+        const double v = a.q.cur_pose[((size_t)b * NC + i / 12) * 12 + i % 12];
+        s_H[i / 12][i % 12] = v;
+        s_Pf[i / 12][i % 12] = (float)v;
+    }
     for (int i = t; i < n; i += LMC_THREADS) {
         s_lambda[i] = a.p.lm_lambda0;
         s_state[i] = 1;
@@ -326,7 +332,7 @@ __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 
         cw[ci] = (int16_t)best_m;  // local mode index in the row, -1: none
     };
     // The pass; act: this thread's hypothesis takes part, P: its pose.
-    auto pass = [&](bool act, const double *P, bool trial, int rbuf, int wbuf) {
+    auto pass = [&](bool act, const float *P, bool trial, int rbuf, int wbuf) {
         LmcPass o;
 #pragma unroll
         for (int k = 0; k < 28; ++k) o.acc[k] = 0.f;
@@ -335,9 +341,9 @@ __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 
         float r00 = 0.f, r01 = 0.f, r02 = 0.f, tx = 0.f, r10 = 0.f, r11 = 0.f, r12 = 0.f, ty = 0.f;
         float r20 = 0.f, r21 = 0.f, r22 = 0.f, tz = 0.f;
         if (act) {
-            r00 = (float)P[0]; r01 = (float)P[1]; r02 = (float)P[2]; tx = (float)P[3];
-            r10 = (float)P[4]; r11 = (float)P[5]; r12 = (float)P[6]; ty = (float)P[7];
-            r20 = (float)P[8]; r21 = (float)P[9]; r22 = (float)P[10]; tz = (float)P[11];
+            r00 = P[0]; r01 = P[1]; r02 = P[2]; tx = P[3];
+            r10 = P[4]; r11 = P[5]; r12 = P[6]; ty = P[7];
+            r20 = P[8]; r21 = P[9]; r22 = P[10]; tz = P[11];
         }
         const int16_t *cr = corr0 + (size_t)rbuf * cstride;
         int16_t *cw = corr0 + (size_t)wbuf * cstride;
@@ -490,15 +496,17 @@ __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 
 
     // normal equations and correspondences at the initial poses
     {
-        const LmcPass o = pass(mine, s_H[hl < n ? hl : 0], false, 0, 0);
+        const LmcPass o = pass(mine, s_Pf[hl < n ? hl : 0], false, 0, 0);
         reduce(o, 0, s_tot);
     }
     for (int it = 0; it < a.p.lm_max_iter; ++it) {
-        // damped FP64 solve; hypothesis h on thread (h % 8) * 32 + h / 8,
-        // spreading the narrow FP64 pipe's work over all warps
+        // damped FP64 solve; hypothesis h on lane h / 4 of warp h % 4.  Each
+        // SM sub-partition has its own narrow FP64 pipe, which a warp
+        // instruction holds for the same time whatever its active lanes: one
+        // warp on each of the four sub-partitions is the shortest schedule.
         {
-            const int h = (t & 31) * 8 + (t >> 5);
-            if ((t & 31) < LMC_HMAX / 8 && h < n && s_state[h]) {
+            const int h = (t & 31) * 4 + (t >> 5);
+            if (t < 128 && (t & 31) < LMC_HMAX / 4 && h < n && s_state[h]) {
                 const float *T = s_tot[h];
                 bool stop = T[28] < 3.f;
                 double step[6];
@@ -525,7 +533,10 @@ __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 
                     double Hn[12];
                     for (int i = 0; i < 12; ++i) Hn[i] = s_H[h][i];
                     se3_left(step, Hn);
-                    for (int i = 0; i < 12; ++i) s_Hn[h][i] = Hn[i];
+                    for (int i = 0; i < 12; ++i) {
+                        s_Hn[h][i] = Hn[i];
+                        s_Pf[h][i] = (float)Hn[i];
+                    }
                 }
             }
         }
@@ -540,7 +551,7 @@ __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 
         // normal equations at the trial pose (used if the step is accepted)
         const bool act = mine && s_state[hl];
         const int ob = act ? s_cbuf[hl] : 0;
-        const LmcPass o = pass(act, s_Hn[hl < n ? hl : 0], true, ob, ob ^ 1);
+        const LmcPass o = pass(act, s_Pf[hl < n ? hl : 0], true, ob, ob ^ 1);
         reduce(o, (it + 1) & 1, s_new);
         for (int h = t; h < n; h += LMC_THREADS) {
             if (!s_state[h]) continue;

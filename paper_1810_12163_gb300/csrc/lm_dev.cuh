@@ -41,7 +41,8 @@ __device__ __forceinline__ void lm_accumulate(float y0, float y1, float y2, floa
 }
 
 // Solves A x = b for symmetric positive definite A (row-major 6x6) by
-// Cholesky, with one reciprocal per pivot instead of a division per entry.
+// Cholesky.  One reciprocal square root per pivot gives both the pivot
+// (s / sqrt s) and its reciprocal, so no entry needs a division.
 __device__ __forceinline__ bool chol_solve6(const double A[36], const double b[6], double x[6]) {
     double L[36], inv[6];
 #pragma unroll
@@ -53,8 +54,9 @@ __device__ __forceinline__ bool chol_solve6(const double A[36], const double b[6
             for (int k = 0; k < j; ++k) s -= L[6 * i + k] * L[6 * j + k];
             if (i == j) {
                 if (!(s > 0.0)) return false;
-                L[6 * i + i] = sqrt(s);
-                inv[i] = 1.0 / L[6 * i + i];
+                const double rs = rsqrt(s);
+                L[6 * i + i] = s * rs;
+                inv[i] = rs;
             } else {
                 L[6 * i + j] = s * inv[j];
             }
