@@ -1,9 +1,14 @@
 // Levenberg-Marquardt refinement of a preemptive round (Sec. 3.2.3) with one
 // thread-block cluster per frame.
 //
-// The LMC_CTAS CTAs of a cluster share the frame's surviving hypotheses
+// The CTAS CTAs of a cluster share the frame's surviving hypotheses
 // (n <= 64) and split its pixel set by tiles of LMC_P pixels: CTA c takes
-// tiles c, c + LMC_CTAS, ...  A pass streams the CTA's tiles of the mode
+// tiles c, c + CTAS, ...  The first round (most hypotheses, fewest pixels)
+// uses clusters of 4; later rounds have few hypotheses and up to 3.5x the
+// pixels, and a frame's LM there is a chain of passes whose length is set by
+// its slowest hypothesis, so they use clusters of 8 to shorten each pass.
+// The cluster size is a function of the round alone, so a frame's results
+// do not depend on the batch it runs in.  A pass streams the CTA's tiles of the mode
 // table (rows of decoded M(u)) into shared memory with bulk asynchronous
 // copies on an mbarrier pipeline; thread t works for hypothesis t % HB on
 // pixel group t / HB (HB = next power of two >= n), so the lanes of a warp
@@ -42,7 +47,8 @@ namespace rl {
 
 namespace cg = cooperative_groups;
 
-constexpr int LMC_CTAS = 4;
+constexpr int LMC_CTAS_FIRST = 4;  // cluster size of the first preemptive round
+constexpr int LMC_CTAS_LATER = 8;  // and of the later rounds
 constexpr int LMC_THREADS = 256;
 constexpr int LMC_P = 16;        // pixels per tile (max_pix is a multiple)
 constexpr int LMC_STAGES = 2;
@@ -133,7 +139,8 @@ struct LmcPass {
     float trial;
 };
 
-__global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k_lm_cluster(LmArgs a) {
+template <int CTAS>
+__global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k_lm_cluster(LmArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     cg::cluster_group cluster = cg::this_cluster();
     const int crank = (int)cluster.block_rank();
@@ -180,7 +187,7 @@ __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 
     int16_t *corr0 = (int16_t *)(a.q.corr + (size_t)b * NC * a.p.max_pix);
     const size_t cstride = (size_t)NC * a.p.max_pix;
     const int n_tiles = (a.n_pix + LMC_P - 1) / LMC_P;
-    const int my_tiles = crank < n_tiles ? (n_tiles - crank + LMC_CTAS - 1) / LMC_CTAS : 0;
+    const int my_tiles = crank < n_tiles ? (n_tiles - crank + CTAS - 1) / CTAS : 0;
     const float thr2 = (float)(a.p.lm_inlier_thresh * a.p.lm_inlier_thresh);
 
     for (int i = t; i < n * 12; i += LMC_THREADS) {
@@ -205,7 +212,7 @@ __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 
     auto issue = [&](int j, int s) {
         const uint32_t bar = bar0 + 8 * s;
         const uint32_t st = sbase + s * L.stage;
-        const size_t r = (size_t)(crank + j * LMC_CTAS) * LMC_P;  // first row of the tile
+        const size_t r = (size_t)(crank + j * CTAS) * LMC_P;  // first row of the tile
         const uint32_t rows = (uint32_t)LMC_P * stride;
         mbar_expect_tx(bar, L.tx);
         bulk_g2s(st + L.t0, g_t0 + r * stride, rows * 16, bar);
@@ -230,7 +237,7 @@ __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 
         const float *s_t2 = (const float *)(st + L.t2);
         const float4 *s_xc = (const float4 *)(st + L.xc);
         const int16_t *s_cnt = (const int16_t *)(st + L.cnt);
-        const int i0 = (crank + j * LMC_CTAS) * LMC_P;
+        const int i0 = (crank + j * CTAS) * LMC_P;
         const int il = g;
         const bool on = live && il < min(LMC_P, a.n_pix - i0);
         const int cnt = on ? (int)s_cnt[il] : 0;
@@ -371,7 +378,7 @@ __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 
                 const float *s_t2 = (const float *)(st + L.t2);
                 const float4 *s_xc = (const float4 *)(st + L.xc);
                 const int16_t *s_cnt = (const int16_t *)(st + L.cnt);
-                const int i0 = (crank + j * LMC_CTAS) * LMC_P;
+                const int i0 = (crank + j * CTAS) * LMC_P;
                 const int np = min(LMC_P, a.n_pix - i0);
                 for (int il = g; il < np; il += Gp) {
                     const size_t ci = (size_t)(i0 + il) * n + hl;
@@ -488,7 +495,7 @@ __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 
         cluster.sync();
         for (int e = t; e < n * LMC_NV; e += LMC_THREADS) {
             float v = 0.f;
-            for (int r = 0; r < LMC_CTAS; ++r) v += cluster.map_shared_rank(loc, r)[e];
+            for (int r = 0; r < CTAS; ++r) v += cluster.map_shared_rank(loc, r)[e];
             dst[e / LMC_NV][e % LMC_NV] = v;
         }
         __syncthreads();
@@ -585,14 +592,24 @@ __global__ void __cluster_dims__(LMC_CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 
 size_t lm_cluster_smem(int mpad, bool cov) { return lmc_layout(mpad, cov).total; }
 
 rl_status launch_lm_cluster(const LmArgs &a, int n, cudaStream_t s) {
-    dim3 grid(LMC_CTAS, n);
-    k_lm_cluster<<<grid, LMC_THREADS, lm_cluster_smem(a.p.mpad, a.p.use_cov), s>>>(a);
+    const size_t sm = lm_cluster_smem(a.p.mpad, a.p.use_cov);
+    const bool first = a.n_pix <= 2 * a.p.eta;  // round r refines on eta * (r + 2) pixels
+    if (first) {
+        k_lm_cluster<LMC_CTAS_FIRST><<<dim3(LMC_CTAS_FIRST, n), LMC_THREADS, sm, s>>>(a);
+    } else {
+        k_lm_cluster<LMC_CTAS_LATER><<<dim3(LMC_CTAS_LATER, n), LMC_THREADS, sm, s>>>(a);
+    }
     RL_LAUNCH_CK();
     return RL_OK;
 }
 
 rl_status prepare_lm_cluster() {
-    RL_CK(cudaFuncSetAttribute(k_lm_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLmClusterSmemMax));
+    RL_CK(cudaFuncSetAttribute(k_lm_cluster<LMC_CTAS_FIRST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kLmClusterSmemMax));
+    RL_CK(cudaFuncSetAttribute(k_lm_cluster<LMC_CTAS_LATER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kLmClusterSmemMax));
+    if (LMC_CTAS_LATER > 8)  // clusters above 8 CTAs are not portable and must be allowed explicitly
+        RL_CK(cudaFuncSetAttribute(k_lm_cluster<LMC_CTAS_LATER>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     return RL_OK;
 }
 
