@@ -10,9 +10,12 @@
 // The cluster size is a function of the round alone, so a frame's results
 // do not depend on the batch it runs in.  A pass streams the CTA's tiles of the mode
 // table (rows of decoded M(u)) into shared memory with bulk asynchronous
-// copies on an mbarrier pipeline; thread t works for hypothesis t % HB on
-// pixel group t / HB (HB = next power of two >= n), so the lanes of a warp
-// mostly read the same staged row (broadcast) and share control flow.  Per
+// copies on an mbarrier pipeline.  A pass covers the hypotheses still
+// iterating, listed in increasing order: thread t works for list entry
+// t % HB on pixel group t / HB (HB = next power of two >= their count), so
+// the lanes of a warp mostly read the same staged row (broadcast) and share
+// control flow, and the passes after most hypotheses have stopped spread the
+// few remaining ones over all lanes.  Per
 // (hypothesis, pixel) a pass finds the nearest mode under the pixel's
 // Mahalanobis metric, keeps it if within the inlier radius and adds its
 // terms to FP32 normal equations.
@@ -59,7 +62,7 @@ constexpr uint32_t kWaitLimit = 1u << 22;
 
 struct LmcLayout {
     uint32_t t0, t1, t2, xc, cnt, stage, tx;
-    uint32_t H, Hn, Pf, lambda, tot, nw, loc, state, cbuf, flag, bar, total;
+    uint32_t H, Hn, Pf, lambda, tot, nw, loc, state, cbuf, act, flag, bar, total;
 };
 
 __host__ __device__ inline uint32_t lmc_a16(uint32_t x) { return (x + 15u) & ~15u; }
@@ -90,6 +93,7 @@ __host__ __device__ inline LmcLayout lmc_layout(int stride, bool cov) {
     L.loc = o; o += 2 * LMC_HMAX * LMC_NV * 4;
     L.state = o; o += LMC_HMAX * 4;
     L.cbuf = o; o += LMC_HMAX * 4;
+    L.act = o; o += LMC_HMAX * 4 + 16;  // list, then its length
     L.flag = o; o += 16;
     L.bar = o; o += LMC_STAGES * 8;
     L.total = lmc_a16(o);
@@ -150,17 +154,7 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
     const bool cov = a.p.use_cov;
     const int stride = a.p.mpad;
     const LmcLayout L = lmc_layout(stride, cov);
-    int HB = 1;
-    while (HB < n) HB <<= 1;
-    const int G = LMC_THREADS / HB;
-    // With fewer than 16 hypotheses a tile has fewer (hypothesis, pixel)
-    // pairs than threads: S adjacent lanes then share a pair and split its
-    // mode scan (every S-th mode), and the nearest mode is found by a
-    // shuffle reduction (ties: lower index, as a sequential scan finds it).
-    const int S = G > LMC_P ? G / LMC_P : 1;
-    const int Gp = G / S;  // pixel groups
-    const int t = threadIdx.x, sub = t % S, hl = (t / S) % HB, g = (t / S) / HB;
-    const bool mine = hl < n;
+    const int t = threadIdx.x;
 
     float *s_acc = (float *)smem;
     double(*s_H)[12] = (double(*)[12])(smem + L.H);
@@ -172,6 +166,8 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
     float *s_loc = (float *)(smem + L.loc);  // two buffers of [LMC_HMAX][LMC_NV]
     int *s_state = (int *)(smem + L.state);
     int *s_cbuf = (int *)(smem + L.cbuf);
+    int *s_act = (int *)(smem + L.act);  // hypotheses of the next pass, increasing
+    int *s_nact = s_act + LMC_HMAX;      // and their count
     volatile int *s_abort = (volatile int *)(smem + L.flag);
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
     const uint32_t bar0 = sbase + L.bar;
@@ -190,6 +186,28 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
     const int my_tiles = crank < n_tiles ? (n_tiles - crank + CTAS - 1) / CTAS : 0;
     const float thr2 = (float)(a.p.lm_inlier_thresh * a.p.lm_inlier_thresh);
 
+    // Lane roles of a pass over the k hypotheses listed in s_act: list entry
+    // hs = (t / S) % HB on pixel group g = (t / S) / HB.  With fewer than 16
+    // hypotheses a tile has fewer (hypothesis, pixel) pairs than threads: S
+    // adjacent lanes then share a pair and split its mode scan (every S-th
+    // mode), and the nearest mode is found by a shuffle reduction (ties: lower
+    // index, as a sequential scan finds it).  hl: the hypothesis served.
+    int HB = 1, S = 1, Gp = 1, sub = 0, hs = 0, g = 0, hl = 0, k_act = 0;
+    bool mine = false;
+    auto roles = [&](int k) {
+        k_act = k;
+        HB = 1;
+        while (HB < k) HB <<= 1;
+        const int G = LMC_THREADS / HB;
+        S = G > LMC_P ? G / LMC_P : 1;
+        Gp = G / S;  // pixel groups
+        sub = t % S;
+        hs = (t / S) % HB;
+        g = (t / S) / HB;
+        mine = hs < k;
+        hl = mine ? s_act[hs] : 0;
+    };
+
     for (int i = t; i < n * 12; i += LMC_THREADS) {
         const double v = a.q.cur_pose[((size_t)b * NC + i / 12) * 12 + i % 12];
         s_H[i / 12][i % 12] = v;
@@ -198,6 +216,7 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
     for (int i = t; i < n; i += LMC_THREADS) {
         s_lambda[i] = a.p.lm_lambda0;
         s_state[i] = 1;
+        s_act[i] = i;
         s_cbuf[i] = 0;
     }
     if (t == 0) {
@@ -208,7 +227,8 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
     __syncthreads();
 
     // thread 0 is the producer: my j-th tile into stage s
-    uint32_t issued[LMC_STAGES] = {}, waited[LMC_STAGES] = {};
+    // per stage: copies issued (thread 0), phases consumed, phases seen complete
+    uint32_t issued[LMC_STAGES] = {}, waited[LMC_STAGES] = {}, landed[LMC_STAGES] = {};
     auto issue = [&](int j, int s) {
         const uint32_t bar = bar0 + 8 * s;
         const uint32_t st = sbase + s * L.stage;
@@ -364,9 +384,13 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
             const int s = j % LMC_STAGES;
             const uint32_t parity = waited[s] & 1u;
             ++waited[s];
-            if (!*s_abort && !mbar_wait_bounded(bar0 + 8 * s, parity)) {
-                *s_abort = 1;
-                a.q.dev_err[b] = 1;
+            if (!*s_abort) {
+                if (mbar_wait_bounded(bar0 + 8 * s, parity)) {
+                    ++landed[s];
+                } else {
+                    *s_abort = 1;
+                    a.q.dev_err[b] = 1;
+                }
             }
             if (S > 1) {
                 split_tile(act && !*s_abort, s, j, trial, cr, cw, o, r00, r01, r02, tx, r10, r11, r12, ty, r20, r21,
@@ -482,28 +506,30 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
         mypart[29] = o.trial;
         __syncthreads();
         float *loc = s_loc + lb * (LMC_HMAX * LMC_NV);
-        for (int e = t; e < n * LMC_NV; e += LMC_THREADS) {
-            const int h = e / LMC_NV, k = e % LMC_NV;
+        for (int e = t; e < k_act * LMC_NV; e += LMC_THREADS) {
+            const int j = e / LMC_NV, k = e % LMC_NV;
             float v = 0.f;
-            // the lanes holding hypothesis h's partials, in group order
-            for (int gg = 0; gg < Gp; ++gg) v += s_acc[(S * (gg * HB + h)) * LMC_PS + k];
-            loc[e] = v;
+            // the lanes holding list entry j's partials, in group order
+            for (int gg = 0; gg < Gp; ++gg) v += s_acc[(S * (gg * HB + j)) * LMC_PS + k];
+            loc[s_act[j] * LMC_NV + k] = v;
         }
         // Double-buffered loc: a CTA rewrites buffer lb two reductions later,
         // after the next barrier, which every CTA reaches only after reading
         // buffer lb here; one barrier per reduction suffices.
         cluster.sync();
-        for (int e = t; e < n * LMC_NV; e += LMC_THREADS) {
+        for (int e = t; e < k_act * LMC_NV; e += LMC_THREADS) {
+            const int h = s_act[e / LMC_NV], k = e % LMC_NV;
             float v = 0.f;
-            for (int r = 0; r < CTAS; ++r) v += cluster.map_shared_rank(loc, r)[e];
-            dst[e / LMC_NV][e % LMC_NV] = v;
+            for (int r = 0; r < CTAS; ++r) v += cluster.map_shared_rank(loc, r)[h * LMC_NV + k];
+            dst[h][k] = v;
         }
         __syncthreads();
     };
 
     // normal equations and correspondences at the initial poses
     {
-        const LmcPass o = pass(mine, s_Pf[hl < n ? hl : 0], false, 0, 0);
+        roles(n);
+        const LmcPass o = pass(mine, s_Pf[hl], false, 0, 0);
         reduce(o, 0, s_tot);
     }
     for (int it = 0; it < a.p.lm_max_iter; ++it) {
@@ -553,12 +579,22 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
         // and the cluster barriers stay paired (a CTA that left the loop alone
         // would be read through distributed shared memory after it exits).
         __syncthreads();
-        if (!__syncthreads_or(mine && s_state[hl])) break;  // identical in every CTA
+        if (!__syncthreads_or(t < n && s_state[t])) break;  // identical in every CTA
+        // list the hypotheses still iterating (the same list in every CTA)
+        if (t < 32) {
+            const bool on0 = t < n && s_state[t], on1 = t + 32 < n && s_state[t + 32];
+            const unsigned m0 = __ballot_sync(0xffffffffu, on0), m1 = __ballot_sync(0xffffffffu, on1);
+            const unsigned below = (1u << t) - 1u;
+            if (on0) s_act[__popc(m0 & below)] = t;
+            if (on1) s_act[__popc(m0) + __popc(m1 & below)] = t + 32;
+            if (t == 0) *s_nact = __popc(m0) + __popc(m1);
+        }
+        __syncthreads();
+        roles(*s_nact);
         // trial cost of the step on the current correspondences, and the
         // normal equations at the trial pose (used if the step is accepted)
-        const bool act = mine && s_state[hl];
-        const int ob = act ? s_cbuf[hl] : 0;
-        const LmcPass o = pass(act, s_Pf[hl < n ? hl : 0], true, ob, ob ^ 1);
+        const int ob = mine ? s_cbuf[hl] : 0;
+        const LmcPass o = pass(mine, s_Pf[hl], true, ob, ob ^ 1);
         reduce(o, (it + 1) & 1, s_new);
         for (int h = t; h < n; h += LMC_THREADS) {
             if (!s_state[h]) continue;
@@ -577,7 +613,7 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
     if (crank == 0)
         for (int i = t; i < n * 12; i += LMC_THREADS)
             a.q.cur_pose[((size_t)b * NC + i / 12) * 12 + i % 12] = s_H[i / 12][i % 12];
-    if (a.work && mine) {
+    if (a.work && (w_pairs | w_modes | w_in | w_trial)) {
         atomicAdd(&a.work[W_LM_PAIRS], (unsigned long long)w_pairs);
         atomicAdd(&a.work[W_LM_MODES], (unsigned long long)w_modes);
         atomicAdd(&a.work[W_LM_INLIERS], (unsigned long long)w_in);
@@ -585,7 +621,7 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
     }
     if (t == 0 && *s_abort)  // copies still in flight must land before the CTA exits
         for (int s = 0; s < LMC_STAGES; ++s)
-            if (issued[s] > waited[s]) mbar_wait_bounded(bar0 + 8 * s, (issued[s] - 1) & 1u);
+            while (landed[s] < issued[s] && mbar_wait_bounded(bar0 + 8 * s, landed[s] & 1u)) ++landed[s];
     cluster.sync();  // no CTA leaves while another may still read its shared memory
 }
 
