@@ -110,6 +110,10 @@ def _declare(L):
     L.orc_update_modes.argtypes = [P, P, P, I32, I32, I32, I32, F32, F32, I32, I32, F32, I32,
                                    P, P, P, P, P, P]
     L.orc_kabsch.argtypes = [P, P, I32, P, P]
+    L.orc_chol_solve6.argtypes = [P, P, P]
+    L.orc_chol_solve6.restype = I32
+    L.orc_se3_left_update.argtypes = [P, P]
+    L.orc_se3_left_update.restype = None
     L.orc_energy.argtypes = [P, P, I32, P, I32, I32, F32, F32, F32, F32, P, I32, I32,
                              P, P, P, I32, I32, I32]
     L.orc_energy.restype = F64
@@ -257,6 +261,25 @@ def kabsch(a, b):
     t = np.zeros(3)
     lib().orc_kabsch(_p(a), _p(b), a.shape[0], _p(R), _p(t))
     return R.reshape(3, 3), t
+
+
+def chol_solve6(A, b):
+    """Solves A x = b for a symmetric positive-definite 6x6 A (the damped
+    normal equations of the LM step, Sec. 3.2.3); None when A is not positive
+    definite."""
+    A = _c(A, np.float64)
+    b = _c(b, np.float64)
+    x = np.zeros(6)
+    return x if lib().orc_chol_solve6(_p(A), _p(b), _p(x)) else None
+
+
+def se3_left_update(xi, pose):
+    """exp(xi^) H for xi = (v, w) in se(3), the LM pose update of Sec. 3.2.3;
+    pose is 4x4 (or 3x4) camera->world, the result 4x4."""
+    H = np.array(np.asarray(pose, np.float64)[:3, :4], dtype=np.float64, order="C", copy=True)
+    xi = _c(xi, np.float64)
+    lib().orc_se3_left_update(_p(xi), _p(H))
+    return np.vstack([H, [0.0, 0.0, 0.0, 1.0]])
 
 
 PARAM_DEFAULTS = dict(

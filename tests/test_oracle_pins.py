@@ -200,6 +200,46 @@ def _brute_energy(H4, pix, depth, K, leaves, modes, S_all, k_top, use_cov, lpt):
     return E
 
 
+def _twist(xi):
+    v, w = np.asarray(xi[:3], float), np.asarray(xi[3:], float)
+    X = np.zeros((4, 4))
+    X[:3, :3] = [[0, -w[2], w[1]], [w[2], 0, -w[0]], [-w[1], w[0], 0]]
+    X[:3, 3] = v
+    return X
+
+
+@pytest.mark.parametrize("theta", [0.0, 1e-9, 1e-3, 0.3, 2.5])
+def test_se3_left_update_is_the_matrix_exponential(theta):
+    """The LM update exp(xi^) H of Sec. 3.2.3 against scipy's matrix
+    exponential of the 4x4 twist: a non-identity H tells a left update from a
+    right one, distinct v and w tell their order, and the angles span the
+    small-angle branch and the closed form."""
+    expm = pytest.importorskip("scipy.linalg").expm
+    rng = np.random.default_rng(7)
+    H0 = np.eye(4)
+    H0[:3, :3] = _rot(rng.normal(size=3), 0.7)
+    H0[:3, 3] = [1.5, -0.4, 2.0]
+    axis = rng.normal(size=3)
+    xi = np.concatenate([[0.03, -0.02, 0.05], theta * axis / np.linalg.norm(axis)])
+    got = oracle.se3_left_update(xi, H0)
+    want = expm(_twist(xi)) @ H0
+    assert np.abs(got - want).max() < 1e-12
+    np.testing.assert_allclose(got[:3, :3] @ got[:3, :3].T, np.eye(3), atol=1e-12)
+
+
+def test_cholesky_solve_matches_numpy_and_rejects_indefinite():
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        M = rng.normal(size=(6, 6))
+        A = M @ M.T + 0.1 * np.eye(6)
+        b = rng.normal(size=6)
+        x = oracle.chol_solve6(A, b)
+        np.testing.assert_allclose(x, np.linalg.solve(A, b), rtol=1e-9, atol=1e-12)
+    A = np.diag([1.0, 2.0, 3.0, -1e-3, 5.0, 6.0])
+    assert oracle.chol_solve6(A, np.ones(6)) is None
+    assert oracle.chol_solve6(np.zeros((6, 6)), np.ones(6)) is None
+
+
 def test_energy_brute_force():
     rng = np.random.default_rng(3)
     depth, leaves, modes, S_all = _tiny_model(rng)
@@ -614,6 +654,38 @@ def test_generation_rederived_with_independent_philox(small_run):
             Rh, th = _horn(*pair)
             P = r["debug"]["hyp_pose"][slot].reshape(3, 4)
             assert np.abs(P[:, :3] - Rh).max() < 1e-8 and np.abs(P[:, 3] - th).max() < 1e-8
+
+
+def test_batch_pixels_rederived_with_independent_philox(small_run):
+    """Reading R12: pixel j of batch b is the first of up to batch_attempts
+    Philox draws (counter (b, 4 << 16 | level, j, a)) with depth and a
+    non-empty M(u), or none; re-derived here with the Python Philox."""
+    w, f, modes, runs = small_run
+    p = dict(oracle.PARAM_DEFAULTS, **w.ransac)
+    lpt = 1 << w.forest["depth"]
+    for d, c, T, seed, lv, r in runs:
+        key = philox_ref.key_of(seed)
+        WH = d.size
+        bp = r["debug"]["batch_pix"]
+        n_batches = r["debug"]["n_rounds"] + 1
+        assert n_batches >= 2
+        skipped = 0
+        for b in range(n_batches):
+            for j in range(p["eta"]):
+                want = -1
+                for a in range(p["batch_attempts"]):
+                    q = philox_ref.below(philox_ref.philox4x32_10((b, (4 << 16) | p["level"], j, a), key)[0], WH)
+                    if not d.flat[q] > 0:
+                        continue
+                    cnt = sum(min(int(modes.nmodes[t * lpt + int(lv[t].flat[q])]), p["k_top"])
+                              for t in range(p["n_trees_used"]))
+                    if cnt == 0:
+                        continue
+                    want = q
+                    break
+                skipped += want < 0
+                assert bp[b][j] == want, (b, j)
+        assert skipped < n_batches * p["eta"]
 
 
 def test_cull_keeps_lowest_brute_force_energies(small_run):
