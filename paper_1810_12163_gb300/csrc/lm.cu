@@ -4,18 +4,19 @@
 // The CTAS CTAs of a cluster share the frame's surviving hypotheses
 // (n <= 64) and split its pixel set by tiles of LMC_P pixels: CTA c takes
 // tiles c, c + CTAS, ...  The first round (most hypotheses, fewest pixels)
-// uses clusters of 4; later rounds have few hypotheses and up to 3.5x the
-// pixels, and a frame's LM there is a chain of passes whose length is set by
-// its slowest hypothesis, so they use clusters of 8 to shorten each pass.
-// The cluster size is a function of the round alone, so a frame's results
-// do not depend on the batch it runs in.  A pass streams the CTA's tiles of the mode
-// table (rows of decoded M(u)) into shared memory with bulk asynchronous
-// copies on an mbarrier pipeline.  A pass covers the hypotheses still
-// iterating, listed in increasing order: thread t works for list entry
-// t % HB on pixel group t / HB (HB = next power of two >= their count), so
-// the lanes of a warp mostly read the same staged row (broadcast) and share
-// control flow, and the passes after most hypotheses have stopped spread the
-// few remaining ones over all lanes.  Per
+// uses clusters of 4.  Later rounds have few hypotheses and up to 3.5x the
+// pixels; a frame's LM there is a chain of passes whose length is set by its
+// slowest hypothesis, so they use clusters of 8 to shorten each pass.  The
+// cluster size is a function of the round alone, so a frame's results do not
+// depend on the batch it runs in.
+//
+// A pass streams the CTA's tiles of the mode table (rows of decoded M(u))
+// into shared memory with bulk asynchronous copies on an mbarrier pipeline.
+// It covers the hypotheses still iterating, listed in increasing order:
+// thread t works for list entry t % HB on pixel group t / HB (HB = next power
+// of two >= their count), so the lanes of a warp mostly read the same staged
+// row (broadcast) and share control flow, and once most hypotheses have
+// stopped the few remaining ones are spread over all lanes.  Per
 // (hypothesis, pixel) a pass finds the nearest mode under the pixel's
 // Mahalanobis metric, keeps it if within the inlier radius and adds its
 // terms to FP32 normal equations.
