@@ -301,6 +301,59 @@ def test_ground_truth_is_energy_minimum_and_lm_converges():
             assert dt < 1e-5 and dr < 1e-3, (use_cov, dt, dr, it)
 
 
+def test_lm_reaches_the_weighted_least_squares_optimum():
+    """LM (Sec. 3.2.3) on noisy modes with anisotropic precision factors U:
+    its end point is the minimiser of sum |U (H x - mu)|^2 found by scipy's
+    trust-region least squares (pose update through scipy's expm).  The two
+    optima with and without U differ, so a wrong weighting, Jacobian or
+    update fails."""
+    so = pytest.importorskip("scipy.optimize")
+    expm = pytest.importorskip("scipy.linalg").expm
+    w = workloads.CONFIG1
+    rng = np.random.default_rng(21)
+    gt = rooms.look_pose([1.7, 1.4, 1.2], 0.4, 0.1)
+    d, c, leaves, modes, pix = _exact_room_model(w, gt, n_pix=64, extra_modes=0)
+    modes.pos[:, 0] += (rng.normal(size=(pix.size, 3)) * 0.01).astype(np.float32)
+    U = np.zeros((pix.size, 6), np.float32)
+    U[:, [0, 3, 5]] = rng.uniform(10.0, 40.0, size=(pix.size, 3))
+    U[:, [1, 2, 4]] = rng.uniform(-5.0, 5.0, size=(pix.size, 3))
+    modes.U[:, 0] = U
+    K = w.K
+    Hh, W = d.shape
+    xs = []
+    for p in pix:
+        u, v, dd = p % W, p // W, np.float32(d.flat[p])
+        xs.append([np.float32((np.float32(u) - np.float32(K.cx)) * dd) / np.float32(K.fx),
+                   np.float32((np.float32(v) - np.float32(K.cy)) * dd) / np.float32(K.fy), dd])
+    X = np.array(xs, np.float64)
+    MU = modes.pos[:, 0].astype(np.float64)
+    Um = np.zeros((pix.size, 3, 3))
+    Um[:, 0, :] = U[:, 0:3]
+    Um[:, 1, 1:] = U[:, 3:5]
+    Um[:, 2, 2] = U[:, 5]
+    P0 = np.eye(4)
+    P0[:3, :3] = _rot([0.3, -0.5, 0.8], 0.004) @ gt[:3, :3]
+    P0[:3, 3] = gt[:3, 3] + [0.006, -0.004, 0.005]
+
+    def optimum(weighted):
+        def res(xi):
+            Pn = expm(_twist(xi)) @ P0
+            e = X @ Pn[:3, :3].T + Pn[:3, 3] - MU
+            return (np.einsum("nij,nj->ni", Um, e) if weighted else e).ravel()
+        r = so.least_squares(res, np.zeros(6), method="trf", x_scale="jac", xtol=1e-15, ftol=1e-15, gtol=1e-15)
+        return expm(_twist(r.x)) @ P0
+
+    P_w, P_u = optimum(True), optimum(False)
+    dt, dr = H.pose_err(P_w, P_u)
+    assert dt > 2e-4                      # the weighting moves the optimum
+    P_lm, it = oracle.lm_refine(P0, pix, d, K, leaves, modes, 1, 1, pix.size, max_iter=50, stop=1e-12)
+    dt, dr = H.pose_err(P_lm, P_w)
+    assert dt < 1e-7 and dr < 1e-5, (dt, dr, it)
+    P_lm0, _ = oracle.lm_refine(P0, pix, d, K, leaves, modes, 1, 0, pix.size, max_iter=50, stop=1e-12)
+    dt, dr = H.pose_err(P_lm0, P_u)
+    assert dt < 1e-7 and dr < 1e-5, (dt, dr)
+
+
 def test_lm_needs_three_inliers():
     w = workloads.CONFIG1
     gt = rooms.look_pose([1.7, 1.4, 1.2], 0.4, 0.1)
