@@ -301,14 +301,10 @@ def test_ground_truth_is_energy_minimum_and_lm_converges():
             assert dt < 1e-5 and dr < 1e-3, (use_cov, dt, dr, it)
 
 
-def test_lm_reaches_the_weighted_least_squares_optimum():
-    """LM (Sec. 3.2.3) on noisy modes with anisotropic precision factors U:
-    its end point is the minimiser of sum |U (H x - mu)|^2 found by scipy's
-    trust-region least squares (pose update through scipy's expm).  The two
-    optima with and without U differ, so a wrong weighting, Jacobian or
-    update fails."""
-    so = pytest.importorskip("scipy.optimize")
-    expm = pytest.importorskip("scipy.linalg").expm
+def _noisy_lm_case():
+    """64 pixels of a noise-free render, one mode each at the exact world
+    point plus 1 cm noise, anisotropic precision factors U; the camera points
+    X, means MU, factors Um (3x3) and a start pose 6 mm / 0.23 deg away."""
     w = workloads.CONFIG1
     rng = np.random.default_rng(21)
     gt = rooms.look_pose([1.7, 1.4, 1.2], 0.4, 0.1)
@@ -334,6 +330,18 @@ def test_lm_reaches_the_weighted_least_squares_optimum():
     P0 = np.eye(4)
     P0[:3, :3] = _rot([0.3, -0.5, 0.8], 0.004) @ gt[:3, :3]
     P0[:3, 3] = gt[:3, 3] + [0.006, -0.004, 0.005]
+    return d, K, leaves, modes, pix, X, MU, Um, P0
+
+
+def test_lm_reaches_the_weighted_least_squares_optimum():
+    """LM (Sec. 3.2.3) on noisy modes with anisotropic precision factors U:
+    its end point is the minimiser of sum |U (H x - mu)|^2 found by scipy's
+    trust-region least squares (pose update through scipy's expm).  The two
+    optima with and without U differ, so a wrong weighting, Jacobian or
+    update fails."""
+    so = pytest.importorskip("scipy.optimize")
+    expm = pytest.importorskip("scipy.linalg").expm
+    d, K, leaves, modes, pix, X, MU, Um, P0 = _noisy_lm_case()
 
     def optimum(weighted):
         def res(xi):
@@ -352,6 +360,35 @@ def test_lm_reaches_the_weighted_least_squares_optimum():
     P_lm0, _ = oracle.lm_refine(P0, pix, d, K, leaves, modes, 1, 0, pix.size, max_iter=50, stop=1e-12)
     dt, dr = H.pose_err(P_lm0, P_u)
     assert dt < 1e-7 and dr < 1e-5, (dt, dr)
+
+
+def test_lm_first_step_is_the_marquardt_damped_step():
+    """One LM iteration from P0: xi solves (A + lambda diag(A)) xi = -g with
+    A = sum J^T J, g = sum J^T r, r = U (y - mu), J = U [I | -[y]x] (left
+    perturbation, y = H x), and the accepted pose is exp(xi^) P0.  Written
+    here from the definitions; lambda = 1 makes the damping form matter."""
+    expm = pytest.importorskip("scipy.linalg").expm
+    d, K, leaves, modes, pix, X, MU, Um, P0 = _noisy_lm_case()
+    Y = X @ P0[:3, :3].T + P0[:3, 3]
+    r = np.einsum("nij,nj->ni", Um, Y - MU)
+    Jp = np.zeros((len(Y), 3, 6))
+    Jp[:, :, :3] = np.eye(3)
+    Jp[:, 0, 4], Jp[:, 0, 5] = Y[:, 2], -Y[:, 1]
+    Jp[:, 1, 3], Jp[:, 1, 5] = -Y[:, 2], Y[:, 0]
+    Jp[:, 2, 3], Jp[:, 2, 4] = Y[:, 1], -Y[:, 0]
+    J = np.einsum("nij,njk->nik", Um, Jp)
+    A = np.einsum("nij,nik->jk", J, J)
+    g = np.einsum("nij,ni->j", J, r)
+    lam = 1.0
+    xi = np.linalg.solve(A + lam * np.diag(np.diag(A)), -g)
+    P1 = expm(_twist(xi)) @ P0
+    r1 = np.einsum("nij,nj->ni", Um, X @ P1[:3, :3].T + P1[:3, 3] - MU)
+    assert (r1 ** 2).sum() < (r ** 2).sum()          # the step is accepted
+    xi_lev = np.linalg.solve(A + lam * np.eye(6), -g)
+    assert np.abs(xi_lev - xi).max() > 1e-4          # the damping form matters here
+    P_lm, it = oracle.lm_refine(P0, pix, d, K, leaves, modes, 1, 1, pix.size, max_iter=1, lambda0=lam,
+                                stop=1e-15)
+    assert np.abs(P_lm - P1).max() < 1e-12
 
 
 def test_lm_needs_three_inliers():
@@ -453,6 +490,33 @@ def test_rqs_parent_is_nearest_denser_point():
     assert list(r["parent"]) == [-1] * 5 and r["k"] == 5
 
 
+def test_rqs_densities_are_the_parzen_sums():
+    """rho_i = sum_j exp(-|x_i - x_j|^2 / (2 sigma^2)) over all points of
+    the leaf (Sec. 3.2.2), recomputed in numpy."""
+    rng = np.random.default_rng(5)
+    pts = (rng.normal(size=(40, 3)) * 0.08 + [1.0, 2.0, 0.5]).astype(np.float32)
+    for sigma in (0.05, 0.1, 0.3):
+        r = oracle.rqs_leaf(pts, np.zeros((40, 3), np.uint8), sigma, 0.05, 1, 10)
+        X = pts.astype(np.float64)
+        d2 = ((X[:, None, :] - X[None, :, :]) ** 2).sum(-1)
+        np.testing.assert_allclose(r["density"], np.exp(-d2 / (2.0 * float(np.float32(sigma)) ** 2)).sum(1),
+                                   rtol=1e-12)
+
+
+def test_rqs_equal_densities_link_to_the_lower_index():
+    """Reading of the parent rule at equal densities: the point of lower
+    index counts as denser, so of two mirror-image points the second links
+    to the first, which is the root."""
+    pts = np.array([[0, 0, 0], [0.03, 0, 0]], np.float32)
+    r = oracle.rqs_leaf(pts, np.zeros((2, 3), np.uint8), 0.1, 0.05, 1, 5)
+    assert r["density"][0] == r["density"][1]
+    assert list(r["parent"]) == [-1, 0] and list(r["root"]) == [0, 0] and r["k"] == 1
+    pts = np.array([[0.03, 0, 0], [0, 0, 0], [0.06, 0, 0]], np.float32)  # middle first
+    r = oracle.rqs_leaf(pts, np.zeros((3, 3), np.uint8), 0.1, 0.05, 1, 5)
+    assert r["density"][1] == r["density"][2] and r["density"][0] > r["density"][1]
+    assert list(r["parent"]) == [-1, 0, 0]
+
+
 def test_mode_store_encoding():
     """FP16 offsets from an FP32 leaf centroid (numpy's IEEE half rounding),
     colour rounding and U^T U = (cov + eps I)^-1."""
@@ -547,6 +611,26 @@ def _corner_view():
     return rooms.look_pose(pos, math.atan2(tgt[1], tgt[0]), math.atan2(tgt[2], math.hypot(tgt[0], tgt[1])))
 
 
+def test_depth_score_needs_a_tenth_of_the_rays_on_the_model():
+    """Eq. 8: the score is the masked mean depth difference when at least a
+    tenth of the synthetic depth image is valid, else infinite.  Cameras
+    outside the box see it with 36% and 6% of their rays (counted here with
+    the numpy renderer)."""
+    w = workloads.CONFIG1
+    room = w.room()
+    d, _ = rooms.render(room, w.K, rooms.look_pose([1.7, 1.4, 1.2], 0.4, 0.1), noise_sigma=0.0)
+    for yaw_deg, finite in ((-100.0, True), (-83.0, False)):
+        P = rooms.look_pose([room.hi[0] + 0.5, 0.5 * (room.lo[1] + room.hi[1]), 1.2], math.radians(yaw_deg), 0.0)
+        syn = _numpy_box_depth(P, w.K, room.lo, room.hi)
+        frac_np = np.isfinite(syn).mean()
+        assert (frac_np > 0.3) if finite else (0.02 < frac_np < 0.08)
+        s, mu, frac = oracle.depth_score(P, d, w.K, room.lo, room.hi)
+        assert abs(frac - frac_np) <= 2.0 / d.size
+        m = np.isfinite(syn) & (d > 0)
+        np.testing.assert_allclose(mu, np.abs(d[m] - syn[m]).mean(), rtol=1e-6)
+        assert (s == mu) if finite else math.isinf(s)
+
+
 def test_icp_recovers_exact_pose_of_corner_view():
     """Noise-free depth: the true pose zeroes every residual, so ICP started a
     few cm / degrees away must land on it (a wrong sign, index or transposed
@@ -569,6 +653,58 @@ def test_icp_recovers_exact_pose_of_corner_view():
               T + np.block([[np.zeros((3, 3)), np.array([[0.04], [-0.03], [0.02]])], [np.zeros((1, 4))]])):
         R, ok, _ = oracle.icp_refine(P, d, _ICP_K, _ICP_ROOM.lo, _ICP_ROOM.hi)
         assert ok and H.pose_err(R, T)[0] < 1e-6 and H.pose_err(R, T)[1] < 1e-4
+
+
+def test_icp_first_step_is_the_ridge_damped_point_to_plane_step():
+    """One ICP iteration (reading R21) re-derived in numpy from its
+    definition: projective association with the first box face along each
+    pixel ray, residual n . (q - p), inliers within the radius, camera-frame
+    Jacobian (m, x x m) with m = R^T n, step (A + ridge tr(A)/6 I) xi = -g,
+    pose H exp(xi^).  A large ridge makes its scaling matter."""
+    expm = pytest.importorskip("scipy.linalg").expm
+    T = _corner_view()
+    d, _ = rooms.render(_ICP_ROOM, _ICP_K, T, noise_sigma=0.0)
+    P = T.copy()
+    P[:3, :3] = _rot_deg([0.2, 1.0, -0.4], 1.5) @ T[:3, :3]
+    P[:3, 3] += [0.02, -0.015, 0.01]
+    stride, dist, ridge = 4, 0.1, 0.05
+    K = _ICP_K
+    lo, hi = np.asarray(_ICP_ROOM.lo, float), np.asarray(_ICP_ROOM.hi, float)
+    R0, o = P[:3, :3], P[:3, 3]
+    A = np.zeros((6, 6))
+    g = np.zeros(6)
+    for v in range(0, K.height, stride):
+        for u in range(0, K.width, stride):
+            dep = float(d[v, u])
+            if not dep > 0:
+                continue
+            c = np.array([(u - K.cx) / K.fx, (v - K.cy) / K.fy, 1.0])
+            w_ = R0 @ c
+            with np.errstate(divide="ignore", invalid="ignore"):
+                t1, t2 = (lo - o) / w_, (hi - o) / w_
+            tmin, tmax = np.minimum(t1, t2), np.maximum(t1, t2)
+            tn, an, tf, af = tmin.max(), int(tmin.argmax()), tmax.min(), int(tmax.argmin())
+            if tn > tf:
+                continue
+            sh, ax = (tn, an) if tn > 0 else (tf, af)
+            if not sh > 0:
+                continue
+            e = (dep - sh) * w_
+            if e @ e > dist * dist:
+                continue
+            m = R0[ax]
+            x = dep * c
+            J = np.concatenate([m, np.cross(x, m)])
+            A += np.outer(J, J)
+            g += J * e[ax]
+    xi = np.linalg.solve(A + ridge * np.trace(A) / 6.0 * np.eye(6), -g)
+    want = P @ expm(_twist(xi))
+    got, ok, _ = oracle.icp_refine(P, d, K, _ICP_ROOM.lo, _ICP_ROOM.hi, levels=1, stride=(stride,), iters=(1,),
+                                   dist=(dist,), ridge=ridge, min_frac=0.0)
+    assert ok
+    assert np.abs(got - want).max() < 1e-10
+    xi_abs = np.linalg.solve(A + ridge * np.eye(6), -g)
+    assert np.abs(xi_abs - xi).max() > 1e-4          # the ridge scaling matters here
 
 
 def test_icp_single_wall_keeps_unconstrained_directions():
@@ -741,6 +877,54 @@ def test_batch_pixels_rederived_with_independent_philox(small_run):
         assert skipped < n_batches * p["eta"]
 
 
+def test_generation_rederived_at_the_paper_colour_threshold():
+    """The re-derivation of the generation test with check 1 at its
+    configured strength (colour 30 instead of the parity case's loosened
+    120), so the colour test (L-infinity over RGB) decides most attempts."""
+    w = H.WORKLOADS[H.SMALL]
+    f, res, modes = H.oracle_model(w.name)
+    p = dict(oracle.PARAM_DEFAULTS, **dict(w.ransac, colour_thresh=30))
+    d, c, T, seed = w.query(0)
+    lv = oracle.forest_leaves(f, d, c, w.K.fx, n_trees=p["n_trees_used"])
+    r = oracle.relocalise(p, d, c, w.K, lv, modes, w.room().lo, w.room().hi, seed, 1 << w.forest["depth"],
+                          debug=True)
+    key = philox_ref.key_of(seed)
+    it = r["debug"]["hyp_iter"]
+    assert 0 < (it >= 0).sum() < p["n_hyp"]
+    for slot in range(0, p["n_hyp"], 5):
+        last = it[slot] if it[slot] >= 0 else p["max_iter"]
+        for k in range(min(last, 150)):
+            assert _numpy_attempt(w, p, d, c, lv, modes, key, slot, k) is None, (slot, k)
+        if it[slot] >= 0:
+            assert _numpy_attempt(w, p, d, c, lv, modes, key, slot, it[slot]) is not None
+
+
+@pytest.mark.parametrize("offset, passes", [((20, 20, 20), True), ((30, 0, 0), True), ((0, -31, 0), False)])
+def test_colour_check_is_the_largest_channel_difference(offset, passes):
+    """Check 1 (Sec. 3.2.3) accepts a pair iff max over R, G, B of the
+    absolute difference between the pixel's colour and the mode's colour
+    centroid is at most the threshold: uniform frame colour 100, every mode
+    coloured 100 + offset, checks 2 and 3 opened, colour threshold 30."""
+    w = H.WORKLOADS[H.SMALL]
+    f, res, modes0 = H.oracle_model(w.name)
+    modes = oracle.Modes(modes0.nmodes.size, modes0.m_max)
+    for k in ("nmodes", "centroid", "pos", "U", "size"):
+        getattr(modes, k)[:] = getattr(modes0, k)
+    modes.rgb[:] = np.array([100, 100, 100]) + np.array(offset)
+    p = dict(oracle.PARAM_DEFAULTS, **dict(w.ransac, colour_thresh=30, min_sq_dist=1e-6, max_trans_err=1e9,
+                                           pose_update=0, rank=0))
+    d, c, T, seed = w.query(0)
+    c = np.full_like(c, 100)
+    lv = oracle.forest_leaves(f, d, w.query(0)[1], w.K.fx, n_trees=p["n_trees_used"])
+    r = oracle.relocalise(p, d, c, w.K, lv, modes, w.room().lo, w.room().hi, seed, 1 << w.forest["depth"],
+                          debug=True)
+    it = r["debug"]["hyp_iter"]
+    if passes:
+        assert (it >= 0).all() and np.median(it) <= 1
+    else:
+        assert (it < 0).all() and r["n_hypotheses"] == 0
+
+
 def test_cull_keeps_lowest_brute_force_energies(small_run):
     w, f, modes, runs = small_run
     p = dict(oracle.PARAM_DEFAULTS, **w.ransac)
@@ -785,6 +969,16 @@ def test_halving_and_chosen_set(small_run):
             assert (np.diff(e) >= 0).all()
             prev = cur
             off += k
+        # the chosen set is the first survivor set of at most k_out hypotheses
+        seq = [min(r["n_hypotheses"], p["n_cull"])] + counts
+        first = next(i for i, k in enumerate(seq) if k <= p["k_out"])
+        assert r["n_chosen"] == seq[first]
+        if first == 0:
+            want = dbg["cull_slot"][: seq[0]]
+        else:
+            o = sum(counts[: first - 1])
+            want = dbg["round_slot"][o: o + seq[first]]
+        assert list(r["chosen_slot"]) == list(want)
         # ranking returns the argmin of the chosen scores, recomputed here
         room = w.room()
         sc = []
