@@ -52,6 +52,19 @@ M = [
  ("ICP inlier radius 2x", "icp.c", "            if (e[0] * e[0] + e[1] * e[1] + e[2] * e[2] > dist * dist)", "            if (e[0] * e[0] + e[1] * e[1] + e[2] * e[2] > 4.0 * dist * dist)"),
  ("ICP ridge not scaled", "icp.c", "                A[6 * i + i] += ip->ridge * tr / 6.0;", "                A[6 * i + i] += ip->ridge;"),
  ("ICP min_frac ignored", "icp.c", "    return S.n_valid > 0 && (double)S.n_in >= ip->min_frac * (double)S.n_valid;", "    return S.n_valid > 0;"),
+ ("reservoir draw U[0, c-1]", "oracle.c", "                    uint64_t j = ((uint64_t)r[0] * ((uint64_t)c + 1)) >> 32; /* U[0, c] */",
+  "                    uint64_t j = ((uint64_t)r[0] * ((uint64_t)c)) >> 32;"),
+ ("reservoir grid from 0", "oracle.c", "    for (int y = grid_origin; y < H; y += grid_step) {", "    for (int y = 0; y < H; y += grid_step) {"),
+ ("forest p_depth inverted", "oracle.c", "            const int is_depth = (double)r0[0] < (double)p_depth * 4294967296.0;",
+  "            const int is_depth = (double)r0[0] >= (double)p_depth * 4294967296.0;"),
+ ("cluster size floor strict", "adapt.c", "        if (parent[r] < 0 && csize[r] >= min_cluster_size)", "        if (parent[r] < 0 && csize[r] > min_cluster_size)"),
+ ("clusters ascending", "adapt.c", "        while (b >= 0 && csize[order[b]] < csize[v]) {", "        while (b >= 0 && csize[order[b]] > csize[v]) {"),
+ ("covariance biased", "adapt.c", "            cov[6 * k + q] = cnt > 1 ? c[q] / (double)(cnt - 1) : 0.0;", "            cov[6 * k + q] = cnt > 1 ? c[q] / (double)cnt : 0.0;"),
+ ("colour centroid truncated", "adapt.c", "        colour[3 * k + 0] = (uint8_t)((sr + cnt / 2) / cnt);", "        colour[3 * k + 0] = (uint8_t)(sr / cnt);"),
+ ("eps on one diagonal only", "adapt.c", "    const double d = cov[3] + eps, e = cov[4], f = cov[5] + eps;", "    const double d = cov[3], e = cov[4], f = cov[5];"),
+ ("cascade strict threshold", "ransac.c", "        if (l == n_levels - 1 || (out->status == 0 && out->score <= thresholds[l]))",
+  "        if (l == n_levels - 1 || (out->status == 0 && out->score < thresholds[l]))"),
+ ("ICP rotation Jacobian m x x", "icp.c", "                                 x[1] * m[2] - x[2] * m[1],", "                                 x[2] * m[1] - x[1] * m[2],"),
 ]
 RUNNER = r'''
 import sys

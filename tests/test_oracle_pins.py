@@ -451,6 +451,12 @@ def test_reservoir_fills_in_order_below_capacity():
     xs = [(res.pos[0, e, 0], res.pos[0, e, 1]) for e in range(15)]
     grid = [((u - 8) / 16, (v - 8) / 16) for v in range(0, 16, 4) for u in range(0, 16, 4) if (u, v) != (4, 4)]
     assert np.allclose(xs, grid)
+    # the grid's origin is a parameter (reading R4 takes 0); origin 2 shifts it
+    res = oracle.Reservoirs(f, 32, seed=5)
+    res.add_frame(d, np.zeros((16, 16, 3), np.uint8), K, np.eye(4), grid_step=4, grid_origin=2)
+    grid = [((u - 8) / 16, (v - 8) / 16) for v in range(2, 16, 4) for u in range(2, 16, 4)]
+    assert res.count[0] == len(grid) == 16
+    assert np.allclose([(res.pos[0, e, 0], res.pos[0, e, 1]) for e in range(16)], grid)
 
 
 # ---------------------------------------------------------------- RQS + modes
@@ -501,6 +507,18 @@ def test_rqs_densities_are_the_parzen_sums():
         d2 = ((X[:, None, :] - X[None, :, :]) ** 2).sum(-1)
         np.testing.assert_allclose(r["density"], np.exp(-d2 / (2.0 * float(np.float32(sigma)) ** 2)).sum(1),
                                    rtol=1e-12)
+
+
+def test_rqs_mode_colour_is_the_rounded_mean():
+    """A mode's colour is the mean of its members' colours per channel,
+    rounded to the nearest integer with halves up (reading of "colour
+    centroid" for 8-bit colours)."""
+    pts = np.array([[0, 0, 0], [0.01, 0, 0], [0.0, 0.01, 0]], np.float32)
+    cols = np.array([[10, 200, 7], [11, 201, 8], [11, 201, 8]], np.uint8)   # means 10.67, 200.67, 7.67
+    r = oracle.rqs_leaf(pts, cols, 0.1, 0.05, 1, 5)
+    assert r["k"] == 1 and list(r["colour"][0]) == [11, 201, 8]
+    r = oracle.rqs_leaf(pts[:2], cols[:2], 0.1, 0.05, 1, 5)                # means 10.5, 200.5, 7.5
+    assert r["k"] == 1 and list(r["colour"][0]) == [11, 201, 8]
 
 
 def test_rqs_equal_densities_link_to_the_lower_index():
