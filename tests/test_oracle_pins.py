@@ -1076,3 +1076,27 @@ def test_no_depth_frame_has_no_pose():
     r = oracle.relocalise(w.ransac, d, c, w.K, lv, modes, w.room().lo, w.room().hi, 1,
                           1 << w.forest["depth"])
     assert r["status"] == 1 and r["n_hypotheses"] == 0 and math.isinf(r["score"])
+
+
+def test_oracle_results_do_not_depend_on_its_thread_count():
+    """The oracle's OpenMP loops split independent leaves and pixel rows
+    only: modes, leaf maps and a relocalisation are bit-identical with one
+    thread and with four."""
+    w = H.WORKLOADS[H.SMALL]
+    out = []
+    for n in (1, 4):
+        oracle.set_threads(n)
+        try:
+            f, res, modes = H.oracle_model.__wrapped__(w.name)      # not the cached model
+            d, c, T, seed = w.query(1)
+            lv = oracle.forest_leaves(f, d, c, w.K.fx, n_trees=w.ransac["n_trees_used"])
+            r = oracle.relocalise(w.ransac, d, c, w.K, lv, modes, w.room().lo, w.room().hi, seed,
+                                  1 << w.forest["depth"])
+        finally:
+            oracle.set_threads(1)
+        out.append((modes, lv, r))
+    (m1, l1, r1), (m4, l4, r4) = out
+    for k in ("nmodes", "pos", "rgb", "U", "size"):
+        assert np.array_equal(getattr(m1, k), getattr(m4, k)), k
+    assert np.array_equal(l1, l4)
+    assert np.array_equal(r1["pose"], r4["pose"]) and r1["score"] == r4["score"]
