@@ -65,6 +65,11 @@ M = [
  ("cascade strict threshold", "ransac.c", "        if (l == n_levels - 1 || (out->status == 0 && out->score <= thresholds[l]))",
   "        if (l == n_levels - 1 || (out->status == 0 && out->score < thresholds[l]))"),
  ("ICP rotation Jacobian m x x", "icp.c", "                                 x[1] * m[2] - x[2] * m[1],", "                                 x[2] * m[1] - x[1] * m[2],"),
+ ("half rounding truncates", "adapt.c", "    double q = nearbyint(ldexp(a, 10 - E)); /* in [1024, 2048] */",
+  "    double q = floor(ldexp(a, 10 - E));"),
+ ("forest dy from the dx word", "oracle.c", "            dy[i] = delta_lo + span * unit24(r0[2]);", "            dy[i] = delta_lo + span * unit24(r0[1]);"),
+ ("batch draws share the generation tag", "ransac.c", "            uint32_t c[4] = {(uint32_t)b, (4u << 16) | (uint32_t)p->level, (uint32_t)j, (uint32_t)a};",
+  "            uint32_t c[4] = {(uint32_t)b, (3u << 16) | (uint32_t)p->level, (uint32_t)j, (uint32_t)a};"),
 ]
 RUNNER = r'''
 import sys

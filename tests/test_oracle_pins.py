@@ -54,11 +54,41 @@ def test_forest_random_distribution():
     td = f["tau"][~rgb]
     tr = f["tau"][rgb]
     assert td.min() >= -0.2 and td.max() < 0.2 and tr.min() >= -50 and tr.max() < 50
+    assert abs(np.corrcoef(f["dx"], f["dy"])[0, 1]) < 0.05         # independent offsets
     z = oracle.forest_random(1, 6, 0.4, tau_zero=True, seed=9)
     assert (z["tau"] == 0).all()
     # all-depth and all-colour forests
     assert (oracle.forest_random(1, 8, 1.0, seed=1)["type"] == 0).all()
     assert (oracle.forest_random(1, 8, 0.0, seed=1)["type"] == 1).all()
+
+
+def test_forest_nodes_rederived_with_independent_philox():
+    """Reading R2 node by node: node n of tree t draws Philox blocks at
+    counters (t, 1 << 16, n, 0) and (t, 1 << 16, n, 1); Depth iff
+    r0[0] < p 2^32; dx, dy from r0[1], r0[2] and the channel from r0[3]; tau
+    from r1[0]; uniforms are the top 24 bits scaled to [0, 1) in FP32."""
+    lo, hi, tlo, thi, clo, chi = -130.0, 130.0, -0.2, 0.2, -50.0, 50.0
+    seed = 0x1234_5678_9ABC
+    f = oracle.forest_random(3, 7, 0.4, (lo, hi), (tlo, thi), (clo, chi), False, seed)
+    key = philox_ref.key_of(seed)
+    f32 = np.float32
+
+    def uni(u):
+        return f32((int(u) >> 8) * 2.0 ** -24)
+
+    nb = (1 << 7) - 1
+    for t in range(3):
+        for n in range(0, nb, 5):
+            r0 = philox_ref.philox4x32_10((t, 1 << 16, n, 0), key)
+            r1 = philox_ref.philox4x32_10((t, 1 << 16, n, 1), key)
+            i = t * nb + n
+            depth = r0[0] < 0.4 * 4294967296.0
+            assert f["type"][i] == (0 if depth else 1)
+            span = f32(hi) - f32(lo)
+            assert f["dx"][i] == f32(lo) + span * uni(r0[1]) and f["dy"][i] == f32(lo) + span * uni(r0[2])
+            assert f["channel"][i] == (0 if depth else philox_ref.below(r0[3], 3))
+            a, b = (tlo, thi) if depth else (clo, chi)
+            assert f["tau"][i] == f32(a) + (f32(b) - f32(a)) * uni(r1[0])
 
 
 # ---------------------------------------------------------------- Eq. 1-3
