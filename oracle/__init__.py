@@ -86,6 +86,10 @@ class Result(ctypes.Structure):
     ]
 
 
+class Resume(ctypes.Structure):
+    _fields_ = [("stage", ctypes.c_int32), ("n", ctypes.c_int32), ("slot", P), ("pose", P)]
+
+
 class Debug(ctypes.Structure):
     _fields_ = [
         ("hyp_pose", P), ("hyp_iter", P), ("cull_slot", P), ("cull_energy", P),
@@ -109,6 +113,8 @@ def _declare(L):
     L.orc_rqs_leaf.restype = I32
     L.orc_update_modes.argtypes = [P, P, P, I32, I32, I32, I32, F32, F32, I32, I32, F32, I32,
                                    P, P, P, P, P, P]
+    L.orc_set_mode_positions.argtypes = [P, P, P, I32, I32, I32, P]
+    L.orc_set_mode_positions.restype = None
     L.orc_kabsch.argtypes = [P, P, I32, P, P]
     L.orc_chol_solve6.argtypes = [P, P, P]
     L.orc_chol_solve6.restype = I32
@@ -126,6 +132,10 @@ def _declare(L):
     L.orc_relocalise.argtypes = [ctypes.POINTER(Params), P, P, I32, I32, F32, F32, F32, F32,
                                  P, I32, I32, P, P, P, P, I32, P, P, U64,
                                  ctypes.POINTER(Result), ctypes.POINTER(Debug)]
+    L.orc_relocalise_from.argtypes = [ctypes.POINTER(Params), P, P, I32, I32, F32, F32, F32, F32,
+                                      P, I32, I32, P, P, P, P, I32, P, P, U64,
+                                      ctypes.POINTER(Resume), ctypes.POINTER(Result),
+                                      ctypes.POINTER(Debug)]
     L.orc_cascade.argtypes = [I32, ctypes.POINTER(Params), P, P, P, P, P, P, P, P, P, P,
                               I32, I32, P, P, P, P, I32, P, P, U64, ctypes.POINTER(Result)]
     L.orc_cascade.restype = I32
@@ -246,6 +256,17 @@ def update_modes(res: Reservoirs, modes: Modes, sigma, tau_c, min_cluster_size,
                            leaf_count, L, sigma, tau_c, min_cluster_size, modes.m_max, cov_eps,
                            int(fp16_offsets), _p(modes.nmodes), _p(modes.centroid), _p(modes.pos),
                            _p(modes.rgb), _p(modes.U), _p(modes.size))
+    return modes
+
+
+def set_mode_positions(modes: Modes, pos, fp16_offsets: bool):
+    """Writes positions ([L][m_max][3] FP32) into the stored modes in the
+    store's precision: FP32, or FP16 offsets from the leaf's FP32 centroid
+    (Sec. 3.2.2 mode layout); ranks beyond a leaf's mode count are untouched."""
+    pos = _c(pos, np.float32)
+    assert pos.shape == modes.pos.shape
+    lib().orc_set_mode_positions(_p(pos), _p(modes.nmodes), _p(modes.centroid), modes.pos.shape[0],
+                                 modes.m_max, int(fp16_offsets), _p(modes.pos))
     return modes
 
 
@@ -401,7 +422,11 @@ def _result_dict(r: Result):
 
 
 def relocalise(params: dict, depth_img, rgb, K, leaves, modes: Modes, box_lo, box_hi, seed,
-               leaves_per_tree, debug=False):
+               leaves_per_tree, debug=False, resume=None):
+    """One relocalisation (Sec. 3.2.3-3.2.4).  resume = (stage, slots,
+    poses [n][12]) hands a survivor set in at a stage boundary of the
+    preemptive loop (stage 0: after the cull; r + 1: after round r); see
+    orc_resume in oracle.h."""
     p = make_params(**params)
     d = _c(depth_img, np.float32)
     c = _c(rgb, np.uint8)
@@ -422,10 +447,18 @@ def relocalise(params: dict, depth_img, rgb, K, leaves, modes: Modes, box_lo, bo
         )
         for k, a in arrays.items():
             setattr(dbg, k, _p(a))
-    lib().orc_relocalise(ctypes.byref(p), _p(d), _p(c), W, H, K.fx, K.fy, K.cx, K.cy, _p(lv),
-                         lv.shape[0], leaves_per_tree, _p(modes.nmodes), _p(modes.pos),
-                         _p(modes.rgb), _p(modes.U), modes.m_max, _p(lo), _p(hi), seed,
-                         ctypes.byref(res), ctypes.byref(dbg) if debug else None)
+    rs = None
+    if resume is not None:
+        stage, slots, poses = resume
+        rs_slot = _c(slots, np.int32)
+        rs_pose = _c(np.asarray(poses, np.float64).reshape(-1, 12), np.float64)
+        assert rs_slot.shape[0] == rs_pose.shape[0]
+        rs = Resume(int(stage), int(rs_slot.shape[0]), _p(rs_slot), _p(rs_pose))
+    lib().orc_relocalise_from(ctypes.byref(p), _p(d), _p(c), W, H, K.fx, K.fy, K.cx, K.cy, _p(lv),
+                              lv.shape[0], leaves_per_tree, _p(modes.nmodes), _p(modes.pos),
+                              _p(modes.rgb), _p(modes.U), modes.m_max, _p(lo), _p(hi), seed,
+                              ctypes.byref(rs) if rs is not None else None,
+                              ctypes.byref(res), ctypes.byref(dbg) if debug else None)
     out = _result_dict(res)
     if debug:
         arrays["n_rounds"] = dbg.n_rounds

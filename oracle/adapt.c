@@ -242,3 +242,27 @@ void orc_update_modes(const float *res_pos, const uint8_t *res_rgb, const uint32
         free(par); free(rt); free(den);
     }
 }
+
+/* Mode positions written back into a store (Sec. 3.2.2 mode layout): FP32
+ * as given, or as FP16 offsets from the leaf's FP32 centroid, i.e. the half
+ * (round to nearest even) of the FP64 difference, decoded as centroid +
+ * offset in FP32 -- the same encoding orc_update_modes applies to the modal
+ * centroids.  Entries at ranks >= nmodes[leaf] are left untouched. */
+void orc_set_mode_positions(const float *pos, const uint8_t *nmodes, const float *centroid,
+                            int n_leaves, int m_max, int fp16_offsets, float *mpos)
+{
+    for (int L = 0; L < n_leaves; ++L)
+        for (int m = 0; m < nmodes[L] && m < m_max; ++m) {
+            const size_t e = (size_t)L * m_max + m;
+            for (int a = 0; a < 3; ++a) {
+                const float x = pos[e * 3 + a];
+                if (fp16_offsets) {
+                    const float c = centroid[(size_t)L * 3 + a];
+                    const uint16_t h = half_from_double((double)x - (double)c);
+                    mpos[e * 3 + a] = c + (float)half_to_double(h);
+                } else {
+                    mpos[e * 3 + a] = x;
+                }
+            }
+        }
+}

@@ -82,6 +82,12 @@ void orc_update_modes(const float *res_pos, const uint8_t *res_rgb, const uint32
                       uint8_t *nmodes, float *centroid, float *mpos, uint8_t *mrgb,
                       float *mU, int32_t *msize);
 
+/* Writes positions pos[L][m_max][3] into the store's mpos in its precision
+ * (FP32, or FP16 offsets from the leaf's FP32 centroid as orc_update_modes
+ * encodes them); ranks >= nmodes[L] are untouched. */
+void orc_set_mode_positions(const float *pos, const uint8_t *nmodes, const float *centroid,
+                            int n_leaves, int m_max, int fp16_offsets, float *mpos);
+
 /* ---- Kabsch (Sec. 3.2.3), Eq. 5, LM and ranking ----------------------- */
 /* Rigid transform (R,t) minimising sum |R a_i + t - b_i|^2 over 3D pairs. */
 void orc_kabsch(const double *a, const double *b, int n, double R[9], double t[3]);
@@ -170,6 +176,33 @@ void orc_relocalise(const orc_params *p,
                     const float *mU, int m_max,
                     const double box_lo[3], const double box_hi[3],
                     uint64_t query_seed, orc_result *out, orc_debug *dbg);
+
+/* Survivor set handed to orc_relocalise_from at a stage boundary of the
+ * preemptive loop (Sec. 3.2.3): stage 0 = straight after the initial cull,
+ * stage r + 1 = after the halving of preemptive round r.  The n survivors
+ * (generation slot ids and 3x4 row-major poses) replace the oracle's own
+ * set at that point; their energies are recomputed in FP64 on the pixel set
+ * of that point and the set is re-sorted by (E, slot).  Everything after it
+ * (later rounds, the chosen set, ICP, ranking) runs as in orc_relocalise.
+ * The tests use it to keep comparing a query whose survivor set or LM
+ * trajectory legitimately left the oracle's. */
+typedef struct {
+    int32_t stage;
+    int32_t n;
+    const int32_t *slot;      /* [n] */
+    const double *pose;       /* [n][12] */
+} orc_resume;
+
+/* orc_relocalise with an optional survivor set handed in (NULL: none). */
+void orc_relocalise_from(const orc_params *p,
+                         const float *depth_img, const uint8_t *rgb, int W, int H,
+                         float fx, float fy, float cx, float cy,
+                         const uint16_t *leaves, int n_trees_forest, int leaves_per_tree,
+                         const uint8_t *nmodes, const float *mpos, const uint8_t *mrgb,
+                         const float *mU, int m_max,
+                         const double box_lo[3], const double box_hi[3],
+                         uint64_t query_seed, const orc_resume *rs, orc_result *out,
+                         orc_debug *dbg);
 
 /* Eq. 5 energy of one pose on a pixel set (pixel ids into the frame). */
 double orc_energy(const double pose12[12], const int32_t *pix, int n_pix,

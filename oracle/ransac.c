@@ -594,6 +594,27 @@ static void sample_batch(const orc_params *p, const uint32_t key[2], int b,
     }
 }
 
+/* State handed in at a stage boundary (orc_relocalise_from): the survivor
+ * set replaces the oracle's own, and each survivor's Eq. 5 energy is
+ * recomputed in FP64 on the pixel set of that point before the usual
+ * stable sort by (E, slot). */
+static void replace_survivors(const orc_resume *rs, hyp_t *hyp, int *n, const int32_t *I, int nI,
+                              const float *depth_img, int W, int Himg, float fx, float fy,
+                              float cx, float cy, const uint16_t *leaves, const orc_params *p,
+                              int leaves_per_tree, const uint8_t *nmodes, const float *mpos,
+                              const float *mU, int m_max)
+{
+    *n = rs->n;
+    for (int h = 0; h < rs->n; ++h) {
+        hyp[h].slot = rs->slot[h];
+        memcpy(hyp[h].H, rs->pose + 12 * (size_t)h, sizeof(hyp[h].H));
+        hyp[h].E = orc_energy(hyp[h].H, I, nI, depth_img, W, Himg, fx, fy, cx, cy, leaves,
+                              p->n_trees_used, leaves_per_tree, nmodes, mpos, mU, m_max,
+                              p->k_top, p->use_cov);
+    }
+    qsort(hyp, (size_t)*n, sizeof(hyp_t), hyp_cmp);
+}
+
 void orc_relocalise(const orc_params *p,
                     const float *depth_img, const uint8_t *rgb, int W, int Himg,
                     float fx, float fy, float cx, float cy,
@@ -602,6 +623,21 @@ void orc_relocalise(const orc_params *p,
                     const float *mU, int m_max,
                     const double box_lo[3], const double box_hi[3],
                     uint64_t query_seed, orc_result *out, orc_debug *dbg)
+{
+    orc_relocalise_from(p, depth_img, rgb, W, Himg, fx, fy, cx, cy, leaves, n_trees_forest,
+                        leaves_per_tree, nmodes, mpos, mrgb, mU, m_max, box_lo, box_hi,
+                        query_seed, NULL, out, dbg);
+}
+
+void orc_relocalise_from(const orc_params *p,
+                         const float *depth_img, const uint8_t *rgb, int W, int Himg,
+                         float fx, float fy, float cx, float cy,
+                         const uint16_t *leaves, int n_trees_forest, int leaves_per_tree,
+                         const uint8_t *nmodes, const float *mpos, const uint8_t *mrgb,
+                         const float *mU, int m_max,
+                         const double box_lo[3], const double box_hi[3],
+                         uint64_t query_seed, const orc_resume *rs, orc_result *out,
+                         orc_debug *dbg)
 {
     (void)n_trees_forest;
     const int WH = W * Himg;
@@ -665,6 +701,9 @@ void orc_relocalise(const orc_params *p,
     qsort(hyp, (size_t)n, sizeof(hyp_t), hyp_cmp);
     if (n > p->n_cull)
         n = p->n_cull;
+    if (rs && rs->stage == 0)
+        replace_survivors(rs, hyp, &n, I, nI, depth_img, W, Himg, fx, fy, cx, cy, leaves, p,
+                          leaves_per_tree, nmodes, mpos, mU, m_max);
     if (dbg && dbg->cull_slot)
         for (int h = 0; h < n; ++h) {
             dbg->cull_slot[h] = hyp[h].slot;
@@ -699,6 +738,9 @@ void orc_relocalise(const orc_params *p,
         }
         qsort(hyp, (size_t)n, sizeof(hyp_t), hyp_cmp);
         n = (n + 1) / 2;
+        if (rs && rs->stage == n_rounds + 1)
+            replace_survivors(rs, hyp, &n, I, nI, depth_img, W, Himg, fx, fy, cx, cy, leaves, p,
+                              leaves_per_tree, nmodes, mpos, mU, m_max);
         if (dbg && n_rounds < 16) {
             if (dbg->round_count) dbg->round_count[n_rounds] = n;
             for (int h = 0; h < n; ++h) {
