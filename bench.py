@@ -55,6 +55,9 @@ def parse():
                     help="serving workload (3 rooms, 8 streams, cascade): latency and saturation sweep")
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="length of the 30 Hz serving run")
     ap.add_argument("--sweep-seconds", type=float, default=4.0, help="length of each saturation point")
+    ap.add_argument("--no-serving-leg", action="store_true",
+                    help="skip the short serving leg (batched vs per-frame) of the default line")
+    ap.add_argument("--leg-seconds", type=float, default=2.0, help="length of each serving-leg point")
     ap.add_argument("--profile-only", action="store_true",
                     help="short run for an external profiler (no baselines)")
     ap.add_argument("--arena-gb", type=float, default=24.0,
@@ -539,7 +542,7 @@ def run_ours(args):
     rel = rg.Relocaliser(forest, scene, w.ransac, w.width, w.height, B)
 
     # distinct query frames for this rank, resident in device memory
-    n_distinct = min(B, 32)
+    n_distinct = B
     qs = [w.query(rank * 1000 + i) for i in range(n_distinct)]
     D = torch.from_numpy(np.stack([qs[i % n_distinct][0] for i in range(B)])).cuda()
     C = torch.from_numpy(np.stack([qs[i % n_distinct][1] for i in range(B)])).cuda()
@@ -558,7 +561,8 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
 
-    rel.profile(True)
+    # the timed region: the product path (each step replays the captured
+    # CUDA graph of the 64-frame launch sequence)
     step_ms = []
     results = None
     with ClockSampler(local) as clk:
@@ -575,9 +579,24 @@ def run_ours(args):
             e1.synchronize()
             step_ms.append(e0.elapsed_time(e1))
         torch.cuda.synchronize()
+    total_s = sum(step_ms) / 1e3
+    # a profiled pass of the same steps (same seeds, so the same work):
+    # kernels launched one by one with CUDA events around each launch and
+    # work counters on the device; the per-kernel rooflines come from it
+    rel.profile(True)
+    prof_ms = []
+    for k in range(args.steps):
+        flush.fill_(k & 255)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rel.relocalise_batch(D, C, w.K, seeds(k), stream=stream, raw=True)
+        e1.record(stream)
+        e1.synchronize()
+        prof_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
     kernels, work = rel.profile_read()
     rel.profile(False)
-    total_s = sum(step_ms) / 1e3
     if world > 1:
         torch.distributed.barrier()
     total_s = max_over_ranks(total_s, "cuda")
@@ -644,6 +663,9 @@ def run_ours(args):
         "e2e": {"value": job_throughput(B * e2e_steps, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(sum(k["launches"] for k in kernels.values())),
+        "timed_path": "CUDA graph replay (one graph per batch size); per-kernel figures from a "
+                      "profiled pass of the same steps launched kernel by kernel",
+        "profiled_pass_ms_per_step": float(np.mean(prof_ms)),
         "kernels_ms": {k: round(v["ms"], 4) for k, v in kernels.items()},
         "roofline": roofline(kernels, work, w.ransac, B * args.steps, w, sm_count, pk, batch=B),
         "kernel_rooflines": kernel_rooflines(kernels, work, w.ransac, sm_count, pk, n_frames=B * args.steps, w=w,
@@ -688,6 +710,10 @@ def run_ours(args):
             "max_energy_rel": float(e[:, 2].max()), "max_score_rel": float(e[:, 3].max()),
             "within_1mm_0.05deg": int(((e[:, 0] <= 1e-3) & (e[:, 1] <= 0.05)).sum())}
     line["arena_peak_gb"] = ctx.usage()[1] / (1 << 30)
+    if rank == 0 and world == 1 and not args.no_serving_leg and not args.profile_only:
+        sctx = rg.Context(local, arena_bytes=32 << 30)
+        line["serving"] = serving_leg(rg, sctx, args.leg_seconds)
+        sctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     rel1.close()
@@ -774,45 +800,46 @@ def _serve(srv, models, pools, arrivals):
     return st
 
 
-def run_serving(args):
-    import multiprocessing
+class ServingBench:
+    """Config 4: three rooms, each with its own five-tree forest trained on
+    its 200-frame trajectory, served through the library's serving loop
+    with the config-3 cascade per room."""
 
-    import torch
-    import paper_1810_12163_gb300 as rg
-    torch.cuda.set_device(0)
-    ctx = rg.Context(0, arena_bytes=32 << 30)
-    # three rooms, each with its own forest trained on its 200-frame trajectory
-    forests, scenes = [], []
-    mp = multiprocessing.get_context("spawn")
-    with mp.Pool(min(16, os.cpu_count() or 1)) as pool:
-        for w in workloads.SERVING_ROOMS:
-            f = rg.Forest.random(ctx, w.forest, w.forest_seed)
-            for d, c, T in pool.map(_render_training, [(w, i) for i in range(w.n_train)], chunksize=4):
-                f.adapt(d, c, w.K, T)
-            f.update_modes(-1)
-            forests.append(f)
-            scenes.append(rg.Scene(ctx, w.room().lo, w.room().hi))
-    pools = _serving_pools()
-    subsample = [s for s, _ in workloads.CASCADE_LEVELS]
-    levels = [p for _, p in workloads.CASCADE_LEVELS]
-    thresholds = workloads.cascade_thresholds()
+    def __init__(self, rg, ctx):
+        import multiprocessing
+        self.rg, self.ctx = rg, ctx
+        forests, scenes = [], []
+        mp = multiprocessing.get_context("spawn")
+        with mp.Pool(min(16, os.cpu_count() or 1)) as pool:
+            for w in workloads.SERVING_ROOMS:
+                f = rg.Forest.random(ctx, w.forest, w.forest_seed)
+                for d, c, T in pool.map(_render_training, [(w, i) for i in range(w.n_train)], chunksize=4):
+                    f.adapt(d, c, w.K, T)
+                f.update_modes(-1)
+                forests.append(f)
+                scenes.append(rg.Scene(ctx, w.room().lo, w.room().hi))
+        self.forests, self.scenes = forests, scenes
+        self.pools = _serving_pools()
 
-    def make_server(max_batch):
-        srv = rg.Server(ctx, max_batch=max_batch, memory_budget=2 << 30)
-        models = [srv.add_cascade_model(forests[r], scenes[r], levels, subsample, thresholds, 640, 480)
+    def make_server(self, max_batch):
+        srv = self.rg.Server(self.ctx, max_batch=max_batch, memory_budget=2 << 30)
+        subsample = [s for s, _ in workloads.CASCADE_LEVELS]
+        levels = [p for _, p in workloads.CASCADE_LEVELS]
+        thresholds = workloads.cascade_thresholds()
+        models = [srv.add_cascade_model(self.forests[r], self.scenes[r], levels, subsample, thresholds, 640, 480)
                   for r in range(3)]
         # warm the graphs of every batch size the run can form
-        d, c, K, T, seed = pools[0][0]
+        d, c, K, T, seed = self.pools[0][0]
         for n in range(1, max_batch + 1):
             ts = [srv.submit(models[0], d, c, K, seed + i) for i in range(n)]
             for t in ts:
                 srv.wait(t, 600_000)
         return srv, models
 
-    def run_point(max_batch, seconds, scale):
-        srv, models = make_server(max_batch)
+    def point(self, max_batch, seconds, scale):
+        srv, models = self.make_server(max_batch)
         srv.reset_stats()
-        st = _serve(srv, models, pools, workloads.serving_arrivals(seconds, scale))
+        st = _serve(srv, models, self.pools, workloads.serving_arrivals(seconds, scale))
         srv.close()
         keys = ("p50_ms", "p99_ms", "mean_ms", "frames_per_s", "success_5cm_5deg", "offered_per_s",
                 "submitted_per_s", "refused")
@@ -821,6 +848,33 @@ def run_serving(args):
         out["rate_scale"] = scale
         return out
 
+    def close(self):
+        for s in self.scenes:
+            s.close()
+        for f in self.forests:
+            f.close()
+
+
+def serving_leg(rg, ctx, seconds):
+    """Short serving run for the default line: the config-4 load at x8 and
+    x32 the 30 Hz rate, continuous batching (<= 16 frames) vs per-frame."""
+    sb = ServingBench(rg, ctx)
+    out = {"workload": "3 rooms, 8 streams (even 640x480, odd 320x240), Poisson arrivals, 3-level cascade",
+           "seconds_per_point": seconds}
+    for scale in (8, 32):
+        out[f"x{scale}"] = {"batched_max16": sb.point(16, seconds, scale), "per_frame": sb.point(1, seconds, scale)}
+    sb.close()
+    return out
+
+
+def run_serving(args):
+    import torch
+    import paper_1810_12163_gb300 as rg
+    torch.cuda.set_device(0)
+    ctx = rg.Context(0, arena_bytes=32 << 30)
+    sb = ServingBench(rg, ctx)
+    run_point = sb.point
+    # three rooms, each with its own forest trained on its 200-frame trajectory
     line = {"impl": "ours", "metric": "serving: frames relocalised/s with p50/p99 latency",
             "workload": "3 rooms (4x3x2.5, 6x5x3, 10x8x3 m), 5-tree d15 forest each, 8 streams "
                         "(even 640x480, odd 320x240), Poisson 30 Hz per stream, 3-level cascade",

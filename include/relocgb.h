@@ -287,13 +287,16 @@ rl_status rl_icp_poses(rl_scene *s, const float *depth, const rl_intrinsics *K,
  *   NULL.  The call only enqueues work on `stream` and returns.
  * Its partial sums live in a fixed 1 MiB device array inside the library
  * (65536 records of one 1024-pixel tile per pose): n * ceil(W*H/1024) must
- * not exceed 65536 (e.g. n <= 218 at 640x480), else RL_ERR_INVALID_ARG with
- * the limit in rl_last_error().  Every GPU that loads the library holds the
- * array until the process exits.  All calls share it and it keeps the last
- * call's contents; nothing in it needs to start at zero.  Calls that overlap
- * on the GPU (unordered streams) race on it.  The first call on a device
- * looks up the array's device address with that device current; make that
- * first call before any stream capture. */
+ * not exceed 65536 (e.g. n <= 218 at 640x480) and n must not exceed 65535,
+ * else RL_ERR_INVALID_ARG with the limit in rl_last_error().  Every GPU that
+ * loads the library holds the array until the process exits.  All calls
+ * share it and it keeps the last call's contents; nothing in it needs to
+ * start at zero.  Calls that overlap on the GPU (unordered streams) race on
+ * it.  The first call on a device looks up the array's device address with
+ * that device current; make that first call before any stream capture.  The
+ * address is remembered with the CUDA context it belongs to and looked up
+ * again when the device's current context changes (after cudaDeviceReset):
+ * the first call after such a reset must likewise come before any capture. */
 rl_status rl_score_poses_noalloc(const double box_lo[3], const double box_hi[3],
                                  const float *depth, const rl_intrinsics *K,
                                  const double *poses, int32_t n, void *stream,

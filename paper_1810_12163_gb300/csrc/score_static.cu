@@ -11,6 +11,8 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <cuda.h>
+
 #include <mutex>
 
 #include "internal.h"
@@ -27,6 +29,7 @@ struct Partial {
 
 constexpr int kTilePixels = 1024;             // 256 threads x 4 pixels
 constexpr int kMaxPartials = 65536;           // 65536 x 16 B = 1 MiB per device
+constexpr int kMaxPoses = 65535;              // poses run on the grid's y dimension
 
 // The scratch itself.  Every GPU that loads the library holds these 1 MiB
 // until the process exits.  Calls share it: a call overwrites what the last
@@ -34,25 +37,58 @@ constexpr int kMaxPartials = 65536;           // 65536 x 16 B = 1 MiB per device
 // ordering between them) race on it.
 static __device__ __align__(256) Partial g_score_scratch[kMaxPartials];
 
-// Device address of g_score_scratch per device, looked up once per device
-// with that device current (host code may not use the symbol's own name as
-// a device address).
+// Device address of g_score_scratch per device, looked up with that device
+// current (host code may not use the symbol's own name as a device address).
+// The address belongs to the CUDA context it was looked up in, so each
+// entry remembers that context and is looked up again when the device's
+// current context is another one (after cudaDeviceReset, or when the primary
+// context was released and created anew).
 constexpr int kMaxDevices = 64;
-Partial *g_scratch_ptr[kMaxDevices] = {};
+struct ScratchEntry {
+    CUcontext ctx;
+    Partial *ptr;
+};
+ScratchEntry g_scratch[kMaxDevices] = {};
 std::mutex g_scratch_mu;
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+
+// cuCtxGetCurrent through the runtime's driver entry-point query, so the
+// library needs no link against the driver library; null if unavailable.
+CtxGetCurrentFn ctx_get_current() {
+    static CtxGetCurrentFn fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<CtxGetCurrentFn>(f);
+    }();
+    return fn;
+}
+
+CUcontext current_context() {
+    CUcontext c = nullptr;
+    if (CtxGetCurrentFn f = ctx_get_current())
+        if (f(&c) != CUDA_SUCCESS) c = nullptr;
+    return c;
+}
 
 rl_status scratch_for_current_device(Partial **out) {
     int dev = -1;
     RL_CK(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return fail(RL_ERR_INVALID_ARG, "device index beyond 63");
     std::lock_guard<std::mutex> g(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
+    ScratchEntry &e = g_scratch[dev];
+    const CUcontext now = current_context();
+    if (!e.ptr || (now && now != e.ctx)) {
         void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_score_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_score_scratch)", __FILE__, __LINE__);
-        g_scratch_ptr[dev] = static_cast<Partial *>(p);
+        cudaError_t err = cudaGetSymbolAddress(&p, g_score_scratch);
+        if (err != cudaSuccess) return cuda_fail(err, "cudaGetSymbolAddress(g_score_scratch)", __FILE__, __LINE__);
+        e.ptr = static_cast<Partial *>(p);
+        e.ctx = current_context();  // the lookup made the device's context current if it was not
     }
-    *out = g_scratch_ptr[dev];
+    *out = e.ptr;
     return RL_OK;
 }
 
@@ -205,6 +241,11 @@ extern "C" rl_status rl_score_poses_noalloc(const double box_lo[3], const double
     if (K->width < 1 || K->height < 1 || K->width > 8192 || K->height > 8192 || !(K->fx > 0) || !(K->fy > 0))
         return fail(RL_ERR_INVALID_ARG, "bad intrinsics");
     if (n < 1) return fail(RL_ERR_INVALID_ARG, "n must be >= 1");
+    if (n > kMaxPoses) {
+        char buf[128];
+        snprintf(buf, sizeof(buf), "n = %d exceeds the limit of %d poses per call", n, kMaxPoses);
+        return fail(RL_ERR_INVALID_ARG, buf);
+    }
     const int64_t tiles = ((int64_t)K->width * K->height + kTilePixels - 1) / kTilePixels;
     if ((int64_t)n * tiles > kMaxPartials) {
         char buf[256];

@@ -57,15 +57,14 @@ def oracle_model(w_name: str, n_train: int | None = None):
     return f, res, modes
 
 
-def oracle_query(w_name: str, q: int, params=None, debug=True):
+def oracle_query(w_name: str, q: int, params=None):
+    """(OracleRun of query q of a workload, ground-truth pose)."""
     w = WORKLOADS[w_name]
     f, res, modes = oracle_model(w_name)
     d, c, T, seed = w.query(q)
     p = dict(w.ransac if params is None else params)
     lv = oracle.forest_leaves(f, d, c, w.K.fx, n_trees=p["n_trees_used"])
-    r = oracle.relocalise(p, d, c, w.K, lv, modes, w.room().lo, w.room().hi, seed,
-                          1 << w.forest["depth"], debug=debug)
-    return r, T
+    return OracleRun(p, d, c, w.K, lv, modes, w.room().lo, w.room().hi, seed, 1 << w.forest["depth"]), T
 
 
 WORKLOADS = {w.name: w for w in [workloads.CONFIG1, workloads.CONFIG2, workloads.small_case()]}
@@ -83,47 +82,35 @@ def gpu_model(ctx, w: workloads.Workload, n_train=None):
     return forest
 
 
-LM_SEPARATIONS = []
-
-
-def check_refined_pose(dt, dr, e_gpu, e_ora, what):
-    """Poses after LM agree within 1 mm / 0.05 deg.  LM is iterative and
-    non-smooth (inlier set and accept/reject decisions): when such a decision
-    falls within FP32 rounding of its threshold, the FP32-accumulated GPU
-    trajectory and the FP64 oracle trajectory of a hypothesis with few
-    inliers can separate along a flat direction of Eq. 5.  Then the pose is
-    not unique and the test checks what is: both poses have the same energy
-    (1e-4 relative), and such separations stay rare."""
-    if dt <= POSE_T_TOL and dr <= POSE_R_TOL:
-        return
-    assert abs(e_gpu - e_ora) <= ENERGY_RTOL * abs(e_ora), (what, dt, dr, e_gpu, e_ora)
-    LM_SEPARATIONS.append((what, dt, dr))
-    assert len(LM_SEPARATIONS) <= 3, LM_SEPARATIONS
-
-
+# Per-session counts of the comparisons (printed at the end of a pytest run
+# by tests/conftest.py): queries compared, queries compared down to their
+# output, survivor sets handed back to the oracle after a legitimate
+# divergence, LM trajectories that separated, ICP decisions taken at their
+# threshold.
+SESSION = dict(queries=0, to_output=0, resumes=0, separations=0, icp_threshold=0)
 SEP_ENERGY_RTOL = 1e-3
 
 
-def lm_separated(gpu_poses, ora_poses, gpu_slots, ora_slots, gpu_E, ora_E, what):
-    """True when a survivor's LM trajectory separated from the oracle's: the
-    same hypothesis at the same rank ends more than 1 mm / 0.05 deg away.
-    After an accept/reject decision falls within FP32 rounding of its
-    threshold, the two trajectories continue from different points of a flat
-    valley of Eq. 5 and end at different poses, so their energies are no
-    longer those of one pose: they must agree within SEP_ENERGY_RTOL, the
-    separation counts toward the session's limit and the comparison of this
-    query stops (what follows from it differs legitimately)."""
-    for i, (sg, so) in enumerate(zip(gpu_slots, ora_slots)):
-        if sg != so:
-            continue
-        dt, dr = pose_err(as44(gpu_poses[i]), as44(ora_poses[i]))
-        if dt <= POSE_T_TOL and dr <= POSE_R_TOL:
-            continue
-        assert abs(gpu_E[i] - ora_E[i]) <= SEP_ENERGY_RTOL * abs(ora_E[i]), (what, i, dt, dr, gpu_E[i], ora_E[i])
-        LM_SEPARATIONS.append((what, dt, dr))
-        assert len(LM_SEPARATIONS) <= 3, LM_SEPARATIONS
-        return True
-    return False
+class OracleRun:
+    """The oracle's run of one query together with its inputs, so that a
+    comparison can hand the oracle the GPU's survivor set and poses after a
+    legitimate divergence and keep comparing what follows (oracle.relocalise
+    with resume)."""
+
+    def __init__(self, params, d, c, K, lv, modes, lo, hi, seed, lpt):
+        self.args = (params, d, c, K, lv, modes, lo, hi, seed, lpt)
+        self.p = dict(oracle.PARAM_DEFAULTS, **params)
+        self.d, self.K, self.lv, self.modes, self.lpt = d, K, lv, modes, lpt
+        self.result = oracle.relocalise(*self.args, debug=True)
+
+    def resume(self, stage, slots, poses):
+        return oracle.relocalise(*self.args, debug=True,
+                                 resume=(stage, np.asarray(slots, np.int32), np.asarray(poses)))
+
+    def energy(self, pose12, pix):
+        p = self.p
+        return oracle.energy(pose12, pix, self.d, self.K, self.lv, self.modes, p["k_top"], p["use_cov"],
+                             self.lpt, p["n_trees_used"])
 
 
 def score_tolerances(gpu_poses, ora_poses, ora_scores, max_range=6.0, incidence=10.0):
@@ -148,14 +135,18 @@ def check_scores(gpu_scores, ora_scores, tol, what):
     assert (np.abs(g[f] - o[f]) <= tol[f]).all(), (what, g, o, tol)
 
 
+def _energy_close(e_g, e_o):
+    return abs(e_g - e_o) <= ENERGY_RTOL * max(abs(e_o), 1e-30) + 1e-6
+
+
 def compare_survivors(gpu_slots, gpu_E, ora_slots, ora_E, what):
     """Equal survivor sets, allowing swaps between energies within SWAP_RTOL
-    of the cut.  Returns True when the sets are identical."""
+    of the cut; energies rank by rank within 1e-4 relative.  Returns True
+    when the sets are identical."""
     gs, os_ = list(gpu_slots), list(ora_slots)
     assert len(gs) == len(os_), f"{what}: {len(gs)} vs {len(os_)} survivors"
     for e_g, e_o in zip(gpu_E, ora_E):
-        assert abs(e_g - e_o) <= ENERGY_RTOL * max(abs(e_o), 1e-30) + 1e-6, \
-            f"{what}: energy {e_g} vs {e_o}"
+        assert _energy_close(e_g, e_o), f"{what}: energy {e_g} vs {e_o}"
     if set(gs) == set(os_):
         return True
     cut = max(ora_E)
@@ -165,61 +156,148 @@ def compare_survivors(gpu_slots, gpu_E, ora_slots, ora_E, what):
     return False
 
 
-def compare_results(rg, gr, dbg, orr, params, what):
-    """GPU result and debug record of one query against the oracle's, with
-    the bars stated in the module docstring."""
+def _by_slot_energies(gpu_slots, gpu_E, ora_slots, ora_E, what):
+    """Identical survivor sets; each survivor's energy within 1e-4 relative
+    of the oracle's FP64 energy of the same hypothesis."""
+    o = {int(s): e for s, e in zip(ora_slots, ora_E)}
+    assert set(o) == {int(s) for s in gpu_slots}, (what, sorted(o), sorted(gpu_slots))
+    for s, e in zip(gpu_slots, gpu_E):
+        assert _energy_close(e, o[int(s)]), f"{what}: slot {s} energy {e} vs {o[int(s)]}"
+
+
+def compare_results(rg, gr, dbg, orun, params, what):
+    """GPU result and debug record of one query against the oracle's
+    (an OracleRun), stage by stage, down to the output pose.
+
+    Bars: bit-exact winning iterations and pixel batches; hypothesis poses
+    1e-6 m / 1e-4 deg; energies 1e-4 relative; survivor sets equal up to
+    swaps of energies within 1e-5 relative of the cut; refined and output
+    poses 1 mm / 0.05 deg.  After a legitimate divergence -- a swap at the
+    cut, or an LM trajectory that separated along a flat valley of Eq. 5
+    after an accept/reject decision fell within FP32 rounding of its
+    threshold -- the oracle is handed the GPU's survivor set and poses at
+    that stage boundary and the comparison continues at the same bars
+    against its re-run.  A separated hypothesis must end within
+    SEP_ENERGY_RTOL of the oracle's energy, and its GPU energy within 1e-4 of
+    the FP64 energy of the GPU's own pose.  Returns the counts of this query
+    (also added to SESSION)."""
+    assert isinstance(orun, OracleRun)
+    rep = dict(resumes=0, separations=0, icp_threshold=0)
+    orr = orun.result
     od = orr["debug"]
+    SESSION["queries"] += 1
     # generation: identical winning iteration for every slot (bit-exact choices)
-    assert np.array_equal(dbg["hyp_iter"], od["hyp_iter"])
-    ok = dbg["hyp_iter"] >= 0
-    for s in np.nonzero(ok)[0]:
+    assert np.array_equal(dbg["hyp_iter"], od["hyp_iter"]), what
+    for s in np.nonzero(dbg["hyp_iter"] >= 0)[0]:
         dt, dr = pose_err(as44(dbg["hyp_pose"][s]), as44(od["hyp_pose"][s]))
         assert dt < 1e-6 and dr < 1e-4, (what, s, dt, dr)
-    assert gr["n_hypotheses"] == orr["n_hypotheses"]
+    assert gr["n_hypotheses"] == orr["n_hypotheses"], what
     if orr["n_hypotheses"] == 0:
-        assert gr["status"] == rg.RL_NO_POSE and orr["status"] == 1
-        return
-    # batch pixels: bit-exact
+        assert gr["status"] == rg.RL_NO_POSE and orr["status"] == 1, what
+        SESSION["to_output"] += 1
+        return rep
+    # pixel batches: bit-exact
     nb = min(16, dbg["n_rounds"] + 1)
-    assert np.array_equal(dbg["batch_pix"][:nb], od["batch_pix"][:nb])
-    # cull survivors
+    assert np.array_equal(dbg["batch_pix"][:nb], od["batch_pix"][:nb]), what
+    # initial cull
     nc = min(params["n_cull"], orr["n_hypotheses"])
-    same = compare_survivors(dbg["cull_slot"][:nc], dbg["cull_energy"][:nc],
-                             od["cull_slot"][:nc], od["cull_energy"][:nc], f"{what} cull")
-    if not same:
-        return
+    gs, ge = dbg["cull_slot"][:nc], dbg["cull_energy"][:nc]
+    if not compare_survivors(gs, ge, od["cull_slot"][:nc], od["cull_energy"][:nc], f"{what} cull"):
+        orr = orun.resume(0, gs, od["hyp_pose"][gs])
+        od = orr["debug"]
+        rep["resumes"] += 1
+        _by_slot_energies(gs, ge, od["cull_slot"][:nc], od["cull_energy"][:nc], f"{what} cull (handed in)")
     # preemptive rounds
-    assert dbg["n_rounds"] == od["n_rounds"]
+    assert dbg["n_rounds"] == od["n_rounds"], what
     off = 0
     for r in range(dbg["n_rounds"]):
-        k = od["round_count"][r]
-        assert dbg["round_count"][r] == k
-        gs, ge = dbg["round_slot"][r][:k], dbg["round_energy"][r][:k]
-        os_, oe = od["round_slot"][off:off + k], od["round_energy"][off:off + k]
-        if lm_separated(dbg["round_pose"][r][:k], od["round_pose"][off:off + k], gs, os_, ge, oe,
-                        f"{what} round {r}"):
-            return
-        if not compare_survivors(gs, ge, os_, oe, f"{what} round {r}"):
-            return
-        for i in range(k):
-            dt, dr = pose_err(as44(dbg["round_pose"][r][i]), as44(od["round_pose"][off + i]))
-            check_refined_pose(dt, dr, ge[i], oe[i], f"{what} round {r} survivor {i}")
+        k = int(od["round_count"][r])
+        assert dbg["round_count"][r] == k, what
+        gs, ge, gp = dbg["round_slot"][r][:k], dbg["round_energy"][r][:k], dbg["round_pose"][r][:k]
+        os_, oe, op = od["round_slot"][off:off + k], od["round_energy"][off:off + k], od["round_pose"][off:off + k]
+        oi = {int(s): i for i, s in enumerate(os_)}
+        separated = []
+        for i, s in enumerate(gs):
+            if int(s) not in oi:
+                continue
+            j = oi[int(s)]
+            dt, dr = pose_err(as44(gp[i]), as44(op[j]))
+            if dt > POSE_T_TOL or dr > POSE_R_TOL:
+                assert abs(ge[i] - oe[j]) <= SEP_ENERGY_RTOL * abs(oe[j]), (what, r, int(s), dt, dr, ge[i], oe[j])
+                separated.append((int(s), dt, dr))
+        diverged = bool(separated)
+        if not diverged:
+            diverged = not compare_survivors(gs, ge, os_, oe, f"{what} round {r}")
+        if diverged:
+            orr = orun.resume(r + 1, gs, gp)
+            od = orr["debug"]
+            rep["resumes"] += 1
+            rep["separations"] += len(separated)
+            _by_slot_energies(gs, ge, od["round_slot"][off:off + k], od["round_energy"][off:off + k],
+                              f"{what} round {r} (handed in)")
         off += k
-    # ranking scores of the chosen set, then the output pose
-    assert gr["n_chosen"] == orr["n_chosen"]
-    if params.get("icp") and not check_icp(gr, orr, params, what):
-        return
+    # the chosen set, matched by generation slot
+    assert gr["n_chosen"] == orr["n_chosen"], what
+    nch = gr["n_chosen"]
+    g_slots = [int(s) for s in gr["chosen_slot"][:nch]]
+    o_slots = [int(s) for s in orr["chosen_slot"][:nch]]
+    assert sorted(g_slots) == sorted(o_slots), (what, g_slots, o_slots)
+    om = [o_slots.index(s) for s in g_slots]          # oracle index of GPU chosen c
+    for c, o in enumerate(om):
+        assert _energy_close(gr["chosen_energy"][c], orr["chosen_energy"][o]), (what, c)
+    icp_same = [True] * nch
+    if params.get("icp"):
+        mf = dict(oracle.PARAM_DEFAULTS, **params)["icp_min_frac"]
+        if params["rank"]:
+            for c, o in enumerate(om):
+                icp_same[c] = check_icp_one(bool(gr["icp_mask"] >> c & 1), gr["chosen_icp_frac"][c],
+                                            gr["chosen_pose"][c], bool(orr["icp_mask"] >> o & 1),
+                                            orr["chosen_icp_frac"][o], orr["chosen_pose"][o], mf,
+                                            f"{what} chosen {c}")
+        else:
+            icp_same[0] = check_icp_one(bool(gr["icp_mask"] & 1), gr["chosen_icp_frac"][0], gr["pose"],
+                                        bool(orr["icp_mask"] & 1), orr["chosen_icp_frac"][0], orr["pose"],
+                                        mf, f"{what} output")
+        rep["icp_threshold"] += icp_same.count(False)
     if params["rank"]:
-        tol = score_tolerances(gr["chosen_pose"], orr["chosen_pose"], orr["chosen_score"])
-        check_scores(gr["chosen_score"], orr["chosen_score"], tol, what)
-        if gr["best"] != orr["best"]:
-            # argmin between near-tied scores: either choice is valid
-            a, b = gr["best"], orr["best"]
-            assert abs(orr["chosen_score"][a] - orr["chosen_score"][b]) <= tol[a] + tol[b], (what, a, b)
-            return
-    dt, dr = pose_err(gr["pose"], orr["pose"])
-    np.testing.assert_allclose(gr["energy"], orr["energy"], rtol=ENERGY_RTOL)
-    check_refined_pose(dt, dr, gr["energy"], orr["energy"], f"{what} output")
+        for c, o in enumerate(om):
+            if not icp_same[c]:
+                continue
+            dt, dr = pose_err(gr["chosen_pose"][c], orr["chosen_pose"][o])
+            assert dt <= POSE_T_TOL and dr <= POSE_R_TOL, (what, "chosen", c, dt, dr)
+        keep = [c for c in range(nch) if icp_same[c]]
+        gsc = np.array([gr["chosen_score"][c] for c in keep])
+        osc = np.array([orr["chosen_score"][om[c]] for c in keep])
+        tol = score_tolerances([gr["chosen_pose"][c] for c in keep],
+                               [orr["chosen_pose"][om[c]] for c in keep], osc)
+        check_scores(gsc, osc, tol, what)
+        gb, ob = gr["best"], orr["best"]
+        if g_slots[gb] != o_slots[ob]:
+            # argmin between near-tied scores (or a pose whose ICP decision
+            # fell at its threshold): either choice is valid
+            a, b = om[gb], ob
+            if icp_same[gb] and icp_same[om.index(ob)]:
+                ta = tol[keep.index(gb)]
+                tb = tol[keep.index(om.index(ob))]
+                assert abs(orr["chosen_score"][a] - orr["chosen_score"][b]) <= ta + tb, (what, a, b)
+        # the output is the GPU's chosen pose xi* and its RANSAC energy
+        assert np.array_equal(gr["pose"], gr["chosen_pose"][gb]), what
+        o_out_pose, o_out_E = orr["chosen_pose"][om[gb]], orr["chosen_energy"][om[gb]]
+        out_same = icp_same[gb]
+    else:
+        o_out_pose, o_out_E = orr["pose"], orr["energy"]
+        out_same = icp_same[0] if params.get("icp") else True
+    np.testing.assert_allclose(gr["energy"], o_out_E, rtol=ENERGY_RTOL, err_msg=what)
+    if out_same:
+        dt, dr = pose_err(gr["pose"], o_out_pose)
+        assert dt <= POSE_T_TOL and dr <= POSE_R_TOL, (what, "output", dt, dr)
+    SESSION["to_output"] += 1
+    for k in ("resumes", "separations", "icp_threshold"):
+        SESSION[k] += rep[k]
+    # separations stay rare: at most one query in ten (and three per session
+    # below thirty queries)
+    assert SESSION["separations"] <= max(3, SESSION["queries"] // 10), SESSION
+    return rep
 
 
 ICP_FRAC_TOL = 1e-3   # inlier fractions: a few pixels at the inlier radius flip in FP32
@@ -244,32 +322,3 @@ def check_icp_one(ok_g, frac_g, P_g, ok_o, frac_o, P_o, min_frac, what):
     dt, dr = pose_err(P_g, P_o)
     assert dt <= POSE_T_TOL and dr <= POSE_R_TOL, (what, dt, dr)
     return True
-
-
-def check_icp(gr, orr, params, what):
-    """ICP outputs of a relocalisation (ranked: every chosen pose;
-    unranked: the output pose).  False when a success decision differs at
-    the threshold (what follows from it then differs legitimately)."""
-    mf = dict(oracle.PARAM_DEFAULTS, **params)["icp_min_frac"]
-    if params["rank"]:
-        same = True
-        for c in range(gr["n_chosen"]):
-            same &= check_icp_one(bool(gr["icp_mask"] >> c & 1), gr["chosen_icp_frac"][c], gr["chosen_pose"][c],
-                                  bool(orr["icp_mask"] >> c & 1), orr["chosen_icp_frac"][c], orr["chosen_pose"][c],
-                                  mf, f"{what} chosen {c}")
-        return same
-    return check_icp_one(bool(gr["icp_mask"] & 1), gr["chosen_icp_frac"][0], gr["pose"],
-                         bool(orr["icp_mask"] & 1), orr["chosen_icp_frac"][0], orr["pose"], mf, f"{what} output")
-
-
-def oracle_modes_from_export(ex, m_max):
-    """Oracle mode store holding exactly the library's decoded modes (both
-    sides then score the same mode positions)."""
-    L = ex["nmodes"].shape[0]
-    m = oracle.Modes(L, m_max)
-    m.nmodes[:] = ex["nmodes"]
-    m.pos[:] = ex["mode_pos"]
-    m.rgb[:] = ex["mode_rgb"]
-    m.U[:] = ex["mode_U"]
-    m.size[:] = ex["mode_size"]
-    return m

@@ -3,10 +3,12 @@
 50), 60% of the stored modes moved to points uniform in the room volume, and
 leaf modes stored as FP16 offsets from FP32 centroids versus all FP32.
 
-The oracle reads the library's decoded modes (the positions both sides
-score are identical), so parity keeps the usual bars; the 5 cm / 5 degree
-success rate over 200 seeded queries is measured for both storage
-precisions."""
+The oracle builds its own mode store: its reservoirs and Really Quick Shift
+modes of the config-2 training, the same outlier draw (synth.outliers) on
+its own decoded positions, written back in the store's precision by the
+oracle.  The library's decoded positions must equal the oracle's bit for
+bit, and parity keeps the usual bars; the 5 cm / 5 degree success rate over
+200 seeded queries is measured for both storage precisions."""
 import numpy as np
 import pytest
 
@@ -44,6 +46,22 @@ def queries():
 @pytest.fixture(scope="module")
 def nodes():
     return H.oracle_forest_nodes(workloads.CONFIG2)
+
+
+def _oracle_modes(w):
+    """The oracle's config-5 mode store: config-2 reservoirs clustered in
+    the workload's storage precision, 60% of the stored modes moved by the
+    outlier draw, positions written back in that precision."""
+    f, res, _ = H.oracle_model(workloads.CONFIG2.name)
+    fp = w.forest
+    modes = oracle.Modes(res.n_leaves, fp["m_max"])
+    oracle.update_modes(res, modes, fp["sigma"], fp["tau_c"], fp["min_cluster_size"],
+                        cov_eps=fp["cov_eps"], fp16_offsets=bool(fp["mode_precision"]))
+    room = w.room()
+    pos, hit = outliers.replace_modes(modes.pos, modes.nmodes, room.lo, room.hi,
+                                      workloads.CONFIG5_OUTLIER_FRACTION, workloads.CONFIG5_OUTLIER_SEED)
+    oracle.set_mode_positions(modes, pos, bool(fp["mode_precision"]))
+    return modes
 
 
 def _success(pose, truth):
@@ -87,15 +105,18 @@ def test_config5_outlier_modes(rg, ctx, queries, nodes, precision):
     SUCCESS[precision] = ok / N_SUCCESS
     print(f"config 5 {w.name}: success {ok}/{N_SUCCESS}")
 
-    # parity with the FP64 oracle on the library's decoded modes
-    modes = H.oracle_modes_from_export(ex2, M)
+    # the oracle's own store: same modes, same decoded outlier positions
+    modes = _oracle_modes(w)
+    assert np.array_equal(ex2["nmodes"], modes.nmodes)
+    assert np.array_equal(ex2["mode_pos"][stored].view(np.uint32), modes.pos[stored].view(np.uint32))
+    assert np.array_equal(ex2["mode_rgb"][stored], modes.rgb[stored])
+    np.testing.assert_allclose(ex2["mode_U"][stored], modes.U[stored], rtol=2e-7, atol=0)
     rel1 = rg.Relocaliser(forest, scene, w.ransac, w.width, w.height, 1)
     for q in range(N_ORACLE):
         d, c, T, seed = queries[q]
         gr = rel1.relocalise(d, c, w.K, seed)
         lv = oracle.forest_leaves(nodes, d, c, w.K.fx, n_trees=w.ransac["n_trees_used"])
-        orr = oracle.relocalise(w.ransac, d, c, w.K, lv, modes, room.lo, room.hi, seed,
-                                1 << w.forest["depth"], debug=True)
+        orr = H.OracleRun(w.ransac, d, c, w.K, lv, modes, room.lo, room.hi, seed, 1 << w.forest["depth"])
         H.compare_results(rg, gr, rel1.debug(0), orr, w.ransac, f"config5 {w.name} q{q}")
     rel1.close()
     forest.close()

@@ -94,8 +94,8 @@ def test_reservoirs_and_modes_bitexact(rg, small):
 def _compare_query(rg, rel, w, q, params):
     d, c, T, seed = w.query(q)
     gr = rel.relocalise(d, c, w.K, seed)
-    orr, _ = H.oracle_query(w.name, q, params)
-    H.compare_results(rg, gr, rel.debug(0), orr, params, f"q{q}")
+    orun, _ = H.oracle_query(w.name, q, params)
+    return H.compare_results(rg, gr, rel.debug(0), orun, params, f"q{q}")
 
 
 def test_relocalise_parity_small(rg, ctx, small):

@@ -57,8 +57,8 @@ def test_parity_on_corrupted_inputs(rg, ctx, kind, level):
             d = workloads.corrupt(d, kind, level, 10000 + q)
             gr = rel.relocalise(d, c, w.K, seed)
             lv = oracle.forest_leaves(f, d, c, w.K.fx, n_trees=params["n_trees_used"])
-            orr = oracle.relocalise(params, d, c, w.K, lv, modes, room.lo, room.hi, seed,
-                                    1 << w.forest["depth"], debug=True)
+            orr = H.OracleRun(params, d, c, w.K, lv, modes, room.lo, room.hi, seed,
+                                    1 << w.forest["depth"])
             H.compare_results(rg, gr, rel.debug(0), orr, params, f"{kind} {level} q{q} icp={params.get('icp', 0)}")
         rel.close()
     scene.close()
@@ -79,8 +79,7 @@ def test_config2_query_with_90_percent_missing_depth(rg, ctx):
     d = workloads.corrupt(d, "missing", 0.9, 10003)
     gr = rel.relocalise(d, c, w.K, seed)
     lv = oracle.forest_leaves(f, d, c, w.K.fx, n_trees=w.ransac["n_trees_used"])
-    orr = oracle.relocalise(w.ransac, d, c, w.K, lv, modes, room.lo, room.hi, seed, 1 << w.forest["depth"],
-                            debug=True)
+    orr = H.OracleRun(w.ransac, d, c, w.K, lv, modes, room.lo, room.hi, seed, 1 << w.forest["depth"])
     H.compare_results(rg, gr, rel.debug(0), orr, w.ransac, "config2 missing 0.9")
     rel.close()
     scene.close()

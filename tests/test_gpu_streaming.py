@@ -155,8 +155,8 @@ def test_tracking_loss_protocol_parity(rg, ctx):
         if t >= 1:
             gr = rel.fetch(stream=sR)[0]
             lv = oracle.forest_leaves(f, d, c, w.K.fx, n_trees=w.ransac["n_trees_used"])
-            orr = oracle.relocalise(w.ransac, d, c, w.K, lv, modes, room.lo, room.hi, seed,
-                                    1 << w.forest["depth"], debug=True)
+            orr = H.OracleRun(w.ransac, d, c, w.K, lv, modes, room.lo, room.hi, seed,
+                                    1 << w.forest["depth"])
             H.compare_results(rg, gr, rel.debug(0), orr, w.ransac, f"tracking loss frame {t}")
             found += gr["status"] == rg.RL_POSE_FOUND
         res.add_frame(d, c, w.K, T, w.forest["grid_step"], w.forest["grid_origin"])
@@ -208,8 +208,7 @@ def test_tracking_loss_step_config2(rg, ctx):
     seed = 123457
     gr = rel.relocalise(d, c, w.K, seed)
     lv = oracle.forest_leaves(f, d, c, w.K.fx)
-    orr = oracle.relocalise(w.ransac, d, c, w.K, lv, modes, room.lo, room.hi, seed, 1 << w.forest["depth"],
-                            debug=True)
+    orr = H.OracleRun(w.ransac, d, c, w.K, lv, modes, room.lo, room.hi, seed, 1 << w.forest["depth"])
     H.compare_results(rg, gr, rel.debug(0), orr, w.ransac, "config2 tracking-loss frame 3")
     rel.close()
     scene.close()

@@ -6,13 +6,15 @@ synchronisation of cudaMalloc/cudaFree).
 The entry point is called through the C ABI with device inputs and outputs
 only, twice in a row (the second call reuses the library's fixed scratch
 array), and each result is checked against the allocating entry point
-rl_score_poses on the same poses."""
+rl_score_poses on the same poses and against the FP64 oracle's score
+(Eq. 6-7) of every pose."""
 import ctypes
 import math
 
 import numpy as np
 import pytest
 
+import oracle
 from synth import rooms, workloads
 
 pytestmark = pytest.mark.gpu
@@ -71,6 +73,15 @@ def test_noalloc_scores_match_allocating_entry_point():
         np.testing.assert_allclose(s[fin], ref_s[fin], rtol=1e-4)
         np.testing.assert_allclose(f, ref_f, atol=1e-6)
         assert np.isinf(s[-1]) and fin.sum() >= 10
+        # the FP64 oracle: same finite/infinite split, scores within 1e-4
+        # relative (FP32 ray arithmetic, FP64 partial sums), valid fractions
+        # within a few rays of the FP64 decision
+        for i in range(n):
+            o_s, _, o_f = oracle.depth_score(poses[i], depth, w.K, room.lo, room.hi)
+            assert np.isinf(s[i]) == np.isinf(o_s), (call_no, i, s[i], o_s)
+            if np.isfinite(o_s):
+                assert abs(s[i] - o_s) <= 1e-4 * o_s, (call_no, i, s[i], o_s)
+            assert abs(f[i] - o_f) <= 1e-5, (call_no, i, f[i], o_f)
     # a request beyond the fixed scratch is refused with the limit spelled out
     n = 300
     p_dev = torch.zeros((n, 16), dtype=torch.float64, device="cuda")
@@ -81,4 +92,12 @@ def test_noalloc_scores_match_allocating_entry_point():
                                   ctypes.c_void_p(s_dev.data_ptr()), None)
     assert st == 1  # RL_ERR_INVALID_ARG
     assert b"at most 218 poses" in L.rl_last_error()
+    # more poses than the launch grid takes, even where the scratch would
+    # fit them (frames of at most 1024 pixels need one record per pose)
+    K1 = rg.intrinsics(rooms.Intrinsics(20.0, 20.0, 16.0, 16.0, 32, 32))
+    st = L.rl_score_poses_noalloc(lo.ctypes.data_as(ctypes.c_void_p), hi.ctypes.data_as(ctypes.c_void_p),
+                                  ctypes.c_void_p(d_dev.data_ptr()), ctypes.byref(K1),
+                                  ctypes.c_void_p(p_dev.data_ptr()), 65536, stream,
+                                  ctypes.c_void_p(s_dev.data_ptr()), None)
+    assert st == 1 and b"limit of 65535 poses" in L.rl_last_error()
     scene.close()
