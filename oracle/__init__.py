@@ -134,7 +134,7 @@ def _declare(L):
                                  ctypes.POINTER(Result), ctypes.POINTER(Debug)]
     L.orc_relocalise_from.argtypes = [ctypes.POINTER(Params), P, P, I32, I32, F32, F32, F32, F32,
                                       P, I32, I32, P, P, P, P, I32, P, P, U64,
-                                      ctypes.POINTER(Resume), ctypes.POINTER(Result),
+                                      ctypes.POINTER(Resume), I32, ctypes.POINTER(Result),
                                       ctypes.POINTER(Debug)]
     L.orc_cascade.argtypes = [I32, ctypes.POINTER(Params), P, P, P, P, P, P, P, P, P, P,
                               I32, I32, P, P, P, P, I32, P, P, U64, ctypes.POINTER(Result)]
@@ -423,10 +423,10 @@ def _result_dict(r: Result):
 
 def relocalise(params: dict, depth_img, rgb, K, leaves, modes: Modes, box_lo, box_hi, seed,
                leaves_per_tree, debug=False, resume=None):
-    """One relocalisation (Sec. 3.2.3-3.2.4).  resume = (stage, slots,
-    poses [n][12]) hands a survivor set in at a stage boundary of the
-    preemptive loop (stage 0: after the cull; r + 1: after round r); see
-    orc_resume in oracle.h."""
+    """One relocalisation (Sec. 3.2.3-3.2.4).  resume = a list of
+    (stage, slots, poses [n][12]) hands survivor sets in at stage boundaries
+    of the preemptive loop (stage 0: after the cull; r + 1: after round r),
+    at most one per stage; see orc_resume in oracle.h."""
     p = make_params(**params)
     d = _c(depth_img, np.float32)
     c = _c(rgb, np.uint8)
@@ -447,17 +447,21 @@ def relocalise(params: dict, depth_img, rgb, K, leaves, modes: Modes, box_lo, bo
         )
         for k, a in arrays.items():
             setattr(dbg, k, _p(a))
-    rs = None
-    if resume is not None:
-        stage, slots, poses = resume
-        rs_slot = _c(slots, np.int32)
-        rs_pose = _c(np.asarray(poses, np.float64).reshape(-1, 12), np.float64)
-        assert rs_slot.shape[0] == rs_pose.shape[0]
-        rs = Resume(int(stage), int(rs_slot.shape[0]), _p(rs_slot), _p(rs_pose))
+    rs, keep = None, []
+    if resume:
+        stages = [int(st) for st, _, _ in resume]
+        assert len(set(stages)) == len(stages), "one hand-in per stage"
+        rs = (Resume * len(resume))()
+        for k, (stage, slots, poses) in enumerate(resume):
+            rs_slot = _c(slots, np.int32)
+            rs_pose = _c(np.asarray(poses, np.float64).reshape(-1, 12), np.float64)
+            assert rs_slot.shape[0] == rs_pose.shape[0]
+            keep += [rs_slot, rs_pose]
+            rs[k] = Resume(int(stage), int(rs_slot.shape[0]), _p(rs_slot), _p(rs_pose))
     lib().orc_relocalise_from(ctypes.byref(p), _p(d), _p(c), W, H, K.fx, K.fy, K.cx, K.cy, _p(lv),
                               lv.shape[0], leaves_per_tree, _p(modes.nmodes), _p(modes.pos),
                               _p(modes.rgb), _p(modes.U), modes.m_max, _p(lo), _p(hi), seed,
-                              ctypes.byref(rs) if rs is not None else None,
+                              rs, len(resume) if resume else 0,
                               ctypes.byref(res), ctypes.byref(dbg) if debug else None)
     out = _result_dict(res)
     if debug:

@@ -184,8 +184,9 @@ void orc_relocalise(const orc_params *p,
  * set at that point; their energies are recomputed in FP64 on the pixel set
  * of that point and the set is re-sorted by (E, slot).  Everything after it
  * (later rounds, the chosen set, ICP, ranking) runs as in orc_relocalise.
- * The tests use it to keep comparing a query whose survivor set or LM
- * trajectory legitimately left the oracle's. */
+ * Several hand-ins (distinct stages) apply in stage order.  The tests use
+ * them to keep comparing a query whose survivor set or LM trajectory
+ * legitimately left the oracle's. */
 typedef struct {
     int32_t stage;
     int32_t n;
@@ -193,7 +194,7 @@ typedef struct {
     const double *pose;       /* [n][12] */
 } orc_resume;
 
-/* orc_relocalise with an optional survivor set handed in (NULL: none). */
+/* orc_relocalise with n_rs survivor sets handed in (rs may be NULL if 0). */
 void orc_relocalise_from(const orc_params *p,
                          const float *depth_img, const uint8_t *rgb, int W, int H,
                          float fx, float fy, float cx, float cy,
@@ -201,7 +202,7 @@ void orc_relocalise_from(const orc_params *p,
                          const uint8_t *nmodes, const float *mpos, const uint8_t *mrgb,
                          const float *mU, int m_max,
                          const double box_lo[3], const double box_hi[3],
-                         uint64_t query_seed, const orc_resume *rs, orc_result *out,
+                         uint64_t query_seed, const orc_resume *rs, int n_rs, orc_result *out,
                          orc_debug *dbg);
 
 /* Eq. 5 energy of one pose on a pixel set (pixel ids into the frame). */

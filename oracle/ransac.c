@@ -598,6 +598,14 @@ static void sample_batch(const orc_params *p, const uint32_t key[2], int b,
  * set replaces the oracle's own, and each survivor's Eq. 5 energy is
  * recomputed in FP64 on the pixel set of that point before the usual
  * stable sort by (E, slot). */
+static const orc_resume *handin_at(const orc_resume *rs, int n_rs, int stage)
+{
+    for (int k = 0; k < n_rs; ++k)
+        if (rs[k].stage == stage)
+            return &rs[k];
+    return NULL;
+}
+
 static void replace_survivors(const orc_resume *rs, hyp_t *hyp, int *n, const int32_t *I, int nI,
                               const float *depth_img, int W, int Himg, float fx, float fy,
                               float cx, float cy, const uint16_t *leaves, const orc_params *p,
@@ -626,7 +634,7 @@ void orc_relocalise(const orc_params *p,
 {
     orc_relocalise_from(p, depth_img, rgb, W, Himg, fx, fy, cx, cy, leaves, n_trees_forest,
                         leaves_per_tree, nmodes, mpos, mrgb, mU, m_max, box_lo, box_hi,
-                        query_seed, NULL, out, dbg);
+                        query_seed, NULL, 0, out, dbg);
 }
 
 void orc_relocalise_from(const orc_params *p,
@@ -636,10 +644,11 @@ void orc_relocalise_from(const orc_params *p,
                          const uint8_t *nmodes, const float *mpos, const uint8_t *mrgb,
                          const float *mU, int m_max,
                          const double box_lo[3], const double box_hi[3],
-                         uint64_t query_seed, const orc_resume *rs, orc_result *out,
+                         uint64_t query_seed, const orc_resume *rs, int n_rs, orc_result *out,
                          orc_debug *dbg)
 {
     (void)n_trees_forest;
+    const orc_resume *hand;
     const int WH = W * Himg;
     const uint32_t key[2] = {(uint32_t)query_seed, (uint32_t)(query_seed >> 32)};
     memset(out, 0, sizeof(*out));
@@ -701,8 +710,8 @@ void orc_relocalise_from(const orc_params *p,
     qsort(hyp, (size_t)n, sizeof(hyp_t), hyp_cmp);
     if (n > p->n_cull)
         n = p->n_cull;
-    if (rs && rs->stage == 0)
-        replace_survivors(rs, hyp, &n, I, nI, depth_img, W, Himg, fx, fy, cx, cy, leaves, p,
+    if ((hand = handin_at(rs, n_rs, 0)) != NULL)
+        replace_survivors(hand, hyp, &n, I, nI, depth_img, W, Himg, fx, fy, cx, cy, leaves, p,
                           leaves_per_tree, nmodes, mpos, mU, m_max);
     if (dbg && dbg->cull_slot)
         for (int h = 0; h < n; ++h) {
@@ -738,8 +747,8 @@ void orc_relocalise_from(const orc_params *p,
         }
         qsort(hyp, (size_t)n, sizeof(hyp_t), hyp_cmp);
         n = (n + 1) / 2;
-        if (rs && rs->stage == n_rounds + 1)
-            replace_survivors(rs, hyp, &n, I, nI, depth_img, W, Himg, fx, fy, cx, cy, leaves, p,
+        if ((hand = handin_at(rs, n_rs, n_rounds + 1)) != NULL)
+            replace_survivors(hand, hyp, &n, I, nI, depth_img, W, Himg, fx, fy, cx, cy, leaves, p,
                               leaves_per_tree, nmodes, mpos, mU, m_max);
         if (dbg && n_rounds < 16) {
             if (dbg->round_count) dbg->round_count[n_rounds] = n;

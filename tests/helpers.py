@@ -101,11 +101,14 @@ class OracleRun:
         self.args = (params, d, c, K, lv, modes, lo, hi, seed, lpt)
         self.p = dict(oracle.PARAM_DEFAULTS, **params)
         self.d, self.K, self.lv, self.modes, self.lpt = d, K, lv, modes, lpt
+        self.handins = []
         self.result = oracle.relocalise(*self.args, debug=True)
 
     def resume(self, stage, slots, poses):
-        return oracle.relocalise(*self.args, debug=True,
-                                 resume=(stage, np.asarray(slots, np.int32), np.asarray(poses)))
+        """Re-runs the oracle with this survivor set handed in at `stage`,
+        on top of every earlier hand-in of this query."""
+        self.handins.append((stage, np.array(slots, np.int32), np.array(poses, np.float64)))
+        return oracle.relocalise(*self.args, debug=True, resume=self.handins)
 
     def energy(self, pose12, pix):
         p = self.p

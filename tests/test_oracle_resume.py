@@ -39,12 +39,17 @@ def test_hand_in_of_own_state_reproduces_the_run(run):
     w, modes, lv, d, args, r = run
     dbg = r["debug"]
     for stage in range(dbg["n_rounds"] + 1):
-        r2 = oracle.relocalise(*args, debug=True, resume=(stage,) + _stage_state(dbg, stage))
+        r2 = oracle.relocalise(*args, debug=True, resume=[(stage,) + _stage_state(dbg, stage)])
         for k in ("pose", "energy", "score", "n_chosen", "best", "chosen_pose", "chosen_score",
                   "chosen_slot", "n_pixels"):
             assert np.array_equal(r[k], r2[k]), (stage, k)
         for k in ("cull_slot", "cull_energy", "round_slot", "round_energy", "round_pose", "round_count"):
             assert np.array_equal(dbg[k], r2["debug"][k]), (stage, k)
+    # every stage handed in at once: the same again
+    r3 = oracle.relocalise(*args, debug=True,
+                           resume=[(st,) + _stage_state(dbg, st) for st in range(dbg["n_rounds"] + 1)])
+    assert np.array_equal(r["pose"], r3["pose"]) and np.array_equal(r["chosen_slot"], r3["chosen_slot"])
+    assert np.array_equal(dbg["round_pose"], r3["debug"]["round_pose"])
 
 
 def test_hand_in_replaces_the_survivor_set(run):
@@ -58,7 +63,7 @@ def test_hand_in_replaces_the_survivor_set(run):
     culled = [s for s in np.nonzero(dbg["hyp_iter"] >= 0)[0] if s not in set(slots)]
     slots = np.array(list(slots[:-1]) + [culled[0]], np.int32)
     poses = dbg["hyp_pose"][slots]
-    r2 = oracle.relocalise(*args, debug=True, resume=(0, slots, poses))
+    r2 = oracle.relocalise(*args, debug=True, resume=[(0, slots, poses)])
     d2 = r2["debug"]
     n = len(slots)
     assert sorted(d2["cull_slot"][:n]) == sorted(slots)
@@ -72,6 +77,12 @@ def test_hand_in_replaces_the_survivor_set(run):
     np.testing.assert_allclose(d2["cull_energy"][:n], np.sort(E), rtol=1e-12)
     k = d2["round_count"][0]
     assert set(d2["round_slot"][:k]) <= set(slots) and culled[0] in set(d2["cull_slot"][:n])
+    # a later hand-in keeps the earlier one: the modified run's own round-1
+    # survivors handed in on top reproduce the modified run
+    hand = [(0, slots, poses), (2,) + _stage_state(d2, 2)]
+    r3 = oracle.relocalise(*args, debug=True, resume=hand)
+    assert np.array_equal(r3["pose"], r2["pose"]) and np.array_equal(r3["chosen_slot"], r2["chosen_slot"])
+    assert np.array_equal(r3["debug"]["cull_slot"], d2["cull_slot"])
 
 
 def _U_full(modes):
