@@ -394,11 +394,13 @@ rl_status rl_tuning_cache_write(const char *path, const char *key, const rl_tuni
  * LM trial evaluations, rays cast, generation attempts (stage 1: draws and
  * colour check), generation stage-2 evaluations (spread and rigidity), ICP
  * pixel evaluations (valid pixels visited, over all iterations), ranking rays
- * re-evaluated in FP64 (hit decision within the FP32 margin)).
+ * re-evaluated in FP64 (hit decision within the FP32 margin), LM
+ * (H,px,mode) distances actually evaluated (below the LM triples where a
+ * certified bound settled the nearest mode without a full search)).
  * Enabling resets all counters.  The
  * paper has no counterpart; its Sec. A.1 timing breakdown is per stage. */
 #define RL_N_KERNELS 12
-#define RL_N_WORK 11
+#define RL_N_WORK 12
 rl_status rl_reloc_profile(rl_reloc *r, int32_t enable);
 rl_status rl_reloc_profile_read(rl_reloc *r, double *ms /* [RL_N_KERNELS] */,
                                 int64_t *launches /* [RL_N_KERNELS] */,

@@ -348,7 +348,7 @@ class Relocaliser:
         names = [lib().rl_kernel_name(i).decode() for i in range(N_KERNELS)]
         kernels = {names[i]: dict(ms=float(ms[i]), launches=int(launches[i])) for i in range(N_KERNELS)}
         keys = ["energy_pairs", "energy_modes", "lm_pairs", "lm_modes", "lm_inliers", "lm_trial", "rays",
-                "hyp_attempts", "hyp_stage2", "icp_pixels", "rays_fp64"]
+                "hyp_attempts", "hyp_stage2", "icp_pixels", "rays_fp64", "lm_evals"]
         return kernels, {k: int(v) for k, v in zip(keys, work)}
 
     def debug(self, q: int = 0):

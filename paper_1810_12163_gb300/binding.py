@@ -35,7 +35,7 @@ RL_HOST, RL_DEVICE = 0, 1
 RL_POSE_FOUND, RL_NO_POSE = 0, 1
 RL_MODES_FP32, RL_MODES_FP16_OFFSET = 0, 1
 RL_N_KERNELS = 12  # kernels the profiler reports (RL_N_KERNELS of the header)
-RL_N_WORK = 11     # work counters (RL_N_WORK of the header)
+RL_N_WORK = 12     # work counters (RL_N_WORK of the header)
 
 
 class Intrinsics(ctypes.Structure):

@@ -191,6 +191,10 @@ struct QueryState {
     float4 *tab1;            // [B][max_pix][mpad] U01 U02 U11 U12
     float *tab2;             // [B][max_pix][mpad] U22
     int16_t *tab_cnt;        // [B][max_pix] |M(u)| (0 for a skipped draw)
+    float2 *tab_lm;          // [B][max_pix] per row: max over its modes of the Frobenius
+                             // norm of U (1 without covariances), max |mu|
+    float4 *lm_anc;          // [B][n_cull][max_pix] LM nearest-mode anchors: y, slack^2
+    int16_t *lm_anc_b;       // [B][n_cull][max_pix] nearest mode at the anchor
     int32_t *n_pix;          // [B]
     double *cur_pose;        // [B][n_cull][12]
     int32_t *cur_slot;       // [B][n_cull]
@@ -234,12 +238,15 @@ enum KernelId {
     K_HYPPOSE, K_CMASK, K_ICP, K_COUNT
 };
 // work counters: energy (H,px) pairs, energy (H,px,mode) triples, LM pass-1
-// (H,px) evaluations, LM (H,px,mode) triples, LM inlier accumulations, LM
-// pass-2 evaluations, raycast rays, generation attempts and stage-2
-// evaluations, ICP valid-pixel evaluations, raycast rays re-evaluated in FP64
+// (H,px) evaluations, LM (H,px,mode) triples of the nearest-mode searches
+// the method defines, LM inlier accumulations, LM pass-2 evaluations,
+// raycast rays, generation attempts and stage-2 evaluations, ICP
+// valid-pixel evaluations, raycast rays re-evaluated in FP64, LM
+// (H,px,mode) distances actually evaluated (fewer than the method's triples
+// where a certified bound settles the nearest mode)
 enum WorkId {
     W_E_PAIRS = 0, W_E_MODES, W_LM_PAIRS, W_LM_MODES, W_LM_INLIERS, W_LM_TRIAL, W_RAYS, W_HYP_ATTEMPTS,
-    W_HYP_STAGE2, W_ICP_PIX, W_RAY64, W_COUNT
+    W_HYP_STAGE2, W_ICP_PIX, W_RAY64, W_LM_EVALS, W_COUNT
 };
 
 struct Profiler {

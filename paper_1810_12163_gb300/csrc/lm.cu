@@ -60,10 +60,14 @@ constexpr int LMC_HMAX = 64;
 constexpr int LMC_NV = 30;       // 21 J^T J + 6 J^T r + cost, inlier count, trial cost
 constexpr int LMC_PS = 31;       // odd stride of the per-thread partials (no bank conflicts)
 constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr int LMC_KP = 4;                       // pixels of a thread per tile (staged) or chunk (direct)
+constexpr int LMC_LIST = LMC_THREADS * LMC_KP;  // full-search list capacity of a tile or chunk
+constexpr int LMC_SB = 8;                       // lanes per full nearest-mode search
+constexpr int LMC_DIRECT = 4;                   // at most this many hypotheses: rows read from global memory
 
 struct LmcLayout {
     uint32_t t0, t1, t2, xc, cnt, stage, tx;
-    uint32_t H, Hn, Pf, lambda, tot, nw, loc, state, cbuf, act, flag, bar, total;
+    uint32_t H, Hn, Pf, lambda, tot, nw, loc, state, cbuf, act, list, flag, bar, total;
 };
 
 __host__ __device__ inline uint32_t lmc_a16(uint32_t x) { return (x + 15u) & ~15u; }
@@ -95,6 +99,7 @@ __host__ __device__ inline LmcLayout lmc_layout(int stride, bool cov) {
     L.state = o; o += LMC_HMAX * 4;
     L.cbuf = o; o += LMC_HMAX * 4;
     L.act = o; o += LMC_HMAX * 4 + 16;  // list, then its length
+    L.list = o; o += LMC_LIST * 4;      // pairs to search in full (int16) and their nearest modes (int16)
     L.flag = o; o += 16;
     L.bar = o; o += LMC_STAGES * 8;
     L.total = lmc_a16(o);
@@ -200,7 +205,7 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
         HB = 1;
         while (HB < k) HB <<= 1;
         const int G = LMC_THREADS / HB;
-        S = G > LMC_P ? G / LMC_P : 1;
+        S = 1;
         Gp = G / S;  // pixel groups
         sub = t % S;
         hs = (t / S) % HB;
@@ -246,121 +251,145 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
         ++issued[s];
     };
 
-    unsigned w_pairs = 0, w_modes = 0, w_in = 0, w_trial = 0;
-    // One tile of a pass with S > 1: pixel g of the tile for hypothesis hl,
-    // modes sub, sub + S, ... on this lane; every lane reaches the shuffles.
-    auto split_tile = [&](bool live, int s, int j, bool trial, const int16_t *cr, int16_t *cw, LmcPass &o,
-                          float r00, float r01, float r02, float tx, float r10, float r11, float r12, float ty,
-                          float r20, float r21, float r22, float tz) {
-        const uint8_t *st = smem + s * L.stage;
-        const float4 *s_t0 = (const float4 *)(st + L.t0);
-        const float4 *s_t1 = (const float4 *)(st + L.t1);
-        const float *s_t2 = (const float *)(st + L.t2);
-        const float4 *s_xc = (const float4 *)(st + L.xc);
-        const int16_t *s_cnt = (const int16_t *)(st + L.cnt);
-        const int i0 = (crank + j * CTAS) * LMC_P;
-        const int il = g;
-        const bool on = live && il < min(LMC_P, a.n_pix - i0);
-        const int cnt = on ? (int)s_cnt[il] : 0;
-        const int base = il * stride;
-        float y0 = 0.f, y1 = 0.f, y2 = 0.f;
-        if (cnt > 0) {
-            const float4 x = s_xc[il];
-            y0 = fmaf(r00, x.x, fmaf(r01, x.y, fmaf(r02, x.z, tx)));
-            y1 = fmaf(r10, x.x, fmaf(r11, x.y, fmaf(r12, x.z, ty)));
-            y2 = fmaf(r20, x.x, fmaf(r21, x.y, fmaf(r22, x.z, tz)));
-        }
-        float best = INFINITY;
-        int best_m = -1;
+    unsigned w_pairs = 0, w_modes = 0, w_in = 0, w_trial = 0, w_evals = 0;
+
+    // Nearest-mode anchors.  Each (hypothesis, pixel) pair keeps, from its
+    // last full nearest-mode search, the transformed point y there, the
+    // nearest mode b and a slack.  d_m(y) = |U_m (y - mu_m)| moves by at
+    // most L |dy| when y moves by dy (L >= the largest |U_m|_2 of the pixel's
+    // modes; the table holds the largest Frobenius norm), so while
+    // |y - y_anchor| <= (d_2 - d_b - margin) / 2L, with d_2 the second-nearest
+    // distance at the anchor, b is still the strict nearest mode; the margin
+    // covers the FP32 rounding of the four distances involved.  Such a pair
+    // reads only b's record.  The other pairs go to a list that LMC_SB lanes
+    // per pair search in full (nearest and second-nearest, ties to the lower
+    // index), re-anchoring them.  The nearest mode used is therefore always
+    // the one a full FP32 search finds.  A pass either streams the CTA's
+    // tiles of the mode table into shared memory (many hypotheses share each
+    // row) or, for frames with at most LMC_DIRECT hypotheses, reads the rows
+    // from global memory (few share a row, and the anchors spare most reads).
+    uint16_t *s_list = (uint16_t *)(smem + L.list);           // [LMC_LIST] local pixel << 6 | list entry
+    int16_t *s_res = (int16_t *)(smem + L.list) + LMC_LIST;   // [LMC_LIST] nearest mode of the entry
+    int *s_nl = (int *)(smem + L.flag) + 1;                   // two list counters, by tile parity
+    const float2 *g_lm = a.q.tab_lm + row0;
+    float4 *g_anc = a.q.lm_anc + (size_t)b * cstride;
+    int16_t *g_ancb = a.q.lm_anc_b + (size_t)b * cstride;
+    // squared distance (Eq. 5 form) of y to the record m of a row
+    auto q_at = [&](const float4 *r0, const float4 *r1, const float *r2, int m, float y0, float y1, float y2) {
+        const float4 m0 = r0[m];
+        const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
         if (cov) {
-            auto d2of = [&](int m) {
-                const float4 m0 = s_t0[base + m], m1 = s_t1[base + m];
-                const float u22 = s_t2[base + m];
-                const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
-                const float w0 = fmaf(m0.w, v0, fmaf(m1.x, v1, m1.y * v2));
-                const float w1 = fmaf(m1.z, v1, m1.w * v2);
-                const float w2 = u22 * v2;
-                return fmaf(w0, w0, fmaf(w1, w1, w2 * w2));
-            };
-            int m = sub;
-            for (; m + S < cnt; m += 2 * S) {
-                const float da = d2of(m), db = d2of(m + S);
-                if (da < best) { best = da; best_m = m; }
-                if (db < best) { best = db; best_m = m + S; }
-            }
-            if (m < cnt) {
-                const float da = d2of(m);
-                if (da < best) { best = da; best_m = m; }
-            }
-        } else {
-            auto d2of = [&](int m) {
-                const float4 m0 = s_t0[base + m];
-                const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
-                return fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
-            };
-            int m = sub;
-            for (; m + S < cnt; m += 2 * S) {
-                const float da = d2of(m), db = d2of(m + S);
-                if (da < best) { best = da; best_m = m; }
-                if (db < best) { best = db; best_m = m + S; }
-            }
-            if (m < cnt) {
-                const float da = d2of(m);
-                if (da < best) { best = da; best_m = m; }
-            }
+            const float4 m1 = r1[m];
+            const float w0 = fmaf(m0.w, v0, fmaf(m1.x, v1, m1.y * v2));
+            const float w1 = fmaf(m1.z, v1, m1.w * v2);
+            const float w2 = r2[m] * v2;
+            return fmaf(w0, w0, fmaf(w1, w1, w2 * w2));
         }
-        for (int off = 1; off < S; off <<= 1) {
-            const float ob = __shfl_xor_sync(0xffffffffu, best, off);
-            const int om = __shfl_xor_sync(0xffffffffu, best_m, off);
-            if (om >= 0 && (best_m < 0 || ob < best || (ob == best && om < best_m))) {
-                best = ob;
-                best_m = om;
-            }
-        }
-        if (sub != 0 || !on) return;
-        const size_t ci = (size_t)(i0 + il) * n + hl;
+        return fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
+    };
+    // inlier test and normal-equation terms of a pair whose nearest mode is
+    // bm, the trial cost of its previous correspondence, its new one
+    auto finish = [&](const float4 *r0, const float4 *r1, const float *r2, size_t ci, float y0, float y1,
+                      float y2, int bm, bool trial, const int16_t *cr, int16_t *cw, LmcPass &o) {
         const int m_old = trial ? (int)cr[ci] : -1;
-        if (cnt > 0) {
-            ++w_pairs;
-            w_modes += cnt;
-            if (best_m >= 0) {
-                const float4 m0 = s_t0[base + best_m];
-                const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
-                if (fmaf(v0, v0, fmaf(v1, v1, v2 * v2)) <= thr2) {
-                    ++o.nin;
-                    ++w_in;
-                    if (cov) {
-                        const float4 m1 = s_t1[base + best_m];
-                        lm_accumulate(y0, y1, y2, v0, v1, v2, m0.w, m1.x, m1.y, m1.z, m1.w, s_t2[base + best_m],
-                                      o.acc);
-                    } else {
-                        lm_accumulate(y0, y1, y2, v0, v1, v2, 1.f, 0.f, 0.f, 1.f, 0.f, 1.f, o.acc);
-                    }
-                } else {
-                    best_m = -1;
-                }
-            }
-            if (m_old >= 0) {  // the previous correspondence at the trial pose
-                ++w_trial;
-                const float4 m0 = s_t0[base + m_old];
-                const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+        int best_m = bm;
+        if (bm >= 0) {
+            const float4 m0 = r0[bm];
+            const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+            if (fmaf(v0, v0, fmaf(v1, v1, v2 * v2)) <= thr2) {
+                ++o.nin;
+                ++w_in;
                 if (cov) {
-                    const float4 m1 = s_t1[base + m_old];
-                    const float q0 = fmaf(m0.w, v0, fmaf(m1.x, v1, m1.y * v2));
-                    const float q1 = fmaf(m1.z, v1, m1.w * v2);
-                    const float q2 = s_t2[base + m_old] * v2;
-                    o.trial = fmaf(q0, q0, fmaf(q1, q1, fmaf(q2, q2, o.trial)));
+                    const float4 m1 = r1[bm];
+                    lm_accumulate(y0, y1, y2, v0, v1, v2, m0.w, m1.x, m1.y, m1.z, m1.w, r2[bm], o.acc);
                 } else {
-                    o.trial = fmaf(v0, v0, fmaf(v1, v1, fmaf(v2, v2, o.trial)));
+                    lm_accumulate(y0, y1, y2, v0, v1, v2, 1.f, 0.f, 0.f, 1.f, 0.f, 1.f, o.acc);
                 }
+            } else {
+                best_m = -1;
             }
-        } else {
-            best_m = -1;
+        }
+        if (m_old >= 0) {  // the previous correspondence at the trial pose
+            ++w_trial;
+            if (cov) {
+                o.trial += q_at(r0, r1, r2, m_old, y0, y1, y2);
+            } else {
+                const float4 m0 = r0[m_old];
+                const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+                o.trial = fmaf(v0, v0, fmaf(v1, v1, fmaf(v2, v2, o.trial)));
+            }
         }
         cw[ci] = (int16_t)best_m;  // local mode index in the row, -1: none
     };
-    // The pass; act: this thread's hypothesis takes part, P: its pose.
-    auto pass = [&](bool act, const float *P, bool trial, int rbuf, int wbuf) {
+    // Full search of one listed pair by the LMC_SB lanes of a group (every
+    // lane of the warp calls it; `on` marks a real entry); lane 0 of the
+    // group re-anchors the pair.  Returns the nearest mode (-1: none).
+    auto search = [&](bool on, const float4 *r0, const float4 *r1, const float *r2, int cnt, int i, size_t ci,
+                      float y0, float y1, float y2) {
+        const int sub = t % LMC_SB;
+        float best = INFINITY, second = INFINITY;
+        int best_m = -1;
+        for (int m = sub; m < cnt; m += LMC_SB) {
+            const float qm = q_at(r0, r1, r2, m, y0, y1, y2);
+            if (qm < best) {
+                second = best;
+                best = qm;
+                best_m = m;
+            } else {
+                second = fminf(second, qm);
+            }
+        }
+#pragma unroll
+        for (int off = 1; off < LMC_SB; off <<= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+            const float os = __shfl_xor_sync(0xffffffffu, second, off);
+            const int om = __shfl_xor_sync(0xffffffffu, best_m, off);
+            if (om >= 0 && (best_m < 0 || ob < best || (ob == best && om < best_m))) {
+                second = fminf(best, fminf(second, os));
+                best = ob;
+                best_m = om;
+            } else {
+                second = fminf(second, fminf(ob, os));
+            }
+        }
+        if (on && sub == 0) {
+            w_evals += cnt;
+            float slack2 = -1.f;
+            if (best_m >= 0) {
+                if (!(second < INFINITY)) {
+                    slack2 = 0.25f;  // a single mode stays the nearest (bounded to 0.5 m)
+                } else {
+                    const float2 lm = g_lm[i];
+                    const float Lf = (cov ? lm.x : 1.f) * 1.00001f;
+                    const float db = sqrtf(best), d2 = sqrtf(second);
+                    const float ny = sqrtf(fmaf(y0, y0, fmaf(y1, y1, y2 * y2)));
+                    const float margin = 4e-6f * (Lf * (ny + 0.5f + lm.y) + d2 + 1.f);
+                    const float sl = fminf(0.5f, (d2 - db - margin) / (2.f * Lf));
+                    if (sl > 0.f) slack2 = sl * sl * 0.99999f;
+                }
+            }
+            g_anc[ci] = make_float4(y0, y1, y2, slack2);
+            g_ancb[ci] = (int16_t)best_m;
+        }
+        return best_m;
+    };
+    // The certified case of a pair: true (and the pair finished) when its
+    // anchor still settles the nearest mode.
+    auto anchored = [&](const float4 *r0, const float4 *r1, const float *r2, size_t ci, float y0, float y1, float y2,
+                        bool trial, const int16_t *cr, int16_t *cw, LmcPass &o) {
+        const float4 an = g_anc[ci];
+        const float e0 = y0 - an.x, e1 = y1 - an.y, e2 = y2 - an.z;
+        if (!(fmaf(e0, e0, fmaf(e1, e1, e2 * e2)) <= an.w)) return false;
+        ++w_evals;
+        finish(r0, r1, r2, ci, y0, y1, y2, (int)g_ancb[ci], trial, cr, cw, o);
+        return true;
+    };
+
+    // A pass over the k hypotheses listed in s_act (thread t: list entry hs =
+    // t % HB, pixel group g = t / HB of Gp); act: this thread's hypothesis
+    // takes part, P: its pose; first: the round's first pass (no anchors
+    // yet, every pair is searched in full).
+    auto pass = [&](bool act, const float *P, bool trial, int rbuf, int wbuf, bool first) {
         LmcPass o;
 #pragma unroll
         for (int k = 0; k < 28; ++k) o.acc[k] = 0.f;
@@ -375,14 +404,91 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
         }
         const int16_t *cr = corr0 + (size_t)rbuf * cstride;
         int16_t *cw = corr0 + (size_t)wbuf * cstride;
+        const int n_local = my_tiles * LMC_P;
+        // local pixel indices must fit 10 bits in the list entries; the
+        // choice is the same in every CTA of the cluster
+        const bool direct = n <= LMC_DIRECT && (n_tiles + CTAS - 1) / CTAS * LMC_P <= 1024;
         // region 0 was last written by threads (partials): order those writes
         // before the copies that overwrite it
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (t == 0) s_nl[0] = s_nl[1] = 0;
         __syncthreads();
+        if (direct) {
+            // rows from global memory; chunks of Gp * LMC_KP of the CTA's pixels
+            auto pixel_of = [&](int j) { return (crank + (j / LMC_P) * CTAS) * LMC_P + j % LMC_P; };
+            int c = 0;
+            for (int c0 = 0; c0 < n_local; c0 += Gp * LMC_KP, c ^= 1) {
+                int pend[LMC_KP];
+#pragma unroll
+                for (int k = 0; k < LMC_KP; ++k) {
+                    pend[k] = -1;
+                    const int j = c0 + g + k * Gp;
+                    if (!act || j >= n_local) continue;
+                    const int i = pixel_of(j);
+                    if (i >= a.n_pix) continue;
+                    const size_t ci = (size_t)i * n + hl;
+                    const int cnt = g_cnt[i];
+                    if (cnt == 0) {
+                        cw[ci] = -1;
+                        continue;
+                    }
+                    ++w_pairs;
+                    w_modes += cnt;
+                    if (!first) {
+                        const float4 x = g_xc[i];
+                        const float y0 = fmaf(r00, x.x, fmaf(r01, x.y, fmaf(r02, x.z, tx)));
+                        const float y1 = fmaf(r10, x.x, fmaf(r11, x.y, fmaf(r12, x.z, ty)));
+                        const float y2 = fmaf(r20, x.x, fmaf(r21, x.y, fmaf(r22, x.z, tz)));
+                        const size_t rb = (size_t)i * stride;
+                        if (anchored(g_t0 + rb, g_t1 + rb, g_t2 + rb, ci, y0, y1, y2, trial, cr, cw, o)) continue;
+                    }
+                    pend[k] = atomicAdd(&s_nl[c], 1);
+                    s_list[pend[k]] = (uint16_t)((j << 6) | hs);
+                }
+                __syncthreads();
+                if (t == 0) s_nl[c ^ 1] = 0;
+                const int nl = s_nl[c];
+                for (int e0 = 0; e0 < nl; e0 += LMC_THREADS / LMC_SB) {
+                    const int e = e0 + t / LMC_SB;
+                    const bool on = e < nl;
+                    int i = 0, cnt = 0, h = 0;
+                    float y0 = 0.f, y1 = 0.f, y2 = 0.f;
+                    if (on) {
+                        const int v = s_list[e];
+                        i = pixel_of(v >> 6);
+                        h = s_act[v & 63];
+                        cnt = g_cnt[i];
+                        const float4 x = g_xc[i];
+                        const float *Q = s_Pf[h];
+                        y0 = fmaf(Q[0], x.x, fmaf(Q[1], x.y, fmaf(Q[2], x.z, Q[3])));
+                        y1 = fmaf(Q[4], x.x, fmaf(Q[5], x.y, fmaf(Q[6], x.z, Q[7])));
+                        y2 = fmaf(Q[8], x.x, fmaf(Q[9], x.y, fmaf(Q[10], x.z, Q[11])));
+                    }
+                    const size_t rb = (size_t)i * stride;
+                    const int bm = search(on, g_t0 + rb, g_t1 + rb, g_t2 + rb, cnt, i, (size_t)i * n + h, y0, y1, y2);
+                    if (on && t % LMC_SB == 0) s_res[e] = (int16_t)bm;
+                }
+                __syncthreads();
+#pragma unroll
+                for (int k = 0; k < LMC_KP; ++k) {
+                    if (pend[k] < 0) continue;
+                    const int i = pixel_of(c0 + g + k * Gp);
+                    const float4 x = g_xc[i];
+                    const float y0 = fmaf(r00, x.x, fmaf(r01, x.y, fmaf(r02, x.z, tx)));
+                    const float y1 = fmaf(r10, x.x, fmaf(r11, x.y, fmaf(r12, x.z, ty)));
+                    const float y2 = fmaf(r20, x.x, fmaf(r21, x.y, fmaf(r22, x.z, tz)));
+                    const size_t rb = (size_t)i * stride;
+                    finish(g_t0 + rb, g_t1 + rb, g_t2 + rb, (size_t)i * n + hl, y0, y1, y2, (int)s_res[pend[k]],
+                           trial, cr, cw, o);
+                }
+                __syncthreads();  // the list is rewritten two chunks later
+            }
+            return o;
+        }
         if (t == 0 && !*s_abort)
             for (int j = 0; j < LMC_STAGES && j < my_tiles; ++j) issue(j, j);
         for (int j = 0; j < my_tiles; ++j) {
-            const int s = j % LMC_STAGES;
+            const int s = j % LMC_STAGES, c = j & 1;
             const uint32_t parity = waited[s] & 1u;
             ++waited[s];
             if (!*s_abort) {
@@ -393,104 +499,76 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
                     a.q.dev_err[b] = 1;
                 }
             }
-            if (S > 1) {
-                split_tile(act && !*s_abort, s, j, trial, cr, cw, o, r00, r01, r02, tx, r10, r11, r12, ty, r20, r21,
-                           r22, tz);
-            } else if (act && !*s_abort) {
-                const uint8_t *st = smem + s * L.stage;
-                const float4 *s_t0 = (const float4 *)(st + L.t0);
-                const float4 *s_t1 = (const float4 *)(st + L.t1);
-                const float *s_t2 = (const float *)(st + L.t2);
-                const float4 *s_xc = (const float4 *)(st + L.xc);
-                const int16_t *s_cnt = (const int16_t *)(st + L.cnt);
-                const int i0 = (crank + j * CTAS) * LMC_P;
-                const int np = min(LMC_P, a.n_pix - i0);
-                for (int il = g; il < np; il += Gp) {
-                    const size_t ci = (size_t)(i0 + il) * n + hl;
-                    const int m_old = trial ? (int)cr[ci] : -1;
-                    const int cnt = s_cnt[il];
-                    int best_m = -1;
-                    if (cnt > 0) {
-                        ++w_pairs;
-                        w_modes += cnt;
-                        const float4 x = s_xc[il];
-                        const float y0 = fmaf(r00, x.x, fmaf(r01, x.y, fmaf(r02, x.z, tx)));
-                        const float y1 = fmaf(r10, x.x, fmaf(r11, x.y, fmaf(r12, x.z, ty)));
-                        const float y2 = fmaf(r20, x.x, fmaf(r21, x.y, fmaf(r22, x.z, tz)));
-                        const int base = il * stride;
-                        float best = INFINITY;
-                        // two modes per step (independent chains), compared in mode order
-                        if (cov) {
-                            auto d2of = [&](int m) {
-                                const float4 m0 = s_t0[base + m], m1 = s_t1[base + m];
-                                const float u22 = s_t2[base + m];
-                                const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
-                                const float w0 = fmaf(m0.w, v0, fmaf(m1.x, v1, m1.y * v2));
-                                const float w1 = fmaf(m1.z, v1, m1.w * v2);
-                                const float w2 = u22 * v2;
-                                return fmaf(w0, w0, fmaf(w1, w1, w2 * w2));
-                            };
-                            int m = 0;
-                            for (; m + 1 < cnt; m += 2) {
-                                const float da = d2of(m), db = d2of(m + 1);
-                                if (da < best) { best = da; best_m = m; }
-                                if (db < best) { best = db; best_m = m + 1; }
-                            }
-                            if (m < cnt) {
-                                const float da = d2of(m);
-                                if (da < best) { best = da; best_m = m; }
-                            }
-                        } else {
-                            auto d2of = [&](int m) {
-                                const float4 m0 = s_t0[base + m];
-                                const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
-                                return fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
-                            };
-                            int m = 0;
-                            for (; m + 1 < cnt; m += 2) {
-                                const float da = d2of(m), db = d2of(m + 1);
-                                if (da < best) { best = da; best_m = m; }
-                                if (db < best) { best = db; best_m = m + 1; }
-                            }
-                            if (m < cnt) {
-                                const float da = d2of(m);
-                                if (da < best) { best = da; best_m = m; }
-                            }
-                        }
-                        if (best_m >= 0) {
-                            const float4 m0 = s_t0[base + best_m];
-                            const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
-                            if (fmaf(v0, v0, fmaf(v1, v1, v2 * v2)) <= thr2) {
-                                ++o.nin;
-                                ++w_in;
-                                if (cov) {
-                                    const float4 m1 = s_t1[base + best_m];
-                                    lm_accumulate(y0, y1, y2, v0, v1, v2, m0.w, m1.x, m1.y, m1.z, m1.w,
-                                                  s_t2[base + best_m], o.acc);
-                                } else {
-                                    lm_accumulate(y0, y1, y2, v0, v1, v2, 1.f, 0.f, 0.f, 1.f, 0.f, 1.f, o.acc);
-                                }
-                            } else {
-                                best_m = -1;
-                            }
-                        }
-                        if (m_old >= 0) {  // the previous correspondence at the trial pose
-                            ++w_trial;
-                            const float4 m0 = s_t0[base + m_old];
-                            const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
-                            if (cov) {
-                                const float4 m1 = s_t1[base + m_old];
-                                const float q0 = fmaf(m0.w, v0, fmaf(m1.x, v1, m1.y * v2));
-                                const float q1 = fmaf(m1.z, v1, m1.w * v2);
-                                const float q2 = s_t2[base + m_old] * v2;
-                                o.trial = fmaf(q0, q0, fmaf(q1, q1, fmaf(q2, q2, o.trial)));
-                            } else {
-                                o.trial = fmaf(v0, v0, fmaf(v1, v1, fmaf(v2, v2, o.trial)));
-                            }
-                        }
-                    }
-                    cw[ci] = (int16_t)best_m;  // local mode index in the row, -1: none
+            const bool live = !*s_abort;  // the same in every thread of the CTA after the barrier below
+            const uint8_t *st = smem + s * L.stage;
+            const float4 *s_t0 = (const float4 *)(st + L.t0);
+            const float4 *s_t1 = (const float4 *)(st + L.t1);
+            const float *s_t2 = (const float *)(st + L.t2);
+            const float4 *s_xc = (const float4 *)(st + L.xc);
+            const int16_t *s_cnt = (const int16_t *)(st + L.cnt);
+            const int i0 = (crank + j * CTAS) * LMC_P;
+            const int np = min(LMC_P, a.n_pix - i0);
+            int pend[LMC_KP];
+#pragma unroll
+            for (int k = 0; k < LMC_KP; ++k) {
+                pend[k] = -1;
+                const int il = g + k * Gp;
+                if (!act || !live || il >= np) continue;
+                const size_t ci = (size_t)(i0 + il) * n + hl;
+                const int cnt = s_cnt[il];
+                if (cnt == 0) {
+                    cw[ci] = -1;
+                    continue;
                 }
+                ++w_pairs;
+                w_modes += cnt;
+                if (!first) {
+                    const float4 x = s_xc[il];
+                    const float y0 = fmaf(r00, x.x, fmaf(r01, x.y, fmaf(r02, x.z, tx)));
+                    const float y1 = fmaf(r10, x.x, fmaf(r11, x.y, fmaf(r12, x.z, ty)));
+                    const float y2 = fmaf(r20, x.x, fmaf(r21, x.y, fmaf(r22, x.z, tz)));
+                    const int rb = il * stride;
+                    if (anchored(s_t0 + rb, s_t1 + rb, s_t2 + rb, ci, y0, y1, y2, trial, cr, cw, o)) continue;
+                }
+                pend[k] = atomicAdd(&s_nl[c], 1);
+                s_list[pend[k]] = (uint16_t)((il << 6) | hs);
+            }
+            __syncthreads();
+            if (t == 0) s_nl[c ^ 1] = 0;
+            const int nl = s_nl[c];
+            for (int e0 = 0; e0 < nl; e0 += LMC_THREADS / LMC_SB) {
+                const int e = e0 + t / LMC_SB;
+                const bool on = e < nl;
+                int il = 0, cnt = 0, h = 0;
+                float y0 = 0.f, y1 = 0.f, y2 = 0.f;
+                if (on) {
+                    const int v = s_list[e];
+                    il = v >> 6;
+                    h = s_act[v & 63];
+                    cnt = s_cnt[il];
+                    const float4 x = s_xc[il];
+                    const float *Q = s_Pf[h];
+                    y0 = fmaf(Q[0], x.x, fmaf(Q[1], x.y, fmaf(Q[2], x.z, Q[3])));
+                    y1 = fmaf(Q[4], x.x, fmaf(Q[5], x.y, fmaf(Q[6], x.z, Q[7])));
+                    y2 = fmaf(Q[8], x.x, fmaf(Q[9], x.y, fmaf(Q[10], x.z, Q[11])));
+                }
+                const int rb = il * stride;
+                const int bm = search(on, s_t0 + rb, s_t1 + rb, s_t2 + rb, cnt, i0 + il, (size_t)(i0 + il) * n + h,
+                                      y0, y1, y2);
+                if (on && t % LMC_SB == 0) s_res[e] = (int16_t)bm;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < LMC_KP; ++k) {
+                if (pend[k] < 0) continue;
+                const int il = g + k * Gp;
+                const float4 x = s_xc[il];
+                const float y0 = fmaf(r00, x.x, fmaf(r01, x.y, fmaf(r02, x.z, tx)));
+                const float y1 = fmaf(r10, x.x, fmaf(r11, x.y, fmaf(r12, x.z, ty)));
+                const float y2 = fmaf(r20, x.x, fmaf(r21, x.y, fmaf(r22, x.z, tz)));
+                const int rb = il * stride;
+                finish(s_t0 + rb, s_t1 + rb, s_t2 + rb, (size_t)(i0 + il) * n + hl, y0, y1, y2, (int)s_res[pend[k]],
+                       trial, cr, cw, o);
             }
             __syncthreads();  // stage s consumed by every thread
             if (t == 0 && !*s_abort && j + LMC_STAGES < my_tiles) issue(j + LMC_STAGES, s);
@@ -530,7 +608,7 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
     // normal equations and correspondences at the initial poses
     {
         roles(n);
-        const LmcPass o = pass(mine, s_Pf[hl], false, 0, 0);
+        const LmcPass o = pass(mine, s_Pf[hl], false, 0, 0, true);
         reduce(o, 0, s_tot);
     }
     for (int it = 0; it < a.p.lm_max_iter; ++it) {
@@ -595,7 +673,7 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
         // trial cost of the step on the current correspondences, and the
         // normal equations at the trial pose (used if the step is accepted)
         const int ob = mine ? s_cbuf[hl] : 0;
-        const LmcPass o = pass(mine, s_Pf[hl], true, ob, ob ^ 1);
+        const LmcPass o = pass(mine, s_Pf[hl], true, ob, ob ^ 1, false);
         reduce(o, (it + 1) & 1, s_new);
         for (int h = t; h < n; h += LMC_THREADS) {
             if (!s_state[h]) continue;
@@ -614,11 +692,12 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
     if (crank == 0)
         for (int i = t; i < n * 12; i += LMC_THREADS)
             a.q.cur_pose[((size_t)b * NC + i / 12) * 12 + i % 12] = s_H[i / 12][i % 12];
-    if (a.work && (w_pairs | w_modes | w_in | w_trial)) {
+    if (a.work && (w_pairs | w_modes | w_in | w_trial | w_evals)) {
         atomicAdd(&a.work[W_LM_PAIRS], (unsigned long long)w_pairs);
         atomicAdd(&a.work[W_LM_MODES], (unsigned long long)w_modes);
         atomicAdd(&a.work[W_LM_INLIERS], (unsigned long long)w_in);
         atomicAdd(&a.work[W_LM_TRIAL], (unsigned long long)w_trial);
+        atomicAdd(&a.work[W_LM_EVALS], (unsigned long long)w_evals);
     }
     if (t == 0 && *s_abort)  // copies still in flight must land before the CTA exits
         for (int s = 0; s < LMC_STAGES; ++s)
