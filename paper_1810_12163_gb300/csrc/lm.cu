@@ -191,6 +191,10 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
     const int n_tiles = (a.n_pix + LMC_P - 1) / LMC_P;
     const int my_tiles = crank < n_tiles ? (n_tiles - crank + CTAS - 1) / CTAS : 0;
     const float thr2 = (float)(a.p.lm_inlier_thresh * a.p.lm_inlier_thresh);
+    // direct passes after the first: at most LMC_DIRECT hypotheses, and the
+    // CTA's local pixel indices fit the list entries' 10 bits (the same
+    // decision in every CTA of the cluster)
+    const bool dir_ok = n <= LMC_DIRECT && (n_tiles + CTAS - 1) / CTAS * LMC_P <= 1024;
 
     // Lane roles of a pass over the k hypotheses listed in s_act: list entry
     // hs = (t / S) % HB on pixel group g = (t / S) / HB.  With fewer than 16
@@ -200,12 +204,12 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
     // index, as a sequential scan finds it).  hl: the hypothesis served.
     int HB = 1, S = 1, Gp = 1, sub = 0, hs = 0, g = 0, hl = 0, k_act = 0;
     bool mine = false;
-    auto roles = [&](int k) {
+    auto roles = [&](int k, bool direct) {
         k_act = k;
         HB = 1;
         while (HB < k) HB <<= 1;
         const int G = LMC_THREADS / HB;
-        S = 1;
+        S = !direct && G > LMC_P ? G / LMC_P : 1;
         Gp = G / S;  // pixel groups
         sub = t % S;
         hs = (t / S) % HB;
@@ -321,6 +325,26 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
         }
         cw[ci] = (int16_t)best_m;  // local mode index in the row, -1: none
     };
+    // Anchor of pair ci (pixel row i) from a full search at y: nearest and
+    // second-nearest squared distances and the nearest mode.
+    auto anchor = [&](int i, size_t ci, float y0, float y1, float y2, float best, float second, int best_m) {
+        float slack2 = -1.f;
+        if (best_m >= 0) {
+            if (!(second < INFINITY)) {
+                slack2 = 0.25f;  // a single mode stays the nearest (bounded to 0.5 m)
+            } else {
+                const float2 lm = g_lm[i];
+                const float Lf = (cov ? lm.x : 1.f) * 1.00001f;
+                const float db = sqrtf(best), d2 = sqrtf(second);
+                const float ny = sqrtf(fmaf(y0, y0, fmaf(y1, y1, y2 * y2)));
+                const float margin = 4e-6f * (Lf * (ny + 0.5f + lm.y) + d2 + 1.f);
+                const float sl = fminf(0.5f, (d2 - db - margin) / (2.f * Lf));
+                if (sl > 0.f) slack2 = sl * sl * 0.99999f;
+            }
+        }
+        g_anc[ci] = make_float4(y0, y1, y2, slack2);
+        g_ancb[ci] = (int16_t)best_m;
+    };
     // Full search of one listed pair by the LMC_SB lanes of a group (every
     // lane of the warp calls it; `on` marks a real entry); lane 0 of the
     // group re-anchors the pair.  Returns the nearest mode (-1: none).
@@ -354,22 +378,7 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
         }
         if (on && sub == 0) {
             w_evals += cnt;
-            float slack2 = -1.f;
-            if (best_m >= 0) {
-                if (!(second < INFINITY)) {
-                    slack2 = 0.25f;  // a single mode stays the nearest (bounded to 0.5 m)
-                } else {
-                    const float2 lm = g_lm[i];
-                    const float Lf = (cov ? lm.x : 1.f) * 1.00001f;
-                    const float db = sqrtf(best), d2 = sqrtf(second);
-                    const float ny = sqrtf(fmaf(y0, y0, fmaf(y1, y1, y2 * y2)));
-                    const float margin = 4e-6f * (Lf * (ny + 0.5f + lm.y) + d2 + 1.f);
-                    const float sl = fminf(0.5f, (d2 - db - margin) / (2.f * Lf));
-                    if (sl > 0.f) slack2 = sl * sl * 0.99999f;
-                }
-            }
-            g_anc[ci] = make_float4(y0, y1, y2, slack2);
-            g_ancb[ci] = (int16_t)best_m;
+            anchor(i, ci, y0, y1, y2, best, second, best_m);
         }
         return best_m;
     };
@@ -385,10 +394,128 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
         return true;
     };
 
-    // A pass over the k hypotheses listed in s_act (thread t: list entry hs =
-    // t % HB, pixel group g = t / HB of Gp); act: this thread's hypothesis
-    // takes part, P: its pose; first: the round's first pass (no anchors
-    // yet, every pair is searched in full).
+    // One tile of a pass with S > 1: pixel g of the tile for hypothesis hl,
+    // modes sub, sub + S, ... on this lane; every lane reaches the shuffles.
+    auto split_tile = [&](bool live, int s, int j, bool trial, bool rec, const int16_t *cr, int16_t *cw, LmcPass &o,
+                          float r00, float r01, float r02, float tx, float r10, float r11, float r12, float ty,
+                          float r20, float r21, float r22, float tz) {
+        const uint8_t *st = smem + s * L.stage;
+        const float4 *s_t0 = (const float4 *)(st + L.t0);
+        const float4 *s_t1 = (const float4 *)(st + L.t1);
+        const float *s_t2 = (const float *)(st + L.t2);
+        const float4 *s_xc = (const float4 *)(st + L.xc);
+        const int16_t *s_cnt = (const int16_t *)(st + L.cnt);
+        const int i0 = (crank + j * CTAS) * LMC_P;
+        const int il = g;
+        const bool on = live && il < min(LMC_P, a.n_pix - i0);
+        const int cnt = on ? (int)s_cnt[il] : 0;
+        const int base = il * stride;
+        float y0 = 0.f, y1 = 0.f, y2 = 0.f;
+        if (cnt > 0) {
+            const float4 x = s_xc[il];
+            y0 = fmaf(r00, x.x, fmaf(r01, x.y, fmaf(r02, x.z, tx)));
+            y1 = fmaf(r10, x.x, fmaf(r11, x.y, fmaf(r12, x.z, ty)));
+            y2 = fmaf(r20, x.x, fmaf(r21, x.y, fmaf(r22, x.z, tz)));
+        }
+        float best = INFINITY, second = INFINITY;  // second: for the anchor (direct passes follow)
+        int best_m = -1;
+        if (cov) {
+            auto d2of = [&](int m) {
+                const float4 m0 = s_t0[base + m], m1 = s_t1[base + m];
+                const float u22 = s_t2[base + m];
+                const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+                const float w0 = fmaf(m0.w, v0, fmaf(m1.x, v1, m1.y * v2));
+                const float w1 = fmaf(m1.z, v1, m1.w * v2);
+                const float w2 = u22 * v2;
+                return fmaf(w0, w0, fmaf(w1, w1, w2 * w2));
+            };
+            int m = sub;
+            for (; m + S < cnt; m += 2 * S) {
+                const float da = d2of(m), db = d2of(m + S);
+                if (da < best) { second = best; best = da; best_m = m; } else { second = fminf(second, da); }
+                if (db < best) { second = best; best = db; best_m = m + S; } else { second = fminf(second, db); }
+            }
+            if (m < cnt) {
+                const float da = d2of(m);
+                if (da < best) { second = best; best = da; best_m = m; } else { second = fminf(second, da); }
+            }
+        } else {
+            auto d2of = [&](int m) {
+                const float4 m0 = s_t0[base + m];
+                const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+                return fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
+            };
+            int m = sub;
+            for (; m + S < cnt; m += 2 * S) {
+                const float da = d2of(m), db = d2of(m + S);
+                if (da < best) { second = best; best = da; best_m = m; } else { second = fminf(second, da); }
+                if (db < best) { second = best; best = db; best_m = m + S; } else { second = fminf(second, db); }
+            }
+            if (m < cnt) {
+                const float da = d2of(m);
+                if (da < best) { second = best; best = da; best_m = m; } else { second = fminf(second, da); }
+            }
+        }
+        for (int off = 1; off < S; off <<= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+            const float os = __shfl_xor_sync(0xffffffffu, second, off);
+            const int om = __shfl_xor_sync(0xffffffffu, best_m, off);
+            if (om >= 0 && (best_m < 0 || ob < best || (ob == best && om < best_m))) {
+                second = fminf(best, fminf(second, os));
+                best = ob;
+                best_m = om;
+            } else {
+                second = fminf(second, fminf(ob, os));
+            }
+        }
+        if (sub != 0 || !on) return;
+        const size_t ci = (size_t)(i0 + il) * n + hl;
+        if (rec && cnt > 0) anchor(i0 + il, ci, y0, y1, y2, best, second, best_m);
+        const int m_old = trial ? (int)cr[ci] : -1;
+        if (cnt > 0) {
+            ++w_pairs;
+            w_modes += cnt;
+            w_evals += cnt;
+            if (best_m >= 0) {
+                const float4 m0 = s_t0[base + best_m];
+                const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+                if (fmaf(v0, v0, fmaf(v1, v1, v2 * v2)) <= thr2) {
+                    ++o.nin;
+                    ++w_in;
+                    if (cov) {
+                        const float4 m1 = s_t1[base + best_m];
+                        lm_accumulate(y0, y1, y2, v0, v1, v2, m0.w, m1.x, m1.y, m1.z, m1.w, s_t2[base + best_m],
+                                      o.acc);
+                    } else {
+                        lm_accumulate(y0, y1, y2, v0, v1, v2, 1.f, 0.f, 0.f, 1.f, 0.f, 1.f, o.acc);
+                    }
+                } else {
+                    best_m = -1;
+                }
+            }
+            if (m_old >= 0) {  // the previous correspondence at the trial pose
+                ++w_trial;
+                const float4 m0 = s_t0[base + m_old];
+                const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+                if (cov) {
+                    const float4 m1 = s_t1[base + m_old];
+                    const float q0 = fmaf(m0.w, v0, fmaf(m1.x, v1, m1.y * v2));
+                    const float q1 = fmaf(m1.z, v1, m1.w * v2);
+                    const float q2 = s_t2[base + m_old] * v2;
+                    o.trial = fmaf(q0, q0, fmaf(q1, q1, fmaf(q2, q2, o.trial)));
+                } else {
+                    o.trial = fmaf(v0, v0, fmaf(v1, v1, fmaf(v2, v2, o.trial)));
+                }
+            }
+        } else {
+            best_m = -1;
+        }
+        cw[ci] = (int16_t)best_m;  // local mode index in the row, -1: none
+    };
+    // The pass; act: this thread's hypothesis takes part, P: its pose;
+    // first: the round's first pass.  Frames with at most LMC_DIRECT
+    // hypotheses stream their tiles in the first pass, which anchors every
+    // pair, and read the table from global memory in the later passes.
     auto pass = [&](bool act, const float *P, bool trial, int rbuf, int wbuf, bool first) {
         LmcPass o;
 #pragma unroll
@@ -404,17 +531,16 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
         }
         const int16_t *cr = corr0 + (size_t)rbuf * cstride;
         int16_t *cw = corr0 + (size_t)wbuf * cstride;
-        const int n_local = my_tiles * LMC_P;
-        // local pixel indices must fit 10 bits in the list entries; the
-        // choice is the same in every CTA of the cluster
-        const bool direct = n <= LMC_DIRECT && (n_tiles + CTAS - 1) / CTAS * LMC_P <= 1024;
         // region 0 was last written by threads (partials): order those writes
         // before the copies that overwrite it
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         if (t == 0) s_nl[0] = s_nl[1] = 0;
         __syncthreads();
-        if (direct) {
-            // rows from global memory; chunks of Gp * LMC_KP of the CTA's pixels
+        if (dir_ok && !first) {
+            // rows from global memory; chunks of Gp * LMC_KP of the CTA's
+            // pixels (local pixel j is pixel j % 16 of tile crank + (j / 16) * CTAS)
+            const int n_local = my_tiles * LMC_P;
+            const int lane = t & 31;
             auto pixel_of = [&](int j) { return (crank + (j / LMC_P) * CTAS) * LMC_P + j % LMC_P; };
             int c = 0;
             for (int c0 = 0; c0 < n_local; c0 += Gp * LMC_KP, c ^= 1) {
@@ -422,28 +548,34 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
 #pragma unroll
                 for (int k = 0; k < LMC_KP; ++k) {
                     pend[k] = -1;
+                    bool need = false;
                     const int j = c0 + g + k * Gp;
-                    if (!act || j >= n_local) continue;
-                    const int i = pixel_of(j);
-                    if (i >= a.n_pix) continue;
-                    const size_t ci = (size_t)i * n + hl;
-                    const int cnt = g_cnt[i];
-                    if (cnt == 0) {
-                        cw[ci] = -1;
-                        continue;
+                    const int i = j < n_local ? pixel_of(j) : a.n_pix;
+                    if (act && i < a.n_pix) {
+                        const size_t ci = (size_t)i * n + hl;
+                        const int cnt = g_cnt[i];
+                        if (cnt == 0) {
+                            cw[ci] = -1;
+                        } else {
+                            ++w_pairs;
+                            w_modes += cnt;
+                            const float4 x = g_xc[i];
+                            const float y0 = fmaf(r00, x.x, fmaf(r01, x.y, fmaf(r02, x.z, tx)));
+                            const float y1 = fmaf(r10, x.x, fmaf(r11, x.y, fmaf(r12, x.z, ty)));
+                            const float y2 = fmaf(r20, x.x, fmaf(r21, x.y, fmaf(r22, x.z, tz)));
+                            const size_t rb = (size_t)i * stride;
+                            need = !anchored(g_t0 + rb, g_t1 + rb, g_t2 + rb, ci, y0, y1, y2, trial, cr, cw, o);
+                        }
                     }
-                    ++w_pairs;
-                    w_modes += cnt;
-                    if (!first) {
-                        const float4 x = g_xc[i];
-                        const float y0 = fmaf(r00, x.x, fmaf(r01, x.y, fmaf(r02, x.z, tx)));
-                        const float y1 = fmaf(r10, x.x, fmaf(r11, x.y, fmaf(r12, x.z, ty)));
-                        const float y2 = fmaf(r20, x.x, fmaf(r21, x.y, fmaf(r22, x.z, tz)));
-                        const size_t rb = (size_t)i * stride;
-                        if (anchored(g_t0 + rb, g_t1 + rb, g_t2 + rb, ci, y0, y1, y2, trial, cr, cw, o)) continue;
+                    // one list append per warp
+                    const unsigned mk = __ballot_sync(0xffffffffu, need);
+                    int base = 0;
+                    if (lane == 0 && mk) base = atomicAdd(&s_nl[c], __popc(mk));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (need) {
+                        pend[k] = base + __popc(mk & ((1u << lane) - 1u));
+                        s_list[pend[k]] = (uint16_t)((j << 6) | hs);
                     }
-                    pend[k] = atomicAdd(&s_nl[c], 1);
-                    s_list[pend[k]] = (uint16_t)((j << 6) | hs);
                 }
                 __syncthreads();
                 if (t == 0) s_nl[c ^ 1] = 0;
@@ -485,10 +617,11 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
             }
             return o;
         }
+        const bool rec = dir_ok && first;  // anchor every pair for the direct passes that follow
         if (t == 0 && !*s_abort)
             for (int j = 0; j < LMC_STAGES && j < my_tiles; ++j) issue(j, j);
         for (int j = 0; j < my_tiles; ++j) {
-            const int s = j % LMC_STAGES, c = j & 1;
+            const int s = j % LMC_STAGES;
             const uint32_t parity = waited[s] & 1u;
             ++waited[s];
             if (!*s_abort) {
@@ -499,76 +632,105 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
                     a.q.dev_err[b] = 1;
                 }
             }
-            const bool live = !*s_abort;  // the same in every thread of the CTA after the barrier below
-            const uint8_t *st = smem + s * L.stage;
-            const float4 *s_t0 = (const float4 *)(st + L.t0);
-            const float4 *s_t1 = (const float4 *)(st + L.t1);
-            const float *s_t2 = (const float *)(st + L.t2);
-            const float4 *s_xc = (const float4 *)(st + L.xc);
-            const int16_t *s_cnt = (const int16_t *)(st + L.cnt);
-            const int i0 = (crank + j * CTAS) * LMC_P;
-            const int np = min(LMC_P, a.n_pix - i0);
-            int pend[LMC_KP];
-#pragma unroll
-            for (int k = 0; k < LMC_KP; ++k) {
-                pend[k] = -1;
-                const int il = g + k * Gp;
-                if (!act || !live || il >= np) continue;
-                const size_t ci = (size_t)(i0 + il) * n + hl;
-                const int cnt = s_cnt[il];
-                if (cnt == 0) {
-                    cw[ci] = -1;
-                    continue;
+            if (S > 1) {
+                split_tile(act && !*s_abort, s, j, trial, rec, cr, cw, o, r00, r01, r02, tx, r10, r11, r12, ty, r20,
+                           r21, r22, tz);
+            } else if (act && !*s_abort) {
+                const uint8_t *st = smem + s * L.stage;
+                const float4 *s_t0 = (const float4 *)(st + L.t0);
+                const float4 *s_t1 = (const float4 *)(st + L.t1);
+                const float *s_t2 = (const float *)(st + L.t2);
+                const float4 *s_xc = (const float4 *)(st + L.xc);
+                const int16_t *s_cnt = (const int16_t *)(st + L.cnt);
+                const int i0 = (crank + j * CTAS) * LMC_P;
+                const int np = min(LMC_P, a.n_pix - i0);
+                for (int il = g; il < np; il += Gp) {
+                    const size_t ci = (size_t)(i0 + il) * n + hl;
+                    const int m_old = trial ? (int)cr[ci] : -1;
+                    const int cnt = s_cnt[il];
+                    int best_m = -1;
+                    if (cnt > 0) {
+                        ++w_pairs;
+                        w_modes += cnt;
+                        w_evals += cnt;
+                        const float4 x = s_xc[il];
+                        const float y0 = fmaf(r00, x.x, fmaf(r01, x.y, fmaf(r02, x.z, tx)));
+                        const float y1 = fmaf(r10, x.x, fmaf(r11, x.y, fmaf(r12, x.z, ty)));
+                        const float y2 = fmaf(r20, x.x, fmaf(r21, x.y, fmaf(r22, x.z, tz)));
+                        const int base = il * stride;
+                        float best = INFINITY;
+                        // two modes per step (independent chains), compared in mode order
+                        if (cov) {
+                            auto d2of = [&](int m) {
+                                const float4 m0 = s_t0[base + m], m1 = s_t1[base + m];
+                                const float u22 = s_t2[base + m];
+                                const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+                                const float w0 = fmaf(m0.w, v0, fmaf(m1.x, v1, m1.y * v2));
+                                const float w1 = fmaf(m1.z, v1, m1.w * v2);
+                                const float w2 = u22 * v2;
+                                return fmaf(w0, w0, fmaf(w1, w1, w2 * w2));
+                            };
+                            int m = 0;
+                            for (; m + 1 < cnt; m += 2) {
+                                const float da = d2of(m), db = d2of(m + 1);
+                                if (da < best) { best = da; best_m = m; }
+                                if (db < best) { best = db; best_m = m + 1; }
+                            }
+                            if (m < cnt) {
+                                const float da = d2of(m);
+                                if (da < best) { best = da; best_m = m; }
+                            }
+                        } else {
+                            auto d2of = [&](int m) {
+                                const float4 m0 = s_t0[base + m];
+                                const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+                                return fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
+                            };
+                            int m = 0;
+                            for (; m + 1 < cnt; m += 2) {
+                                const float da = d2of(m), db = d2of(m + 1);
+                                if (da < best) { best = da; best_m = m; }
+                                if (db < best) { best = db; best_m = m + 1; }
+                            }
+                            if (m < cnt) {
+                                const float da = d2of(m);
+                                if (da < best) { best = da; best_m = m; }
+                            }
+                        }
+                        if (best_m >= 0) {
+                            const float4 m0 = s_t0[base + best_m];
+                            const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+                            if (fmaf(v0, v0, fmaf(v1, v1, v2 * v2)) <= thr2) {
+                                ++o.nin;
+                                ++w_in;
+                                if (cov) {
+                                    const float4 m1 = s_t1[base + best_m];
+                                    lm_accumulate(y0, y1, y2, v0, v1, v2, m0.w, m1.x, m1.y, m1.z, m1.w,
+                                                  s_t2[base + best_m], o.acc);
+                                } else {
+                                    lm_accumulate(y0, y1, y2, v0, v1, v2, 1.f, 0.f, 0.f, 1.f, 0.f, 1.f, o.acc);
+                                }
+                            } else {
+                                best_m = -1;
+                            }
+                        }
+                        if (m_old >= 0) {  // the previous correspondence at the trial pose
+                            ++w_trial;
+                            const float4 m0 = s_t0[base + m_old];
+                            const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
+                            if (cov) {
+                                const float4 m1 = s_t1[base + m_old];
+                                const float q0 = fmaf(m0.w, v0, fmaf(m1.x, v1, m1.y * v2));
+                                const float q1 = fmaf(m1.z, v1, m1.w * v2);
+                                const float q2 = s_t2[base + m_old] * v2;
+                                o.trial = fmaf(q0, q0, fmaf(q1, q1, fmaf(q2, q2, o.trial)));
+                            } else {
+                                o.trial = fmaf(v0, v0, fmaf(v1, v1, fmaf(v2, v2, o.trial)));
+                            }
+                        }
+                    }
+                    cw[ci] = (int16_t)best_m;  // local mode index in the row, -1: none
                 }
-                ++w_pairs;
-                w_modes += cnt;
-                if (!first) {
-                    const float4 x = s_xc[il];
-                    const float y0 = fmaf(r00, x.x, fmaf(r01, x.y, fmaf(r02, x.z, tx)));
-                    const float y1 = fmaf(r10, x.x, fmaf(r11, x.y, fmaf(r12, x.z, ty)));
-                    const float y2 = fmaf(r20, x.x, fmaf(r21, x.y, fmaf(r22, x.z, tz)));
-                    const int rb = il * stride;
-                    if (anchored(s_t0 + rb, s_t1 + rb, s_t2 + rb, ci, y0, y1, y2, trial, cr, cw, o)) continue;
-                }
-                pend[k] = atomicAdd(&s_nl[c], 1);
-                s_list[pend[k]] = (uint16_t)((il << 6) | hs);
-            }
-            __syncthreads();
-            if (t == 0) s_nl[c ^ 1] = 0;
-            const int nl = s_nl[c];
-            for (int e0 = 0; e0 < nl; e0 += LMC_THREADS / LMC_SB) {
-                const int e = e0 + t / LMC_SB;
-                const bool on = e < nl;
-                int il = 0, cnt = 0, h = 0;
-                float y0 = 0.f, y1 = 0.f, y2 = 0.f;
-                if (on) {
-                    const int v = s_list[e];
-                    il = v >> 6;
-                    h = s_act[v & 63];
-                    cnt = s_cnt[il];
-                    const float4 x = s_xc[il];
-                    const float *Q = s_Pf[h];
-                    y0 = fmaf(Q[0], x.x, fmaf(Q[1], x.y, fmaf(Q[2], x.z, Q[3])));
-                    y1 = fmaf(Q[4], x.x, fmaf(Q[5], x.y, fmaf(Q[6], x.z, Q[7])));
-                    y2 = fmaf(Q[8], x.x, fmaf(Q[9], x.y, fmaf(Q[10], x.z, Q[11])));
-                }
-                const int rb = il * stride;
-                const int bm = search(on, s_t0 + rb, s_t1 + rb, s_t2 + rb, cnt, i0 + il, (size_t)(i0 + il) * n + h,
-                                      y0, y1, y2);
-                if (on && t % LMC_SB == 0) s_res[e] = (int16_t)bm;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int k = 0; k < LMC_KP; ++k) {
-                if (pend[k] < 0) continue;
-                const int il = g + k * Gp;
-                const float4 x = s_xc[il];
-                const float y0 = fmaf(r00, x.x, fmaf(r01, x.y, fmaf(r02, x.z, tx)));
-                const float y1 = fmaf(r10, x.x, fmaf(r11, x.y, fmaf(r12, x.z, ty)));
-                const float y2 = fmaf(r20, x.x, fmaf(r21, x.y, fmaf(r22, x.z, tz)));
-                const int rb = il * stride;
-                finish(s_t0 + rb, s_t1 + rb, s_t2 + rb, (size_t)(i0 + il) * n + hl, y0, y1, y2, (int)s_res[pend[k]],
-                       trial, cr, cw, o);
             }
             __syncthreads();  // stage s consumed by every thread
             if (t == 0 && !*s_abort && j + LMC_STAGES < my_tiles) issue(j + LMC_STAGES, s);
@@ -607,7 +769,7 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
 
     // normal equations and correspondences at the initial poses
     {
-        roles(n);
+        roles(n, false);
         const LmcPass o = pass(mine, s_Pf[hl], false, 0, 0, true);
         reduce(o, 0, s_tot);
     }
@@ -669,7 +831,7 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
             if (t == 0) *s_nact = __popc(m0) + __popc(m1);
         }
         __syncthreads();
-        roles(*s_nact);
+        roles(*s_nact, dir_ok);
         // trial cost of the step on the current correspondences, and the
         // normal equations at the trial pose (used if the step is accepted)
         const int ob = mine ? s_cbuf[hl] : 0;
