@@ -193,8 +193,8 @@ struct QueryState {
     int16_t *tab_cnt;        // [B][max_pix] |M(u)| (0 for a skipped draw)
     float2 *tab_lm;          // [B][max_pix] per row: max over its modes of the Frobenius
                              // norm of U (1 without covariances), max |mu|
-    float4 *lm_anc;          // [B][n_cull][max_pix] LM nearest-mode anchors: y, slack^2
-    int16_t *lm_anc_b;       // [B][n_cull][max_pix] nearest mode at the anchor
+    float4 *lm_anc;          // [B][n_cull][max_pix] LM nearest-mode anchors: y, slack^2 with
+                             // the nearest mode in its low 8 bits
     int32_t *n_pix;          // [B]
     double *cur_pose;        // [B][n_cull][12]
     int32_t *cur_slot;       // [B][n_cull]

@@ -63,7 +63,7 @@ constexpr uint32_t kWaitLimit = 1u << 22;
 constexpr int LMC_KP = 4;                       // pixels of a thread per tile (staged) or chunk (direct)
 constexpr int LMC_LIST = LMC_THREADS * LMC_KP;  // full-search list capacity of a tile or chunk
 constexpr int LMC_SB = 8;                       // lanes per full nearest-mode search
-constexpr int LMC_DIRECT = 4;                   // at most this many hypotheses: rows read from global memory
+constexpr int LMC_DIRECT = 8;                   // at most this many hypotheses: rows read from global memory
 
 struct LmcLayout {
     uint32_t t0, t1, t2, xc, cnt, stage, tx;
@@ -277,7 +277,6 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
     int *s_nl = (int *)(smem + L.flag) + 1;                   // two list counters, by tile parity
     const float2 *g_lm = a.q.tab_lm + row0;
     float4 *g_anc = a.q.lm_anc + (size_t)b * cstride;
-    int16_t *g_ancb = a.q.lm_anc_b + (size_t)b * cstride;
     // squared distance (Eq. 5 form) of y to the record m of a row
     auto q_at = [&](const float4 *r0, const float4 *r1, const float *r2, int m, float y0, float y1, float y2) {
         const float4 m0 = r0[m];
@@ -342,8 +341,11 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
                 if (sl > 0.f) slack2 = sl * sl * 0.99999f;
             }
         }
-        g_anc[ci] = make_float4(y0, y1, y2, slack2);
-        g_ancb[ci] = (int16_t)best_m;
+        // the nearest mode rides in the low 8 bits of slack^2, which is first
+        // shrunk by 1e-4 relative so that the packed value stays below it
+        slack2 = slack2 > 0.f ? slack2 * 0.9999f : -1.f;
+        const int packed = (__float_as_int(slack2) & ~0xFF) | (best_m >= 0 ? best_m : 0);
+        g_anc[ci] = make_float4(y0, y1, y2, __int_as_float(packed));
     };
     // Full search of one listed pair by the LMC_SB lanes of a group (every
     // lane of the warp calls it; `on` marks a real entry); lane 0 of the
@@ -390,7 +392,7 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
         const float e0 = y0 - an.x, e1 = y1 - an.y, e2 = y2 - an.z;
         if (!(fmaf(e0, e0, fmaf(e1, e1, e2 * e2)) <= an.w)) return false;
         ++w_evals;
-        finish(r0, r1, r2, ci, y0, y1, y2, (int)g_ancb[ci], trial, cr, cw, o);
+        finish(r0, r1, r2, ci, y0, y1, y2, __float_as_int(an.w) & 0xFF, trial, cr, cw, o);
         return true;
     };
 
@@ -636,6 +638,8 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
                 split_tile(act && !*s_abort, s, j, trial, rec, cr, cw, o, r00, r01, r02, tx, r10, r11, r12, ty, r20,
                            r21, r22, tz);
             } else if (act && !*s_abort) {
+                // one lane per pair: at least 16 hypotheses, so never a frame
+                // whose pairs need anchors (rec implies S > 1)
                 const uint8_t *st = smem + s * L.stage;
                 const float4 *s_t0 = (const float4 *)(st + L.t0);
                 const float4 *s_t1 = (const float4 *)(st + L.t1);

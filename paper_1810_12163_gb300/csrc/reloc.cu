@@ -532,7 +532,6 @@ extern "C" rl_status rl_reloc_create(rl_forest *f, rl_scene *scene, const rl_ran
     A(tab_cnt, B * MP);
     A(tab_lm, B * MP);
     A(lm_anc, B * NC * MP);
-    A(lm_anc_b, B * NC * MP);
     A(n_pix, B);
     A(cur_pose, B * NC * 12);
     A(cur_slot, B * NC);
