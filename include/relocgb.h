@@ -354,7 +354,7 @@ rl_status rl_reloc_debug(rl_reloc *r, int32_t q, double *hyp_pose /* n_hyp*12 */
  * (every kernel computes the same values in the same order for each of
  * them).  Defaults: {4, 128, 128, 256}. */
 typedef struct {
-    int32_t hypgen_warps;     /* warps (slots) per block of generation: 2, 4 or 8 */
+    int32_t hypgen_warps;     /* warps (slots) per block of generation: 2, 4, 8 or 16 */
     int32_t energy_threads;   /* at most this many hypotheses per block of Eq. 5: 32, 64, 128 or 256 */
     int32_t leaves_threads;   /* pixels per block of the forest walk: 64, 128, 256 or 512 */
     int32_t mask_threads;     /* pixels per block of the colour-check masks: 64, 128 or 256 */

@@ -94,6 +94,37 @@ __device__ __forceinline__ void stage1_mask2(const HypArgs &a, const Frame &fr, 
     sB = mask_decide(b0, b1, b2, rB, dB);
 }
 
+// Stage 1 from the non-empty-M(u) bitmap (staged in shared memory) and the
+// colour-check masks: the three draws must have a non-empty M(u) (three
+// bit tests), and only the checked pixel j's mask word is gathered, for its
+// |M(u)| and colour bits; the mode indices of the other two pixels are drawn
+// in stage 2.  The decision is the same as mask_decide's.
+__device__ __forceinline__ bool bit_set(const uint32_t *bits, int p) { return (bits[p >> 5] >> (p & 31)) & 1u; }
+
+__device__ __forceinline__ void stage1_bits2(const HypArgs &a, const Frame &fr, const uint2 *cm,
+                                             const uint32_t *s_bits, int slot, int itA, int itB, Draw &dA,
+                                             Draw &dB, bool &sA, bool &sB) {
+    dA = draw(a, fr, slot, itA);
+    dB = draw(a, fr, slot, itB);
+    const int pjA = dA.j == 0 ? dA.pix[0] : (dA.j == 1 ? dA.pix[1] : dA.pix[2]);
+    const int pjB = dB.j == 0 ? dB.pix[0] : (dB.j == 1 ? dB.pix[1] : dB.pix[2]);
+    const uint2 wA = cm[pjA], wB = cm[pjB];
+    const bool okA = bit_set(s_bits, dA.pix[0]) && bit_set(s_bits, dA.pix[1]) && bit_set(s_bits, dA.pix[2]);
+    const bool okB = bit_set(s_bits, dB.pix[0]) && bit_set(s_bits, dB.pix[1]) && bit_set(s_bits, dB.pix[2]);
+    const uint32_t ctr1 = (TAG_HYP << 16) | (uint32_t)a.p.level;
+    const uint4 rA = philox(make_uint4(slot, ctr1, itA, 1), fr.key0, fr.key1);
+    const uint4 rB = philox(make_uint4(slot, ctr1, itB, 1), fr.key0, fr.key1);
+    auto decide = [](bool ok, uint2 w, uint4 r, const Draw &d) {
+        if (!ok) return false;
+        const uint32_t rj = d.j == 0 ? r.x : (d.j == 1 ? r.y : r.z);
+        const uint32_t mj = draw_below(rj, w.y >> 24);
+        const uint32_t bits = mj < 32 ? w.x >> mj : w.y >> (mj - 32);
+        return (bits & 1u) != 0;
+    };
+    sA = decide(okA, wA, rA, dA);
+    sB = decide(okB, wB, rB, dB);
+}
+
 __device__ __forceinline__ bool stage2(const HypArgs &a, const CheckThr &ct, const Frame &fr,
                                        const uint16_t *lv, const uint4 *pr, const int pix[3],
                                        const int m[3]) {
@@ -143,12 +174,20 @@ template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_hypgen(HypArgs a) {
     constexpr int HG_WARPS = WARPS;
     __shared__ int4 s_ring[HG_WARPS][HG_RING];   // it | j << 30, pixels of the triple
-    __shared__ uint2 s_mode[HG_WARPS][HG_RING];  // mode indices m0 | m1 << 16, m2
+    __shared__ uint2 s_mode[HG_WARPS][HG_RING];  // mode indices m0 | m1 << 16, m2 (without the bitmap)
+    extern __shared__ uint32_t s_bits[];         // the frame's non-empty-M(u) bitmap (with pbits)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int slot = blockIdx.x * HG_WARPS + w;
     const int b = blockIdx.y;
-    if (slot >= a.p.n_hyp) return;
     const Frame fr = a.frames[b];
+    const bool use_bits = a.pbits != nullptr && a.pcm != nullptr;
+    if (use_bits) {  // every thread of the block stages the bitmap, before any may leave
+        const int nw = (fr.W * fr.H + 31) >> 5;
+        const uint32_t *src = a.pbits + (size_t)b * (a.hw_max / 32 + 1);
+        for (int k = threadIdx.x; k < nw; k += blockDim.x) s_bits[k] = src[k];
+        __syncthreads();
+    }
+    if (slot >= a.p.n_hyp) return;
     int32_t *iter_out = a.hyp_iter + (size_t)b * a.p.n_hyp + slot;
     if (fr.W * fr.H == 0) {  // empty frame (e.g. accepted by an earlier cascade level)
         if (lane == 0) *iter_out = -1;
@@ -182,10 +221,23 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_hypgen(HypArgs a) {
         if ((unsigned)lane < n) {
             const unsigned e = (head + lane) % HG_RING;
             const int4 r = ring[e];
-            const uint2 mm = rmode[e];
             const int pix[3] = {r.y, r.z, r.w};
-            const int m[3] = {(int)(mm.x & 0xffffu), (int)(mm.x >> 16), (int)mm.y};
             it = r.x & 0x3fffffff;
+            int m[3];
+            if (use_bits) {
+                // the mode draws of the attempt, from its second Philox block
+                // and the three |M(u)|
+                const uint32_t ctr1 = (TAG_HYP << 16) | (uint32_t)a.p.level;
+                const uint4 r1 = philox(make_uint4(slot, ctr1, it, 1), fr.key0, fr.key1);
+                m[0] = (int)draw_below(r1.x, cm[pix[0]].y >> 24);
+                m[1] = (int)draw_below(r1.y, cm[pix[1]].y >> 24);
+                m[2] = (int)draw_below(r1.z, cm[pix[2]].y >> 24);
+            } else {
+                const uint2 mm = rmode[e];
+                m[0] = (int)(mm.x & 0xffffu);
+                m[1] = (int)(mm.x >> 16);
+                m[2] = (int)mm.y;
+            }
             ok = stage2(a, ct, fr, lv, pr, pix, m);
         }
         const unsigned win = __ballot_sync(0xffffffffu, ok);
@@ -198,7 +250,7 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_hypgen(HypArgs a) {
         if (s1) {
             const unsigned e = (tail + __popc(mask & lt)) % HG_RING;
             ring[e] = make_int4(it | (d.j << 30), d.pix[0], d.pix[1], d.pix[2]);
-            rmode[e] = make_uint2(d.m[0] | (d.m[1] << 16), d.m[2]);
+            if (!use_bits) rmode[e] = make_uint2(d.m[0] | (d.m[1] << 16), d.m[2]);
         }
         tail += __popc(mask);
     };
@@ -210,7 +262,10 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_hypgen(HypArgs a) {
             Draw dA, dB;
             bool sA, sB;
             const int itA = base + lane, itB = base + 32 + lane;
-            stage1_mask2(a, fr, cm, slot, itA, itB, dA, dB, sA, sB);
+            if (use_bits)
+                stage1_bits2(a, fr, cm, s_bits, slot, itA, itB, dA, dB, sA, sB);
+            else
+                stage1_mask2(a, fr, cm, slot, itA, itB, dA, dB, sA, sB);
             append(sA && itA < a.p.max_iter, itA, dA);
             append(sB && itB < a.p.max_iter, itB, dB);
         } else {
@@ -240,13 +295,18 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_hypgen(HypArgs a) {
 __global__ void __launch_bounds__(256) k_colour_mask(const Frame *__restrict__ frames,
                                                      const uint16_t *__restrict__ mcount,
                                                      const uint4 *__restrict__ prec, int hw_max, ModeView mv,
-                                                     RParams p, uint2 *__restrict__ pcm) {
+                                                     RParams p, uint2 *__restrict__ pcm,
+                                                     uint32_t *__restrict__ pbits) {
     const int b = blockIdx.y;
     const Frame fr = frames[b];
     const int px = blockIdx.x * blockDim.x + threadIdx.x;
-    if (px >= fr.W * fr.H) return;
+    const bool in = px < fr.W * fr.H;
     const size_t o = (size_t)b * hw_max + px;
-    const int cnt = mcount[o];
+    const int cnt = in ? (int)mcount[o] : 0;
+    // bit px of the non-empty-M(u) bitmap: a warp covers one 32-pixel word
+    const unsigned word = __ballot_sync(0xffffffffu, cnt > 0);
+    if (in && (threadIdx.x & 31) == 0) pbits[(size_t)b * (hw_max / 32 + 1) + (px >> 5)] = word;
+    if (!in) return;
     uint32_t lo = 0, hi = 0;
     if (cnt > 0) {
         const uint4 rec = prec[o];
@@ -270,10 +330,10 @@ __global__ void __launch_bounds__(256) k_colour_mask(const Frame *__restrict__ f
 }
 
 rl_status launch_colour_mask(const Frame *frames, const uint16_t *mcount, const uint4 *prec, int hw_max,
-                             ModeView mv, const RParams &p, uint2 *pcm, int n, int max_hw, cudaStream_t s,
-                             int threads) {
+                             ModeView mv, const RParams &p, uint2 *pcm, uint32_t *pbits, int n, int max_hw,
+                             cudaStream_t s, int threads) {
     dim3 grid((max_hw + threads - 1) / threads, n);
-    k_colour_mask<<<grid, threads, 0, s>>>(frames, mcount, prec, hw_max, mv, p, pcm);
+    k_colour_mask<<<grid, threads, 0, s>>>(frames, mcount, prec, hw_max, mv, p, pcm, pbits);
     RL_LAUNCH_CK();
     return RL_OK;
 }
@@ -341,16 +401,29 @@ __global__ void k_sample_batch(const Frame *__restrict__ frames, const uint16_t 
 }
 
 rl_status launch_hypgen(const Frame *frames, const uint16_t *leaves, const uint16_t *mcount,
-                        const uint4 *prec, const uint2 *pcm, int hw_max, ModeView mv, const RParams &p,
-                        double *hyp_pose, int32_t *hyp_iter, unsigned long long *work, int n, cudaStream_t s,
-                        int warps) {
-    HypArgs a{frames, leaves, mcount, prec, pcm, hw_max, mv, p, hyp_pose, hyp_iter, work};
+                        const uint4 *prec, const uint2 *pcm, const uint32_t *pbits, int hw_max, ModeView mv,
+                        const RParams &p, double *hyp_pose, int32_t *hyp_iter, unsigned long long *work, int n,
+                        cudaStream_t s, int warps) {
+    // the bitmap path needs the frame's bitmap in shared memory
+    const size_t bits_smem = (size_t)(hw_max / 32 + 1) * 4;
+    const bool bits = pcm && pbits && bits_smem <= kHypBitsSmemMax;
+    HypArgs a{frames, leaves, mcount, prec, pcm, hw_max, mv, p, hyp_pose, hyp_iter, work, bits ? pbits : nullptr};
+    const size_t sm = bits ? bits_smem : 0;
     switch (warps) {
-    case 2: k_hypgen<2><<<dim3((p.n_hyp + 1) / 2, n), 64, 0, s>>>(a); break;
-    case 8: k_hypgen<8><<<dim3((p.n_hyp + 7) / 8, n), 256, 0, s>>>(a); break;
-    default: k_hypgen<4><<<dim3((p.n_hyp + 3) / 4, n), 128, 0, s>>>(a); break;
+    case 2: k_hypgen<2><<<dim3((p.n_hyp + 1) / 2, n), 64, sm, s>>>(a); break;
+    case 8: k_hypgen<8><<<dim3((p.n_hyp + 7) / 8, n), 256, sm, s>>>(a); break;
+    case 16: k_hypgen<16><<<dim3((p.n_hyp + 15) / 16, n), 512, sm, s>>>(a); break;
+    default: k_hypgen<4><<<dim3((p.n_hyp + 3) / 4, n), 128, sm, s>>>(a); break;
     }
     RL_LAUNCH_CK();
+    return RL_OK;
+}
+
+rl_status prepare_hypgen() {
+    RL_CK(cudaFuncSetAttribute(k_hypgen<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHypBitsSmemMax));
+    RL_CK(cudaFuncSetAttribute(k_hypgen<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHypBitsSmemMax));
+    RL_CK(cudaFuncSetAttribute(k_hypgen<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHypBitsSmemMax));
+    RL_CK(cudaFuncSetAttribute(k_hypgen<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHypBitsSmemMax));
     return RL_OK;
 }
 

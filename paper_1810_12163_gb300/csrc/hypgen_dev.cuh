@@ -20,6 +20,7 @@ struct HypArgs {
     double *hyp_pose;        // [B][N][12]
     int32_t *hyp_iter;       // [B][N]
     unsigned long long *work;  // profiling counters or null
+    const uint32_t *pbits;   // [B][hw_max / 32 + 1] non-empty-M(u) bitmap (with pcm), or null
 };
 
 __device__ __forceinline__ float3 backproject(const Frame &fr, int p) {

@@ -179,6 +179,7 @@ struct QueryState {
     uint16_t *mcount;        // [B][HWmax] |M(u)| per pixel
     uint4 *prec;             // [B][HWmax] per-pixel leaves + counts (<= 5 trees), else null
     uint2 *pcm;              // [B][HWmax] colour-check bits of M(u) | |M(u)| << 56 (|M(u)| <= 56), else null
+    uint32_t *pbits;         // [B][HWmax / 32 + 1] bit p: M(u) of pixel p is non-empty (with pcm)
     double *hyp_pose;        // [B][N][12]
     int32_t *hyp_iter;       // [B][N]
     int32_t *hyp_list;       // [B][N] slots of successful hypotheses
@@ -290,7 +291,7 @@ struct rl_reloc {
     cudaStream_t capture_stream = nullptr;
     bool use_graphs = true;
     uint64_t calls = 0;
-    rl_tuning tune{4, 128, 128, 256};  // launch shapes (results do not depend on them)
+    rl_tuning tune{16, 128, 128, 256};  // launch shapes (results do not depend on them)
     // streaming forests: recorded after the last launch that read mode store b
     cudaEvent_t read_done[2] = {nullptr, nullptr};
     bool read_valid[2] = {false, false};

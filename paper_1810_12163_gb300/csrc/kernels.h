@@ -122,14 +122,18 @@ rl_status launch_score_poses(const RaycastArgs &a, int n_poses, int npx, float *
 rl_status launch_finalize(const QueryState &q, const RParams &p, int n_tiles, int ranked, int n,
                           cudaStream_t s);
 rl_status launch_hypgen(const Frame *frames, const uint16_t *leaves, const uint16_t *mcount,
-                        const uint4 *prec, const uint2 *pcm, int hw_max, ModeView mv, const RParams &p,
-                        double *hyp_pose, int32_t *hyp_iter, unsigned long long *work, int n, cudaStream_t s,
-                        int warps = 4);
+                        const uint4 *prec, const uint2 *pcm, const uint32_t *pbits, int hw_max, ModeView mv,
+                        const RParams &p, double *hyp_pose, int32_t *hyp_iter, unsigned long long *work, int n,
+                        cudaStream_t s, int warps = 16);
+// Generation stages the frame's non-empty-M(u) bitmap (W*H/8 bytes) in shared
+// memory when it fits this bound (640x480: 38.4 KB).
+constexpr size_t kHypBitsSmemMax = 64 * 1024;
+rl_status prepare_hypgen();
 // Largest |M(u)| the colour-check masks cover.
 constexpr int kMaskModes = 56;
 rl_status launch_colour_mask(const Frame *frames, const uint16_t *mcount, const uint4 *prec, int hw_max,
-                             ModeView mv, const RParams &p, uint2 *pcm, int n, int max_hw, cudaStream_t s,
-                             int threads = 256);
+                             ModeView mv, const RParams &p, uint2 *pcm, uint32_t *pbits, int n, int max_hw,
+                             cudaStream_t s, int threads = 256);
 rl_status launch_hyppose(const Frame *frames, const uint16_t *leaves, const uint16_t *mcount,
                          const uint4 *prec, int hw_max, ModeView mv, const RParams &p,
                          double *hyp_pose, int32_t *hyp_iter, int n, cudaStream_t s);

@@ -165,8 +165,8 @@ rl_status run_relocalise(rl_reloc *r, int n, int level, cudaStream_t s) {
     RL_CK(cudaMemsetAsync(q.dev_err, 0, sizeof(int32_t) * n, s));
     unsigned long long *work = r->prof.on ? r->prof.work : nullptr;
     { PROF(K_LEAVES); RL_TRY(launch_leaves(f, q.frames, n, p.n_trees, hw_max, q.leaves, r->max_w, r->max_h, s, p.k_top, q.mcount, q.prec, r->tune.leaves_threads)); }
-    if (q.pcm) { PROF(K_CMASK); RL_TRY(launch_colour_mask(q.frames, q.mcount, q.prec, hw_max, mv, p, q.pcm, n, hw_max, s, r->tune.mask_threads)); }
-    { PROF(K_HYPGEN); RL_TRY(launch_hypgen(q.frames, q.leaves, q.mcount, q.prec, q.pcm, hw_max, mv, p, q.hyp_pose, q.hyp_iter, work, n, s, r->tune.hypgen_warps)); }
+    if (q.pcm) { PROF(K_CMASK); RL_TRY(launch_colour_mask(q.frames, q.mcount, q.prec, hw_max, mv, p, q.pcm, q.pbits, n, hw_max, s, r->tune.mask_threads)); }
+    { PROF(K_HYPGEN); RL_TRY(launch_hypgen(q.frames, q.leaves, q.mcount, q.prec, q.pcm, q.pbits, hw_max, mv, p, q.hyp_pose, q.hyp_iter, work, n, s, r->tune.hypgen_warps)); }
     { PROF(K_HYPPOSE); RL_TRY(launch_hyppose(q.frames, q.leaves, q.mcount, q.prec, hw_max, mv, p, q.hyp_pose, q.hyp_iter, n, s)); }
     { PROF(K_COMPACT); RL_TRY(launch_compact(q.hyp_iter, N, q.hyp_list, q.n_hyp, n, s)); }
     { PROF(K_SAMPLE); RL_TRY(launch_sample_batch(q.frames, q.mcount, hw_max, p, 0, q.pix, q.xc, n, s));
@@ -520,6 +520,7 @@ extern "C" rl_status rl_reloc_create(rl_forest *f, rl_scene *scene, const rl_ran
     A(mcount, B * hw);
     if (p->n_trees_used <= kRecTrees) A(prec, B * hw);
     if (p->n_trees_used <= kRecTrees && maxm <= kMaskModes) A(pcm, B * hw);
+    if (q.pcm) A(pbits, B * (hw / 32 + 1));
     A(hyp_pose, B * N * 12);
     A(hyp_iter, B * N);
     A(hyp_list, B * N);
@@ -1220,7 +1221,7 @@ static bool one_of(int v, std::initializer_list<int> l) {
 }
 
 static bool valid_tuning(const rl_tuning &t) {
-    return one_of(t.hypgen_warps, {2, 4, 8}) && one_of(t.energy_threads, {32, 64, 128, 256}) &&
+    return one_of(t.hypgen_warps, {2, 4, 8, 16}) && one_of(t.energy_threads, {32, 64, 128, 256}) &&
            one_of(t.leaves_threads, {64, 128, 256, 512}) && one_of(t.mask_threads, {64, 128, 256});
 }
 
@@ -1338,7 +1339,7 @@ extern "C" rl_status rl_reloc_autotune(rl_reloc *r, int32_t n, const float *dept
         std::vector<int> values;
         int kid;
     };
-    std::vector<Knob> knobs = {{&rl_tuning::hypgen_warps, {2, 4, 8}, K_HYPGEN},
+    std::vector<Knob> knobs = {{&rl_tuning::hypgen_warps, {4, 8, 16}, K_HYPGEN},
                                {&rl_tuning::energy_threads, {32, 64, 128, 256}, K_ENERGY},
                                {&rl_tuning::leaves_threads, {64, 128, 256, 512}, K_LEAVES}};
     if (r->q.pcm) knobs.push_back({&rl_tuning::mask_threads, {64, 128, 256}, K_CMASK});

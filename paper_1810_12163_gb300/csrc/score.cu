@@ -1296,6 +1296,7 @@ rl_status prepare_kernels() {
     if (done) return RL_OK;
     RL_CK(cudaFuncSetAttribute(k_lm_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLmSmemMax));
     RL_TRY(prepare_lm_cluster());
+    RL_TRY(prepare_hypgen());
     done = true;
     return RL_OK;
 }
