@@ -337,6 +337,17 @@ rl_status rl_reloc_fetch(rl_reloc *r, int32_t n, void *stream, rl_result *out);
  * of a given batch size performs the capture and must not itself run under
  * the caller's stream capture. */
 rl_status rl_reloc_set_graphs(rl_reloc *r, int32_t enable);
+/* Failure injection for tests of the device-side failure path (the paper
+ * has no counterpart).  The LM kernel waits, with a bound, for the bulk
+ * copies that stage its mode-table tiles; a wait that runs out marks the
+ * frame, the kernel skips the rest of that frame's work, drains its copies
+ * in flight (always with the full bound) and the call returns
+ * RL_ERR_TIMEOUT.  `probes` sets how many times a tile wait probes before it
+ * gives up (0: at once); a negative value restores the default (2^22).
+ * Synchronises the device and drops the relocaliser's captured graphs,
+ * which hold the limit; a cascade's graphs keep the limit they were captured
+ * with. */
+rl_status rl_reloc_set_wait_limit(rl_reloc *r, int64_t probes);
 
 /* Intermediate results of frame `q` of the last call (HOST buffers, any may
  * be NULL): per generation slot the 3x4 pose and the iteration that

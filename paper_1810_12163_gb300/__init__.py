@@ -335,6 +335,12 @@ class Relocaliser:
         """Replay captured CUDA graphs (default) or launch kernels one by one."""
         call("rl_reloc_set_graphs", self.h, int(enable))
 
+    def set_wait_limit(self, probes: int = -1):
+        """Failure injection: probes of the LM kernel's waits for staged tiles
+        before they give up (0: at once, negative: the default); see
+        rl_reloc_set_wait_limit."""
+        call("rl_reloc_set_wait_limit", self.h, int(probes))
+
     def profile(self, enable: bool = True):
         """Turn per-kernel event timing and work counters on/off (resets them)."""
         call("rl_reloc_profile", self.h, int(enable))

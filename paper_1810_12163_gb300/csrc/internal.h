@@ -173,6 +173,9 @@ struct Frame {
     uint32_t key0, key1;
 };
 
+// Probes of the LM kernel's bounded waits on its own bulk copies.
+constexpr uint32_t kLmWaitLimit = 1u << 22;
+
 // Device-resident per-query RANSAC state (arrays sized for max_batch).
 struct QueryState {
     uint16_t *leaves;        // [B][T][HWmax]
@@ -292,6 +295,7 @@ struct rl_reloc {
     bool use_graphs = true;
     uint64_t calls = 0;
     rl_tuning tune{16, 128, 128, 256};  // launch shapes (results do not depend on them)
+    uint32_t lm_wait_limit = kLmWaitLimit;  // probes of the LM kernel's waits for staged tiles
     // streaming forests: recorded after the last launch that read mode store b
     cudaEvent_t read_done[2] = {nullptr, nullptr};
     bool read_valid[2] = {false, false};

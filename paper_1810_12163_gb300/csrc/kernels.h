@@ -56,6 +56,7 @@ struct LmArgs {
     unsigned long long *work;  // profiling counters or null
     int maxm;                  // |M(u)| bound: trees x min(k_top, m_max)
     int maxm_pad;              // maxm rounded up to an odd count (shared-memory rows)
+    uint32_t wait_limit;       // probes of a wait for a staged tile before it gives up
 };
 
 // Shared memory of the tiled LM kernel for a padded row of maxm_pad modes;

@@ -59,7 +59,7 @@ constexpr int LMC_STAGES = 2;
 constexpr int LMC_HMAX = 64;
 constexpr int LMC_NV = 30;       // 21 J^T J + 6 J^T r + cost, inlier count, trial cost
 constexpr int LMC_PS = 31;       // odd stride of the per-thread partials (no bank conflicts)
-constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr uint32_t kWaitLimit = kLmWaitLimit;
 constexpr int LMC_KP = 4;                       // pixels of a thread per tile (staged) or chunk (direct)
 constexpr int LMC_LIST = LMC_THREADS * LMC_KP;  // full-search list capacity of a tile or chunk
 constexpr int LMC_SB = 8;                       // lanes per full nearest-mode search
@@ -126,8 +126,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kWaitLimit; ++i)
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint32_t limit = kWaitLimit) {
+    for (uint32_t i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -627,7 +627,7 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
             const uint32_t parity = waited[s] & 1u;
             ++waited[s];
             if (!*s_abort) {
-                if (mbar_wait_bounded(bar0 + 8 * s, parity)) {
+                if (mbar_wait_bounded(bar0 + 8 * s, parity, a.wait_limit)) {
                     ++landed[s];
                 } else {
                     *s_abort = 1;

@@ -223,7 +223,7 @@ rl_status run_relocalise(rl_reloc *r, int n, int level, cudaStream_t s) {
         { PROF(K_SAMPLE); RL_TRY(launch_sample_batch(q.frames, q.mcount, hw_max, p, round + 1, q.pix, q.xc, n, s));
           RL_TRY(launch_build_table(q, hw_max, mv, p, round + 1, n, s)); }
         if (p.pose_update && p.lm_max_iter > 0) {
-            LmArgs la{q, q.leaves, hw_max, mv, p, n_pix, work, maxm, maxm | 1};
+            LmArgs la{q, q.leaves, hw_max, mv, p, n_pix, work, maxm, maxm | 1, r->lm_wait_limit};
             PROF(K_LM);
             RL_TRY(launch_lm(la, n, s));
         }
@@ -1024,6 +1024,16 @@ extern "C" const char *rl_kernel_name(int32_t kid) {
 extern "C" rl_status rl_reloc_set_graphs(rl_reloc *r, int32_t enable) {
     if (!r) return fail(RL_ERR_INVALID_ARG, "null relocaliser");
     r->use_graphs = enable != 0;
+    return RL_OK;
+}
+
+extern "C" rl_status rl_reloc_set_wait_limit(rl_reloc *r, int64_t probes) {
+    if (!r) return fail(RL_ERR_INVALID_ARG, "null relocaliser");
+    if (probes > (int64_t)UINT32_MAX) return fail(RL_ERR_INVALID_ARG, "probe limit beyond 2^32 - 1");
+    RL_CK(cudaSetDevice(r->forest->ctx->device));
+    RL_CK(cudaDeviceSynchronize());
+    r->lm_wait_limit = probes < 0 ? kLmWaitLimit : (uint32_t)probes;
+    graphs_free(r);  // captured launches hold the old limit
     return RL_OK;
 }
 

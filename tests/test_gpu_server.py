@@ -137,3 +137,75 @@ def test_cascade_model_matches_the_cascade_alone(setup):
         assert alone["energy"] == r["energy"] and alone["n_hypotheses"] == r["n_hypotheses"]
         assert (alone["score"] == r["score"]) or (np.isinf(alone["score"]) and np.isinf(r["score"]))
     assert used  # at least one level produced the results
+
+
+def _oracle_room(w):
+    """The oracle's forest nodes and modes of a serving room's workload."""
+    import oracle
+    f = H.oracle_forest_nodes(w)
+    res = oracle.Reservoirs(f, w.forest["kappa"], w.forest_seed)
+    for d, c, T in w.training_frames():
+        res.add_frame(d, c, w.K, T, w.forest["grid_step"], w.forest["grid_origin"])
+    modes = oracle.Modes(res.n_leaves, w.forest["m_max"])
+    oracle.update_modes(res, modes, w.forest["sigma"], w.forest["tau_c"], w.forest["min_cluster_size"],
+                        cov_eps=w.forest["cov_eps"], fp16_offsets=bool(w.forest["mode_precision"]))
+    return f, modes
+
+
+def test_config4_rooms_served_against_the_oracle():
+    """Config 4 through the serving loop: the 6x5x3 m and 10x8x3 m rooms,
+    each with its own five-tree depth-15 forest trained on its 200-frame
+    trajectory, served as the config-3 cascade; a 640x480 query and a
+    320x240 query (the same view at half resolution, K / 2) per room,
+    submitted together, each compared with the FP64 oracle's cascade."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle
+    import paper_1810_12163_gb300 as rg
+    ctx = rg.Context(0, arena_bytes=16 << 30)
+    th = workloads.cascade_thresholds()
+    subsample = [s for s, _ in workloads.CASCADE_LEVELS]
+    levels = [p for _, p in workloads.CASCADE_LEVELS]
+    srv = rg.Server(ctx, max_batch=4, memory_budget=1 << 30)
+    jobs = []
+    keep = []
+    for w in workloads.SERVING_ROOMS[1:]:
+        g = H.gpu_model(ctx, w)
+        scene = rg.Scene(ctx, w.room().lo, w.room().hi)
+        keep += [g, scene]
+        m = srv.add_cascade_model(g, scene, levels, subsample, th, w.width, w.height)
+        d, c, T, seed = w.query(2)
+        ds, cs, Ks = rooms.subsample(d, c, w.K, 2)
+        for dd, cc, KK, sd in ((d, c, w.K, seed), (ds, cs, Ks, seed + 1)):
+            jobs.append((w, dd, cc, KK, sd, srv.submit(m, dd, cc, KK, sd)))
+    got = [srv.wait(tk, 120_000) for *_, tk in jobs]
+    srv.close()
+    lpt = 1 << workloads.FOREST_DEFAULT["depth"]
+    models = {}
+    for (w, d, c, K, seed, _), r in zip(jobs, got):
+        if w.name not in models:
+            models[w.name] = _oracle_room(w)
+        f, modes = models[w.name]
+        frames, maps, params = [], [], []
+        for lvl, (s, p) in enumerate(workloads.CASCADE_LEVELS):
+            ds, cs, Ks = rooms.subsample(d, c, K, s) if s > 1 else (d, c, K)
+            frames.append((ds, cs, Ks))
+            maps.append(oracle.forest_leaves(f, ds, cs, Ks.fx, n_trees=p["n_trees_used"]))
+            params.append(dict(p, level=lvl))
+        o = oracle.cascade(params, th, frames, maps, modes, w.room().lo, w.room().hi, seed, lpt)
+        what = f"{w.name} {K.width}x{K.height}"
+        assert r["n_hypotheses"] >= 0
+        if r["level"] != o["level"]:
+            # a fall-back decision on a score within its tolerance of tau
+            lvl = min(r["level"], o["level"])
+            assert abs(min(r["score"], o["score"]) - th[lvl]) <= 1e-4 + 1e-3 * th[lvl], what
+            continue
+        assert r["n_hypotheses"] == o["n_hypotheses"], what
+        dt, dr = H.pose_err(r["pose"], o["pose"])
+        assert dt <= H.POSE_T_TOL and dr <= H.POSE_R_TOL, (what, dt, dr)
+        tol = H.score_tolerances([r["pose"]], [o["pose"]], [o["score"]])
+        H.check_scores([r["score"]], [o["score"]], tol, what)
+    for x in keep:
+        x.close()
+    ctx.close()
