@@ -200,7 +200,11 @@ rl_status rl_forest_adapt(rl_forest *f, const float *depth, const uint8_t *rgb,
                           void *stream);
 /* Sec. 3.2.2 step 3: Really Quick Shift on the next `n_leaves` leaves in
  * round-robin order (n_leaves < 0: every leaf); keeps the largest M_max
- * clusters per leaf with centroid, colour, covariance. */
+ * clusters per leaf with centroid, colour, covariance.  Ordered by CUDA
+ * events against relocalisation on other streams (the serving loop's
+ * included): the update waits on `stream` for launches already enqueued
+ * that read the modes, and launches enqueued after this call wait for the
+ * update.  rl_forest_reset_leaves is ordered the same way. */
 rl_status rl_forest_update_modes(rl_forest *f, int32_t n_leaves, void *stream);
 /* Streaming adaptation (Sec. 3.2.2: leaves are re-clustered a few hundred
  * per frame while the relocaliser keeps running): enable = 1 gives the

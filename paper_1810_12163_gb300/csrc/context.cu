@@ -158,6 +158,19 @@ static rl_status wait_readers(rl_forest *f, int b, cudaStream_t s) {
     return RL_OK;
 }
 
+// An in-place update of a one-store forest's modes, enqueued on s: it waits
+// for the launches that read the store, and launches enqueued after it (on
+// any stream) wait for `ready`, recorded after it.
+template <class F>
+static rl_status in_place_update(rl_forest *f, cudaStream_t s, F &&update) {
+    std::lock_guard<std::mutex> g(f->mu);
+    RL_TRY(wait_readers(f, 0, s));
+    RL_TRY(update());
+    if (!f->ready) RL_CK(cudaEventCreateWithFlags(&f->ready, cudaEventDisableTiming));
+    RL_CK(cudaEventRecord(f->ready, s));
+    return RL_OK;
+}
+
 static rl_status streaming_update(rl_forest *f, int64_t begin, int64_t count, cudaStream_t s) {
     std::lock_guard<std::mutex> g(f->mu);
     const int back = 1 - f->mode_buf;
@@ -317,7 +330,7 @@ extern "C" rl_status rl_forest_reset_leaves(rl_forest *f, void *stream) {
     if (!f) return fail(RL_ERR_INVALID_ARG, "null forest");
     RL_CK(cudaSetDevice(f->ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
-    if (!f->streaming) return reset_leaves(f, s);
+    if (!f->streaming) return in_place_update(f, s, [&] { return reset_leaves(f, s); });
     // both stores emptied once no launch reads either
     std::lock_guard<std::mutex> g(f->mu);
     RL_TRY(wait_readers(f, 0, s));
@@ -374,10 +387,11 @@ extern "C" rl_status rl_forest_update_modes(rl_forest *f, int32_t n_leaves, void
     RL_CK(cudaSetDevice(f->ctx->device));
     int64_t count = n_leaves < 0 ? f->n_leaves : std::min<int64_t>(n_leaves, f->n_leaves);
     int64_t begin = n_leaves < 0 ? 0 : f->cursor;
+    cudaStream_t s = (cudaStream_t)stream;
     if (f->streaming)
-        RL_TRY(streaming_update(f, begin, count, (cudaStream_t)stream));
+        RL_TRY(streaming_update(f, begin, count, s));
     else
-        RL_TRY(update_modes(f, begin, count, (cudaStream_t)stream));
+        RL_TRY(in_place_update(f, s, [&] { return update_modes(f, begin, count, s); }));
     if (n_leaves >= 0) f->cursor = (f->cursor + count) % f->n_leaves;
     return RL_OK;
 }

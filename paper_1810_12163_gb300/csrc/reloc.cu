@@ -300,10 +300,11 @@ static void graphs_free(rl_reloc *r) {
     r->capture_stream = nullptr;
 }
 
-// Reader side of a streaming forest (see rl_forest_set_streaming): under the
-// forest's lock, the launch waits for the last mode update and records, after
-// its own work, the event that the next update of the store it read waits
-// for.  A non-streaming forest has one store and no events.
+// Reader side of a forest's mode store: under the forest's lock, the launch
+// waits for the last mode update (on whatever stream it was enqueued) and
+// records, after its own work, the event that the next update of the store
+// it read waits for.  A streaming forest (see rl_forest_set_streaming) has
+// two stores; the others have one, which updates overwrite in place.
 struct ModeReadScope {
     rl_forest *f;
     std::unique_lock<std::mutex> lk;
@@ -311,11 +312,10 @@ struct ModeReadScope {
     ModeReadScope(rl_forest *forest, cudaStream_t s, rl_status *st) : f(forest), lk(forest->mu) {
         buf = f->mode_buf;
         *st = RL_OK;
-        if (f->streaming && cudaStreamWaitEvent(s, f->ready, 0) != cudaSuccess)
+        if (f->ready && cudaStreamWaitEvent(s, f->ready, 0) != cudaSuccess)
             *st = fail(RL_ERR_CUDA, "waiting for the mode snapshot failed");
     }
     rl_status done(rl_reloc *r, cudaStream_t s) {
-        if (!f->streaming) return RL_OK;
         if (!r->read_done[buf]) RL_CK(cudaEventCreateWithFlags(&r->read_done[buf], cudaEventDisableTiming));
         RL_CK(cudaEventRecord(r->read_done[buf], s));
         r->read_valid[buf] = true;

@@ -157,7 +157,11 @@ def test_config4_rooms_served_against_the_oracle():
     each with its own five-tree depth-15 forest trained on its 200-frame
     trajectory, served as the config-3 cascade; a 640x480 query and a
     320x240 query (the same view at half resolution, K / 2) per room,
-    submitted together, each compared with the FP64 oracle's cascade."""
+    submitted together, each compared with the FP64 oracle's cascade and
+    with the same cascade run alone.  The second room's forest trains on
+    the default stream while the first room's requests run on the serving
+    loop's streams, and its own requests follow its last mode update at
+    once: the library must order both by itself."""
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -170,10 +174,18 @@ def test_config4_rooms_served_against_the_oracle():
     srv = rg.Server(ctx, max_batch=4, memory_budget=1 << 30)
     jobs = []
     keep = []
+    models, g_of, scene_of = {}, {}, {}
     for w in workloads.SERVING_ROOMS[1:]:
         g = H.gpu_model(ctx, w)
         scene = rg.Scene(ctx, w.room().lo, w.room().hi)
         keep += [g, scene]
+        g_of[w.name], scene_of[w.name] = g, scene
+        # the room's forest and modes equal the oracle's
+        f, modes = models[w.name] = _oracle_room(w)
+        e = g.export()
+        assert np.array_equal(e["nmodes"], modes.nmodes), w.name
+        mm = np.arange(w.forest["m_max"])[None, :] < modes.nmodes[:, None]
+        assert np.array_equal(e["mode_pos"][mm].view(np.uint32), modes.pos[mm].view(np.uint32)), w.name
         m = srv.add_cascade_model(g, scene, levels, subsample, th, w.width, w.height)
         d, c, T, seed = w.query(2)
         ds, cs, Ks = rooms.subsample(d, c, w.K, 2)
@@ -182,10 +194,7 @@ def test_config4_rooms_served_against_the_oracle():
     got = [srv.wait(tk, 120_000) for *_, tk in jobs]
     srv.close()
     lpt = 1 << workloads.FOREST_DEFAULT["depth"]
-    models = {}
     for (w, d, c, K, seed, _), r in zip(jobs, got):
-        if w.name not in models:
-            models[w.name] = _oracle_room(w)
         f, modes = models[w.name]
         frames, maps, params = [], [], []
         for lvl, (s, p) in enumerate(workloads.CASCADE_LEVELS):
@@ -194,7 +203,18 @@ def test_config4_rooms_served_against_the_oracle():
             maps.append(oracle.forest_leaves(f, ds, cs, Ks.fx, n_trees=p["n_trees_used"]))
             params.append(dict(p, level=lvl))
         o = oracle.cascade(params, th, frames, maps, modes, w.room().lo, w.room().hi, seed, lpt)
-        what = f"{w.name} {K.width}x{K.height}"
+        what = f"{w.name} {K.width}x{K.height} level {r['level']}/{o['level']}"
+        # the same cascade run on its own
+        lv = [rg.Relocaliser(g_of[w.name], scene_of[w.name], p, (K.width + s - 1) // s, (K.height + s - 1) // s, 1)
+              for s, p in workloads.CASCADE_LEVELS]
+        cas = rg.Cascade(lv, th, subsample)
+        alone = cas.relocalise_batch(d[None], c[None], K, [seed])[0]
+        cas.close()
+        for x in lv:
+            x.close()
+        # served in a batch with the other resolution: bit-identical to alone
+        assert r["level"] == alone["level"] and r["n_hypotheses"] == alone["n_hypotheses"], what
+        assert np.array_equal(r["pose"], alone["pose"]), what
         assert r["n_hypotheses"] >= 0
         if r["level"] != o["level"]:
             # a fall-back decision on a score within its tolerance of tau
