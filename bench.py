@@ -69,6 +69,10 @@ def parse():
     ap.add_argument("--tracking-loss", action="store_true",
                     help="tracking-loss recovery along a fresh trajectory from empty leaves")
     ap.add_argument("--track-frames", type=int, default=120)
+    ap.add_argument("--track-depth", type=int, default=15,
+                    help="tree depth of the tracking-loss forest (13: 5 x 8192 = 40,960 leaves)")
+    ap.add_argument("--track-leaves", default="256,8192,65536",
+                    help="leaves re-clustered per frame, one arm each (comma separated)")
     ap.add_argument("--rqs-leaves", type=int, default=0,
                     help="time Really Quick Shift on this many leaves of the trained config-2 forest")
     ap.add_argument("--streaming", action="store_true",
@@ -1003,6 +1007,7 @@ def run_tracking_loss(args):
     import paper_1810_12163_gb300 as rg
     from synth import rooms
     w = workloads.CONFIG2
+    fp = dict(w.forest, depth=args.track_depth)
     room = w.room()
     n = args.track_frames
     poses = rooms.training_trajectory(room, n, seed=21)
@@ -1014,8 +1019,8 @@ def run_tracking_loss(args):
     ctx = rg.Context(0, arena_bytes=24 << 30)
     scene = rg.Scene(ctx, room.lo, room.hi)
     out = []
-    for k in (256, 8192, 65536):
-        forest = rg.Forest.random(ctx, w.forest, w.forest_seed)
+    for k in [int(x) for x in args.track_leaves.split(",")]:
+        forest = rg.Forest.random(ctx, fp, w.forest_seed)
         forest.set_streaming(True)
         rel = rg.Relocaliser(forest, scene, w.ransac, w.width, w.height, 1)
         sR, sT = torch.cuda.Stream(), torch.cuda.Stream()
@@ -1048,7 +1053,7 @@ def run_tracking_loss(args):
                                            "p99": float(np.percentile(train_ms[1:], 99))},
                     "reloc_ms": {"median": float(np.median(reloc_ms)), "p99": float(np.percentile(reloc_ms, 99))}})
     line = {"metric": "tracking-loss recovery: 5 cm / 5 deg success per frame", "workload": w.name,
-            "frames": n, "forest_leaves": int(w.forest["n_trees"] << w.forest["depth"]),
+            "frames": n, "tree_depth": args.track_depth, "forest_leaves": int(fp["n_trees"] << fp["depth"]),
             "sequence": "seeded trajectory (seed 21) of the config-2 room, 2 mm depth noise", "arms": out}
     print(json.dumps(line), flush=True)
     scene.close()

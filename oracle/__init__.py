@@ -71,7 +71,7 @@ class Params(ctypes.Structure):
         ("lm_max_iter", ctypes.c_int32), ("batch_attempts", ctypes.c_int32),
         ("lm_lambda0", F64), ("lm_inlier_thresh", F64), ("lm_stop", F64),
         ("rank", ctypes.c_int32), ("halve_to_one", ctypes.c_int32), ("level", ctypes.c_int32),
-        ("icp", ctypes.c_int32), ("icp_p", IcpParams),
+        ("icp", ctypes.c_int32), ("redraw", ctypes.c_int32), ("icp_p", IcpParams),
     ]
 
 
@@ -307,7 +307,7 @@ PARAM_DEFAULTS = dict(
     n_hyp=1024, max_iter=6000, n_cull=64, eta=512, k_out=16, pose_update=1, use_cov=1,
     colour_thresh=30, min_sq_dist=0.09, max_trans_err=0.05, k_top=10, n_trees_used=5,
     lm_max_iter=10, batch_attempts=32, lm_lambda0=1e-3, lm_inlier_thresh=0.1, lm_stop=1e-6,
-    rank=1, halve_to_one=0, level=0,
+    rank=1, halve_to_one=0, level=0, redraw=0,
     icp=0, icp_levels=3, icp_stride=(4, 2, 1), icp_iters=(6, 3, 2), icp_dist=(0.1, 0.05, 0.025),
     icp_min_frac=0.5, icp_ridge=1e-4,
 )

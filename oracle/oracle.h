@@ -125,6 +125,7 @@ typedef struct {
     int32_t halve_to_one;     /* keep halving to 1 after the chosen set */
     int32_t level;            /* cascade level, part of the random stream */
     int32_t icp;              /* ICP of the chosen set (ranked) or output pose (R21) */
+    int32_t redraw;           /* R8b: an invalid pixel draw is redrawn within its iteration */
     orc_icp_params icp_p;
 } orc_params;
 

@@ -519,6 +519,20 @@ static int try_hypothesis(const orc_params *p, const uint32_t key[2], int slot, 
     double xc[3][3], xw[3][3];
     for (int i = 0; i < 3; ++i) {
         pix[i] = (int)below(r0[i], (uint32_t)WH);
+        /* R8: a pixel without depth or with an empty M(u) fails the
+         * iteration.  R8b (redraw): it is redrawn within the iteration, as
+         * the batch sampler of R12 does, up to batch_attempts draws in all;
+         * draw a >= 1 of pixel i takes word 0 of the Philox block with
+         * counter (slot, 5 << 16 | level, it, 4a + i). */
+        for (int a = 1; p->redraw && a < p->batch_attempts; ++a) {
+            if (depth_img[pix[i]] > 0.0f &&
+                mode_count(pix[i], WH, leaves, p->n_trees_used, leaves_per_tree, nmodes, p->k_top) > 0)
+                break;
+            uint32_t c2[4] = {(uint32_t)slot, (5u << 16) | (uint32_t)p->level, (uint32_t)it, 4u * (uint32_t)a + (uint32_t)i};
+            uint32_t r2[4];
+            orc_philox4x32_10(c2, key, r2);
+            pix[i] = (int)below(r2[0], (uint32_t)WH);
+        }
         if (!(depth_img[pix[i]] > 0.0f))
             return 0;
         const int nm = mode_count(pix[i], WH, leaves, p->n_trees_used, leaves_per_tree, nmodes, p->k_top);

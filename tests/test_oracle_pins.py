@@ -823,15 +823,26 @@ def _numpy_attempt(w, p, d, c, lv, modes, key, slot, it):
     r0 = philox_ref.philox4x32_10((slot, (3 << 16) | p["level"], it, 0), key)
     r1 = philox_ref.philox4x32_10((slot, (3 << 16) | p["level"], it, 1), key)
     lpt = 1 << w.forest["depth"]
-    xs, xw, pix, me = [], [], [], []
-    for i in range(3):
-        q = philox_ref.below(r0[i], WH)
-        if not d.flat[q] > 0:
-            return None
+
+    def modes_of(q):
         ms = []
         for t in range(p["n_trees_used"]):
             L = t * lpt + int(lv[t].flat[q])
             ms += [(L, m) for m in range(min(int(modes.nmodes[L]), p["k_top"]))]
+        return ms
+
+    xs, xw, pix, me = [], [], [], []
+    for i in range(3):
+        q = philox_ref.below(r0[i], WH)
+        # reading R8b: an unusable pixel is redrawn within the iteration
+        for a in range(1, p["batch_attempts"] if p.get("redraw") else 1):
+            if d.flat[q] > 0 and modes_of(q):
+                break
+            r2 = philox_ref.philox4x32_10((slot, (5 << 16) | p["level"], it, 4 * a + i), key)
+            q = philox_ref.below(r2[0], WH)
+        if not d.flat[q] > 0:
+            return None
+        ms = modes_of(q)
         if not ms:
             return None
         L, m = ms[philox_ref.below(r1[i], len(ms))]
@@ -856,6 +867,44 @@ def _numpy_attempt(w, p, d, c, lv, modes, key, slot, it):
         if abs(dw - dc) > p["max_trans_err"]:
             return None
     return np.array(xs), np.array(xw)
+
+
+def test_generation_redraw_reading_rederived():
+    """Reading R8b (redraw within the iteration) on a query with 70% of its
+    depth missing: each slot's winning iteration is the first accepted one
+    of the numpy re-derivation with redraws, the accepted triple gives the
+    oracle's pose, and redrawing keeps far more hypotheses than R8."""
+    w = H.WORKLOADS[H.SMALL]
+    f, res, modes = H.oracle_model(w.name)
+    d, c, T, seed = w.query(1)
+    d = rooms.mask_depth(d, 0.7, seed=17)
+    lv = oracle.forest_leaves(f, d, c, w.K.fx, n_trees=w.ransac["n_trees_used"])
+    args = (d, c, w.K, lv, modes, w.room().lo, w.room().hi, seed, 1 << w.forest["depth"])
+    p = dict(oracle.PARAM_DEFAULTS, **w.ransac, redraw=1)
+    r = oracle.relocalise(p, *args, debug=True)
+    r8 = oracle.relocalise(dict(p, redraw=0), *args, debug=True)
+    assert r["n_hypotheses"] >= 3 * max(1, r8["n_hypotheses"]), (r["n_hypotheses"], r8["n_hypotheses"])
+    key = philox_ref.key_of(seed)
+    it = r["debug"]["hyp_iter"]
+    for slot in range(0, p["n_hyp"], 11):
+        last = it[slot] if it[slot] >= 0 else p["max_iter"]
+        for k in range(min(last, 40)):
+            assert _numpy_attempt(w, p, d, c, lv, modes, key, slot, k) is None
+        if it[slot] >= 0:
+            pair = _numpy_attempt(w, p, d, c, lv, modes, key, slot, it[slot])
+            assert pair is not None
+            Rh, th = _horn(*pair)
+            P = r["debug"]["hyp_pose"][slot].reshape(3, 4)
+            assert np.abs(P[:, :3] - Rh).max() < 1e-9 and np.abs(P[:, 3] - th).max() < 1e-9
+    # without missing depth every first draw is usable: the readings agree
+    d0, c0, _, _ = w.query(1)
+    lv0 = oracle.forest_leaves(f, d0, c0, w.K.fx, n_trees=w.ransac["n_trees_used"])
+    a0 = (d0, c0, w.K, lv0, modes, w.room().lo, w.room().hi, seed, 1 << w.forest["depth"])
+    ra = oracle.relocalise(p, *a0, debug=True)
+    rb = oracle.relocalise(dict(p, redraw=0), *a0, debug=True)
+    if (d0 > 0).all() and all((modes.nmodes[t * (1 << w.forest["depth"]) + lv0[t].astype(int)] > 0).all()
+                              for t in range(p["n_trees_used"])):
+        assert np.array_equal(ra["debug"]["hyp_iter"], rb["debug"]["hyp_iter"])
 
 
 @pytest.fixture(scope="module")
