@@ -967,7 +967,12 @@ def run_robustness(args):
                                            for i, q in enumerate(queries)])).cuda()
             C = torch.from_numpy(np.stack([q[1] for q in queries])).cuda()
             row = {"level": lvl, "valid_depth": float((D > 0).float().mean())}
-            for name, p in (("no_icp", w.ransac), ("icp", dict(w.ransac, **workloads.ICP_ON))):
+            # readings R8 (an unusable draw fails its iteration) and R8b
+            # (redrawn within the iteration), each without and with ICP
+            variants = (("no_icp", w.ransac), ("icp", dict(w.ransac, **workloads.ICP_ON)),
+                        ("redraw_no_icp", dict(w.ransac, redraw=1)),
+                        ("redraw_icp", dict(w.ransac, redraw=1, **workloads.ICP_ON)))
+            for name, p in variants:
                 rel = rg.Relocaliser(forest, scene, p, w.width, w.height, nq)
                 rs = rel.relocalise_batch(D, C, w.K, [q[3] for q in queries])
                 rel.close()
@@ -982,7 +987,8 @@ def run_robustness(args):
     line = {"metric": "5 cm / 5 deg success vs depth corruption", "workload": w.name, "queries": nq,
             "arms": {"missing": "training frames and queries masked",
                      "missing_queries_only": "queries masked, forest adapted from clean frames",
-                     "noise": "training frames and queries noisy"}, **out,
+                     "noise": "training frames and queries noisy",
+                     "redraw_*": "reading R8b: generation redraws an unusable pixel within its iteration"}, **out,
             "icp": {k: (list(v) if isinstance(v, tuple) else v) for k, v in workloads.ICP_ON.items()},
             "seconds": time.perf_counter() - t0}
     print(json.dumps(line), flush=True)

@@ -137,7 +137,11 @@ typedef struct {
     int32_t halve_to_one;     /* keep halving after the chosen set is taken */
     int32_t icp;              /* 1: ICP before ranking (each chosen pose; the
                                  output pose alone when rank == 0); needs a scene */
-    int32_t pad;
+    int32_t redraw;           /* 0: a generation draw of a pixel without depth or
+                                 with an empty M(u) fails its iteration (the
+                                 default reading); 1: it is redrawn within the
+                                 iteration, up to batch_attempts draws in all
+                                 (the paper does not say which it does) */
     rl_icp_params icp_p;
 } rl_ransac_params;
 

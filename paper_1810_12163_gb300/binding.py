@@ -65,7 +65,7 @@ class RansacParams(ctypes.Structure):
                 ("k_top", I32), ("n_trees_used", I32), ("lm_max_iter", I32),
                 ("batch_attempts", I32), ("lm_lambda0", ctypes.c_double),
                 ("lm_inlier_thresh", ctypes.c_double), ("lm_stop", ctypes.c_double),
-                ("rank", I32), ("halve_to_one", I32), ("icp", I32), ("pad", I32),
+                ("rank", I32), ("halve_to_one", I32), ("icp", I32), ("redraw", I32),
                 ("icp_p", IcpParams)]
 
 

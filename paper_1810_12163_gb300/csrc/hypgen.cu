@@ -41,7 +41,7 @@ struct CheckThr {
 __device__ __forceinline__ bool stage1(const HypArgs &a, const Frame &fr, const uint16_t *lv,
                                        const uint16_t *mc, const uint4 *pr, int slot, int it,
                                        Draw &d) {
-    d = draw(a, fr, slot, it);
+    d = draw(a, fr, slot, it, [&](int q) { return mc[q] != 0; });
     const int c0 = mc[d.pix[0]], c1 = mc[d.pix[1]], c2 = mc[d.pix[2]];
     if (c0 == 0 || c1 == 0 || c2 == 0) return false;
     const uint32_t ctr1 = (TAG_HYP << 16) | (uint32_t)a.p.level;
@@ -83,8 +83,9 @@ __device__ __forceinline__ bool mask_decide(const uint2 w0, const uint2 w1, cons
 
 __device__ __forceinline__ void stage1_mask2(const HypArgs &a, const Frame &fr, const uint2 *cm, int slot,
                                              int itA, int itB, Draw &dA, Draw &dB, bool &sA, bool &sB) {
-    dA = draw(a, fr, slot, itA);
-    dB = draw(a, fr, slot, itB);
+    auto usable = [&](int q) { return (cm[q].y >> 24) != 0; };
+    dA = draw(a, fr, slot, itA, usable);
+    dB = draw(a, fr, slot, itB, usable);
     const uint2 a0 = cm[dA.pix[0]], a1 = cm[dA.pix[1]], a2 = cm[dA.pix[2]];
     const uint2 b0 = cm[dB.pix[0]], b1 = cm[dB.pix[1]], b2 = cm[dB.pix[2]];
     const uint32_t ctr1 = (TAG_HYP << 16) | (uint32_t)a.p.level;
@@ -104,8 +105,9 @@ __device__ __forceinline__ bool bit_set(const uint32_t *bits, int p) { return (b
 __device__ __forceinline__ void stage1_bits2(const HypArgs &a, const Frame &fr, const uint2 *cm,
                                              const uint32_t *s_bits, int slot, int itA, int itB, Draw &dA,
                                              Draw &dB, bool &sA, bool &sB) {
-    dA = draw(a, fr, slot, itA);
-    dB = draw(a, fr, slot, itB);
+    auto usable = [&](int q) { return bit_set(s_bits, q); };
+    dA = draw(a, fr, slot, itA, usable);
+    dB = draw(a, fr, slot, itB, usable);
     const int pjA = dA.j == 0 ? dA.pix[0] : (dA.j == 1 ? dA.pix[1] : dA.pix[2]);
     const int pjB = dB.j == 0 ? dB.pix[0] : (dB.j == 1 ? dB.pix[1] : dB.pix[2]);
     const uint2 wA = cm[pjA], wB = cm[pjB];

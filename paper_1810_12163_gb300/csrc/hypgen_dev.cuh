@@ -38,7 +38,12 @@ struct Draw {
     int j;
 };
 
-__device__ __forceinline__ Draw draw(const HypArgs &a, const Frame &fr, int slot, int it) {
+// With p.redraw (reading R8b) a pixel that `usable` rejects (no depth or an
+// empty M(u)) is redrawn within the iteration, up to batch_attempts draws in
+// all: draw at >= 1 of pixel i takes word 0 of the Philox block with counter
+// (slot, TAG_REDRAW << 16 | level, it, 4 at + i).
+template <class Usable>
+__device__ __forceinline__ Draw draw(const HypArgs &a, const Frame &fr, int slot, int it, Usable usable) {
     const uint32_t ctr1 = (TAG_HYP << 16) | (uint32_t)a.p.level;
     const uint4 r0 = philox(make_uint4(slot, ctr1, it, 0), fr.key0, fr.key1);
     const uint32_t WH = (uint32_t)(fr.W * fr.H);
@@ -47,6 +52,12 @@ __device__ __forceinline__ Draw draw(const HypArgs &a, const Frame &fr, int slot
     d.pix[1] = (int)draw_below(r0.y, WH);
     d.pix[2] = (int)draw_below(r0.z, WH);
     d.j = (int)draw_below(r0.w, 3);
+    if (a.p.redraw) {
+        const uint32_t ctr2 = (TAG_REDRAW << 16) | (uint32_t)a.p.level;
+        for (int i = 0; i < 3; ++i)
+            for (int at = 1; at < a.p.batch_attempts && !usable(d.pix[i]); ++at)
+                d.pix[i] = (int)draw_below(philox(make_uint4(slot, ctr2, it, 4u * at + i), fr.key0, fr.key1).x, WH);
+    }
     return d;
 }
 

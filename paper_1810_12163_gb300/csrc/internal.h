@@ -161,6 +161,7 @@ struct RParams {
     int maxm;         // bound on |M(u)|: trees x min(k_top, m_max)
     int mpad;         // maxm rounded up to an odd count (mode-table row stride)
     int icp;          // ICP before ranking (or of the output pose when unranked)
+    int redraw;       // generation redraws an unusable pixel within its iteration
     IcpParams icp_p;
 };
 
@@ -337,7 +338,7 @@ struct rl_cascade {
 // ---------------------------------------------------------------------------
 namespace rl {
 
-enum : uint32_t { TAG_FOREST = 1, TAG_RESERVOIR = 2, TAG_HYP = 3, TAG_BATCH = 4 };
+enum : uint32_t { TAG_FOREST = 1, TAG_RESERVOIR = 2, TAG_HYP = 3, TAG_BATCH = 4, TAG_REDRAW = 5 };
 
 // Philox4x32-10 (Salmon et al., SC'11): 10 rounds of the multiply-xor round
 // with Weyl-sequence key schedule.

@@ -162,7 +162,7 @@ __device__ void kabsch3_horn(const double a[3][3], const double b[3][3], double 
 // The accepted triple of (slot, it), re-derived exactly, and its pose.
 __device__ __forceinline__ void accept_triple(const HypArgs &a, const Frame &fr, const uint16_t *lv,
                                            const uint16_t *mc, const uint4 *pr, int slot, int it, double H[12]) {
-    const Draw d = draw(a, fr, slot, it);
+    const Draw d = draw(a, fr, slot, it, [&](int q) { return mc[q] != 0; });
     const uint32_t ctr1 = (TAG_HYP << 16) | (uint32_t)a.p.level;
     const uint4 r1 = philox(make_uint4(slot, ctr1, it, 1), fr.key0, fr.key1);
     const uint32_t u1[3] = {r1.x, r1.y, r1.z};

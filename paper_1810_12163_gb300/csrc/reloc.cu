@@ -35,6 +35,7 @@ static rl_status check_ransac(const rl_ransac_params *p, const rl_forest *f) {
     if (p->lm_max_iter < 0) return fail(RL_ERR_INVALID_ARG, "lm_max_iter must be >= 0");
     if (p->colour_thresh < 0) return fail(RL_ERR_INVALID_ARG, "colour_thresh must be >= 0");
     if (p->icp != 0 && p->icp != 1) return fail(RL_ERR_INVALID_ARG, "icp must be 0 or 1");
+    if (p->redraw != 0 && p->redraw != 1) return fail(RL_ERR_INVALID_ARG, "redraw must be 0 or 1");
     return RL_OK;
 }
 
@@ -501,6 +502,7 @@ extern "C" rl_status rl_reloc_create(rl_forest *f, rl_scene *scene, const rl_ran
     rp.lm_lambda0 = p->lm_lambda0; rp.lm_inlier_thresh = p->lm_inlier_thresh; rp.lm_stop = p->lm_stop;
     rp.rank = p->rank; rp.halve_to_one = p->halve_to_one; rp.level = 0;
     rp.icp = p->icp;
+    rp.redraw = p->redraw;
     if (p->icp) rp.icp_p = icp_device_params(p->icp_p);
     rp.max_rounds = rounds_for(p->n_cull, p->k_out, p->halve_to_one);
     // rows of whole 16-pixel tiles: the LM kernel stages tiles with bulk copies

@@ -84,3 +84,33 @@ def test_config2_query_with_90_percent_missing_depth(rg, ctx):
     rel.close()
     scene.close()
     g.close()
+
+
+@pytest.mark.parametrize("level", [0.7, 0.9])
+def test_redraw_reading_parity(rg, ctx, level):
+    """Reading R8b (an unusable generation draw is redrawn within its
+    iteration): queries with missing depth against the clean small-case
+    forest, every stage compared with the oracle run with the same reading;
+    the reading keeps far more hypotheses than R8."""
+    w = H.WORKLOADS[H.SMALL]
+    g = H.gpu_model(ctx, w)
+    f, res, modes = H.oracle_model(w.name)
+    room = w.room()
+    scene = rg.Scene(ctx, room.lo, room.hi)
+    p = dict(w.ransac, redraw=1)
+    rel = rg.Relocaliser(g, scene, p, w.width, w.height, 1)
+    more = 0
+    for q in range(3):
+        d, c, T, seed = w.query(q)
+        d = workloads.corrupt(d, "missing", level, 10000 + q)
+        gr = rel.relocalise(d, c, w.K, seed)
+        lv = oracle.forest_leaves(f, d, c, w.K.fx, n_trees=p["n_trees_used"])
+        orr = H.OracleRun(p, d, c, w.K, lv, modes, room.lo, room.hi, seed, 1 << w.forest["depth"])
+        H.compare_results(rg, gr, rel.debug(0), orr, p, f"redraw missing {level} q{q}")
+        r8 = oracle.relocalise(dict(p, redraw=0), d, c, w.K, lv, modes, room.lo, room.hi, seed,
+                               1 << w.forest["depth"])
+        more += gr["n_hypotheses"] > 2 * max(1, r8["n_hypotheses"])
+    assert more >= 2
+    rel.close()
+    scene.close()
+    g.close()
