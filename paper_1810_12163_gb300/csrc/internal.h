@@ -196,8 +196,6 @@ struct QueryState {
     float4 *tab1;            // [B][max_pix][mpad] U01 U02 U11 U12
     float *tab2;             // [B][max_pix][mpad] U22
     int16_t *tab_cnt;        // [B][max_pix] |M(u)| (0 for a skipped draw)
-    float2 *tab_lm;          // [B][max_pix] per row: max over its modes of the Frobenius
-                             // norm of U (1 without covariances), max |mu|
     float4 *lm_anc;          // [B][n_cull][max_pix] LM nearest-mode anchors: y, slack^2 with
                              // the nearest mode in its low 8 bits
     int32_t *n_pix;          // [B]

@@ -275,7 +275,6 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
     uint16_t *s_list = (uint16_t *)(smem + L.list);           // [LMC_LIST] local pixel << 6 | list entry
     int16_t *s_res = (int16_t *)(smem + L.list) + LMC_LIST;   // [LMC_LIST] nearest mode of the entry
     int *s_nl = (int *)(smem + L.flag) + 1;                   // two list counters, by tile parity
-    const float2 *g_lm = a.q.tab_lm + row0;
     float4 *g_anc = a.q.lm_anc + (size_t)b * cstride;
     // squared distance (Eq. 5 form) of y to the record m of a row
     auto q_at = [&](const float4 *r0, const float4 *r1, const float *r2, int m, float y0, float y1, float y2) {
@@ -324,19 +323,32 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
         }
         cw[ci] = (int16_t)best_m;  // local mode index in the row, -1: none
     };
-    // Anchor of pair ci (pixel row i) from a full search at y: nearest and
-    // second-nearest squared distances and the nearest mode.
-    auto anchor = [&](int i, size_t ci, float y0, float y1, float y2, float best, float second, int best_m) {
+    // Running maxima over a row's modes for the anchor's bound: |U|_F^2 and
+    // |mu|^2 of record m.
+    auto row_maxima = [&](const float4 *r0, const float4 *r1, const float *r2, int m, float &fro2, float &mu2) {
+        const float4 m0 = r0[m];
+        mu2 = fmaxf(mu2, fmaf(m0.x, m0.x, fmaf(m0.y, m0.y, m0.z * m0.z)));
+        if (cov) {
+            const float4 m1 = r1[m];
+            const float u22 = r2[m];
+            fro2 = fmaxf(fro2, fmaf(m0.w, m0.w, fmaf(m1.x, m1.x, fmaf(m1.y, m1.y, fmaf(m1.z, m1.z,
+                                                                             fmaf(m1.w, m1.w, u22 * u22))))));
+        }
+    };
+    // Anchor of pair ci from a full search at y: nearest and second-nearest
+    // squared distances, the nearest mode, and over the row's modes the
+    // largest squared Frobenius norm of U and the largest |mu|^2.
+    auto anchor = [&](size_t ci, float y0, float y1, float y2, float best, float second, int best_m, float fro2,
+                      float mu2) {
         float slack2 = -1.f;
         if (best_m >= 0) {
             if (!(second < INFINITY)) {
                 slack2 = 0.25f;  // a single mode stays the nearest (bounded to 0.5 m)
             } else {
-                const float2 lm = g_lm[i];
-                const float Lf = (cov ? lm.x : 1.f) * 1.00001f;
+                const float Lf = (cov ? sqrtf(fro2) : 1.f) * 1.00001f;
                 const float db = sqrtf(best), d2 = sqrtf(second);
                 const float ny = sqrtf(fmaf(y0, y0, fmaf(y1, y1, y2 * y2)));
-                const float margin = 4e-6f * (Lf * (ny + 0.5f + lm.y) + d2 + 1.f);
+                const float margin = 4e-6f * (Lf * (ny + 0.5f + sqrtf(mu2)) + d2 + 1.f);
                 const float sl = fminf(0.5f, (d2 - db - margin) / (2.f * Lf));
                 if (sl > 0.f) slack2 = sl * sl * 0.99999f;
             }
@@ -353,7 +365,7 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
     auto search = [&](bool on, const float4 *r0, const float4 *r1, const float *r2, int cnt, int i, size_t ci,
                       float y0, float y1, float y2) {
         const int sub = t % LMC_SB;
-        float best = INFINITY, second = INFINITY;
+        float best = INFINITY, second = INFINITY, fro2 = 0.f, mu2 = 0.f;
         int best_m = -1;
         for (int m = sub; m < cnt; m += LMC_SB) {
             const float qm = q_at(r0, r1, r2, m, y0, y1, y2);
@@ -364,6 +376,7 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
             } else {
                 second = fminf(second, qm);
             }
+            row_maxima(r0, r1, r2, m, fro2, mu2);
         }
 #pragma unroll
         for (int off = 1; off < LMC_SB; off <<= 1) {
@@ -377,10 +390,12 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
             } else {
                 second = fminf(second, fminf(ob, os));
             }
+            fro2 = fmaxf(fro2, __shfl_xor_sync(0xffffffffu, fro2, off));
+            mu2 = fmaxf(mu2, __shfl_xor_sync(0xffffffffu, mu2, off));
         }
         if (on && sub == 0) {
             w_evals += cnt;
-            anchor(i, ci, y0, y1, y2, best, second, best_m);
+            anchor(ci, y0, y1, y2, best, second, best_m, fro2, mu2);
         }
         return best_m;
     };
@@ -420,7 +435,10 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
             y2 = fmaf(r20, x.x, fmaf(r21, x.y, fmaf(r22, x.z, tz)));
         }
         float best = INFINITY, second = INFINITY;  // second: for the anchor (direct passes follow)
+        float fro2 = 0.f, mu2 = 0.f;
         int best_m = -1;
+        if (rec)
+            for (int m = sub; m < cnt; m += S) row_maxima(s_t0 + base, s_t1 + base, s_t2 + base, m, fro2, mu2);
         if (cov) {
             auto d2of = [&](int m) {
                 const float4 m0 = s_t0[base + m], m1 = s_t1[base + m];
@@ -469,10 +487,12 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
             } else {
                 second = fminf(second, fminf(ob, os));
             }
+            fro2 = fmaxf(fro2, __shfl_xor_sync(0xffffffffu, fro2, off));
+            mu2 = fmaxf(mu2, __shfl_xor_sync(0xffffffffu, mu2, off));
         }
         if (sub != 0 || !on) return;
         const size_t ci = (size_t)(i0 + il) * n + hl;
-        if (rec && cnt > 0) anchor(i0 + il, ci, y0, y1, y2, best, second, best_m);
+        if (rec && cnt > 0) anchor(ci, y0, y1, y2, best, second, best_m, fro2, mu2);
         const int m_old = trial ? (int)cr[ci] : -1;
         if (cnt > 0) {
             ++w_pairs;

@@ -533,7 +533,6 @@ extern "C" rl_status rl_reloc_create(rl_forest *f, rl_scene *scene, const rl_ran
     A(tab1, B * MP * (uint64_t)rp.mpad);
     A(tab2, B * MP * (uint64_t)rp.mpad);
     A(tab_cnt, B * MP);
-    A(tab_lm, B * MP);
     A(lm_anc, B * NC * MP);
     A(n_pix, B);
     A(cur_pose, B * NC * 12);

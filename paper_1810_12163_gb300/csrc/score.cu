@@ -940,27 +940,18 @@ __global__ void k_build_table(QueryState q, int hw_max, ModeView mv, RParams p, 
     const float3 mp = mode_pos(mv, L, rank);
     const size_t me = (size_t)L * mv.m_max + rank;
     const size_t o = row * p.mpad + m;
-    float fro = 1.f;
     if (p.use_cov) {
         const float4 u0 = mv.mU[2 * me], u1 = mv.mU[2 * me + 1];
         q.tab0[o] = make_float4(mp.x, mp.y, mp.z, u0.x);
         q.tab1[o] = make_float4(u0.y, u0.z, u0.w, u1.x);
         q.tab2[o] = u1.y;
-        fro = sqrtf(u0.x * u0.x + u0.y * u0.y + u0.z * u0.z + u0.w * u0.w + u1.x * u1.x + u1.y * u1.y);
     } else {
         q.tab0[o] = make_float4(mp.x, mp.y, mp.z, 1.f);
     }
-    // row maxima for the LM's nearest-mode bounds (non-negative floats order
-    // as their bit patterns; the row was zeroed before this launch)
-    const float mu = sqrtf(mp.x * mp.x + mp.y * mp.y + mp.z * mp.z);
-    atomicMax((int *)&q.tab_lm[row].x, __float_as_int(fro));
-    atomicMax((int *)&q.tab_lm[row].y, __float_as_int(mu));
 }
 
 rl_status launch_build_table(const QueryState &q, int hw_max, ModeView mv, const RParams &p, int batch,
                              int n, cudaStream_t s) {
-    RL_CK(cudaMemset2DAsync(q.tab_lm + (size_t)batch * p.eta, sizeof(float2) * p.max_pix, 0,
-                            sizeof(float2) * p.eta, n, s));
     dim3 grid((p.eta * p.mpad + 255) / 256, n);
     k_build_table<<<grid, 256, 0, s>>>(q, hw_max, mv, p, batch);
     RL_LAUNCH_CK();
