@@ -41,7 +41,21 @@ struct Draw {
 // With p.redraw (reading R8b) a pixel that `usable` rejects (no depth or an
 // empty M(u)) is redrawn within the iteration, up to batch_attempts draws in
 // all: draw at >= 1 of pixel i takes word 0 of the Philox block with counter
-// (slot, TAG_REDRAW << 16 | level, it, 4 at + i).
+// (slot, TAG_REDRAW << 16 | level, it, 4 at + i).  Kept out of line: the
+// default reading never calls it.
+template <class Usable>
+__device__ __noinline__ int3 redraw_pixels(const HypArgs &a, const Frame &fr, int slot, int it, Usable usable,
+                                           int3 pix) {
+    const uint32_t WH = (uint32_t)(fr.W * fr.H);
+    const uint32_t ctr2 = (TAG_REDRAW << 16) | (uint32_t)a.p.level;
+    auto fix = [&](int q, int i) {
+        for (int at = 1; at < a.p.batch_attempts && !usable(q); ++at)
+            q = (int)draw_below(philox(make_uint4(slot, ctr2, it, 4u * at + i), fr.key0, fr.key1).x, WH);
+        return q;
+    };
+    return make_int3(fix(pix.x, 0), fix(pix.y, 1), fix(pix.z, 2));
+}
+
 template <class Usable>
 __device__ __forceinline__ Draw draw(const HypArgs &a, const Frame &fr, int slot, int it, Usable usable) {
     const uint32_t ctr1 = (TAG_HYP << 16) | (uint32_t)a.p.level;
@@ -53,10 +67,10 @@ __device__ __forceinline__ Draw draw(const HypArgs &a, const Frame &fr, int slot
     d.pix[2] = (int)draw_below(r0.z, WH);
     d.j = (int)draw_below(r0.w, 3);
     if (a.p.redraw) {
-        const uint32_t ctr2 = (TAG_REDRAW << 16) | (uint32_t)a.p.level;
-        for (int i = 0; i < 3; ++i)
-            for (int at = 1; at < a.p.batch_attempts && !usable(d.pix[i]); ++at)
-                d.pix[i] = (int)draw_below(philox(make_uint4(slot, ctr2, it, 4u * at + i), fr.key0, fr.key1).x, WH);
+        const int3 q = redraw_pixels(a, fr, slot, it, usable, make_int3(d.pix[0], d.pix[1], d.pix[2]));
+        d.pix[0] = q.x;
+        d.pix[1] = q.y;
+        d.pix[2] = q.z;
     }
     return d;
 }

@@ -44,6 +44,7 @@ struct SelectArgs {
     QueryState q;
     RParams p;
     int n_pix;                   // |I| after this phase
+    int energy_from_lm;          // rounds: the LM kernel left each survivor's energy in q.cur_energy
 };
 
 struct LmArgs {
@@ -71,6 +72,9 @@ rl_status prepare_kernels();
 constexpr size_t kLmClusterSmemMax = 200 * 1024;
 size_t lm_cluster_smem(int mpad, bool cov);
 rl_status launch_lm_cluster(const LmArgs &a, int n, cudaStream_t s);
+// True when a round's LM runs in the cluster kernel (which also leaves each
+// refined pose's Eq. 5 energy in q.cur_energy).
+bool lm_uses_cluster(const RParams &p);
 rl_status prepare_lm_cluster();
 
 // Ranking raycast tiles: 256 threads x RC_PIX pixels; one partial record

@@ -57,8 +57,8 @@ constexpr int LMC_THREADS = 256;
 constexpr int LMC_P = 16;        // pixels per tile (max_pix is a multiple)
 constexpr int LMC_STAGES = 2;
 constexpr int LMC_HMAX = 64;
-constexpr int LMC_NV = 30;       // 21 J^T J + 6 J^T r + cost, inlier count, trial cost
-constexpr int LMC_PS = 31;       // odd stride of the per-thread partials (no bank conflicts)
+constexpr int LMC_NV = 31;       // 21 J^T J + 6 J^T r + cost, inlier count, trial cost, Eq. 5 energy
+constexpr int LMC_PS = 33;       // odd stride of the per-thread partials (no bank conflicts)
 constexpr uint32_t kWaitLimit = kLmWaitLimit;
 constexpr int LMC_KP = 4;                       // pixels of a thread per tile (staged) or chunk (direct)
 constexpr int LMC_LIST = LMC_THREADS * LMC_KP;  // full-search list capacity of a tile or chunk
@@ -147,6 +147,7 @@ struct LmcPass {
     float acc[28];
     int nin;
     float trial;
+    float energy;  // Eq. 5 at the pass's pose: sum over the pixels of the nearest mode's distance
 };
 
 template <int CTAS>
@@ -296,6 +297,7 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
         const int m_old = trial ? (int)cr[ci] : -1;
         int best_m = bm;
         if (bm >= 0) {
+            o.energy += sqrtf(q_at(r0, r1, r2, bm, y0, y1, y2));
             const float4 m0 = r0[bm];
             const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
             if (fmaf(v0, v0, fmaf(v1, v1, v2 * v2)) <= thr2) {
@@ -498,6 +500,7 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
             ++w_pairs;
             w_modes += cnt;
             w_evals += cnt;
+            o.energy += sqrtf(best);
             if (best_m >= 0) {
                 const float4 m0 = s_t0[base + best_m];
                 const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
@@ -544,6 +547,7 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
         for (int k = 0; k < 28; ++k) o.acc[k] = 0.f;
         o.nin = 0;
         o.trial = 0.f;
+        o.energy = 0.f;
         float r00 = 0.f, r01 = 0.f, r02 = 0.f, tx = 0.f, r10 = 0.f, r11 = 0.f, r12 = 0.f, ty = 0.f;
         float r20 = 0.f, r21 = 0.f, r22 = 0.f, tz = 0.f;
         if (act) {
@@ -721,6 +725,7 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
                                 if (da < best) { best = da; best_m = m; }
                             }
                         }
+                        o.energy += sqrtf(best);
                         if (best_m >= 0) {
                             const float4 m0 = s_t0[base + best_m];
                             const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
@@ -769,6 +774,7 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
         for (int k = 0; k < 28; ++k) mypart[k] = o.acc[k];
         mypart[28] = (float)o.nin;
         mypart[29] = o.trial;
+        mypart[30] = o.energy;
         __syncthreads();
         float *loc = s_loc + lb * (LMC_HMAX * LMC_NV);
         for (int e = t; e < k_act * LMC_NV; e += LMC_THREADS) {
@@ -866,6 +872,7 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
             if (s_new[h][29] < s_tot[h][27]) {
                 for (int i = 0; i < 12; ++i) s_H[h][i] = s_Hn[h][i];
                 for (int k = 0; k < 29; ++k) s_tot[h][k] = s_new[h][k];
+                s_tot[h][30] = s_new[h][30];  // the energy at the accepted pose
                 s_cbuf[h] ^= 1;
                 s_lambda[h] /= 10.0;
             } else {
@@ -875,9 +882,13 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
         __syncthreads();
     }
     __syncthreads();  // the last accept/reject updates of s_H before other threads write them out
-    if (crank == 0)
+    if (crank == 0) {
         for (int i = t; i < n * 12; i += LMC_THREADS)
             a.q.cur_pose[((size_t)b * NC + i / 12) * 12 + i % 12] = s_H[i / 12][i % 12];
+        // Eq. 5 over the round's pixel set at each refined pose, from the pass
+        // that evaluated that pose: the round needs no separate energy launch
+        for (int h = t; h < n; h += LMC_THREADS) a.q.cur_energy[(size_t)b * NC + h] = s_tot[h][30];
+    }
     if (a.work && (w_pairs | w_modes | w_in | w_trial | w_evals)) {
         atomicAdd(&a.work[W_LM_PAIRS], (unsigned long long)w_pairs);
         atomicAdd(&a.work[W_LM_MODES], (unsigned long long)w_modes);

@@ -223,19 +223,26 @@ rl_status run_relocalise(rl_reloc *r, int n, int level, cudaStream_t s) {
         const int n_pix = p.eta * (round + 2);
         { PROF(K_SAMPLE); RL_TRY(launch_sample_batch(q.frames, q.mcount, hw_max, p, round + 1, q.pix, q.xc, n, s));
           RL_TRY(launch_build_table(q, hw_max, mv, p, round + 1, n, s)); }
-        if (p.pose_update && p.lm_max_iter > 0) {
+        const bool lm = p.pose_update && p.lm_max_iter > 0;
+        if (lm) {
             LmArgs la{q, q.leaves, hw_max, mv, p, n_pix, work, maxm, maxm | 1, r->lm_wait_limit};
             PROF(K_LM);
             RL_TRY(launch_lm(la, n, s));
         }
-        ea.pose = q.cur_pose;
-        ea.pose_stride = NC;
-        ea.idx = nullptr;
-        ea.idx_stride = 0;
-        ea.count = q.n_cur;
-        ea.n_pix = n_pix;
-        ea.round_gate = 1;
-        { PROF(K_ENERGY); RL_TRY(launch_energy(ea, NC, n, s, r->tune.energy_threads)); }
+        // the cluster LM kernel leaves each refined pose's energy on the
+        // round's pixel set; otherwise the energies are computed here
+        sa.energy_from_lm = lm && lm_uses_cluster(p);
+        if (!sa.energy_from_lm) {
+            ea.pose = q.cur_pose;
+            ea.pose_stride = NC;
+            ea.idx = nullptr;
+            ea.idx_stride = 0;
+            ea.count = q.n_cur;
+            ea.n_pix = n_pix;
+            ea.round_gate = 1;
+            PROF(K_ENERGY);
+            RL_TRY(launch_energy(ea, NC, n, s, r->tune.energy_threads));
+        }
         sa.phase = 1;
         sa.round = round;
         sa.count = q.n_cur;

@@ -184,9 +184,13 @@ __global__ void __launch_bounds__(1024) k_select(SelectArgs a) {
     if (a.phase == 1 && !round_active(n, a.p)) return;
     const int N = a.p.n_hyp, NC = a.p.n_cull;
     for (int i = tid; i < n; i += blockDim.x) {
-        const float *pp = a.part + ((size_t)b * a.part_h + i) * a.n_chunks;
         float e = 0.f;
-        for (int c = 0; c < a.n_chunks_used; ++c) e += pp[c];
+        if (a.phase == 1 && a.energy_from_lm) {
+            e = a.q.cur_energy[(size_t)b * NC + i];
+        } else {
+            const float *pp = a.part + ((size_t)b * a.part_h + i) * a.n_chunks;
+            for (int c = 0; c < a.n_chunks_used; ++c) e += pp[c];
+        }
         if (isnan(e)) e = INFINITY;
         sE[i] = e;
         sS[i] = a.phase == 0 ? a.hyp_list[(size_t)b * N + i] : a.q.cur_slot[(size_t)b * NC + i];
@@ -1261,9 +1265,13 @@ rl_status launch_select(const SelectArgs &a, int n, cudaStream_t s) {
     return RL_OK;
 }
 
+bool lm_uses_cluster(const RParams &p) {
+    return p.n_cull <= 64 && lm_cluster_smem(p.mpad, p.use_cov) <= kLmClusterSmemMax;
+}
+
 rl_status launch_lm(const LmArgs &a, int n, cudaStream_t s) {
     const size_t sm = lm_tiled_smem(a.p.mpad);
-    if (a.p.n_cull <= 64 && lm_cluster_smem(a.p.mpad, a.p.use_cov) <= kLmClusterSmemMax) {
+    if (lm_uses_cluster(a.p)) {
         return launch_lm_cluster(a, n, s);
     } else if (a.p.n_cull <= 64) {
         dim3 grid(LM3_BPQ, n);
