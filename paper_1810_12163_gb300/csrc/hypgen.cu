@@ -38,10 +38,12 @@ struct CheckThr {
 // relative) and are re-evaluated in FP64 whenever the FP32 value lies within
 // 2e-5 relative of the threshold, so each decision equals the FP64 decision
 // while the narrow FP64 pipe is almost never used.
+template <int REDRAW>
 __device__ __forceinline__ bool stage1(const HypArgs &a, const Frame &fr, const uint16_t *lv,
                                        const uint16_t *mc, const uint4 *pr, int slot, int it,
                                        Draw &d) {
-    d = draw(a, fr, slot, it, [&](int q) { return mc[q] != 0; });
+    auto usable = [&](int q) { return mc[q] != 0; };
+    d = draw<decltype(usable), REDRAW>(a, fr, slot, it, usable);
     const int c0 = mc[d.pix[0]], c1 = mc[d.pix[1]], c2 = mc[d.pix[2]];
     if (c0 == 0 || c1 == 0 || c2 == 0) return false;
     const uint32_t ctr1 = (TAG_HYP << 16) | (uint32_t)a.p.level;
@@ -81,11 +83,12 @@ __device__ __forceinline__ bool mask_decide(const uint2 w0, const uint2 w1, cons
     return (bits & 1u) != 0;
 }
 
+template <int REDRAW>
 __device__ __forceinline__ void stage1_mask2(const HypArgs &a, const Frame &fr, const uint2 *cm, int slot,
                                              int itA, int itB, Draw &dA, Draw &dB, bool &sA, bool &sB) {
     auto usable = [&](int q) { return (cm[q].y >> 24) != 0; };
-    dA = draw(a, fr, slot, itA, usable);
-    dB = draw(a, fr, slot, itB, usable);
+    dA = draw<decltype(usable), REDRAW>(a, fr, slot, itA, usable);
+    dB = draw<decltype(usable), REDRAW>(a, fr, slot, itB, usable);
     const uint2 a0 = cm[dA.pix[0]], a1 = cm[dA.pix[1]], a2 = cm[dA.pix[2]];
     const uint2 b0 = cm[dB.pix[0]], b1 = cm[dB.pix[1]], b2 = cm[dB.pix[2]];
     const uint32_t ctr1 = (TAG_HYP << 16) | (uint32_t)a.p.level;
@@ -102,12 +105,13 @@ __device__ __forceinline__ void stage1_mask2(const HypArgs &a, const Frame &fr, 
 // in stage 2.  The decision is the same as mask_decide's.
 __device__ __forceinline__ bool bit_set(const uint32_t *bits, int p) { return (bits[p >> 5] >> (p & 31)) & 1u; }
 
+template <int REDRAW>
 __device__ __forceinline__ void stage1_bits2(const HypArgs &a, const Frame &fr, const uint2 *cm,
                                              const uint32_t *s_bits, int slot, int itA, int itB, Draw &dA,
                                              Draw &dB, bool &sA, bool &sB) {
     auto usable = [&](int q) { return bit_set(s_bits, q); };
-    dA = draw(a, fr, slot, itA, usable);
-    dB = draw(a, fr, slot, itB, usable);
+    dA = draw<decltype(usable), REDRAW>(a, fr, slot, itA, usable);
+    dB = draw<decltype(usable), REDRAW>(a, fr, slot, itB, usable);
     const int pjA = dA.j == 0 ? dA.pix[0] : (dA.j == 1 ? dA.pix[1] : dA.pix[2]);
     const int pjB = dB.j == 0 ? dB.pix[0] : (dB.j == 1 ? dB.pix[1] : dB.pix[2]);
     const uint2 wA = cm[pjA], wB = cm[pjB];
@@ -172,7 +176,7 @@ __device__ __forceinline__ bool stage2(const HypArgs &a, const CheckThr &ct, con
 constexpr int HG_RING = 128;  // < 32 pending after a drain + 64 appended
 
 // WARPS slots per block; registers stay capped at 64 (32 warps per SM).
-template <int WARPS>
+template <int WARPS, int REDRAW>
 __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_hypgen(HypArgs a) {
     constexpr int HG_WARPS = WARPS;
     __shared__ int4 s_ring[HG_WARPS][HG_RING];   // it | j << 30, pixels of the triple
@@ -265,15 +269,15 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_hypgen(HypArgs a) {
             bool sA, sB;
             const int itA = base + lane, itB = base + 32 + lane;
             if (use_bits)
-                stage1_bits2(a, fr, cm, s_bits, slot, itA, itB, dA, dB, sA, sB);
+                stage1_bits2<REDRAW>(a, fr, cm, s_bits, slot, itA, itB, dA, dB, sA, sB);
             else
-                stage1_mask2(a, fr, cm, slot, itA, itB, dA, dB, sA, sB);
+                stage1_mask2<REDRAW>(a, fr, cm, slot, itA, itB, dA, dB, sA, sB);
             append(sA && itA < a.p.max_iter, itA, dA);
             append(sB && itB < a.p.max_iter, itB, dB);
         } else {
             const int it = base + lane;
             Draw d;
-            const bool s1 = it < a.p.max_iter && stage1(a, fr, lv, mc, pr, slot, it, d);
+            const bool s1 = it < a.p.max_iter && stage1<REDRAW>(a, fr, lv, mc, pr, slot, it, d);
             append(s1, it, d);
         }
         n_att += (unsigned)min(step, a.p.max_iter - base);
@@ -402,6 +406,17 @@ __global__ void k_sample_batch(const Frame *__restrict__ frames, const uint16_t 
     xc_out[o] = x;
 }
 
+template <int REDRAW>
+static void launch_hypgen_shape(const HypArgs &a, int warps, int n, size_t sm, cudaStream_t s) {
+    const int N = a.p.n_hyp;
+    switch (warps) {
+    case 2: k_hypgen<2, REDRAW><<<dim3((N + 1) / 2, n), 64, sm, s>>>(a); break;
+    case 8: k_hypgen<8, REDRAW><<<dim3((N + 7) / 8, n), 256, sm, s>>>(a); break;
+    case 16: k_hypgen<16, REDRAW><<<dim3((N + 15) / 16, n), 512, sm, s>>>(a); break;
+    default: k_hypgen<4, REDRAW><<<dim3((N + 3) / 4, n), 128, sm, s>>>(a); break;
+    }
+}
+
 rl_status launch_hypgen(const Frame *frames, const uint16_t *leaves, const uint16_t *mcount,
                         const uint4 *prec, const uint2 *pcm, const uint32_t *pbits, int hw_max, ModeView mv,
                         const RParams &p, double *hyp_pose, int32_t *hyp_iter, unsigned long long *work, int n,
@@ -411,22 +426,27 @@ rl_status launch_hypgen(const Frame *frames, const uint16_t *leaves, const uint1
     const bool bits = pcm && pbits && bits_smem <= kHypBitsSmemMax;
     HypArgs a{frames, leaves, mcount, prec, pcm, hw_max, mv, p, hyp_pose, hyp_iter, work, bits ? pbits : nullptr};
     const size_t sm = bits ? bits_smem : 0;
-    switch (warps) {
-    case 2: k_hypgen<2><<<dim3((p.n_hyp + 1) / 2, n), 64, sm, s>>>(a); break;
-    case 8: k_hypgen<8><<<dim3((p.n_hyp + 7) / 8, n), 256, sm, s>>>(a); break;
-    case 16: k_hypgen<16><<<dim3((p.n_hyp + 15) / 16, n), 512, sm, s>>>(a); break;
-    default: k_hypgen<4><<<dim3((p.n_hyp + 3) / 4, n), 128, sm, s>>>(a); break;
-    }
+    if (p.redraw)
+        launch_hypgen_shape<1>(a, warps, n, sm, s);
+    else
+        launch_hypgen_shape<0>(a, warps, n, sm, s);
     RL_LAUNCH_CK();
     return RL_OK;
 }
 
-rl_status prepare_hypgen() {
-    RL_CK(cudaFuncSetAttribute(k_hypgen<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHypBitsSmemMax));
-    RL_CK(cudaFuncSetAttribute(k_hypgen<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHypBitsSmemMax));
-    RL_CK(cudaFuncSetAttribute(k_hypgen<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHypBitsSmemMax));
-    RL_CK(cudaFuncSetAttribute(k_hypgen<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHypBitsSmemMax));
+template <int REDRAW>
+static rl_status prepare_hypgen_reading() {
+    const int sm = (int)kHypBitsSmemMax;
+    RL_CK(cudaFuncSetAttribute(k_hypgen<2, REDRAW>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    RL_CK(cudaFuncSetAttribute(k_hypgen<4, REDRAW>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    RL_CK(cudaFuncSetAttribute(k_hypgen<8, REDRAW>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    RL_CK(cudaFuncSetAttribute(k_hypgen<16, REDRAW>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
     return RL_OK;
+}
+
+rl_status prepare_hypgen() {
+    RL_TRY(prepare_hypgen_reading<0>());
+    return prepare_hypgen_reading<1>();
 }
 
 rl_status launch_compact(const int32_t *hyp_iter, int N, int32_t *hyp_list, int32_t *n_hyp, int n,

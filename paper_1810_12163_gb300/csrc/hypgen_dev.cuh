@@ -56,7 +56,7 @@ __device__ __noinline__ int3 redraw_pixels(const HypArgs &a, const Frame &fr, in
     return make_int3(fix(pix.x, 0), fix(pix.y, 1), fix(pix.z, 2));
 }
 
-template <class Usable>
+template <class Usable, int REDRAW = -1>
 __device__ __forceinline__ Draw draw(const HypArgs &a, const Frame &fr, int slot, int it, Usable usable) {
     const uint32_t ctr1 = (TAG_HYP << 16) | (uint32_t)a.p.level;
     const uint4 r0 = philox(make_uint4(slot, ctr1, it, 0), fr.key0, fr.key1);
@@ -66,7 +66,8 @@ __device__ __forceinline__ Draw draw(const HypArgs &a, const Frame &fr, int slot
     d.pix[1] = (int)draw_below(r0.y, WH);
     d.pix[2] = (int)draw_below(r0.z, WH);
     d.j = (int)draw_below(r0.w, 3);
-    if (a.p.redraw) {
+    // REDRAW: the reading fixed at compile time (0 or 1), or -1: a.p.redraw
+    if (REDRAW == 1 || (REDRAW < 0 && a.p.redraw)) {
         const int3 q = redraw_pixels(a, fr, slot, it, usable, make_int3(d.pix[0], d.pix[1], d.pix[2]));
         d.pix[0] = q.x;
         d.pix[1] = q.y;
