@@ -1046,6 +1046,36 @@ __global__ void __launch_bounds__(256) k_raycast_score(RaycastArgs a) {
             const float *P = sPf[k];
             float sum = 0.f;
             int syn = 0, both = 0;
+            // A camera more than 1 mm inside the box: every ray leaves the
+            // box exactly once, at the nearest exit plane; with t_ax = (bound
+            // - o) / d, bound = hi for d >= +0 and lo for d <= -0 (a zero
+            // component then gives +inf), the depth is min_ax t_ax, a
+            // continuous function of the ray with no hit/miss decision to
+            // certify.  Same value as the slab test below up to FP32 rounding.
+            // The approximate reciprocal (within 2 ulp) maps +-0 to +-inf.
+            const float ox = P[3], oy = P[7], oz = P[11];
+            const bool inside = ox - a.lo[0] > 1e-3f && a.hi[0] - ox > 1e-3f && oy - a.lo[1] > 1e-3f &&
+                                a.hi[1] - oy > 1e-3f && oz - a.lo[2] > 1e-3f && a.hi[2] - oz > 1e-3f;
+            if (inside) {
+                const float lx = a.lo[0] - ox, hx = a.hi[0] - ox, ly = a.lo[1] - oy, hy = a.hi[1] - oy;
+                const float lz = a.lo[2] - oz, hz = a.hi[2] - oz;
+#pragma unroll
+                for (int q = 0; q < RC_PIX; ++q) {
+                    if (!in[q]) continue;
+                    const float d0 = fmaf(P[0], dc0[q], fmaf(P[1], dc1[q], P[2]));
+                    const float d1 = fmaf(P[4], dc0[q], fmaf(P[5], dc1[q], P[6]));
+                    const float d2 = fmaf(P[8], dc0[q], fmaf(P[9], dc1[q], P[10]));
+                    const float t0 = (signbit(d0) ? lx : hx) * __fdividef(1.0f, d0);
+                    const float t1 = (signbit(d1) ? ly : hy) * __fdividef(1.0f, d1);
+                    const float t2 = (signbit(d2) ? lz : hz) * __fdividef(1.0f, d2);
+                    const float depth = fminf(t0, fminf(t1, t2));
+                    ++syn;
+                    if (dl[q] > 0.f) {
+                        ++both;
+                        sum += fabsf(dl[q] - depth);
+                    }
+                }
+            } else {
 #pragma unroll
             for (int q = 0; q < RC_PIX; ++q) {
                 if (!in[q]) continue;
@@ -1092,6 +1122,7 @@ __global__ void __launch_bounds__(256) k_raycast_score(RaycastArgs a) {
                         sum += fabsf(dl[q] - depth);
                     }
                 }
+            }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
