@@ -64,6 +64,7 @@ constexpr int LMC_KP = 4;                       // pixels of a thread per tile (
 constexpr int LMC_LIST = LMC_THREADS * LMC_KP;  // full-search list capacity of a tile or chunk
 constexpr int LMC_SB = 8;                       // lanes per full nearest-mode search
 constexpr int LMC_DIRECT = 8;                   // at most this many hypotheses: rows read from global memory
+constexpr int LMC_COOP = LMC_THREADS / 16;      // at most this many hypotheses: one half-warp per solve
 
 struct LmcLayout {
     uint32_t t0, t1, t2, xc, cnt, stage, tx;
@@ -149,6 +150,60 @@ struct LmcPass {
     float trial;
     float energy;  // Eq. 5 at the pass's pose: sum over the pixels of the nearest mode's distance
 };
+
+// The damped step of one hypothesis by one lane: T its sums (21 J^T J upper
+// triangle, 6 J^T r, cost, inlier count), the FP64 solve, and either the new
+// pose (Hn, FP32 copy Pf) or *state = 0 when the step stops it.  Both solve
+// variants stay out of line, so that their registers do not weigh on the
+// pixel passes.
+__device__ __noinline__ void lm_solve_lane(const float *T, double lambda, const double *H, double lm_stop,
+                                           int *state, double *Hn, float *Pf) {
+    bool stop = T[28] < 3.f;
+    double step[6];
+    if (!stop) {
+        double A[36], rhs[6];
+        int k = 0;
+        for (int r = 0; r < 6; ++r)
+            for (int c = r; c < 6; ++c, ++k) A[6 * r + c] = A[6 * c + r] = (double)T[k];
+        for (int r = 0; r < 6; ++r) {
+            A[6 * r + r] += lambda * (double)T[r * 6 - r * (r - 1) / 2];
+            rhs[r] = -(double)T[21 + r];
+        }
+        if (!chol_solve6(A, rhs, step)) {
+            stop = true;
+        } else {
+            double sn = 0.0;
+            for (int r = 0; r < 6; ++r) sn += step[r] * step[r];
+            stop = sqrt(sn) < lm_stop;
+        }
+    }
+    if (stop) {
+        *state = 0;
+    } else {
+        double N[12];
+        for (int i = 0; i < 12; ++i) N[i] = H[i];
+        se3_left(step, N);
+        for (int i = 0; i < 12; ++i) {
+            Hn[i] = N[i];
+            Pf[i] = (float)N[i];
+        }
+    }
+}
+
+// The same by the 16 lanes q of a half-warp (every lane of the warp calls
+// it); mine: the half-warp's hypothesis is still iterating.
+__device__ __noinline__ void lm_solve_half(const float *T, double lambda, const double *H, double lm_stop, int q,
+                                           bool mine, int *state, double *Hn, float *Pf) {
+    double Nq = 0.0;
+    const bool stop = lm_step_half(T, lambda, H, lm_stop, q, Nq) || T[28] < 3.f;
+    if (!mine) return;
+    if (stop) {
+        if (q == 0) *state = 0;
+    } else if (q < 12) {
+        Hn[q] = Nq;
+        Pf[q] = (float)Nq;
+    }
+}
 
 template <int CTAS>
 __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k_lm_cluster(LmArgs a) {
@@ -804,45 +859,21 @@ __global__ void __cluster_dims__(CTAS, 1, 1) __launch_bounds__(LMC_THREADS, 2) k
         reduce(o, 0, s_tot);
     }
     for (int it = 0; it < a.p.lm_max_iter; ++it) {
-        // damped FP64 solve; hypothesis h on lane h / 4 of warp h % 4.  Each
-        // SM sub-partition has its own narrow FP64 pipe, which a warp
-        // instruction holds for the same time whatever its active lanes: one
-        // warp on each of the four sub-partitions is the shortest schedule.
-        {
+        // damped FP64 solve.  Each SM sub-partition has its own narrow FP64
+        // pipe, which a warp instruction holds for the same time whatever its
+        // active lanes.  Up to LMC_COOP hypotheses: one per half-warp, its
+        // solve spread over the 16 lanes (at most two warps per
+        // sub-partition).  More: hypothesis h on lane h / 4 of warp h % 4,
+        // one warp on each sub-partition.
+        if (n <= LMC_COOP) {
+            const int h = t >> 4;
+            const bool mine = h < n && s_state[h];
+            if (__any_sync(0xffffffffu, mine))  // both half-warps take part in the shuffles
+                lm_solve_half(s_tot[h], s_lambda[h], s_H[h], a.p.lm_stop, t & 15, mine, s_state + h, s_Hn[h], s_Pf[h]);
+        } else {
             const int h = (t & 31) * 4 + (t >> 5);
-            if (t < 128 && (t & 31) < LMC_HMAX / 4 && h < n && s_state[h]) {
-                const float *T = s_tot[h];
-                bool stop = T[28] < 3.f;
-                double step[6];
-                if (!stop) {
-                    double A[36], rhs[6];
-                    int k = 0;
-                    for (int r = 0; r < 6; ++r)
-                        for (int c = r; c < 6; ++c, ++k) A[6 * r + c] = A[6 * c + r] = (double)T[k];
-                    for (int r = 0; r < 6; ++r) {
-                        A[6 * r + r] += s_lambda[h] * (double)T[r * 6 - r * (r - 1) / 2];
-                        rhs[r] = -(double)T[21 + r];
-                    }
-                    if (!chol_solve6(A, rhs, step)) {
-                        stop = true;
-                    } else {
-                        double sn = 0.0;
-                        for (int r = 0; r < 6; ++r) sn += step[r] * step[r];
-                        stop = sqrt(sn) < a.p.lm_stop;
-                    }
-                }
-                if (stop) {
-                    s_state[h] = 0;
-                } else {
-                    double Hn[12];
-                    for (int i = 0; i < 12; ++i) Hn[i] = s_H[h][i];
-                    se3_left(step, Hn);
-                    for (int i = 0; i < 12; ++i) {
-                        s_Hn[h][i] = Hn[i];
-                        s_Pf[h][i] = (float)Hn[i];
-                    }
-                }
-            }
+            if (t < 128 && (t & 31) < LMC_HMAX / 4 && h < n && s_state[h])
+                lm_solve_lane(s_tot[h], s_lambda[h], s_H[h], a.p.lm_stop, s_state + h, s_Hn[h], s_Pf[h]);
         }
         // The stop flags were just written by the solving threads: the
         // predicate below is evaluated before its barrier, so it must see them
