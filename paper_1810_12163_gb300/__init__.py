@@ -483,6 +483,7 @@ def tuning_cache_read(path: str, key: str):
 
 
 def tuning_cache_write(path: str, key: str, tuning: dict):
-    t = binding.Tuning(**tuning)
+    """Records tuning under key (streams defaults to 1)."""
+    t = binding.Tuning(**dict(dict(streams=1), **tuning))
     call("rl_tuning_cache_write", path.encode(), key.encode(), ctypes.byref(t))
 

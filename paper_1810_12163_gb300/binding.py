@@ -75,7 +75,8 @@ class ServerParams(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("hypgen_warps", ctypes.c_int32), ("energy_threads", ctypes.c_int32),
-                ("leaves_threads", ctypes.c_int32), ("mask_threads", ctypes.c_int32)]
+                ("leaves_threads", ctypes.c_int32), ("mask_threads", ctypes.c_int32),
+                ("streams", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):

@@ -293,7 +293,12 @@ struct rl_reloc {
     cudaStream_t capture_stream = nullptr;
     bool use_graphs = true;
     uint64_t calls = 0;
-    rl_tuning tune{16, 128, 128, 256};  // launch shapes (results do not depend on them)
+    rl_tuning tune{16, 128, 128, 256, 4};  // launch shapes (results do not depend on them)
+    // per array of q: byte offset of its pointer in QueryState and bytes per frame
+    std::vector<std::pair<size_t, size_t>> q_layout;
+    // sub-batches of a call (tune.streams): private streams and fork/join events
+    cudaStream_t side[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t fork_ev = nullptr, join_ev[3] = {nullptr, nullptr, nullptr};
     uint32_t lm_wait_limit = kLmWaitLimit;  // probes of the LM kernel's waits for staged tiles
     // streaming forests: recorded after the last launch that read mode store b
     cudaEvent_t read_done[2] = {nullptr, nullptr};
@@ -374,7 +379,11 @@ rl_status adapt_frame(rl_forest *f, const float *depth, const uint8_t *rgb,
 rl_status update_modes(rl_forest *f, int64_t begin, int64_t count, cudaStream_t s);
 rl_status reset_leaves(rl_forest *f, cudaStream_t s);
 ModeView mode_view(const rl_forest *f);
-rl_status run_relocalise(rl_reloc *r, int n, int level, cudaStream_t s);
+// The launch sequence of n frames whose query state is q (r->q, or a slice
+// of it for a sub-batch: query_slice).
+rl_status run_relocalise(rl_reloc *r, const QueryState &q, int n, int level, cudaStream_t s);
+// q for the frames b0, b0 + 1, ... of r's batch.
+QueryState query_slice(const rl_reloc *r, int b0);
 // Batch of n frames whose descriptors (device pointers, per-frame sizes and
 // intrinsics, keys) are given on the host: descriptors are copied and the
 // launch sequence is enqueued on s (graph replay when enabled).

@@ -4,7 +4,10 @@
 #include <math.h>
 #include <string.h>
 
+#include <stddef.h>
+
 #include <algorithm>
+#include <chrono>
 #include <memory>
 
 #include "kernels.h"
@@ -78,6 +81,14 @@ static void graphs_free(rl_reloc *r);
 static void reloc_release(rl_reloc *r) {
     prof_free(r);
     graphs_free(r);
+    for (int i = 0; i < 3; ++i) {
+        if (r->side[i]) cudaStreamDestroy(r->side[i]);
+        if (r->join_ev[i]) cudaEventDestroy(r->join_ev[i]);
+        r->side[i] = nullptr;
+        r->join_ev[i] = nullptr;
+    }
+    if (r->fork_ev) cudaEventDestroy(r->fork_ev);
+    r->fork_ev = nullptr;
     for (void *p : r->allocs) arena_free(r->forest->ctx, p);
     r->allocs.clear();
     if (r->host_frames) cudaFreeHost(r->host_frames);
@@ -152,11 +163,10 @@ static void prof_resolve(rl_reloc *r) {
 
 #define PROF(kid) ProfScope prof_scope_##kid##__LINE__(r, kid, s)
 
-rl_status run_relocalise(rl_reloc *r, int n, int level, cudaStream_t s) {
+rl_status run_relocalise(rl_reloc *r, const QueryState &q, int n, int level, cudaStream_t s) {
     rl_forest *f = r->forest;
     RParams p = r->rp;
     p.level = level;
-    QueryState &q = r->q;
     const int hw_max = r->max_w * r->max_h;
     const ModeView mv = mode_view(f);
     const int N = p.n_hyp, NC = p.n_cull;
@@ -331,6 +341,49 @@ struct ModeReadScope {
     }
 };
 
+QueryState query_slice(const rl_reloc *r, int b0) {
+    QueryState o = r->q;
+    for (const auto &e : r->q_layout) {
+        char *ptr;
+        memcpy(&ptr, (char *)&o + e.first, sizeof(ptr));
+        if (ptr) ptr += (size_t)b0 * e.second;
+        memcpy((char *)&o + e.first, &ptr, sizeof(ptr));
+    }
+    return o;
+}
+
+// Frames per sub-batch below which a call is not split.
+constexpr int kMinPart = 8;
+
+// The call's frames as tune.streams sub-batches on as many streams (the
+// caller's and private ones), forked from and joined back into s.  The
+// frames are independent, so each sub-batch computes what the whole batch
+// would for its frames; their kernels overlap wherever one sub-batch leaves
+// SMs idle (the tails of the preemptive rounds, whose launches last as long
+// as their slowest frame).  Inside a stream capture the fork and join bring
+// the private streams into the same graph.
+static rl_status run_relocalise_parts(rl_reloc *r, int n, int level, cudaStream_t s) {
+    const int parts = r->prof.on ? 1 : std::max(1, std::min(r->tune.streams, n / kMinPart));
+    if (parts <= 1) return run_relocalise(r, r->q, n, level, s);
+    for (int i = 0; i < parts - 1; ++i) {
+        if (!r->side[i]) RL_CK(cudaStreamCreateWithFlags(&r->side[i], cudaStreamNonBlocking));
+        if (!r->join_ev[i]) RL_CK(cudaEventCreateWithFlags(&r->join_ev[i], cudaEventDisableTiming));
+    }
+    if (!r->fork_ev) RL_CK(cudaEventCreateWithFlags(&r->fork_ev, cudaEventDisableTiming));
+    RL_CK(cudaEventRecord(r->fork_ev, s));
+    int b0 = 0;
+    for (int i = 0; i < parts; ++i) {
+        const int nb = n / parts + (i < n % parts ? 1 : 0);
+        cudaStream_t si = i == 0 ? s : r->side[i - 1];
+        if (i > 0) RL_CK(cudaStreamWaitEvent(si, r->fork_ev, 0));
+        RL_TRY(run_relocalise(r, query_slice(r, b0), nb, level, si));
+        if (i > 0) RL_CK(cudaEventRecord(r->join_ev[i - 1], si));
+        b0 += nb;
+    }
+    for (int i = 0; i < parts - 1; ++i) RL_CK(cudaStreamWaitEvent(s, r->join_ev[i], 0));
+    return RL_OK;
+}
+
 static rl_status launch_relocalise_snapshot(rl_reloc *r, int n, int level, int buf, cudaStream_t s);
 
 rl_status launch_relocalise(rl_reloc *r, int n, int level, cudaStream_t s) {
@@ -343,7 +396,7 @@ rl_status launch_relocalise(rl_reloc *r, int n, int level, cudaStream_t s) {
 
 static rl_status launch_relocalise_snapshot(rl_reloc *r, int n, int level, int buf, cudaStream_t s) {
     ++r->calls;
-    if (r->prof.on || !r->use_graphs) return run_relocalise(r, n, level, s);
+    if (r->prof.on || !r->use_graphs) return run_relocalise_parts(r, n, level, s);
     for (auto &g : r->graphs)
         if (g.n == n && g.level == level && g.buf == buf) {
             g.last_use = r->calls;
@@ -354,7 +407,7 @@ static rl_status launch_relocalise_snapshot(rl_reloc *r, int n, int level, int b
     // inputs staged on `s` must be visible to the captured work: the graph
     // is launched on `s`, so only the capture itself runs on the private stream
     RL_CK(cudaStreamBeginCapture(r->capture_stream, cudaStreamCaptureModeThreadLocal));
-    rl_status st = run_relocalise(r, n, level, r->capture_stream);
+    rl_status st = run_relocalise_parts(r, n, level, r->capture_stream);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(r->capture_stream, &g);
     if (st != RL_OK) {
@@ -524,7 +577,11 @@ extern "C" rl_status rl_reloc_create(rl_forest *f, rl_scene *scene, const rl_ran
     const uint64_t B = max_batch, N = p->n_hyp, NC = p->n_cull, MP = rp.max_pix;
     QueryState &q = r->q;
     rl_status s = RL_OK;
-#define A(field, count) if (s == RL_OK) s = ralloc(r, (uint64_t)(count), &q.field)
+#define A(field, count)                                                                            \
+    if (s == RL_OK) {                                                                              \
+        s = ralloc(r, (uint64_t)(count), &q.field);                                                \
+        r->q_layout.push_back({offsetof(QueryState, field), (size_t)((count) / B) * sizeof(*q.field)}); \
+    }
     A(leaves, B * p->n_trees_used * hw);
     A(mcount, B * hw);
     if (p->n_trees_used <= kRecTrees) A(prec, B * hw);
@@ -754,7 +811,7 @@ static rl_status cascade_enqueue(rl_cascade *c, int n, cudaStream_t s) {
                                                  r->stage_rgb, hw);
             RL_LAUNCH_CK();
         }
-        RL_TRY(run_relocalise(r, n, l, s));
+        RL_TRY(run_relocalise(r, r->q, n, l, s));
         LaterFrames later{};
         for (int k = l + 1; k < L && later.n < 8; ++k) later.f[later.n++] = c->levels[k]->q.frames;
         const float tau = l < L - 1 ? (float)c->thresholds[l] : INFINITY;
@@ -1240,7 +1297,8 @@ static bool one_of(int v, std::initializer_list<int> l) {
 
 static bool valid_tuning(const rl_tuning &t) {
     return one_of(t.hypgen_warps, {2, 4, 8, 16}) && one_of(t.energy_threads, {32, 64, 128, 256}) &&
-           one_of(t.leaves_threads, {64, 128, 256, 512}) && one_of(t.mask_threads, {64, 128, 256});
+           one_of(t.leaves_threads, {64, 128, 256, 512}) && one_of(t.mask_threads, {64, 128, 256}) &&
+           one_of(t.streams, {1, 2, 4});
 }
 
 static std::string trim(const std::string &x) {
@@ -1295,8 +1353,10 @@ extern "C" rl_status rl_tuning_cache_read(const char *path, const char *key, rl_
         const size_t eq = l.find('=');
         if (eq == std::string::npos || trim(l.substr(0, eq)) != key) continue;
         rl_tuning t{};
-        if (sscanf(l.c_str() + eq + 1, "%d %d %d %d", &t.hypgen_warps, &t.energy_threads, &t.leaves_threads,
-                   &t.mask_threads) == 4 && valid_tuning(t)) {
+        t.streams = 1;  // entries written before the streams knob hold four values
+        const int got = sscanf(l.c_str() + eq + 1, "%d %d %d %d %d", &t.hypgen_warps, &t.energy_threads,
+                               &t.leaves_threads, &t.mask_threads, &t.streams);
+        if ((got == 4 || got == 5) && valid_tuning(t)) {
             *out = t;
             *found = 1;
         }
@@ -1320,8 +1380,8 @@ extern "C" rl_status rl_tuning_cache_write(const char *path, const char *key, co
         fclose(fp);
     }
     char entry[1100];
-    snprintf(entry, sizeof(entry), "%s = %d %d %d %d", key, t->hypgen_warps, t->energy_threads,
-             t->leaves_threads, t->mask_threads);
+    snprintf(entry, sizeof(entry), "%s = %d %d %d %d %d", key, t->hypgen_warps, t->energy_threads,
+             t->leaves_threads, t->mask_threads, t->streams);
     lines.push_back(entry);
     const std::string tmp = std::string(path) + ".tmp";
     FILE *fp = fopen(tmp.c_str(), "w");
@@ -1387,6 +1447,33 @@ extern "C" rl_status rl_reloc_autotune(rl_reloc *r, int32_t n, const float *dept
         t.*k.field = best_ms < 0.98 * cur_ms ? best : t.*k.field;
     }
     rl_reloc_profile(r, was_on ? 1 : 0);
+    // sub-batches: whole calls on the captured-graph path, timed on the host
+    // (per-kernel times cannot see kernels of different streams overlap)
+    if (st == RL_OK && !was_on && r->use_graphs && n >= 2 * kMinPart) {
+        int best = t.streams;
+        double best_ms = INFINITY, cur_ms = INFINITY;
+        for (int v : {1, 2, 4}) {
+            if (v > 1 && n / kMinPart < v) break;  // would run as fewer sub-batches
+            rl_tuning c = t;
+            c.streams = v;
+            if ((st = rl_reloc_set_tuning(r, &c)) != RL_OK) break;  // drops the captured graphs
+            if ((st = rl_relocalise_batch(r, n, depth, rgb, K, seeds, mem, stream, res.data())) != RL_OK) break;
+            double ms = INFINITY;
+            for (int rep = 0; rep < 3 && st == RL_OK; ++rep) {
+                const auto t0 = std::chrono::steady_clock::now();
+                st = rl_relocalise_batch(r, n, depth, rgb, K, seeds, mem, stream, res.data());
+                ms = std::min(ms, std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                                      .count());
+            }
+            if (st != RL_OK) break;
+            if (v == t.streams) cur_ms = ms;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = v;
+            }
+        }
+        if (st == RL_OK) t.streams = best_ms < 0.98 * cur_ms ? best : t.streams;
+    }
     if (st != RL_OK) {
         r->tune = t;
         return st;

@@ -40,8 +40,8 @@ def test_tuning_never_changes_results(setup, tmp_path):
     rel = rg.Relocaliser(g, scene, w.ransac, w.width, w.height, 4)
     qs = [w.query(q) for q in range(4)]
     base = _run(rel, qs, w)
-    for t in (dict(hypgen_warps=2, energy_threads=32, leaves_threads=64, mask_threads=64),
-              dict(hypgen_warps=8, energy_threads=256, leaves_threads=512, mask_threads=256)):
+    for t in (dict(hypgen_warps=2, energy_threads=32, leaves_threads=64, mask_threads=64, streams=1),
+              dict(hypgen_warps=8, energy_threads=256, leaves_threads=512, mask_threads=256, streams=4)):
         rel.set_tuning(t)
         assert rel.tuning == t
         _same(_run(rel, qs, w), base)
@@ -55,12 +55,33 @@ def test_tuning_never_changes_results(setup, tmp_path):
     rel2 = rg.Relocaliser(g, scene, w.ransac, w.width, w.height, 4)
     assert rel2.tuning_key() == rel.tuning_key()
     rg.tuning_cache_write(cache, rel2.tuning_key(), dict(hypgen_warps=2, energy_threads=64,
-                                                         leaves_threads=256, mask_threads=128))
+                                                         leaves_threads=256, mask_threads=128, streams=2))
     got = rel2.autotune(np.stack([q[0] for q in qs]), np.stack([q[1] for q in qs]), w.K,
                         [q[3] for q in qs], cache_path=cache)
-    assert got == dict(hypgen_warps=2, energy_threads=64, leaves_threads=256, mask_threads=128)
+    assert got == dict(hypgen_warps=2, energy_threads=64, leaves_threads=256, mask_threads=128, streams=2)
     _same(_run(rel2, qs, w), base)
     with pytest.raises(rg.RelocError):
         rel.set_tuning(dict(hypgen_warps=5))
     rel.close()
     rel2.close()
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_sub_batches_on_streams_give_the_batch_results(setup, graphs):
+    """A call of 20 frames split into 2 sub-batches (streams 2, and streams 4,
+    which 20 frames cap at 2 of at least 8 frames) on concurrent streams, on
+    the captured-graph path and launched kernel by kernel: every frame's
+    result is bit-identical to the one-stream batch."""
+    rg, ctx, w, g, scene = setup
+    n = 20
+    rel = rg.Relocaliser(g, scene, w.ransac, w.width, w.height, n)
+    rel.set_graphs(graphs)
+    qs = [w.query(q % 6) for q in range(n)]
+    qs = [(d, c, T, 1000 + i) for i, (d, c, T, _) in enumerate(qs)]
+    base = _run(rel, qs, w)
+    assert sum(r["n_hypotheses"] > 0 for r in base) >= n // 2
+    for streams in (2, 4, 1):
+        rel.set_tuning(dict(streams=streams))
+        _same(_run(rel, qs, w), base)
+        _same(_run(rel, qs, w), base)  # the second call replays the captured graph
+    rel.close()
