@@ -616,6 +616,7 @@ def run_ours(args):
             step_ms.append(e0.elapsed_time(e1))
         torch.cuda.synchronize()
     total_s = sum(step_ms) / 1e3
+    graph_kernels = rel.graph_kernels(B)  # kernels each timed step replayed
     # a profiled pass of the same steps (same seeds, so the same work):
     # kernels launched one by one with CUDA events around each launch and
     # work counters on the device; the per-kernel rooflines come from it
@@ -700,7 +701,9 @@ def run_ours(args):
         "success_5cm_5deg": ok / B,
         "e2e": {"value": job_throughput(B * e2e_steps, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": int(sum(k["launches"] for k in kernels.values())),
+        "gpu_launches": int(graph_kernels * args.steps) if graph_kernels > 0 else None,
+        "gpu_launches_per_step": {"graph_kernel_nodes": graph_kernels,
+                                  "profiled_pass": int(sum(k["launches"] for k in kernels.values())) // args.steps},
         "timed_path": "CUDA graph replay (one graph per batch size); per-kernel figures from a "
                       "profiled pass of the same steps launched kernel by kernel",
         "profiled_pass_ms_per_step": float(np.mean(prof_ms)),

@@ -345,6 +345,10 @@ rl_status rl_reloc_fetch(rl_reloc *r, int32_t n, void *stream, rl_result *out);
  * of a given batch size performs the capture and must not itself run under
  * the caller's stream capture. */
 rl_status rl_reloc_set_graphs(rl_reloc *r, int32_t enable);
+/* Kernel launches in the captured graph of an n-frame call at level 0 (all
+ * its sub-batches), in *out; -1 when no such graph is captured (yet, or
+ * graphs are off).  A call replaying it launches exactly these kernels. */
+rl_status rl_reloc_graph_kernels(rl_reloc *r, int32_t n, int32_t *out);
 /* Failure injection for tests of the device-side failure path (the paper
  * has no counterpart).  The LM kernel waits, with a bound, for the bulk
  * copies that stage its mode-table tiles; a wait that runs out marks the

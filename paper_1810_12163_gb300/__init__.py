@@ -335,6 +335,13 @@ class Relocaliser:
         """Replay captured CUDA graphs (default) or launch kernels one by one."""
         call("rl_reloc_set_graphs", self.h, int(enable))
 
+    def graph_kernels(self, n: int) -> int:
+        """Kernel launches of the captured graph of an n-frame call (-1: none
+        captured)."""
+        k = ctypes.c_int32()
+        call("rl_reloc_graph_kernels", self.h, int(n), ctypes.byref(k))
+        return k.value
+
     def set_wait_limit(self, probes: int = -1):
         """Failure injection: probes of the LM kernel's waits for staged tiles
         before they give up (0: at once, negative: the default); see

@@ -124,6 +124,7 @@ _SIGS = {
     "rl_reloc_debug": [P, I32] + [P] * 10,
     "rl_reloc_profile": [P, I32],
     "rl_reloc_set_graphs": [P, I32],
+    "rl_reloc_graph_kernels": [P, I32, P],
     "rl_reloc_set_wait_limit": [P, ctypes.c_int64],
     "rl_reloc_profile_read": [P, P, P, P],
     "rl_cascade_create": [P, P, P, I32, P],

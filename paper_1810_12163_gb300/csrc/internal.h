@@ -288,12 +288,14 @@ struct rl_reloc {
         int n, level, buf;
         cudaGraphExec_t exec;
         uint64_t last_use;
+        int kernels;  // kernel nodes of the graph
     };
     std::vector<Graph> graphs;
     cudaStream_t capture_stream = nullptr;
     bool use_graphs = true;
     uint64_t calls = 0;
     rl_tuning tune{16, 128, 128, 256, 4};  // launch shapes (results do not depend on them)
+    uint64_t tune_gen = 0;                    // bumped by every rl_reloc_set_tuning
     // per array of q: byte offset of its pointer in QueryState and bytes per frame
     std::vector<std::pair<size_t, size_t>> q_layout;
     // sub-batches of a call (tune.streams): private streams and fork/join events
@@ -329,9 +331,13 @@ struct rl_cascade {
     std::vector<void *> allocs;
     struct Graph {
         int n, buf;
+        uint64_t tune_gen;  // sum of the levels' tune_gen at capture
         cudaGraphExec_t exec;
     };
     std::vector<Graph> graphs;
+    // sub-batches of a call (the first level's tune.streams): private streams and fork/join events
+    cudaStream_t side[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t fork_ev = nullptr, join_ev[3] = {nullptr, nullptr, nullptr};
     cudaStream_t capture_stream = nullptr;
     bool use_graphs = true;
 };

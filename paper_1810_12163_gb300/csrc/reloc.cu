@@ -415,6 +415,18 @@ static rl_status launch_relocalise_snapshot(rl_reloc *r, int n, int level, int b
         return st;
     }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+    int kernels = 0;
+    {
+        size_t nn = 0;
+        if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
+            std::vector<cudaGraphNode_t> nodes(nn);
+            if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+                for (size_t i = 0; i < nn; ++i) {
+                    cudaGraphNodeType t;
+                    if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+                }
+        }
+    }
     cudaGraphExec_t exec = nullptr;
     e = cudaGraphInstantiate(&exec, g, 0);
     cudaGraphDestroy(g);
@@ -426,7 +438,7 @@ static rl_status launch_relocalise_snapshot(rl_reloc *r, int n, int level, int b
         cudaGraphExecDestroy(r->graphs[lru].exec);
         r->graphs.erase(r->graphs.begin() + lru);
     }
-    r->graphs.push_back({n, level, buf, exec, r->calls});
+    r->graphs.push_back({n, level, buf, exec, r->calls, kernels});
     RL_CK(cudaGraphLaunch(exec, s));
     return RL_OK;
 }
@@ -798,26 +810,70 @@ __global__ void k_cascade_decide(QueryState lq, CascadeOut co, LaterFrames later
     }
 }
 
-static rl_status cascade_enqueue(rl_cascade *c, int n, cudaStream_t s) {
+// The cascade outputs of frames b0, b0 + 1, ...
+static CascadeOut cascade_out_slice(const CascadeOut &o, int b0) {
+    const size_t b = (size_t)b0;
+    CascadeOut s = o;
+    s.res += b;
+    s.chosen_pose += b * 16 * 12;
+    s.chosen_energy += b * 16;
+    s.chosen_score += b * 16;
+    s.icp_frac += b * 16;
+    s.chosen_slot += b * 16;
+    s.level += b;
+    s.done += b;
+    return s;
+}
+
+// All levels for the nb frames b0, b0 + 1, ... of the call.
+static rl_status cascade_enqueue_part(rl_cascade *c, int b0, int nb, cudaStream_t s) {
     const int L = (int)c->levels.size();
-    RL_CK(cudaMemsetAsync(c->out.done, 0, sizeof(int32_t) * n, s));
+    const CascadeOut out = cascade_out_slice(c->out, b0);
+    RL_CK(cudaMemsetAsync(out.done, 0, sizeof(int32_t) * nb, s));
     for (int l = 0; l < L; ++l) {
         rl_reloc *r = c->levels[l];
+        const QueryState q = query_slice(r, b0);
         const int sf = c->subsample[l];
         if (sf > 1) {
             const int hw = r->max_w * r->max_h;
-            dim3 grid((hw + 255) / 256, n);
-            k_subsample_all<<<grid, 256, 0, s>>>(c->full_dev, c->out.done, sf, r->stage_depth,
-                                                 r->stage_rgb, hw);
+            dim3 grid((hw + 255) / 256, nb);
+            k_subsample_all<<<grid, 256, 0, s>>>(c->full_dev + b0, out.done, sf, r->stage_depth + (size_t)b0 * hw,
+                                                 r->stage_rgb + (size_t)b0 * hw * 3, hw);
             RL_LAUNCH_CK();
         }
-        RL_TRY(run_relocalise(r, r->q, n, l, s));
+        RL_TRY(run_relocalise(r, q, nb, l, s));
         LaterFrames later{};
-        for (int k = l + 1; k < L && later.n < 8; ++k) later.f[later.n++] = c->levels[k]->q.frames;
+        for (int k = l + 1; k < L && later.n < 8; ++k) later.f[later.n++] = c->levels[k]->q.frames + b0;
         const float tau = l < L - 1 ? (float)c->thresholds[l] : INFINITY;
-        k_cascade_decide<<<(n + 127) / 128, 128, 0, s>>>(r->q, c->out, later, tau, l, l == L - 1, n);
+        k_cascade_decide<<<(nb + 127) / 128, 128, 0, s>>>(q, out, later, tau, l, l == L - 1, nb);
         RL_LAUNCH_CK();
     }
+    return RL_OK;
+}
+
+// A cascade call as sub-batches on concurrent streams, as for one level
+// (run_relocalise_parts): each sub-batch runs every level for its frames.
+static rl_status cascade_enqueue(rl_cascade *c, int n, cudaStream_t s) {
+    bool prof = false;
+    for (rl_reloc *r : c->levels) prof = prof || r->prof.on;
+    const int parts = prof ? 1 : std::max(1, std::min(c->levels[0]->tune.streams, n / kMinPart));
+    if (parts <= 1) return cascade_enqueue_part(c, 0, n, s);
+    for (int i = 0; i < parts - 1; ++i) {
+        if (!c->side[i]) RL_CK(cudaStreamCreateWithFlags(&c->side[i], cudaStreamNonBlocking));
+        if (!c->join_ev[i]) RL_CK(cudaEventCreateWithFlags(&c->join_ev[i], cudaEventDisableTiming));
+    }
+    if (!c->fork_ev) RL_CK(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+    RL_CK(cudaEventRecord(c->fork_ev, s));
+    int b0 = 0;
+    for (int i = 0; i < parts; ++i) {
+        const int nb = n / parts + (i < n % parts ? 1 : 0);
+        cudaStream_t si = i == 0 ? s : c->side[i - 1];
+        if (i > 0) RL_CK(cudaStreamWaitEvent(si, c->fork_ev, 0));
+        RL_TRY(cascade_enqueue_part(c, b0, nb, si));
+        if (i > 0) RL_CK(cudaEventRecord(c->join_ev[i - 1], si));
+        b0 += nb;
+    }
+    for (int i = 0; i < parts - 1; ++i) RL_CK(cudaStreamWaitEvent(s, c->join_ev[i], 0));
     return RL_OK;
 }
 
@@ -846,10 +902,26 @@ static rl_status cascade_launch(rl_cascade *c, int n, cudaStream_t s) {
     return RL_OK;
 }
 
+// Changes with the tuning of any level (a captured graph holds the levels'
+// launch shapes and sub-batches).
+static uint64_t cascade_tune_gen(const rl_cascade *c) {
+    uint64_t g = 0;
+    for (const rl_reloc *r : c->levels) g += r->tune_gen;
+    return g;
+}
+
 static rl_status cascade_launch_snapshot(rl_cascade *c, int n, int buf, cudaStream_t s) {
     bool prof = false;
     for (rl_reloc *r : c->levels) prof = prof || r->prof.on;
     if (prof || !c->use_graphs) return cascade_enqueue(c, n, s);
+    const uint64_t gen = cascade_tune_gen(c);
+    for (size_t i = 0; i < c->graphs.size();)  // captured under another tuning of some level
+        if (c->graphs[i].tune_gen != gen) {
+            cudaGraphExecDestroy(c->graphs[i].exec);
+            c->graphs.erase(c->graphs.begin() + i);
+        } else {
+            ++i;
+        }
     for (auto &g : c->graphs)
         if (g.n == n && g.buf == buf) {
             RL_CK(cudaGraphLaunch(g.exec, s));
@@ -873,7 +945,7 @@ static rl_status cascade_launch_snapshot(rl_cascade *c, int n, int buf, cudaStre
         cudaGraphExecDestroy(c->graphs.front().exec);
         c->graphs.erase(c->graphs.begin());
     }
-    c->graphs.push_back({n, buf, exec});
+    c->graphs.push_back({n, buf, gen, exec});
     RL_CK(cudaGraphLaunch(exec, s));
     return RL_OK;
 }
@@ -929,6 +1001,14 @@ static void cascade_release(rl_cascade *c) {
     c->graphs.clear();
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     c->capture_stream = nullptr;
+    for (int i = 0; i < 3; ++i) {
+        if (c->side[i]) cudaStreamDestroy(c->side[i]);
+        if (c->join_ev[i]) cudaEventDestroy(c->join_ev[i]);
+        c->side[i] = nullptr;
+        c->join_ev[i] = nullptr;
+    }
+    if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+    c->fork_ev = nullptr;
     for (void *p : c->allocs) arena_free(c->ctx, p);
     c->allocs.clear();
 }
@@ -1089,6 +1169,14 @@ extern "C" const char *rl_kernel_name(int32_t kid) {
 extern "C" rl_status rl_reloc_set_graphs(rl_reloc *r, int32_t enable) {
     if (!r) return fail(RL_ERR_INVALID_ARG, "null relocaliser");
     r->use_graphs = enable != 0;
+    return RL_OK;
+}
+
+extern "C" rl_status rl_reloc_graph_kernels(rl_reloc *r, int32_t n, int32_t *out) {
+    if (!r || !out) return fail(RL_ERR_INVALID_ARG, "null argument");
+    *out = -1;
+    for (const auto &g : r->graphs)
+        if (g.n == n && g.level == 0) *out = g.kernels;
     return RL_OK;
 }
 
@@ -1321,6 +1409,7 @@ extern "C" rl_status rl_reloc_set_tuning(rl_reloc *r, const rl_tuning *t) {
     RL_CK(cudaDeviceSynchronize());
     graphs_free(r);
     r->tune = *t;
+    ++r->tune_gen;
     return RL_OK;
 }
 

@@ -117,3 +117,32 @@ def test_config3_cascade(rg, model):
     cas.close()
     for lv in levels:
         lv.close()
+
+
+def test_config3_cascade_sub_batches(rg, model):
+    """A 20-frame cascade call split into two sub-batches on concurrent
+    streams (the first level's default tuning) gives every frame the result
+    of the one-stream call; changing a level's tuning replaces the cascade's
+    captured graph."""
+    ctx, g = model
+    scene = rg.Scene(ctx, W2.room().lo, W2.room().hi)
+    th = workloads.cascade_thresholds()
+    n = 20
+    levels = [rg.Relocaliser(g, scene, p, W2.width // s, W2.height // s, n) for s, p in workloads.CASCADE_LEVELS]
+    cas = rg.Cascade(levels, th, [s for s, _ in workloads.CASCADE_LEVELS])
+    qs = [W2.query(q) for q in range(10)]
+    D = np.stack([qs[i % 10][0] for i in range(n)])
+    C = np.stack([qs[i % 10][1] for i in range(n)])
+    seeds = [qs[i % 10][3] + 7919 * (i // 10) for i in range(n)]
+    assert levels[0].tuning["streams"] > 1
+    split = [cas.relocalise_batch(D, C, W2.K, seeds) for _ in range(2)]
+    levels[0].set_tuning(dict(streams=1))
+    one = cas.relocalise_batch(D, C, W2.K, seeds)
+    for out in split:
+        for a, b in zip(out, one):
+            assert a["level"] == b["level"] and a["n_hypotheses"] == b["n_hypotheses"]
+            assert np.array_equal(a["pose"], b["pose"]) and a["score"] == b["score"]
+    assert len({r["level"] for r in one}) >= 2
+    cas.close()
+    for lv in levels:
+        lv.close()

@@ -80,8 +80,15 @@ def test_sub_batches_on_streams_give_the_batch_results(setup, graphs):
     qs = [(d, c, T, 1000 + i) for i, (d, c, T, _) in enumerate(qs)]
     base = _run(rel, qs, w)
     assert sum(r["n_hypotheses"] > 0 for r in base) >= n // 2
+    kernels = {}
     for streams in (2, 4, 1):
         rel.set_tuning(dict(streams=streams))
         _same(_run(rel, qs, w), base)
         _same(_run(rel, qs, w), base)  # the second call replays the captured graph
+        kernels[streams] = rel.graph_kernels(n)
+    if graphs:
+        # each sub-batch launches the whole sequence; 20 frames make two of at least 8
+        assert kernels[1] > 20 and kernels[2] == kernels[4] == 2 * kernels[1], kernels
+    else:
+        assert set(kernels.values()) == {-1}
     rel.close()
