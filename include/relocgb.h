@@ -375,14 +375,14 @@ rl_status rl_reloc_debug(rl_reloc *r, int32_t q, double *hyp_pose /* n_hyp*12 */
 /* ---- launch-shape tuning ---------------------------------------------- */
 /* Launch shapes of the relocaliser's kernels that do not change any result
  * (every kernel computes the same values in the same order for each of
- * them).  Defaults: {16, 128, 128, 256, 4}. */
+ * them).  Defaults: {16, 128, 128, 256, 8}. */
 typedef struct {
     int32_t hypgen_warps;     /* warps (slots) per block of generation: 2, 4, 8 or 16 */
     int32_t energy_threads;   /* at most this many hypotheses per block of Eq. 5: 32, 64, 128 or 256 */
     int32_t leaves_threads;   /* pixels per block of the forest walk: 64, 128, 256 or 512 */
     int32_t mask_threads;     /* pixels per block of the colour-check masks: 64, 128 or 256 */
-    int32_t streams;          /* sub-batches of a call run concurrently on this many streams: 1, 2
-                               * or 4 (at most one per 8 frames; a call with profiling on runs as
+    int32_t streams;          /* sub-batches of a call run concurrently on this many streams: 1, 2,
+                               * 4 or 8 (at most one per 8 frames; a call with profiling on runs as
                                * one batch).  The frames are independent, so every result is the
                                * same as in one batch. */
 } rl_tuning;

@@ -294,13 +294,13 @@ struct rl_reloc {
     cudaStream_t capture_stream = nullptr;
     bool use_graphs = true;
     uint64_t calls = 0;
-    rl_tuning tune{16, 128, 128, 256, 4};  // launch shapes (results do not depend on them)
+    rl_tuning tune{16, 128, 128, 256, 8};  // launch shapes (results do not depend on them)
     uint64_t tune_gen = 0;                    // bumped by every rl_reloc_set_tuning
     // per array of q: byte offset of its pointer in QueryState and bytes per frame
     std::vector<std::pair<size_t, size_t>> q_layout;
     // sub-batches of a call (tune.streams): private streams and fork/join events
-    cudaStream_t side[3] = {nullptr, nullptr, nullptr};
-    cudaEvent_t fork_ev = nullptr, join_ev[3] = {nullptr, nullptr, nullptr};
+    cudaStream_t side[7] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[7] = {};
     uint32_t lm_wait_limit = kLmWaitLimit;  // probes of the LM kernel's waits for staged tiles
     // streaming forests: recorded after the last launch that read mode store b
     cudaEvent_t read_done[2] = {nullptr, nullptr};
@@ -336,8 +336,8 @@ struct rl_cascade {
     };
     std::vector<Graph> graphs;
     // sub-batches of a call (the first level's tune.streams): private streams and fork/join events
-    cudaStream_t side[3] = {nullptr, nullptr, nullptr};
-    cudaEvent_t fork_ev = nullptr, join_ev[3] = {nullptr, nullptr, nullptr};
+    cudaStream_t side[7] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[7] = {};
     cudaStream_t capture_stream = nullptr;
     bool use_graphs = true;
 };

@@ -81,7 +81,7 @@ static void graphs_free(rl_reloc *r);
 static void reloc_release(rl_reloc *r) {
     prof_free(r);
     graphs_free(r);
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 7; ++i) {
         if (r->side[i]) cudaStreamDestroy(r->side[i]);
         if (r->join_ev[i]) cudaEventDestroy(r->join_ev[i]);
         r->side[i] = nullptr;
@@ -1001,7 +1001,7 @@ static void cascade_release(rl_cascade *c) {
     c->graphs.clear();
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     c->capture_stream = nullptr;
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 7; ++i) {
         if (c->side[i]) cudaStreamDestroy(c->side[i]);
         if (c->join_ev[i]) cudaEventDestroy(c->join_ev[i]);
         c->side[i] = nullptr;
@@ -1386,7 +1386,7 @@ static bool one_of(int v, std::initializer_list<int> l) {
 static bool valid_tuning(const rl_tuning &t) {
     return one_of(t.hypgen_warps, {2, 4, 8, 16}) && one_of(t.energy_threads, {32, 64, 128, 256}) &&
            one_of(t.leaves_threads, {64, 128, 256, 512}) && one_of(t.mask_threads, {64, 128, 256}) &&
-           one_of(t.streams, {1, 2, 4});
+           one_of(t.streams, {1, 2, 4, 8});
 }
 
 static std::string trim(const std::string &x) {
@@ -1541,7 +1541,7 @@ extern "C" rl_status rl_reloc_autotune(rl_reloc *r, int32_t n, const float *dept
     if (st == RL_OK && !was_on && r->use_graphs && n >= 2 * kMinPart) {
         int best = t.streams;
         double best_ms = INFINITY, cur_ms = INFINITY;
-        for (int v : {1, 2, 4}) {
+        for (int v : {1, 2, 4, 8}) {
             if (v > 1 && n / kMinPart < v) break;  // would run as fewer sub-batches
             rl_tuning c = t;
             c.streams = v;
