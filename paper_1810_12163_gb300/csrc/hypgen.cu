@@ -131,14 +131,19 @@ __device__ __forceinline__ void stage1_bits2(const HypArgs &a, const Frame &fr, 
     sB = decide(okB, wB, rB, dB);
 }
 
+// rec, dep: the three pixels' records and depths when already gathered
+// (else read here).
 __device__ __forceinline__ bool stage2(const HypArgs &a, const CheckThr &ct, const Frame &fr,
                                        const uint16_t *lv, const uint4 *pr, const int pix[3],
-                                       const int m[3]) {
+                                       const int m[3], const uint4 *rec = nullptr, const float *dep = nullptr) {
     float3 xw[3];
     for (int i = 0; i < 3; ++i) {
         uint32_t L;
         int rank;
-        lookup(a, lv, pr, pix[i], m[i], &L, &rank);
+        if (rec)
+            mode_at_rec(rec[i], a.p.n_trees, a.mv.leaves_per_tree, m[i], &L, &rank);
+        else
+            lookup(a, lv, pr, pix[i], m[i], &L, &rank);
         xw[i] = mode_pos(a.mv, L, rank);
     }
     // check 2: scene points pairwise at least sqrt(min_sq_dist) apart
@@ -151,7 +156,7 @@ __device__ __forceinline__ bool stage2(const HypArgs &a, const CheckThr &ct, con
     }
     // check 3: rigidity, |d_W - d_C| <= max_trans_err for every pair
     float3 xc[3];
-    for (int i = 0; i < 3; ++i) xc[i] = backproject(fr, pix[i]);
+    for (int i = 0; i < 3; ++i) xc[i] = dep ? backproject_d(fr, pix[i], dep[i]) : backproject(fr, pix[i]);
     for (int k = 0; k < 3; ++k) {
         const float dw = sqrtf(dW2f[k]), dc = sqrtf(dist2_32(xc[PA[k]], xc[PB[k]]));
         const float diff = fabsf(__fsub_rn(dw, dc));
@@ -230,21 +235,40 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_hypgen(HypArgs a) {
             const int pix[3] = {r.y, r.z, r.w};
             it = r.x & 0x3fffffff;
             int m[3];
-            if (use_bits) {
-                // the mode draws of the attempt, from its second Philox block
-                // and the three |M(u)|
+            if (use_bits && pr) {
+                // every gather that depends on the pixels alone, issued
+                // together: |M(u)|, the pixel records and the depths; then
+                // the mode draws of the attempt from its second Philox block
+                uint32_t c3[3];
+                uint4 rec[3];
+                float dep[3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    c3[i] = cm[pix[i]].y >> 24;
+                    rec[i] = pr[pix[i]];
+                    dep[i] = fr.depth[pix[i]];
+                }
                 const uint32_t ctr1 = (TAG_HYP << 16) | (uint32_t)a.p.level;
                 const uint4 r1 = philox(make_uint4(slot, ctr1, it, 1), fr.key0, fr.key1);
-                m[0] = (int)draw_below(r1.x, cm[pix[0]].y >> 24);
-                m[1] = (int)draw_below(r1.y, cm[pix[1]].y >> 24);
-                m[2] = (int)draw_below(r1.z, cm[pix[2]].y >> 24);
+                m[0] = (int)draw_below(r1.x, c3[0]);
+                m[1] = (int)draw_below(r1.y, c3[1]);
+                m[2] = (int)draw_below(r1.z, c3[2]);
+                ok = stage2(a, ct, fr, lv, pr, pix, m, rec, dep);
             } else {
-                const uint2 mm = rmode[e];
-                m[0] = (int)(mm.x & 0xffffu);
-                m[1] = (int)(mm.x >> 16);
-                m[2] = (int)mm.y;
+                if (use_bits) {
+                    const uint32_t ctr1 = (TAG_HYP << 16) | (uint32_t)a.p.level;
+                    const uint4 r1 = philox(make_uint4(slot, ctr1, it, 1), fr.key0, fr.key1);
+                    m[0] = (int)draw_below(r1.x, cm[pix[0]].y >> 24);
+                    m[1] = (int)draw_below(r1.y, cm[pix[1]].y >> 24);
+                    m[2] = (int)draw_below(r1.z, cm[pix[2]].y >> 24);
+                } else {
+                    const uint2 mm = rmode[e];
+                    m[0] = (int)(mm.x & 0xffffu);
+                    m[1] = (int)(mm.x >> 16);
+                    m[2] = (int)mm.y;
+                }
+                ok = stage2(a, ct, fr, lv, pr, pix, m);
             }
-            ok = stage2(a, ct, fr, lv, pr, pix, m);
         }
         const unsigned win = __ballot_sync(0xffffffffu, ok);
         if (win && lane == __ffs(win) - 1) *iter_out = it;

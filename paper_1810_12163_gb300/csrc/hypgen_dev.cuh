@@ -23,12 +23,13 @@ struct HypArgs {
     const uint32_t *pbits;   // [B][hw_max / 32 + 1] non-empty-M(u) bitmap (with pcm), or null
 };
 
-__device__ __forceinline__ float3 backproject(const Frame &fr, int p) {
-    const float d = fr.depth[p];
+__device__ __forceinline__ float3 backproject_d(const Frame &fr, int p, float d) {
     const int u = p % fr.W, v = p / fr.W;
     return make_float3(__fdiv_rn(__fmul_rn(__fsub_rn((float)u, fr.cx), d), fr.fx),
                        __fdiv_rn(__fmul_rn(__fsub_rn((float)v, fr.cy), d), fr.fy), d);
 }
+
+__device__ __forceinline__ float3 backproject(const Frame &fr, int p) { return backproject_d(fr, p, fr.depth[p]); }
 
 // The draws of iteration `it` of `slot`: three pixels, the colour-check pair
 // and the three mode indices into M(u).
