@@ -56,10 +56,10 @@ rl_status launch_forest_random(rl_forest *f, cudaStream_t s) {
 // DA-RGB split C(p,c) - C(q,c), against tau; true goes right (2n+2).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int probe_coord(int p, float off, int extent) {
-    float v = __fadd_rn(__fadd_rn((float)p, off), 0.5f);
-    float f = floorf(v);
-    f = fminf(fmaxf(f, 0.0f), (float)(extent - 1));
-    return (int)f;
+    const float v = __fadd_rn(__fadd_rn((float)p, off), 0.5f);
+    // floor to an integer (saturating beyond the int range, 0 for NaN), then
+    // clamp: the same as clamping floor(v) in FP32 and converting
+    return min(max(__float2int_rd(v), 0), extent - 1);
 }
 
 __device__ __forceinline__ int walk_tree(const float4 *__restrict__ nodes, int depth,
