@@ -90,7 +90,8 @@ __device__ __forceinline__ int walk_tree(const float4 *__restrict__ nodes, int d
 
 // All T trees of one pixel walked level by level, interleaved: T
 // independent chains of dependent node and probe loads in flight at once.
-template <int T>
+// PRE: the nodes' offsets are already multiplied by s (k_scale_nodes).
+template <int T, bool PRE>
 __device__ __forceinline__ void walk_trees(const float4 *__restrict__ nodes, int n_branch, int depth,
                                            const float *__restrict__ D, const uint8_t *__restrict__ C,
                                            int W, int H, float s, int x, int y, float d, float inv,
@@ -106,8 +107,8 @@ __device__ __forceinline__ void walk_trees(const float4 *__restrict__ nodes, int
 #pragma unroll
         for (int t = 0; t < T; ++t) {
             const uint32_t meta = __float_as_uint(nd[t].w);
-            const float ox = __fmul_rn(__fmul_rn(nd[t].x, s), inv);
-            const float oy = __fmul_rn(__fmul_rn(nd[t].y, s), inv);
+            const float ox = __fmul_rn(PRE ? nd[t].x : __fmul_rn(nd[t].x, s), inv);
+            const float oy = __fmul_rn(PRE ? nd[t].y : __fmul_rn(nd[t].y, s), inv);
             const int q = probe_coord(y, oy, H) * W + probe_coord(x, ox, W);
             float f;
             if ((meta & 255u) == 0u) {
@@ -124,13 +125,13 @@ __device__ __forceinline__ void walk_trees(const float4 *__restrict__ nodes, int
     for (int t = 0; t < T; ++t) leaf[t] = n[t] - ((1 << depth) - 1);
 }
 
-template <int T>
+template <int T, bool PRE>
 __device__ __forceinline__ int walk_and_store(const float4 *nodes, int n_branch, int depth, const Frame &fr,
                                               float s, int x, int y, float d, float inv, uint16_t *o,
                                               int hw_max, const uint8_t *nmodes, int lpt, int k_top,
                                               bool count, uint4 *rec) {
     int leaf[kRecTrees], cnt[kRecTrees];
-    walk_trees<T>(nodes, n_branch, depth, fr.depth, fr.rgb, fr.W, fr.H, s, x, y, d, inv, leaf);
+    walk_trees<T, PRE>(nodes, n_branch, depth, fr.depth, fr.rgb, fr.W, fr.H, s, x, y, d, inv, leaf);
     int total = 0;
 #pragma unroll
     for (int t = 0; t < T; ++t) {
@@ -145,10 +146,13 @@ __device__ __forceinline__ int walk_and_store(const float4 *nodes, int n_branch,
 // out: uint16 [frame][tree][hw_max]; one thread per pixel walks every tree.
 // When `mcount` is given it also receives |M(u)| = sum over the trees of
 // min(modes of the reached leaf, k_top) per pixel (0 without depth).
+// nodes_s: the nodes scaled for focal length fx_s (k_scale_nodes), used for
+// the frames of that focal length, or null.
 __global__ void k_leaves(const float4 *__restrict__ nodes, int n_branch, int depth, int n_trees,
                          const Frame *__restrict__ frames, int hw_max, uint16_t *__restrict__ out,
                          const uint8_t *__restrict__ nmodes, int leaves_per_tree, int k_top,
-                         uint16_t *__restrict__ mcount, uint4 *__restrict__ prec) {
+                         uint16_t *__restrict__ mcount, uint4 *__restrict__ prec,
+                         const float4 *__restrict__ nodes_s, float fx_s) {
     const Frame fr = frames[blockIdx.y];
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= fr.W * fr.H) return;
@@ -166,12 +170,19 @@ __global__ void k_leaves(const float4 *__restrict__ nodes, int n_branch, int dep
     const float inv = __frcp_rn(d);
     int total = 0;
     const bool cnt = mcount != nullptr;
+    const bool pre = nodes_s != nullptr && fr.fx == fx_s;  // the same for the whole block (one frame)
+#define RL_WALK(T)                                                                                          \
+    total = pre ? walk_and_store<T, true>(nodes_s, n_branch, depth, fr, s, x, y, d, inv, o, hw_max, nmodes, \
+                                          leaves_per_tree, k_top, cnt, rec)                                  \
+                : walk_and_store<T, false>(nodes, n_branch, depth, fr, s, x, y, d, inv, o, hw_max, nmodes,  \
+                                           leaves_per_tree, k_top, cnt, rec)
     switch (n_trees) {
-    case 1: total = walk_and_store<1>(nodes, n_branch, depth, fr, s, x, y, d, inv, o, hw_max, nmodes, leaves_per_tree, k_top, cnt, rec); break;
-    case 2: total = walk_and_store<2>(nodes, n_branch, depth, fr, s, x, y, d, inv, o, hw_max, nmodes, leaves_per_tree, k_top, cnt, rec); break;
-    case 3: total = walk_and_store<3>(nodes, n_branch, depth, fr, s, x, y, d, inv, o, hw_max, nmodes, leaves_per_tree, k_top, cnt, rec); break;
-    case 4: total = walk_and_store<4>(nodes, n_branch, depth, fr, s, x, y, d, inv, o, hw_max, nmodes, leaves_per_tree, k_top, cnt, rec); break;
-    case 5: total = walk_and_store<5>(nodes, n_branch, depth, fr, s, x, y, d, inv, o, hw_max, nmodes, leaves_per_tree, k_top, cnt, rec); break;
+    case 1: RL_WALK(1); break;
+    case 2: RL_WALK(2); break;
+    case 3: RL_WALK(3); break;
+    case 4: RL_WALK(4); break;
+    case 5: RL_WALK(5); break;
+#undef RL_WALK
     default:
         for (int t = 0; t < n_trees; ++t) {
             const int leaf = walk_tree(nodes + (size_t)t * n_branch, depth, fr.depth, fr.rgb, fr.W, fr.H,
@@ -185,12 +196,31 @@ __global__ void k_leaves(const float4 *__restrict__ nodes, int n_branch, int dep
 
 rl_status launch_leaves(const rl_forest *f, const Frame *frames_dev, int n_frames, int n_trees,
                         int hw_max, uint16_t *out, int max_w, int max_h, cudaStream_t s,
-                        int k_top, uint16_t *mcount, uint4 *prec, int threads) {
+                        int k_top, uint16_t *mcount, uint4 *prec, int threads, const float4 *nodes_s,
+                        float fx_s) {
     const int npx = max_w * max_h;
     dim3 grid((npx + threads - 1) / threads, n_frames);
     k_leaves<<<grid, threads, 0, s>>>(f->nodes, f->n_branch, f->p.depth, n_trees, frames_dev, hw_max, out,
                                   f->nmodes, f->leaves_per_tree, k_top, mcount,
-                                  n_trees <= kRecTrees ? prec : nullptr);
+                                  n_trees <= kRecTrees ? prec : nullptr, nodes_s, fx_s);
+    RL_LAUNCH_CK();
+    return RL_OK;
+}
+
+// The split nodes with their offsets multiplied by s = fx / 585 (Eq. 1-3's
+// depth-normalised probe offset), rounded as the walk rounds its own first
+// product: the walk then needs one product per coordinate.
+__global__ void k_scale_nodes(const float4 *__restrict__ nodes, float4 *__restrict__ out, int count, float fx) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const float s = __fdiv_rn(fx, 585.0f);
+    const float4 v = nodes[i];
+    out[i] = make_float4(__fmul_rn(v.x, s), __fmul_rn(v.y, s), v.z, v.w);
+}
+
+rl_status launch_scale_nodes(const rl_forest *f, int n_trees, float4 *out, float fx, cudaStream_t s) {
+    const int count = n_trees * f->n_branch;
+    k_scale_nodes<<<(count + 255) / 256, 256, 0, s>>>(f->nodes, out, count, fx);
     RL_LAUNCH_CK();
     return RL_OK;
 }

@@ -296,6 +296,7 @@ struct rl_reloc {
     uint64_t calls = 0;
     rl_tuning tune{16, 128, 128, 256, 8};  // launch shapes (results do not depend on them)
     uint64_t tune_gen = 0;                    // bumped by every rl_reloc_set_tuning
+    float4 *nodes_s = nullptr;                // split nodes scaled for the call's focal length
     // per array of q: byte offset of its pointer in QueryState and bytes per frame
     std::vector<std::pair<size_t, size_t>> q_layout;
     // sub-batches of a call (tune.streams): private streams and fork/join events
@@ -379,7 +380,10 @@ rl_status launch_forest_random(rl_forest *f, cudaStream_t s);
 rl_status launch_leaves(const rl_forest *f, const Frame *frames_dev, int n_frames, int n_trees,
                         int hw_max, uint16_t *out, int max_w, int max_h, cudaStream_t s,
                         int k_top = 0, uint16_t *mcount = nullptr, uint4 *prec = nullptr,
-                        int threads = 128);
+                        int threads = 128, const float4 *nodes_s = nullptr, float fx_s = 0.f);
+// The first n_trees trees' split nodes with offsets premultiplied by fx / 585
+// into out (read by launch_leaves for frames of that focal length).
+rl_status launch_scale_nodes(const rl_forest *f, int n_trees, float4 *out, float fx, cudaStream_t s);
 rl_status adapt_frame(rl_forest *f, const float *depth, const uint8_t *rgb,
                       const rl_intrinsics *K, const double T[16], cudaStream_t s);
 rl_status update_modes(rl_forest *f, int64_t begin, int64_t count, cudaStream_t s);

@@ -175,7 +175,7 @@ rl_status run_relocalise(rl_reloc *r, const QueryState &q, int n, int level, cud
     RL_CK(cudaMemsetAsync(q.round_count, 0, sizeof(int32_t) * 16 * n, s));
     RL_CK(cudaMemsetAsync(q.dev_err, 0, sizeof(int32_t) * n, s));
     unsigned long long *work = r->prof.on ? r->prof.work : nullptr;
-    { PROF(K_LEAVES); RL_TRY(launch_leaves(f, q.frames, n, p.n_trees, hw_max, q.leaves, r->max_w, r->max_h, s, p.k_top, q.mcount, q.prec, r->tune.leaves_threads)); }
+    { PROF(K_LEAVES); RL_TRY(launch_leaves(f, q.frames, n, p.n_trees, hw_max, q.leaves, r->max_w, r->max_h, s, p.k_top, q.mcount, q.prec, r->tune.leaves_threads, r->nodes_s, r->host_frames[0].fx)); }
     if (q.pcm) { PROF(K_CMASK); RL_TRY(launch_colour_mask(q.frames, q.mcount, q.prec, hw_max, mv, p, q.pcm, q.pbits, n, hw_max, s, r->tune.mask_threads)); }
     { PROF(K_HYPGEN); RL_TRY(launch_hypgen(q.frames, q.leaves, q.mcount, q.prec, q.pcm, q.pbits, hw_max, mv, p, q.hyp_pose, q.hyp_iter, work, n, s, r->tune.hypgen_warps)); }
     { PROF(K_HYPPOSE); RL_TRY(launch_hyppose(q.frames, q.leaves, q.mcount, q.prec, hw_max, mv, p, q.hyp_pose, q.hyp_iter, n, s)); }
@@ -363,6 +363,9 @@ constexpr int kMinPart = 8;
 // as their slowest frame).  Inside a stream capture the fork and join bring
 // the private streams into the same graph.
 static rl_status run_relocalise_parts(rl_reloc *r, int n, int level, cudaStream_t s) {
+    // nodes scaled for the call's focal length (frames of another one, in a
+    // replayed graph, walk the unscaled nodes)
+    RL_TRY(launch_scale_nodes(r->forest, r->rp.n_trees, r->nodes_s, r->host_frames[0].fx, s));
     const int parts = r->prof.on ? 1 : std::max(1, std::min(r->tune.streams, n / kMinPart));
     if (parts <= 1) return run_relocalise(r, r->q, n, level, s);
     for (int i = 0; i < parts - 1; ++i) {
@@ -638,6 +641,7 @@ extern "C" rl_status rl_reloc_create(rl_forest *f, rl_scene *scene, const rl_ran
     A(result_blob, B * sizeof(DevResult));
     A(dev_err, B);
 #undef A
+    if (s == RL_OK) s = ralloc(r, (uint64_t)p->n_trees_used * f->n_branch, &r->nodes_s);
     if (s == RL_OK) s = ralloc(r, B * hw, &r->stage_depth);
     if (s == RL_OK) s = ralloc(r, B * hw * 3, &r->stage_rgb);
     if (s == RL_OK && cudaMallocHost(&r->host_frames, sizeof(Frame) * B) != cudaSuccess)
@@ -856,6 +860,8 @@ static rl_status cascade_enqueue_part(rl_cascade *c, int b0, int nb, cudaStream_
 static rl_status cascade_enqueue(rl_cascade *c, int n, cudaStream_t s) {
     bool prof = false;
     for (rl_reloc *r : c->levels) prof = prof || r->prof.on;
+    for (rl_reloc *r : c->levels)  // each level's nodes scaled for its focal length
+        RL_TRY(launch_scale_nodes(r->forest, r->rp.n_trees, r->nodes_s, r->host_frames[0].fx, s));
     const int parts = prof ? 1 : std::max(1, std::min(c->levels[0]->tune.streams, n / kMinPart));
     if (parts <= 1) return cascade_enqueue_part(c, 0, n, s);
     for (int i = 0; i < parts - 1; ++i) {
