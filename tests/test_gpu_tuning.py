@@ -94,3 +94,26 @@ def test_sub_batches_on_streams_give_the_batch_results(setup, graphs):
     else:
         assert set(kernels.values()) == {-1}
     rel.close()
+
+
+def test_frames_of_another_focal_length_walk_the_unscaled_nodes(setup):
+    """A call reads split nodes premultiplied by its first frame's fx / 585.
+    A graph captured for one focal length and replayed for another keeps the
+    old scaled nodes, and its frames then walk the unscaled ones: the
+    results equal those of a relocaliser that only saw the second focal
+    length (whose own graph walks the nodes scaled for it)."""
+    from synth import rooms
+    rg, ctx, w, g, scene = setup
+    K2 = rooms.Intrinsics(w.K.fx * 1.05, w.K.fy * 1.05, w.K.cx, w.K.cy, w.K.width, w.K.height)
+    qs = [w.query(q) for q in range(4)]
+    D = np.stack([q[0] for q in qs])
+    C = np.stack([q[1] for q in qs])
+    seeds = [q[3] for q in qs]
+    rel = rg.Relocaliser(g, scene, w.ransac, w.width, w.height, 4)
+    rel.relocalise_batch(D, C, w.K, seeds)             # captures the graph for w.K
+    replayed = rel.relocalise_batch(D, C, K2, seeds)   # replays it for K2
+    fresh = rg.Relocaliser(g, scene, w.ransac, w.width, w.height, 4)
+    _same(replayed, fresh.relocalise_batch(D, C, K2, seeds))
+    assert sum(r["n_hypotheses"] > 0 for r in replayed) >= 2
+    rel.close()
+    fresh.close()
