@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--leg-seconds", type=float, default=2.0, help="length of each serving-leg point")
     ap.add_argument("--profile-only", action="store_true",
                     help="short run for an external profiler (no baselines)")
+    ap.add_argument("--streams", type=int, default=0,
+                    help="sub-batches of each call on concurrent streams (1, 2, 4 or 8; default: autotuned); "
+                         "1 gives an external profiler the launch sequence of the per-kernel profiled pass")
     ap.add_argument("--arena-gb", type=float, default=24.0,
                     help="device memory handed to the library (smaller for profiler captures)")
     ap.add_argument("--robustness", action="store_true",
@@ -591,6 +594,9 @@ def run_ours(args):
 
     # launch shapes picked by the autotuner on this workload (results do not depend on them)
     tuning = rel.autotune(D, C, w.K, seeds(900_000), stream=stream)
+    if args.streams:
+        rel.set_tuning(dict(streams=args.streams))
+        tuning = rel.tuning
     for k in range(args.warmup):
         rel.relocalise_batch(D, C, w.K, seeds(500_000 + k), stream=stream, raw=True)
     torch.cuda.synchronize()
