@@ -135,7 +135,7 @@ __device__ __forceinline__ int walk_and_store(const float4 *nodes, int n_branch,
     int total = 0;
 #pragma unroll
     for (int t = 0; t < T; ++t) {
-        o[(size_t)t * hw_max] = (uint16_t)leaf[t];
+        if (o) o[(size_t)t * hw_max] = (uint16_t)leaf[t];
         cnt[t] = count ? min((int)__ldg(&nmodes[t * lpt + leaf[t]]), k_top) : 0;
         total += cnt[t];
     }
@@ -143,7 +143,8 @@ __device__ __forceinline__ int walk_and_store(const float4 *nodes, int n_branch,
     return total;
 }
 
-// out: uint16 [frame][tree][hw_max]; one thread per pixel walks every tree.
+// out: uint16 [frame][tree][hw_max] (null: not written); one thread per
+// pixel walks every tree.
 // When `mcount` is given it also receives |M(u)| = sum over the trees of
 // min(modes of the reached leaf, k_top) per pixel (0 without depth).
 // nodes_s: the nodes scaled for focal length fx_s (k_scale_nodes), used for
@@ -158,10 +159,11 @@ __global__ void k_leaves(const float4 *__restrict__ nodes, int n_branch, int dep
     if (p >= fr.W * fr.H) return;
     const int x = p % fr.W, y = p / fr.W;
     const float d = __ldg(&fr.depth[p]);
-    uint16_t *o = out + (size_t)blockIdx.y * n_trees * hw_max + p;
+    uint16_t *o = out ? out + (size_t)blockIdx.y * n_trees * hw_max + p : nullptr;  // null: no leaf map
     uint4 *rec = prec ? prec + (size_t)blockIdx.y * hw_max + p : nullptr;
     if (!(d > 0.0f)) {
-        for (int t = 0; t < n_trees; ++t) o[(size_t)t * hw_max] = 0xFFFF;
+        if (o)
+            for (int t = 0; t < n_trees; ++t) o[(size_t)t * hw_max] = 0xFFFF;
         if (mcount) mcount[(size_t)blockIdx.y * hw_max + p] = 0;
         if (rec) *rec = make_uint4(0, 0, 0, 0);
         return;
@@ -187,7 +189,7 @@ __global__ void k_leaves(const float4 *__restrict__ nodes, int n_branch, int dep
         for (int t = 0; t < n_trees; ++t) {
             const int leaf = walk_tree(nodes + (size_t)t * n_branch, depth, fr.depth, fr.rgb, fr.W, fr.H,
                                        s, x, y, d, inv);
-            o[(size_t)t * hw_max] = (uint16_t)leaf;
+            if (o) o[(size_t)t * hw_max] = (uint16_t)leaf;
             if (cnt) total += min((int)__ldg(&nmodes[t * leaves_per_tree + leaf]), k_top);
         }
     }

@@ -60,10 +60,6 @@ struct LmArgs {
     uint32_t wait_limit;       // probes of a wait for a staged tile before it gives up
 };
 
-// Shared memory of the tiled LM kernel for a padded row of maxm_pad modes;
-// above kLmSmemMax the global-memory kernel is used.
-constexpr size_t kLmSmemMax = 200 * 1024;
-size_t lm_tiled_smem(int maxm_pad);
 rl_status prepare_kernels();
 
 // LM with one thread-block cluster per frame (at most 64 hypotheses); its

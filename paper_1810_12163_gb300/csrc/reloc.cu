@@ -175,7 +175,9 @@ rl_status run_relocalise(rl_reloc *r, const QueryState &q, int n, int level, cud
     RL_CK(cudaMemsetAsync(q.round_count, 0, sizeof(int32_t) * 16 * n, s));
     RL_CK(cudaMemsetAsync(q.dev_err, 0, sizeof(int32_t) * n, s));
     unsigned long long *work = r->prof.on ? r->prof.work : nullptr;
-    { PROF(K_LEAVES); RL_TRY(launch_leaves(f, q.frames, n, p.n_trees, hw_max, q.leaves, r->max_w, r->max_h, s, p.k_top, q.mcount, q.prec, r->tune.leaves_threads, r->nodes_s, r->host_frames[0].fx)); }
+    // with pixel records (at most kRecTrees trees) every consumer reads the
+    // leaves from them, so the per-tree leaf map is not written
+    { PROF(K_LEAVES); RL_TRY(launch_leaves(f, q.frames, n, p.n_trees, hw_max, q.prec ? nullptr : q.leaves, r->max_w, r->max_h, s, p.k_top, q.mcount, q.prec, r->tune.leaves_threads, r->nodes_s, r->host_frames[0].fx)); }
     if (q.pcm) { PROF(K_CMASK); RL_TRY(launch_colour_mask(q.frames, q.mcount, q.prec, hw_max, mv, p, q.pcm, q.pbits, n, hw_max, s, r->tune.mask_threads)); }
     { PROF(K_HYPGEN); RL_TRY(launch_hypgen(q.frames, q.leaves, q.mcount, q.prec, q.pcm, q.pbits, hw_max, mv, p, q.hyp_pose, q.hyp_iter, work, n, s, r->tune.hypgen_warps)); }
     { PROF(K_HYPPOSE); RL_TRY(launch_hyppose(q.frames, q.leaves, q.mcount, q.prec, hw_max, mv, p, q.hyp_pose, q.hyp_iter, n, s)); }

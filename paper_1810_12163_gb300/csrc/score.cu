@@ -255,438 +255,9 @@ __global__ void __launch_bounds__(1024) k_select(SelectArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Levenberg-Marquardt in se(3): one warp per hypothesis; lanes stride the
-// pixel set, accumulate J^T J (21), J^T r (6) and the cost in FP32, reduce
-// by an xor butterfly (every lane ends with the same bits); lane 0 solves
-// the damped normal equations in FP64 and applies exp(xi^) on the left.
+// Levenberg-Marquardt in se(3) (Sec. 3.2.3) for rows of the mode table too
+// long for the cluster kernel's staged tiles (lm.cu).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-
-__global__ void __launch_bounds__(128) k_lm(LmArgs a) {
-    const int lane = threadIdx.x & 31;
-    const int h = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int b = blockIdx.y;
-    const int n = a.q.n_cur[b];
-    if (!round_active(n, a.p) || h >= n) return;
-    const int NC = a.p.n_cull;
-    double *Pg = a.q.cur_pose + ((size_t)b * NC + h) * 12;
-    double H[12];
-    for (int k = 0; k < 12; ++k) H[k] = Pg[k];
-    const uint16_t *lv = a.leaves + (size_t)b * a.p.n_trees * a.hw_max;
-    const int32_t *pix = a.q.pix + (size_t)b * a.p.max_pix;
-    const float4 *xcs = a.q.xc + (size_t)b * a.p.max_pix;
-    int32_t *corr = a.q.corr + ((size_t)b * NC + h) * a.p.max_pix;
-    const float thr2 = (float)(a.p.lm_inlier_thresh * a.p.lm_inlier_thresh);
-    const bool cov = a.p.use_cov;
-    double lambda = a.p.lm_lambda0;
-    unsigned w_pairs = 0, w_modes = 0, w_in = 0, w_trial = 0;
-    for (int it = 0; it < a.p.lm_max_iter; ++it) {
-        const float r00 = (float)H[0], r01 = (float)H[1], r02 = (float)H[2], t0 = (float)H[3];
-        const float r10 = (float)H[4], r11 = (float)H[5], r12 = (float)H[6], t1 = (float)H[7];
-        const float r20 = (float)H[8], r21 = (float)H[9], r22 = (float)H[10], t2 = (float)H[11];
-        float acc[28];
-#pragma unroll
-        for (int k = 0; k < 28; ++k) acc[k] = 0.f;
-        int nin = 0;
-        for (int i = lane; i < a.n_pix; i += 32) {
-            const int q = pix[i];
-            int best_e = -1;
-            if (q >= 0) {
-                const float4 x = xcs[i];
-                const float y0 = fmaf(r00, x.x, fmaf(r01, x.y, fmaf(r02, x.z, t0)));
-                const float y1 = fmaf(r10, x.x, fmaf(r11, x.y, fmaf(r12, x.z, t1)));
-                const float y2 = fmaf(r20, x.x, fmaf(r21, x.y, fmaf(r22, x.z, t2)));
-                float best = INFINITY;
-                float bu[6] = {1, 0, 0, 1, 0, 1};
-                float bm0 = 0, bm1 = 0, bm2 = 0;
-                ++w_pairs;
-                for (int t = 0; t < a.p.n_trees; ++t) {
-                    const uint32_t L = (uint32_t)(t * a.mv.leaves_per_tree + lv[(size_t)t * a.hw_max + q]);
-                    int nm = a.mv.nmodes[L];
-                    nm = nm < a.p.k_top ? nm : a.p.k_top;
-                    w_modes += nm;
-                    for (int m = 0; m < nm; ++m) {
-                        const float3 mp = mode_pos(a.mv, L, m);
-                        const size_t me = (size_t)L * a.mv.m_max + m;
-                        const float v0 = y0 - mp.x, v1 = y1 - mp.y, v2 = y2 - mp.z;
-                        float d2;
-                        float4 u0 = make_float4(1, 0, 0, 1), u1 = make_float4(0, 1, 0, 0);
-                        if (cov) {
-                            u0 = a.mv.mU[2 * me];
-                            u1 = a.mv.mU[2 * me + 1];
-                            const float w0 = fmaf(u0.x, v0, fmaf(u0.y, v1, u0.z * v2));
-                            const float w1 = fmaf(u0.w, v1, u1.x * v2);
-                            const float w2 = u1.y * v2;
-                            d2 = fmaf(w0, w0, fmaf(w1, w1, w2 * w2));
-                        } else {
-                            d2 = fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
-                        }
-                        if (d2 < best) {
-                            best = d2;
-                            best_e = (int)me;
-                            bm0 = mp.x; bm1 = mp.y; bm2 = mp.z;
-                            bu[0] = u0.x; bu[1] = u0.y; bu[2] = u0.z;
-                            bu[3] = u0.w; bu[4] = u1.x; bu[5] = u1.y;
-                        }
-                    }
-                }
-                if (best_e >= 0) {
-                    const float v0 = y0 - bm0, v1 = y1 - bm1, v2 = y2 - bm2;
-                    if (fmaf(v0, v0, fmaf(v1, v1, v2 * v2)) > thr2) {
-                        best_e = -1;
-                    } else {
-                        ++nin;
-                        ++w_in;
-                        // rows of J = U [I | -[y]x] and residual r = U v
-                        const float U00 = bu[0], U01 = bu[1], U02 = bu[2];
-                        const float U11 = bu[3], U12 = bu[4], U22 = bu[5];
-                        const float j0[6] = {U00, U01, U02, U02 * y1 - U01 * y2,
-                                             U00 * y2 - U02 * y0, U01 * y0 - U00 * y1};
-                        const float j1[6] = {0.f, U11, U12, U12 * y1 - U11 * y2, -U12 * y0, U11 * y0};
-                        const float j2[6] = {0.f, 0.f, U22, U22 * y1, -U22 * y0, 0.f};
-                        const float rr0 = fmaf(U00, v0, fmaf(U01, v1, U02 * v2));
-                        const float rr1 = fmaf(U11, v1, U12 * v2);
-                        const float rr2 = U22 * v2;
-                        int k = 0;
-#pragma unroll
-                        for (int r = 0; r < 6; ++r)
-#pragma unroll
-                            for (int c = r; c < 6; ++c, ++k)
-                                acc[k] = fmaf(j0[r], j0[c], fmaf(j1[r], j1[c], fmaf(j2[r], j2[c], acc[k])));
-#pragma unroll
-                        for (int r = 0; r < 6; ++r)
-                            acc[21 + r] = fmaf(j0[r], rr0, fmaf(j1[r], rr1, fmaf(j2[r], rr2, acc[21 + r])));
-                        acc[27] = fmaf(rr0, rr0, fmaf(rr1, rr1, fmaf(rr2, rr2, acc[27])));
-                    }
-                }
-            }
-            corr[i] = best_e;
-        }
-#pragma unroll
-        for (int k = 0; k < 28; ++k) acc[k] = warp_sum(acc[k]);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) nin += __shfl_xor_sync(0xffffffffu, nin, o);
-        if (nin < 3) break;
-        // lane 0: damped normal equations (FP64), trial pose
-        int status = 0;  // 0 continue, 1 stop
-        double Hn[12];
-        if (lane == 0) {
-            double A[36], rhs[6], step[6];
-            int k = 0;
-            for (int r = 0; r < 6; ++r)
-                for (int c = r; c < 6; ++c, ++k) A[6 * r + c] = A[6 * c + r] = (double)acc[k];
-            for (int r = 0; r < 6; ++r) {
-                A[6 * r + r] += lambda * (double)acc[r * 6 - r * (r - 1) / 2];
-                rhs[r] = -(double)acc[21 + r];
-            }
-            if (!chol_solve6(A, rhs, step)) {
-                status = 1;
-            } else {
-                double sn = 0.0;
-                for (int r = 0; r < 6; ++r) sn += step[r] * step[r];
-                if (sqrt(sn) < a.p.lm_stop) status = 1;
-            }
-            for (int i = 0; i < 12; ++i) Hn[i] = H[i];
-            if (!status) se3_left(step, Hn);
-        }
-        status = __shfl_sync(0xffffffffu, status, 0);
-        if (status) break;
-        for (int i = 0; i < 12; ++i) Hn[i] = __shfl_sync(0xffffffffu, Hn[i], 0);
-        __syncwarp();
-        // trial cost with the same correspondences
-        const float s00 = (float)Hn[0], s01 = (float)Hn[1], s02 = (float)Hn[2], u0t = (float)Hn[3];
-        const float s10 = (float)Hn[4], s11 = (float)Hn[5], s12 = (float)Hn[6], u1t = (float)Hn[7];
-        const float s20 = (float)Hn[8], s21 = (float)Hn[9], s22 = (float)Hn[10], u2t = (float)Hn[11];
-        float trial = 0.f;
-        for (int i = lane; i < a.n_pix; i += 32) {
-            const int e = corr[i];
-            if (e < 0) continue;
-            ++w_trial;
-            const float4 x = xcs[i];
-            const float y0 = fmaf(s00, x.x, fmaf(s01, x.y, fmaf(s02, x.z, u0t)));
-            const float y1 = fmaf(s10, x.x, fmaf(s11, x.y, fmaf(s12, x.z, u1t)));
-            const float y2 = fmaf(s20, x.x, fmaf(s21, x.y, fmaf(s22, x.z, u2t)));
-            const uint32_t L = (uint32_t)e / (uint32_t)a.mv.m_max;
-            const float3 mp = mode_pos(a.mv, L, e - (int)L * a.mv.m_max);
-            const float v0 = y0 - mp.x, v1 = y1 - mp.y, v2 = y2 - mp.z;
-            if (cov) {
-                const float4 w0 = a.mv.mU[2 * (size_t)e], w1 = a.mv.mU[2 * (size_t)e + 1];
-                const float r0 = fmaf(w0.x, v0, fmaf(w0.y, v1, w0.z * v2));
-                const float r1 = fmaf(w0.w, v1, w1.x * v2);
-                const float r2 = w1.y * v2;
-                trial = fmaf(r0, r0, fmaf(r1, r1, fmaf(r2, r2, trial)));
-            } else {
-                trial = fmaf(v0, v0, fmaf(v1, v1, fmaf(v2, v2, trial)));
-            }
-        }
-        trial = warp_sum(trial);
-        if (trial < acc[27]) {
-            for (int i = 0; i < 12; ++i) H[i] = Hn[i];
-            lambda /= 10.0;
-        } else {
-            lambda *= 10.0;
-        }
-    }
-    if (lane == 0)
-        for (int k = 0; k < 12; ++k) Pg[k] = H[k];
-    if (a.work) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            w_pairs += __shfl_xor_sync(0xffffffffu, w_pairs, o);
-            w_modes += __shfl_xor_sync(0xffffffffu, w_modes, o);
-            w_in += __shfl_xor_sync(0xffffffffu, w_in, o);
-            w_trial += __shfl_xor_sync(0xffffffffu, w_trial, o);
-        }
-        if (lane == 0) {
-            atomicAdd(&a.work[W_LM_PAIRS], (unsigned long long)w_pairs);
-            atomicAdd(&a.work[W_LM_MODES], (unsigned long long)w_modes);
-            atomicAdd(&a.work[W_LM_INLIERS], (unsigned long long)w_in);
-            atomicAdd(&a.work[W_LM_TRIAL], (unsigned long long)w_trial);
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Eq. 6-7: raycast of the box model at each chosen pose, masked mean
-// absolute depth difference, valid fraction.  Block = 256 pixels of one
-// (frame, chosen pose); partial sums in a fixed order.
-// ---------------------------------------------------------------------------
-
-// LM with the pixel set staged in shared memory.  A block holds LM_WARPS
-// hypotheses of one frame (a warp each); every LM iteration walks the pixel
-// set in tiles of 32 (lane i <-> pixel tile + i, the same order as one warp
-// striding alone), each tile's modes decoded once into shared memory and
-// read by every warp of the block.  Warps stop independently; the block
-// keeps iterating while any warp is active.
-constexpr int LM_WARPS = 8;
-constexpr int LM_TILE = 32;
-
-__global__ void __launch_bounds__(LM_WARPS * 32) k_lm_tiled(LmArgs a) {
-    extern __shared__ __align__(16) uint8_t smem[];
-    const int stride = a.p.mpad;                           // odd: conflict-free float4 rows
-    float4 *s_m0 = (float4 *)smem;                         // [TILE][stride] mu.xyz, U00
-    float4 *s_m1 = s_m0 + LM_TILE * stride;                // [TILE][stride] U01 U02 U11 U12
-    float *s_m2 = (float *)(s_m1 + LM_TILE * stride);      // [TILE][stride] U22
-    float4 *s_xc = (float4 *)(s_m2 + LM_TILE * stride + 4);  // [TILE]
-    int *s_cnt = (int *)(s_xc + LM_TILE);                  // [TILE]
-
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int b = blockIdx.y;
-    const int n = a.q.n_cur[b];
-    if (!round_active(n, a.p) || (int)blockIdx.x * LM_WARPS >= n) return;
-    const int h = blockIdx.x * LM_WARPS + warp;
-    bool active = h < n;
-    const int NC = a.p.n_cull;
-    double *Pg = a.q.cur_pose + ((size_t)b * NC + (active ? h : 0)) * 12;
-    double H[12];
-    for (int k = 0; k < 12; ++k) H[k] = active ? Pg[k] : 0.0;
-    const size_t row0 = (size_t)b * a.p.max_pix;           // first mode-table row of the frame
-    const float4 *xcs = a.q.xc + row0;
-    const float4 *t0 = a.q.tab0 + row0 * stride;
-    const float4 *t1 = a.q.tab1 + row0 * stride;
-    const float *t2 = a.q.tab2 + row0 * stride;
-    const int16_t *tcnt = a.q.tab_cnt + row0;
-    int32_t *corr = a.q.corr + ((size_t)b * NC + (active ? h : 0)) * a.p.max_pix;
-    const float thr2 = (float)(a.p.lm_inlier_thresh * a.p.lm_inlier_thresh);
-    const bool cov = a.p.use_cov;
-    double lambda = a.p.lm_lambda0;
-    unsigned w_pairs = 0, w_modes = 0, w_in = 0, w_trial = 0;
-    for (int it = 0; it < a.p.lm_max_iter; ++it) {
-        if (!__syncthreads_or(active)) break;
-        const float r00 = (float)H[0], r01 = (float)H[1], r02 = (float)H[2], tx = (float)H[3];
-        const float r10 = (float)H[4], r11 = (float)H[5], r12 = (float)H[6], ty = (float)H[7];
-        const float r20 = (float)H[8], r21 = (float)H[9], r22 = (float)H[10], tz = (float)H[11];
-        float acc[28];
-#pragma unroll
-        for (int k = 0; k < 28; ++k) acc[k] = 0.f;
-        int nin = 0;
-        for (int t0p = 0; t0p < a.n_pix; t0p += LM_TILE) {
-            const int np = min(LM_TILE, a.n_pix - t0p);
-            // stage the tile: its mode-table rows are contiguous
-            for (int i = threadIdx.x; i < np; i += blockDim.x) {
-                s_xc[i] = xcs[t0p + i];
-                s_cnt[i] = tcnt[t0p + i];
-            }
-            const size_t off = (size_t)t0p * stride;
-            for (int e = threadIdx.x; e < np * stride; e += blockDim.x) {
-                s_m0[e] = t0[off + e];
-                if (cov) {
-                    s_m1[e] = t1[off + e];
-                    s_m2[e] = t2[off + e];
-                }
-            }
-            __syncthreads();
-            if (active && lane < np) {
-                const int cnt = s_cnt[lane];
-                int best_m = -1;
-                if (cnt > 0) {
-                    ++w_pairs;
-                    w_modes += cnt;
-                    const float4 x = s_xc[lane];
-                    const float y0 = fmaf(r00, x.x, fmaf(r01, x.y, fmaf(r02, x.z, tx)));
-                    const float y1 = fmaf(r10, x.x, fmaf(r11, x.y, fmaf(r12, x.z, ty)));
-                    const float y2 = fmaf(r20, x.x, fmaf(r21, x.y, fmaf(r22, x.z, tz)));
-                    const int base = lane * stride;
-                    float best = INFINITY;
-                    int bm = -1;
-                    if (cov) {
-                        for (int m = 0; m < cnt; ++m) {
-                            const float4 m0 = s_m0[base + m], m1 = s_m1[base + m];
-                            const float u22 = s_m2[base + m];
-                            const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
-                            const float w0 = fmaf(m0.w, v0, fmaf(m1.x, v1, m1.y * v2));
-                            const float w1 = fmaf(m1.z, v1, m1.w * v2);
-                            const float w2 = u22 * v2;
-                            const float d2 = fmaf(w0, w0, fmaf(w1, w1, w2 * w2));
-                            if (d2 < best) {
-                                best = d2;
-                                bm = m;
-                            }
-                        }
-                    } else {
-                        for (int m = 0; m < cnt; ++m) {
-                            const float4 m0 = s_m0[base + m];
-                            const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
-                            const float d2 = fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
-                            if (d2 < best) {
-                                best = d2;
-                                bm = m;
-                            }
-                        }
-                    }
-                    if (bm >= 0) {
-                        const float4 m0 = s_m0[base + bm];
-                        const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
-                        if (fmaf(v0, v0, fmaf(v1, v1, v2 * v2)) <= thr2) {
-                            best_m = bm;
-                            ++nin;
-                            ++w_in;
-                            float U00 = 1.f, U01 = 0.f, U02 = 0.f, U11 = 1.f, U12 = 0.f, U22 = 1.f;
-                            if (cov) {
-                                const float4 m1 = s_m1[base + bm];
-                                U00 = m0.w; U01 = m1.x; U02 = m1.y; U11 = m1.z; U12 = m1.w;
-                                U22 = s_m2[base + bm];
-                            }
-                            const float j0[6] = {U00, U01, U02, U02 * y1 - U01 * y2,
-                                                 U00 * y2 - U02 * y0, U01 * y0 - U00 * y1};
-                            const float j1[6] = {0.f, U11, U12, U12 * y1 - U11 * y2, -U12 * y0, U11 * y0};
-                            const float j2[6] = {0.f, 0.f, U22, U22 * y1, -U22 * y0, 0.f};
-                            const float rr0 = fmaf(U00, v0, fmaf(U01, v1, U02 * v2));
-                            const float rr1 = fmaf(U11, v1, U12 * v2);
-                            const float rr2 = U22 * v2;
-                            int k = 0;
-#pragma unroll
-                            for (int r = 0; r < 6; ++r)
-#pragma unroll
-                                for (int c = r; c < 6; ++c, ++k)
-                                    acc[k] = fmaf(j0[r], j0[c], fmaf(j1[r], j1[c], fmaf(j2[r], j2[c], acc[k])));
-#pragma unroll
-                            for (int r = 0; r < 6; ++r)
-                                acc[21 + r] = fmaf(j0[r], rr0, fmaf(j1[r], rr1, fmaf(j2[r], rr2, acc[21 + r])));
-                            acc[27] = fmaf(rr0, rr0, fmaf(rr1, rr1, fmaf(rr2, rr2, acc[27])));
-                        }
-                    }
-                }
-                corr[t0p + lane] = best_m;   // local mode index into the pixel's table row
-            }
-            __syncthreads();
-        }
-        if (!active) continue;
-#pragma unroll
-        for (int k = 0; k < 28; ++k) acc[k] = warp_sum(acc[k]);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) nin += __shfl_xor_sync(0xffffffffu, nin, o);
-        if (nin < 3) {
-            active = false;
-            continue;
-        }
-        int status = 0;
-        double Hn[12];
-        if (lane == 0) {
-            double A[36], rhs[6], step[6];
-            int k = 0;
-            for (int r = 0; r < 6; ++r)
-                for (int c = r; c < 6; ++c, ++k) A[6 * r + c] = A[6 * c + r] = (double)acc[k];
-            for (int r = 0; r < 6; ++r) {
-                A[6 * r + r] += lambda * (double)acc[r * 6 - r * (r - 1) / 2];
-                rhs[r] = -(double)acc[21 + r];
-            }
-            if (!chol_solve6(A, rhs, step)) {
-                status = 1;
-            } else {
-                double sn = 0.0;
-                for (int r = 0; r < 6; ++r) sn += step[r] * step[r];
-                if (sqrt(sn) < a.p.lm_stop) status = 1;
-            }
-            for (int i = 0; i < 12; ++i) Hn[i] = H[i];
-            if (!status) se3_left(step, Hn);
-        }
-        status = __shfl_sync(0xffffffffu, status, 0);
-        if (status) {
-            active = false;
-            continue;
-        }
-        for (int i = 0; i < 12; ++i) Hn[i] = __shfl_sync(0xffffffffu, Hn[i], 0);
-        __syncwarp();
-        // trial cost with the same correspondences, read from the mode table
-        const float s00 = (float)Hn[0], s01 = (float)Hn[1], s02 = (float)Hn[2], u0t = (float)Hn[3];
-        const float s10 = (float)Hn[4], s11 = (float)Hn[5], s12 = (float)Hn[6], u1t = (float)Hn[7];
-        const float s20 = (float)Hn[8], s21 = (float)Hn[9], s22 = (float)Hn[10], u2t = (float)Hn[11];
-        float trial = 0.f;
-#pragma unroll 4
-        for (int i = lane; i < a.n_pix; i += 32) {
-            const int m = corr[i];
-            if (m < 0) continue;
-            ++w_trial;
-            const float4 x = xcs[i];
-            const size_t e = (size_t)i * stride + m;
-            const float4 m0 = t0[e];
-            const float y0 = fmaf(s00, x.x, fmaf(s01, x.y, fmaf(s02, x.z, u0t)));
-            const float y1 = fmaf(s10, x.x, fmaf(s11, x.y, fmaf(s12, x.z, u1t)));
-            const float y2 = fmaf(s20, x.x, fmaf(s21, x.y, fmaf(s22, x.z, u2t)));
-            const float v0 = y0 - m0.x, v1 = y1 - m0.y, v2 = y2 - m0.z;
-            if (cov) {
-                const float4 m1 = t1[e];
-                const float u22 = t2[e];
-                const float r0 = fmaf(m0.w, v0, fmaf(m1.x, v1, m1.y * v2));
-                const float r1 = fmaf(m1.z, v1, m1.w * v2);
-                const float r2 = u22 * v2;
-                trial = fmaf(r0, r0, fmaf(r1, r1, fmaf(r2, r2, trial)));
-            } else {
-                trial = fmaf(v0, v0, fmaf(v1, v1, fmaf(v2, v2, trial)));
-            }
-        }
-        trial = warp_sum(trial);
-        if (trial < acc[27]) {
-            for (int i = 0; i < 12; ++i) H[i] = Hn[i];
-            lambda /= 10.0;
-        } else {
-            lambda *= 10.0;
-        }
-    }
-    if (h < n && lane == 0)
-        for (int k = 0; k < 12; ++k) Pg[k] = H[k];
-    if (a.work && h < n) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            w_pairs += __shfl_xor_sync(0xffffffffu, w_pairs, o);
-            w_modes += __shfl_xor_sync(0xffffffffu, w_modes, o);
-            w_in += __shfl_xor_sync(0xffffffffu, w_in, o);
-            w_trial += __shfl_xor_sync(0xffffffffu, w_trial, o);
-        }
-        if (lane == 0) {
-            atomicAdd(&a.work[W_LM_PAIRS], (unsigned long long)w_pairs);
-            atomicAdd(&a.work[W_LM_MODES], (unsigned long long)w_modes);
-            atomicAdd(&a.work[W_LM_INLIERS], (unsigned long long)w_in);
-            atomicAdd(&a.work[W_LM_TRIAL], (unsigned long long)w_trial);
-        }
-    }
-}
 
 // LM, hypotheses spread over threads.  A round's n hypotheses of a frame are
 // split over up to LM3_BPQ blocks; inside a block, thread t works for
@@ -916,11 +487,6 @@ __global__ void __launch_bounds__(LM3_THREADS, 2) k_lm_spread(LmArgs a) {
         atomicAdd(&a.work[W_LM_INLIERS], (unsigned long long)w_in);
         atomicAdd(&a.work[W_LM_TRIAL], (unsigned long long)w_trial);
     }
-}
-
-size_t lm_tiled_smem(int mpad) {
-    return (size_t)LM_TILE * mpad * (2 * sizeof(float4) + sizeof(float)) + 16 +
-           LM_TILE * (sizeof(float4) + sizeof(int));
 }
 
 // Mode table of batch `batch`: for each drawn pixel, M(u) decoded to FP32
@@ -1300,20 +866,12 @@ bool lm_uses_cluster(const RParams &p) {
     return p.n_cull <= 64 && lm_cluster_smem(p.mpad, p.use_cov) <= kLmClusterSmemMax;
 }
 
+// The cluster kernel, or (rows too long for its staged tiles) the spread
+// kernel; n_cull <= 64 (checked when the relocaliser is created).
 rl_status launch_lm(const LmArgs &a, int n, cudaStream_t s) {
-    const size_t sm = lm_tiled_smem(a.p.mpad);
-    if (lm_uses_cluster(a.p)) {
-        return launch_lm_cluster(a, n, s);
-    } else if (a.p.n_cull <= 64) {
-        dim3 grid(LM3_BPQ, n);
-        k_lm_spread<<<grid, LM3_THREADS, 0, s>>>(a);
-    } else if (sm <= kLmSmemMax) {
-        dim3 grid((a.p.n_cull + LM_WARPS - 1) / LM_WARPS, n);
-        k_lm_tiled<<<grid, LM_WARPS * 32, sm, s>>>(a);
-    } else {
-        dim3 grid((a.p.n_cull + 3) / 4, n);
-        k_lm<<<grid, 128, 0, s>>>(a);
-    }
+    if (lm_uses_cluster(a.p)) return launch_lm_cluster(a, n, s);
+    dim3 grid(LM3_BPQ, n);
+    k_lm_spread<<<grid, LM3_THREADS, 0, s>>>(a);
     RL_LAUNCH_CK();
     return RL_OK;
 }
@@ -1324,7 +882,6 @@ rl_status prepare_kernels() {
     static std::mutex mu;
     std::lock_guard<std::mutex> g(mu);
     if (done) return RL_OK;
-    RL_CK(cudaFuncSetAttribute(k_lm_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLmSmemMax));
     RL_TRY(prepare_lm_cluster());
     RL_TRY(prepare_hypgen());
     done = true;
