@@ -146,7 +146,8 @@ __device__ __forceinline__ int walk_and_store(const float4 *nodes, int n_branch,
 // out: uint16 [frame][tree][hw_max] (null: not written); one thread per
 // pixel walks every tree.
 // When `mcount` is given it also receives |M(u)| = sum over the trees of
-// min(modes of the reached leaf, k_top) per pixel (0 without depth).
+// min(modes of the reached leaf, k_top) per pixel (0 without depth); the
+// pixel records `prec` (at most kRecTrees trees) hold the per-tree counts.
 // nodes_s: the nodes scaled for focal length fx_s (k_scale_nodes), used for
 // the frames of that focal length, or null.
 __global__ void k_leaves(const float4 *__restrict__ nodes, int n_branch, int depth, int n_trees,
@@ -171,7 +172,7 @@ __global__ void k_leaves(const float4 *__restrict__ nodes, int n_branch, int dep
     const float s = __fdiv_rn(fr.fx, 585.0f);
     const float inv = __frcp_rn(d);
     int total = 0;
-    const bool cnt = mcount != nullptr;
+    const bool cnt = mcount != nullptr || prec != nullptr;  // per-tree counts wanted
     const bool pre = nodes_s != nullptr && fr.fx == fx_s;  // the same for the whole block (one frame)
 #define RL_WALK(T)                                                                                          \
     total = pre ? walk_and_store<T, true>(nodes_s, n_branch, depth, fr, s, x, y, d, inv, o, hw_max, nmodes, \

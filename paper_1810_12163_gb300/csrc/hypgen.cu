@@ -42,9 +42,11 @@ template <int REDRAW>
 __device__ __forceinline__ bool stage1(const HypArgs &a, const Frame &fr, const uint16_t *lv,
                                        const uint16_t *mc, const uint4 *pr, int slot, int it,
                                        Draw &d) {
-    auto usable = [&](int q) { return mc[q] != 0; };
+    const int T = a.p.n_trees;
+    auto usable = [&](int q) { return pixel_modes(mc, pr, q, T) != 0; };
     d = draw<decltype(usable), REDRAW>(a, fr, slot, it, usable);
-    const int c0 = mc[d.pix[0]], c1 = mc[d.pix[1]], c2 = mc[d.pix[2]];
+    const int c0 = pixel_modes(mc, pr, d.pix[0], T), c1 = pixel_modes(mc, pr, d.pix[1], T),
+              c2 = pixel_modes(mc, pr, d.pix[2], T);
     if (c0 == 0 || c1 == 0 || c2 == 0) return false;
     const uint32_t ctr1 = (TAG_HYP << 16) | (uint32_t)a.p.level;
     const uint4 r1 = philox(make_uint4(slot, ctr1, it, 1), fr.key0, fr.key1);
@@ -332,14 +334,15 @@ __global__ void __launch_bounds__(256) k_colour_mask(const Frame *__restrict__ f
     const int px = blockIdx.x * blockDim.x + threadIdx.x;
     const bool in = px < fr.W * fr.H;
     const size_t o = (size_t)b * hw_max + px;
-    const int cnt = in ? (int)mcount[o] : 0;
+    const uint4 rec = in ? prec[o] : make_uint4(0, 0, 0, 0);  // masks exist only with pixel records
+    int cnt = 0;
+    for (int t = 0; t < p.n_trees; ++t) cnt += rec_count(rec, t);  // |M(u)|
     // bit px of the non-empty-M(u) bitmap: a warp covers one 32-pixel word
     const unsigned word = __ballot_sync(0xffffffffu, cnt > 0);
     if (in && (threadIdx.x & 31) == 0) pbits[(size_t)b * (hw_max / 32 + 1) + (px >> 5)] = word;
     if (!in) return;
     uint32_t lo = 0, hi = 0;
     if (cnt > 0) {
-        const uint4 rec = prec[o];
         const uint8_t *pc = fr.rgb + (size_t)px * 3;
         const int pr = pc[0], pg = pc[1], pb = pc[2];
         int m = 0;
@@ -403,20 +406,21 @@ __global__ void __launch_bounds__(1024) k_compact(const int32_t *__restrict__ hy
 // until its pixel has a non-empty M(u) (which implies depth); skipped (-1)
 // otherwise.
 __global__ void k_sample_batch(const Frame *__restrict__ frames, const uint16_t *__restrict__ mcount,
-                               int hw_max, RParams p, int batch, int32_t *__restrict__ pix_out,
-                               float4 *__restrict__ xc_out) {
+                               const uint4 *__restrict__ prec, int hw_max, RParams p, int batch,
+                               int32_t *__restrict__ pix_out, float4 *__restrict__ xc_out) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int b = blockIdx.y;
     if (j >= p.eta) return;
     const Frame fr = frames[b];
     const uint16_t *mc = mcount + (size_t)b * hw_max;
+    const uint4 *pr = prec ? prec + (size_t)b * hw_max : nullptr;
     const uint32_t WH = (uint32_t)(fr.W * fr.H);
     int pix = -1;
     for (int at = 0; at < p.batch_attempts && WH > 0; ++at) {
         const uint4 r = philox(make_uint4(batch, (TAG_BATCH << 16) | (uint32_t)p.level, j, at),
                                fr.key0, fr.key1);
         const int q = (int)draw_below(r.x, WH);
-        if (mc[q] == 0) continue;
+        if (pixel_modes(mc, pr, q, p.n_trees) == 0) continue;
         pix = q;
         break;
     }
@@ -480,11 +484,11 @@ rl_status launch_compact(const int32_t *hyp_iter, int N, int32_t *hyp_list, int3
     return RL_OK;
 }
 
-rl_status launch_sample_batch(const Frame *frames, const uint16_t *mcount, int hw_max,
+rl_status launch_sample_batch(const Frame *frames, const uint16_t *mcount, const uint4 *prec, int hw_max,
                               const RParams &p, int batch, int32_t *pix, float4 *xc, int n,
                               cudaStream_t s) {
     dim3 grid((p.eta + 127) / 128, n);
-    k_sample_batch<<<grid, 128, 0, s>>>(frames, mcount, hw_max, p, batch, pix, xc);
+    k_sample_batch<<<grid, 128, 0, s>>>(frames, mcount, prec, hw_max, p, batch, pix, xc);
     RL_LAUNCH_CK();
     return RL_OK;
 }

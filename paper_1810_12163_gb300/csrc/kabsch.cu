@@ -162,7 +162,8 @@ __device__ void kabsch3_horn(const double a[3][3], const double b[3][3], double 
 // The accepted triple of (slot, it), re-derived exactly, and its pose.
 __device__ __forceinline__ void accept_triple(const HypArgs &a, const Frame &fr, const uint16_t *lv,
                                            const uint16_t *mc, const uint4 *pr, int slot, int it, double H[12]) {
-    const Draw d = draw(a, fr, slot, it, [&](int q) { return mc[q] != 0; });
+    const int T = a.p.n_trees;
+    const Draw d = draw(a, fr, slot, it, [&](int q) { return pixel_modes(mc, pr, q, T) != 0; });
     const uint32_t ctr1 = (TAG_HYP << 16) | (uint32_t)a.p.level;
     const uint4 r1 = philox(make_uint4(slot, ctr1, it, 1), fr.key0, fr.key1);
     const uint32_t u1[3] = {r1.x, r1.y, r1.z};
@@ -170,7 +171,7 @@ __device__ __forceinline__ void accept_triple(const HypArgs &a, const Frame &fr,
     for (int i = 0; i < 3; ++i) {
         uint32_t L;
         int rank;
-        lookup(a, lv, pr, d.pix[i], (int)draw_below(u1[i], (uint32_t)mc[d.pix[i]]), &L, &rank);
+        lookup(a, lv, pr, d.pix[i], (int)draw_below(u1[i], (uint32_t)pixel_modes(mc, pr, d.pix[i], T)), &L, &rank);
         const float3 c = backproject(fr, d.pix[i]);
         const float3 w = mode_pos(a.mv, L, rank);
         xc[i][0] = c.x; xc[i][1] = c.y; xc[i][2] = c.z;

@@ -140,7 +140,7 @@ rl_status launch_hyppose(const Frame *frames, const uint16_t *leaves, const uint
                          double *hyp_pose, int32_t *hyp_iter, int n, cudaStream_t s);
 rl_status launch_compact(const int32_t *hyp_iter, int N, int32_t *hyp_list, int32_t *n_hyp, int n,
                          cudaStream_t s);
-rl_status launch_sample_batch(const Frame *frames, const uint16_t *mcount, int hw_max,
+rl_status launch_sample_batch(const Frame *frames, const uint16_t *mcount, const uint4 *prec, int hw_max,
                               const RParams &p, int batch, int32_t *pix, float4 *xc, int n,
                               cudaStream_t s);
 rl_status launch_subsample(const Frame *src, Frame *dst_desc, float *dst_depth, uint8_t *dst_rgb,

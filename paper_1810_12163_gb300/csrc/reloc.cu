@@ -176,13 +176,14 @@ rl_status run_relocalise(rl_reloc *r, const QueryState &q, int n, int level, cud
     RL_CK(cudaMemsetAsync(q.dev_err, 0, sizeof(int32_t) * n, s));
     unsigned long long *work = r->prof.on ? r->prof.work : nullptr;
     // with pixel records (at most kRecTrees trees) every consumer reads the
-    // leaves from them, so the per-tree leaf map is not written
-    { PROF(K_LEAVES); RL_TRY(launch_leaves(f, q.frames, n, p.n_trees, hw_max, q.prec ? nullptr : q.leaves, r->max_w, r->max_h, s, p.k_top, q.mcount, q.prec, r->tune.leaves_threads, r->nodes_s, r->host_frames[0].fx)); }
+    // leaves and |M(u)| from them, so neither the per-tree leaf map nor the
+    // count map is written
+    { PROF(K_LEAVES); RL_TRY(launch_leaves(f, q.frames, n, p.n_trees, hw_max, q.prec ? nullptr : q.leaves, r->max_w, r->max_h, s, p.k_top, q.prec ? nullptr : q.mcount, q.prec, r->tune.leaves_threads, r->nodes_s, r->host_frames[0].fx)); }
     if (q.pcm) { PROF(K_CMASK); RL_TRY(launch_colour_mask(q.frames, q.mcount, q.prec, hw_max, mv, p, q.pcm, q.pbits, n, hw_max, s, r->tune.mask_threads)); }
     { PROF(K_HYPGEN); RL_TRY(launch_hypgen(q.frames, q.leaves, q.mcount, q.prec, q.pcm, q.pbits, hw_max, mv, p, q.hyp_pose, q.hyp_iter, work, n, s, r->tune.hypgen_warps)); }
     { PROF(K_HYPPOSE); RL_TRY(launch_hyppose(q.frames, q.leaves, q.mcount, q.prec, hw_max, mv, p, q.hyp_pose, q.hyp_iter, n, s)); }
     { PROF(K_COMPACT); RL_TRY(launch_compact(q.hyp_iter, N, q.hyp_list, q.n_hyp, n, s)); }
-    { PROF(K_SAMPLE); RL_TRY(launch_sample_batch(q.frames, q.mcount, hw_max, p, 0, q.pix, q.xc, n, s));
+    { PROF(K_SAMPLE); RL_TRY(launch_sample_batch(q.frames, q.mcount, q.prec, hw_max, p, 0, q.pix, q.xc, n, s));
       RL_TRY(launch_build_table(q, hw_max, mv, p, 0, n, s)); }
 
     const int maxm = p.maxm;
@@ -233,7 +234,7 @@ rl_status run_relocalise(rl_reloc *r, const QueryState &q, int n, int level, cud
     // preemptive rounds
     for (int round = 0; round < p.max_rounds; ++round) {
         const int n_pix = p.eta * (round + 2);
-        { PROF(K_SAMPLE); RL_TRY(launch_sample_batch(q.frames, q.mcount, hw_max, p, round + 1, q.pix, q.xc, n, s));
+        { PROF(K_SAMPLE); RL_TRY(launch_sample_batch(q.frames, q.mcount, q.prec, hw_max, p, round + 1, q.pix, q.xc, n, s));
           RL_TRY(launch_build_table(q, hw_max, mv, p, round + 1, n, s)); }
         const bool lm = p.pose_update && p.lm_max_iter > 0;
         if (lm) {

@@ -50,6 +50,17 @@ __device__ __forceinline__ int rec_count(const uint4 &r, int t) {
     return t < 4 ? (int)((r.w >> (8 * t)) & 255u) : (int)((r.z >> 16) & 255u);
 }
 
+// |M(u)| of pixel p: the sum of its record's per-tree counts when there are
+// records (the relocaliser then writes no separate count map), else the
+// count map's entry.
+__device__ __forceinline__ int pixel_modes(const uint16_t *mc, const uint4 *pr, int p, int n_trees) {
+    if (!pr) return mc[p];
+    const uint4 r = pr[p];
+    int s = 0;
+    for (int t = 0; t < n_trees; ++t) s += rec_count(r, t);
+    return s;
+}
+
 __device__ __forceinline__ uint4 make_rec(const int leaf[kRecTrees], const int cnt[kRecTrees], int T) {
     uint4 r = make_uint4(0, 0, 0, 0);
     for (int t = 0; t < T; ++t) {

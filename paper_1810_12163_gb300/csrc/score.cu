@@ -498,7 +498,9 @@ __global__ void k_build_table(QueryState q, int hw_max, ModeView mv, RParams p, 
     const int i = batch * p.eta + e / p.mpad, m = e % p.mpad;
     const size_t row = (size_t)b * p.max_pix + i;
     const int pix = q.pix[row];
-    const int cnt = pix < 0 ? 0 : (int)q.mcount[(size_t)b * hw_max + pix];
+    const int cnt = pix < 0 ? 0
+                            : pixel_modes(q.mcount + (size_t)b * hw_max,
+                                          q.prec ? q.prec + (size_t)b * hw_max : nullptr, pix, p.n_trees);
     if (m == 0) q.tab_cnt[row] = (int16_t)cnt;
     if (m >= cnt) return;
     uint32_t L;
