@@ -67,7 +67,8 @@ def oracle_query(w_name: str, q: int, params=None):
     return OracleRun(p, d, c, w.K, lv, modes, w.room().lo, w.room().hi, seed, 1 << w.forest["depth"]), T
 
 
-WORKLOADS = {w.name: w for w in [workloads.CONFIG1, workloads.CONFIG2, workloads.small_case()]}
+WORKLOADS = {w.name: w for w in [workloads.CONFIG1, workloads.CONFIG2, workloads.small_case(),
+                                  workloads.small_case(n_trees=6)]}
 SMALL = workloads.small_case().name
 
 

@@ -119,6 +119,27 @@ def test_relocalise_parity_small_variants(rg, ctx, small):
         rel.close()
 
 
+def test_relocalise_parity_six_trees(rg, ctx):
+    """Six trees, one more than a pixel record holds: the walk writes the
+    per-tree leaf map and the |M(u)| map, generation checks colours per
+    attempt (no colour-check masks), and every consumer reads the maps."""
+    w = workloads.small_case(n_trees=6)
+    g = H.gpu_model(ctx, w)
+    scene = rg.Scene(ctx, w.room().lo, w.room().hi)
+    rel = rg.Relocaliser(g, scene, w.ransac, w.width, w.height, 1)
+    n_hyp = 0
+    for q in range(3):
+        d, c, T, seed = w.query(q)
+        gr = rel.relocalise(d, c, w.K, seed)
+        n_hyp += gr["n_hypotheses"]
+        orun, _ = H.oracle_query(w.name, q, w.ransac)
+        H.compare_results(rg, gr, rel.debug(0), orun, w.ransac, f"six trees q{q}")
+    assert n_hyp > 0
+    rel.close()
+    scene.close()
+    g.close()
+
+
 def test_batch_invariance(rg, ctx, small):
     """Each frame's result is identical alone and inside a batch."""
     w, g = small
