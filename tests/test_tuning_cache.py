@@ -44,6 +44,17 @@ def test_values_outside_the_lists_are_refused(rg, tmp_path):
     assert rg.tuning_cache_read(path, "i") is None
 
 
+def test_every_stream_count_round_trips(rg, tmp_path):
+    path = str(tmp_path / "tuning.txt")
+    for k in (1, 2, 4, 8):
+        t = dict(hypgen_warps=16, energy_threads=128, leaves_threads=128, mask_threads=256, streams=k)
+        rg.tuning_cache_write(path, f"k{k}", t)
+        assert rg.tuning_cache_read(path, f"k{k}") == t
+    with pytest.raises(rg.RelocError):
+        rg.tuning_cache_write(path, "k16", dict(hypgen_warps=16, energy_threads=128, leaves_threads=128,
+                                                mask_threads=256, streams=16))
+
+
 def test_entries_without_streams_read_as_one_stream(rg, tmp_path):
     path = str(tmp_path / "tuning.txt")
     with open(path, "w") as f:                                     # written before the streams knob
